@@ -1,0 +1,481 @@
+/*
+ * Oracle for Hazelwood & Weinzierl, "Coloured and task-based stencil codes"
+ * (arXiv:1810.04033): plain FP64 C, slow on purpose, written so that each function
+ * can be checked against the paper and the mathematics by eye.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the CPU-baseline
+ * leg of the benchmark.  The GPU library never calls it and shares nothing with it.
+ *
+ * Compile with -ffp-contract=off so that no multiply-add is fused and the x86 and Arm
+ * builds produce identical bits.
+ *
+ * Parity status per function (what pins it; the pins live in tests/):
+ *   oracle_q1_element_matrix  pinned: its 2D assembly reproduces the paper's printed
+ *                             9-point stencil (Fig. 1); 3D row sums, symmetry.
+ *   oracle_apply_elementwise  pinned: equals a Kronecker-product assembly of the global
+ *                             matrix; annihilates constants/linears; exact -Laplacian
+ *                             on cubic polynomials; symbol on sine modes.
+ *   oracle_apply_stencil      pinned: as above plus equality with the element form.
+ *   oracle_gs_coloured        pinned: brute-force dense-matrix Gauss-Seidel in colour
+ *                             order; order-independence inside a colour; convergence
+ *                             to the closed-form discrete solution.
+ *   oracle_gs_coloured_f32    pinned: FP32 sweep vs FP64 sweep within FP32 rounding;
+ *                             float-rounded brute force on tiny grids.
+ *   oracle_gs_coloured_bf16   pinned: bf16 rounding helpers against torch's bf16
+ *                             casts; sweep vs FP32 sweep within bf16 rounding.
+ *   oracle_jacobi             pinned: closed-form eigenmode damping factor; dense
+ *                             brute force.
+ *   oracle_residual           pinned: dense brute force; zero at the discrete solution.
+ *   oracle_ir_solve           pinned: converges to the closed-form discrete solution of
+ *                             the manufactured problem; FP64 inner equals plain GS.
+ *   oracle_patch_*            parity unpinned beyond: a single patch with zero
+ *                             neighbours equals a plain Dirichlet GS; equal-size
+ *                             neighbours copy the first interior layer (the halo rule
+ *                             is a reading, the paper is silent on it).
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---------------------------------------------------------------- grid helpers */
+
+static int64_t nz_cells(int dim, const int64_t *n) { return dim == 3 ? n[2] : 0; }
+
+static int64_t num_points(int dim, const int64_t *n) {
+  return (n[0] + 1) * (n[1] + 1) * (nz_cells(dim, n) + 1);
+}
+
+static int64_t vidx(const int64_t *n, int64_t i, int64_t j, int64_t k) {
+  return (k * (n[1] + 1) + j) * (n[0] + 1) + i;
+}
+
+static int is_interior(int dim, const int64_t *n, int64_t i, int64_t j, int64_t k) {
+  if (i <= 0 || i >= n[0] || j <= 0 || j >= n[1]) return 0;
+  if (dim == 3 && (k <= 0 || k >= n[2])) return 0;
+  return 1;
+}
+
+static int colour_of(int64_t i, int64_t j, int64_t k) {
+  return (int)((i & 1) + 2 * (j & 1) + 4 * (k & 1));
+}
+
+static void set_threads(int nthreads) {
+#ifdef _OPENMP
+  omp_set_num_threads(nthreads > 0 ? nthreads : 1);
+#else
+  (void)nthreads;
+#endif
+}
+
+/* ------------------------------------------------ element matrix and stencil */
+
+void oracle_q1_element_matrix(int dim, double h, double *Ke) {
+  /* 1D element stiffness and mass on [0,h] for the two linear hat functions. */
+  const double a1[2][2] = {{1.0 / h, -1.0 / h}, {-1.0 / h, 1.0 / h}};
+  const double m1[2][2] = {{2.0 * h / 6.0, h / 6.0}, {h / 6.0, 2.0 * h / 6.0}};
+  const int nv = 1 << dim;
+  for (int v = 0; v < nv; ++v) {
+    for (int w = 0; w < nv; ++w) {
+      /* grad.grad integrates to a sum over axes of (stiffness on that axis) times
+         (mass on every other axis). */
+      double sum = 0.0;
+      for (int axis = 0; axis < dim; ++axis) {
+        double prod = 1.0;
+        for (int b = 0; b < dim; ++b) {
+          const int vb = (v >> b) & 1, wb = (w >> b) & 1;
+          prod *= (b == axis) ? a1[vb][wb] : m1[vb][wb];
+        }
+        sum += prod;
+      }
+      Ke[v * nv + w] = sum;
+    }
+  }
+}
+
+double oracle_stencil_weight(int dim, int dx, int dy, int dz) {
+  /* Assembled Q1 stencil, h-free.  A vertex pair that differs in m coordinates is
+     shared by 2^(d-m) cells; summing the element entries gives these weights. */
+  const int m = (dx != 0) + (dy != 0) + (dim == 3 ? (dz != 0) : 0);
+  if (dim == 2) {
+    if (m == 0) return 8.0 / 3.0;
+    return -1.0 / 3.0; /* Fig. 1, right: all eight neighbours -1/3 */
+  }
+  if (m == 0) return 8.0 / 3.0;
+  if (m == 1) return 0.0;
+  if (m == 2) return -1.0 / 6.0;
+  return -1.0 / 12.0;
+}
+
+/* ------------------------------------------------------------------- applies */
+
+void oracle_apply_elementwise(int dim, const int64_t *n, double h,
+                              const double *u, double *y, int nthreads) {
+  const int nv = 1 << dim;
+  double Ke[64];
+  oracle_q1_element_matrix(dim, h, Ke);
+  const int64_t np = num_points(dim, n);
+  const int64_t ncz = dim == 3 ? n[2] : 1;
+  const int64_t nrows = ncz * n[1];
+  set_threads(nthreads);
+  for (int64_t p = 0; p < np; ++p) y[p] = 0.0;
+
+  /* Colour passes over the cells: cells of one colour share no vertex, so the
+     scatter inside one pass is race free. */
+  for (int c = 0; c < nv; ++c) {
+#pragma omp parallel for schedule(static) if (nthreads > 1)
+    for (int64_t row = 0; row < nrows; ++row) {
+      const int64_t ck = dim == 3 ? row / n[1] : 0, cj = row % n[1];
+      for (int64_t ci = 0; ci < n[0]; ++ci) {
+        if (colour_of(ci, cj, ck) != c) continue;
+        int64_t vert[8];
+        for (int v = 0; v < nv; ++v)
+          vert[v] = vidx(n, ci + (v & 1), cj + ((v >> 1) & 1),
+                         dim == 3 ? ck + ((v >> 2) & 1) : 0);
+        for (int v = 0; v < nv; ++v) {
+          double acc = 0.0;
+          for (int w = 0; w < nv; ++w) acc += Ke[v * nv + w] * u[vert[w]];
+          y[vert[v]] += acc;
+        }
+      }
+    }
+  }
+  /* Divide by the lumped mass h^d; boundary rows are not equations. */
+  const double hd = dim == 3 ? h * h * h : h * h;
+  const int64_t nzc = nz_cells(dim, n);
+  for (int64_t k = 0; k <= nzc; ++k)
+    for (int64_t j = 0; j <= n[1]; ++j)
+      for (int64_t i = 0; i <= n[0]; ++i) {
+        const int64_t p = vidx(n, i, j, k);
+        y[p] = is_interior(dim, n, i, j, k) ? y[p] / hd : 0.0;
+      }
+}
+
+/* (S u)_i over all 3^d offsets, dz outer, then dy, then dx, each from -1 to 1.
+   skip_centre leaves the diagonal term out. */
+static double stencil_sum(int dim, const int64_t *n, const double *u, int64_t i,
+                          int64_t j, int64_t k, int skip_centre) {
+  double acc = 0.0;
+  const int zlo = dim == 3 ? -1 : 0, zhi = dim == 3 ? 1 : 0;
+  for (int dz = zlo; dz <= zhi; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        if (skip_centre && dx == 0 && dy == 0 && dz == 0) continue;
+        acc += oracle_stencil_weight(dim, dx, dy, dz) * u[vidx(n, i + dx, j + dy, k + dz)];
+      }
+  return acc;
+}
+
+void oracle_apply_stencil(int dim, const int64_t *n, double h, const double *u,
+                          double *y, int nthreads) {
+  const int64_t nzc = nz_cells(dim, n);
+  const double h2 = h * h;
+  set_threads(nthreads);
+#pragma omp parallel for schedule(static) if (nthreads > 1)
+  for (int64_t k = 0; k <= nzc; ++k)
+    for (int64_t j = 0; j <= n[1]; ++j)
+      for (int64_t i = 0; i <= n[0]; ++i) {
+        const int64_t p = vidx(n, i, j, k);
+        y[p] = is_interior(dim, n, i, j, k) ? stencil_sum(dim, n, u, i, j, k, 0) / h2 : 0.0;
+      }
+}
+
+/* -------------------------------------------------------- coloured Gauss-Seidel */
+
+void oracle_gs_coloured(int dim, const int64_t *n, double h, double *u,
+                        const double *f, int sweeps, int nthreads) {
+  const int ncol = 1 << dim;
+  const int64_t klo = dim == 3 ? 1 : 0;
+  const int64_t nrows = (dim == 3 ? n[2] - 1 : 1) * (n[1] - 1);
+  const double h2 = h * h;
+  const double w0 = oracle_stencil_weight(dim, 0, 0, 0);
+  set_threads(nthreads);
+  for (int s = 0; s < sweeps; ++s) {
+    for (int c = 0; c < ncol; ++c) {
+      /* One colour pass over the interior rows (k, j), lexicographic: its updates
+         read no vertex of the same colour, so the rows may be split across threads
+         (the paper's parallel for over the outer loop). */
+#pragma omp parallel for schedule(static) if (nthreads > 1)
+      for (int64_t row = 0; row < nrows; ++row) {
+        const int64_t k = klo + row / (n[1] - 1), j = 1 + row % (n[1] - 1);
+        for (int64_t i = 1; i < n[0]; ++i) {
+          if (colour_of(i, j, k) != c) continue;
+          /* in-situ update: u_i <- (h^2 f_i - sum_{j != i} s_ij u_j) / s_ii */
+          const double off = stencil_sum(dim, n, u, i, j, k, 1);
+          const int64_t p = vidx(n, i, j, k);
+          u[p] = (h2 * f[p] - off) / w0;
+        }
+      }
+    }
+  }
+}
+
+void oracle_gs_coloured_f32(int dim, const int64_t *n, double h, float *u,
+                            const float *f, int sweeps) {
+  const int ncol = 1 << dim;
+  const int64_t nzc = nz_cells(dim, n);
+  const int64_t klo = dim == 3 ? 1 : 0, khi = dim == 3 ? nzc - 1 : 0;
+  const float h2 = (float)(h * h);
+  const float w0 = (float)oracle_stencil_weight(dim, 0, 0, 0);
+  const int zlo = dim == 3 ? -1 : 0, zhi = dim == 3 ? 1 : 0;
+  for (int s = 0; s < sweeps; ++s)
+    for (int c = 0; c < ncol; ++c)
+      for (int64_t k = klo; k <= khi; ++k)
+        for (int64_t j = 1; j < n[1]; ++j)
+          for (int64_t i = 1; i < n[0]; ++i) {
+            if (colour_of(i, j, k) != c) continue;
+            float off = 0.0f;
+            for (int dz = zlo; dz <= zhi; ++dz)
+              for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                  if (dx == 0 && dy == 0 && dz == 0) continue;
+                  off += (float)oracle_stencil_weight(dim, dx, dy, dz) *
+                         u[vidx(n, i + dx, j + dy, k + dz)];
+                }
+            const int64_t p = vidx(n, i, j, k);
+            u[p] = (h2 * f[p] - off) / w0;
+          }
+}
+
+uint16_t oracle_f32_to_bf16(float x) {
+  /* bf16 keeps the upper 16 bits of the binary32 pattern; round to nearest, ties to
+     even, by adding half an ulp of the kept part (minus one when the kept part is
+     even) before truncating.  NaN stays NaN. */
+  uint32_t b;
+  memcpy(&b, &x, sizeof b);
+  if ((b & 0x7f800000u) == 0x7f800000u && (b & 0x007fffffu) != 0)
+    return (uint16_t)((b >> 16) | 0x0040u);
+  const uint32_t lsb = (b >> 16) & 1u;
+  b += 0x7fffu + lsb;
+  return (uint16_t)(b >> 16);
+}
+
+float oracle_bf16_to_f32(uint16_t v) {
+  const uint32_t b = (uint32_t)v << 16;
+  float x;
+  memcpy(&x, &b, sizeof x);
+  return x;
+}
+
+void oracle_gs_coloured_bf16(int dim, const int64_t *n, double h, uint16_t *u,
+                             const uint16_t *f, int sweeps) {
+  const int ncol = 1 << dim;
+  const int64_t nzc = nz_cells(dim, n);
+  const int64_t klo = dim == 3 ? 1 : 0, khi = dim == 3 ? nzc - 1 : 0;
+  const float h2 = (float)(h * h);
+  const float w0 = (float)oracle_stencil_weight(dim, 0, 0, 0);
+  const int zlo = dim == 3 ? -1 : 0, zhi = dim == 3 ? 1 : 0;
+  for (int s = 0; s < sweeps; ++s)
+    for (int c = 0; c < ncol; ++c)
+      for (int64_t k = klo; k <= khi; ++k)
+        for (int64_t j = 1; j < n[1]; ++j)
+          for (int64_t i = 1; i < n[0]; ++i) {
+            if (colour_of(i, j, k) != c) continue;
+            float off = 0.0f;
+            for (int dz = zlo; dz <= zhi; ++dz)
+              for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                  if (dx == 0 && dy == 0 && dz == 0) continue;
+                  off += (float)oracle_stencil_weight(dim, dx, dy, dz) *
+                         oracle_bf16_to_f32(u[vidx(n, i + dx, j + dy, k + dz)]);
+                }
+            const int64_t p = vidx(n, i, j, k);
+            u[p] = oracle_f32_to_bf16((h2 * oracle_bf16_to_f32(f[p]) - off) / w0);
+          }
+}
+
+/* --------------------------------------------------------------------- Jacobi */
+
+void oracle_jacobi(int dim, const int64_t *n, double h, double *u,
+                   const double *f, double *work, double omega, int sweeps,
+                   int nthreads) {
+  const int64_t nzc = nz_cells(dim, n);
+  const int64_t np = num_points(dim, n);
+  const double h2 = h * h;
+  const double w0 = oracle_stencil_weight(dim, 0, 0, 0);
+  set_threads(nthreads);
+  for (int s = 0; s < sweeps; ++s) {
+    /* every new value is computed from the unchanged old array */
+#pragma omp parallel for schedule(static) if (nthreads > 1)
+    for (int64_t k = 0; k <= nzc; ++k)
+      for (int64_t j = 0; j <= n[1]; ++j)
+        for (int64_t i = 0; i <= n[0]; ++i) {
+          const int64_t p = vidx(n, i, j, k);
+          if (!is_interior(dim, n, i, j, k)) {
+            work[p] = u[p];
+            continue;
+          }
+          /* u + omega * D^-1 (f - A u), D = s_ii / h^2 */
+          const double res = h2 * f[p] - stencil_sum(dim, n, u, i, j, k, 0);
+          work[p] = u[p] + omega * (res / w0);
+        }
+    memcpy(u, work, (size_t)np * sizeof(double));
+  }
+}
+
+/* ------------------------------------------------------------------- residual */
+
+void oracle_residual(int dim, const int64_t *n, double h, const double *u,
+                     const double *f, double *r, double *norms2) {
+  const int64_t nzc = nz_cells(dim, n);
+  const double h2 = h * h;
+  double rr = 0.0, ff = 0.0;
+  for (int64_t k = 0; k <= nzc; ++k)
+    for (int64_t j = 0; j <= n[1]; ++j)
+      for (int64_t i = 0; i <= n[0]; ++i) {
+        const int64_t p = vidx(n, i, j, k);
+        if (!is_interior(dim, n, i, j, k)) {
+          if (r) r[p] = 0.0;
+          continue;
+        }
+        const double ri = f[p] - stencil_sum(dim, n, u, i, j, k, 0) / h2;
+        if (r) r[p] = ri;
+        rr += ri * ri;
+        ff += f[p] * f[p];
+      }
+  norms2[0] = rr;
+  norms2[1] = ff;
+}
+
+/* ------------------------------------------------------ iterative refinement */
+
+/* Steps of one outer iteration, starting from the FP64 iterate x:
+ *   1. r = f - A x in FP64 and rho = ||r|| / ||f||; stop when rho <= tol;
+ *   2. round r to the inner storage type (FP32: round to nearest; bf16: to FP32
+ *      first, then to bf16 with ties to even);
+ *   3. e = 0, then `inner_sweeps` coloured GS sweeps on A e = r in that precision;
+ *   4. x += e, widened exactly to FP64, on interior vertices. */
+int oracle_ir_solve(int dim, const int64_t *n, double h, double *x,
+                    const double *f, double tol, int max_outer, int inner_sweeps,
+                    int inner_prec, double *relres, double *x_hist,
+                    int *converged) {
+  const int64_t np = num_points(dim, n);
+  double *r = (double *)malloc((size_t)np * sizeof(double));
+  double *e64 = (double *)malloc((size_t)np * sizeof(double));
+  float *r32 = (float *)malloc((size_t)np * sizeof(float));
+  float *e32 = (float *)malloc((size_t)np * sizeof(float));
+  uint16_t *r16 = (uint16_t *)malloc((size_t)np * sizeof(uint16_t));
+  uint16_t *e16 = (uint16_t *)malloc((size_t)np * sizeof(uint16_t));
+  int k = 0;
+  *converged = 0;
+  for (;;) {
+    double nrm[2];
+    oracle_residual(dim, n, h, x, f, r, nrm);
+    const double rho = sqrt(nrm[0]) / sqrt(nrm[1]);
+    if (relres) relres[k] = rho;
+    if (rho <= tol) {
+      *converged = 1;
+      break;
+    }
+    if (k >= max_outer) break;
+    for (int64_t p = 0; p < np; ++p) {
+      if (inner_prec == 0) {
+        e64[p] = 0.0;
+      } else if (inner_prec == 1) {
+        r32[p] = (float)r[p];
+        e32[p] = 0.0f;
+      } else {
+        r16[p] = oracle_f32_to_bf16((float)r[p]);
+        e16[p] = 0;
+      }
+    }
+    if (inner_prec == 0)
+      oracle_gs_coloured(dim, n, h, e64, r, inner_sweeps, 1);
+    else if (inner_prec == 1)
+      oracle_gs_coloured_f32(dim, n, h, e32, r32, inner_sweeps);
+    else
+      oracle_gs_coloured_bf16(dim, n, h, e16, r16, inner_sweeps);
+    const int64_t nzc = nz_cells(dim, n);
+    for (int64_t kk = 0; kk <= nzc; ++kk)
+      for (int64_t j = 0; j <= n[1]; ++j)
+        for (int64_t i = 0; i <= n[0]; ++i) {
+          if (!is_interior(dim, n, i, j, kk)) continue;
+          const int64_t p = vidx(n, i, j, kk);
+          const double e = inner_prec == 0   ? e64[p]
+                           : inner_prec == 1 ? (double)e32[p]
+                                             : (double)oracle_bf16_to_f32(e16[p]);
+          x[p] += e;
+        }
+    if (x_hist) memcpy(x_hist + (size_t)k * (size_t)np, x, (size_t)np * sizeof(double));
+    ++k;
+  }
+  free(r);
+  free(e64);
+  free(r32);
+  free(e32);
+  free(r16);
+  free(e16);
+  return k;
+}
+
+/* ----------------------------------------------------------- patch lattices */
+
+/* Halo rule (a reading; the paper only says that regular patches sit inside a
+ * block-structured mesh, Section 2).  Patch p at lattice position P covers
+ * [P, P+1)^3 in lattice units with n_p cells per edge.  Each vertex of p whose index
+ * is 0 or n_p on some axis is refilled as follows: the outward direction d has
+ * d_a = -1 where the index is 0, +1 where it is n_p, 0 otherwise; if P + d lies
+ * outside the lattice the value is 0; otherwise q = P + d and, per axis, the
+ * vertex of q nearest to the halo vertex's position (ties to the lower index),
+ * clamped to q's interior range [1, n_q - 1], supplies the value. */
+void oracle_patch_halo_fill(const int32_t *lat, const int32_t *np,
+                            const int64_t *off, double *u_all) {
+  const int64_t npatch = (int64_t)lat[0] * lat[1] * lat[2];
+  for (int64_t p = 0; p < npatch; ++p) {
+    const int64_t P[3] = {p % lat[0], (p / lat[0]) % lat[1], p / ((int64_t)lat[0] * lat[1])};
+    const int64_t n = np[p];
+    const int64_t nn[3] = {n, n, n};
+    double *u = u_all + off[p];
+    for (int64_t k = 0; k <= n; ++k)
+      for (int64_t j = 0; j <= n; ++j)
+        for (int64_t i = 0; i <= n; ++i) {
+          const int64_t idx[3] = {i, j, k};
+          int d[3], on_shell = 0, outside = 0;
+          int64_t Q[3];
+          for (int a = 0; a < 3; ++a) {
+            d[a] = idx[a] == 0 ? -1 : (idx[a] == n ? 1 : 0);
+            on_shell |= d[a] != 0;
+            Q[a] = P[a] + d[a];
+            outside |= (Q[a] < 0 || Q[a] >= lat[a]);
+          }
+          if (!on_shell) continue;
+          const int64_t dst = vidx(nn, i, j, k);
+          if (outside) {
+            u[dst] = 0.0;
+            continue;
+          }
+          const int64_t q = Q[0] + lat[0] * (Q[1] + (int64_t)lat[1] * Q[2]);
+          const int64_t m = np[q];
+          int64_t iq[3];
+          for (int a = 0; a < 3; ++a) {
+            /* position in q's local cells = (idx - d*n) * m / n; nearest index with
+               ties to the lower one = floor((2*num + n - 1) / (2n)), num >= 0 */
+            const int64_t num = (idx[a] - d[a] * n) * m;
+            int64_t t = (2 * num + n - 1) / (2 * n);
+            if (t < 1) t = 1;
+            if (t > m - 1) t = m - 1;
+            iq[a] = t;
+          }
+          const int64_t mm[3] = {m, m, m};
+          u[dst] = u_all[off[q] + vidx(mm, iq[0], iq[1], iq[2])];
+        }
+  }
+}
+
+void oracle_patch_smooth(const int32_t *lat, const int32_t *np,
+                         const int64_t *off, double *u_all, const double *f_all,
+                         int sweeps, int nthreads) {
+  const int64_t npatch = (int64_t)lat[0] * lat[1] * lat[2];
+  for (int s = 0; s < sweeps; ++s) {
+    oracle_patch_halo_fill(lat, np, off, u_all);
+    for (int64_t p = 0; p < npatch; ++p) {
+      const int64_t nn[3] = {np[p], np[p], np[p]};
+      oracle_gs_coloured(3, nn, 1.0 / (double)np[p], u_all + off[p], f_all + off[p], 1,
+                         nthreads);
+    }
+  }
+}
