@@ -1,0 +1,147 @@
+/*
+ * stencil.h -- C ABI of the GB300 library for the coloured stencil codes of
+ * Hazelwood & Weinzierl, "Coloured and task-based stencil codes" (arXiv:1810.04033).
+ *
+ * The library applies the matrix-free Q1 (d-linear) Laplacian on regular Cartesian
+ * grids and runs the race-free coloured Gauss-Seidel sweep, damped Jacobi and the
+ * residual on one CUDA device.  Every call below is asynchronous on the given stream
+ * unless stated otherwise.
+ *
+ * Conventions shared by all calls
+ * -------------------------------
+ * Grid.  dim = 2 or 3; n[0], n[1], n[2] = cells along x, y, z (n[2] is ignored for
+ *   dim 2).  Arrays hold all (n[0]+1) x (n[1]+1) [x (n[2]+1)] vertices, x fastest:
+ *   element (i,j,k) lives at  k*pitch*(n[1]+1) + j*pitch + i,  pitch >= n[0]+1.
+ *   Vertices with an index 0 or n[a] are the boundary: they hold Dirichlet data,
+ *   are read by the stencil and never written by a smoother.
+ * Operator.  A = S/h^2 where S is the assembled Q1 stencil (Section 2, Fig. 1):
+ *   3D: centre 8/3, face neighbours 0, edge neighbours -1/6, corner neighbours -1/12;
+ *   2D: centre 8/3, all eight neighbours -1/3 (the 9-point stencil of Fig. 1).
+ *   A u = f discretises -Laplace u = f with f sampled at the vertices.
+ * Colours.  Vertex (i,j,k) has colour (i&1) + 2(j&1) + 4(k&1) (2D: (i&1) + 2(j&1));
+ *   a Gauss-Seidel sweep visits the colours in ascending order and updates every
+ *   interior vertex of a colour from the current values of its neighbours
+ *   (Section 3, "Colouring"; Section 2 for the in-situ update).
+ * Memory.  All array arguments are DEVICE pointers owned by the caller unless a call
+ *   says otherwise; the library never frees them.  Element type follows
+ *   stencil_grid_t.dtype.  Pointers must be aligned to their element size; 16-byte
+ *   alignment of the base and an even pitch (F64) give the fastest paths.
+ * Streams.  `stream` is a cudaStream_t passed as void*; NULL selects the legacy
+ *   default stream.  Calls check their arguments synchronously and report launch
+ *   failures synchronously; faults inside kernels surface at the next synchronising
+ *   CUDA call.
+ * Errors.  Every int-returning call returns STENCIL_OK (0) or a negative code below;
+ *   stencil_last_error() then holds a message (per host thread).
+ */
+#ifndef STENCIL_GB300_H
+#define STENCIL_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define STENCIL_OK 0
+#define STENCIL_EINVAL (-1)    /* bad dimension, size, pitch, dtype, pointer or option */
+#define STENCIL_ENOMEM (-2)    /* a device allocation the call needed failed */
+#define STENCIL_EADMIT (-3)    /* server: request footprint exceeds the HBM budget */
+#define STENCIL_ETIMEDOUT (-4) /* a bounded wait ran out */
+#define STENCIL_ECUDA (-5)     /* the CUDA runtime reported an error */
+#define STENCIL_ENOTCONV (-6)  /* solve stopped at max_outer; result still written */
+#define STENCIL_ENOTFOUND (-7) /* server: unknown ticket */
+#define STENCIL_EBUSY (-8)     /* server: request not finished yet (poll) */
+
+/* ---------------------------------------------------------------- element types */
+#define STENCIL_F64 0
+#define STENCIL_F32 1
+#define STENCIL_BF16 2
+
+/* ---------------------------------------------------------------- apply forms */
+#define STENCIL_FORM_ELEMENTWISE 0 /* cell-wise element matrix, 2^d-colour scatter */
+#define STENCIL_FORM_STENCIL 1     /* assembled 3^d-point stencil, gathered */
+
+typedef struct stencil_grid {
+  int32_t dim;   /* 2 or 3 */
+  int32_t dtype; /* STENCIL_F64 | STENCIL_F32 | STENCIL_BF16 */
+  int64_t n[3];  /* cells along x, y, z; each >= 2 (n[2] ignored when dim == 2) */
+  int64_t pitch; /* elements between consecutive x-rows; 0 selects n[0] + 1 */
+  double h;      /* mesh width (> 0) */
+} stencil_grid_t;
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int stencil_version(void);
+
+/* Message for the last failing call on this host thread ("" if none). */
+const char *stencil_last_error(void);
+
+/*
+ * y = A u.  Section 2: a stencil evaluation per vertex from its neighbours' values;
+ * a separate output array makes it the matrix-vector product.
+ *   form = STENCIL_FORM_ELEMENTWISE: every cell computes K_e u_e (K_e the Q1
+ *     element stiffness matrix) and adds it into its 2^d vertices; cells are visited
+ *     in 2^d colour passes (cell colour = parity of its lower-corner indices), so that
+ *     no two cells of a pass share a vertex (Section 3, "Colouring").
+ *   form = STENCIL_FORM_STENCIL: every interior vertex gathers the assembled stencil.
+ * Both give the same y up to rounding.  Interior rows are divided by the lumped mass
+ * h^d, so y = S u / h^2; boundary rows of y are set to 0.
+ * u, y: device arrays of g->dtype (F64 only at present), must not overlap.
+ * Returns STENCIL_EINVAL for a bad grid/form/pointer, STENCIL_ECUDA on launch failure.
+ */
+int stencil_apply(const stencil_grid_t *g, const void *u, void *y, int form, void *stream);
+
+/*
+ * `sweeps` coloured Gauss-Seidel sweeps on A u = f, in place on u (Section 2:
+ * in-situ update; Section 3: 2^d colours in ascending order, independent updates
+ * inside a colour).  Each interior vertex i of the current colour becomes
+ *   u_i = (h^2 f_i - sum_{j != i} S_ij u_j) / S_ii.
+ * Boundary values of u are read, never written; f on the boundary is ignored.
+ * u: device array (in/out); f: device array, may not alias u.  dtype F64 or F32.
+ * The call may use an internal device workspace of the size of u (allocated on first
+ * use and kept; see stencil_release_workspace).
+ * Returns STENCIL_EINVAL, STENCIL_ENOMEM, STENCIL_ECUDA.
+ */
+int stencil_smooth_coloured(const stencil_grid_t *g, void *u, const void *f, int sweeps,
+                            void *stream);
+
+/*
+ * `sweeps` damped Jacobi sweeps, out of place:
+ *   u_i <- u_i + omega * (h^2 f_i - (S u)_i) / S_ii   on interior vertices,
+ * every new value computed from the previous sweep's array (the contrast to the
+ * in-situ update of Section 2).  work: caller-owned device array with the layout of u;
+ * its boundary is overwritten with u's.  The result of the last sweep is in u.
+ * dtype F64.  Returns STENCIL_EINVAL, STENCIL_ECUDA.
+ */
+int stencil_smooth_jacobi(const stencil_grid_t *g, void *u, const void *f, void *work,
+                          int sweeps, double omega, void *stream);
+
+/*
+ * One damped Jacobi sweep, out of place: u_out = u_in + omega D^-1 (f - A u_in) on
+ * interior vertices and u_out = u_in on the boundary (the primitive that
+ * stencil_smooth_jacobi repeats).  u_in, f, u_out: device arrays of one layout, u_out
+ * overlapping neither input.  dtype F64.  Returns STENCIL_EINVAL, STENCIL_ECUDA.
+ */
+int stencil_jacobi_step(const stencil_grid_t *g, const void *u_in, const void *f, void *u_out,
+                        double omega, void *stream);
+
+/*
+ * Residual and norms: r = f - A u on interior vertices (0 on the boundary), and
+ * d_norms2[0] = sum of r_i^2, d_norms2[1] = sum of f_i^2 over interior vertices, both
+ * in FP64 by a fixed-order two-level reduction (the same bits on every call with the
+ * same input and device).  r may be NULL (norms only).  d_norms2: device, 2 doubles.
+ * The reduction uses a library-owned device scratch buffer (allocated on first use).
+ * dtype F64.  Returns STENCIL_EINVAL, STENCIL_ENOMEM, STENCIL_ECUDA.
+ */
+int stencil_residual(const stencil_grid_t *g, const void *u, const void *f, void *r,
+                     double *d_norms2, void *stream);
+
+/* Frees the internal workspaces of the current device (not thread-safe against
+ * concurrent calls on that device). */
+int stencil_release_workspace(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STENCIL_GB300_H */

@@ -35,7 +35,7 @@ def lib():
             "oracle_gs_coloured_f32": (None, [ci, i64p, cd, fp, fp, ci]),
             "oracle_gs_coloured_bf16": (None, [ci, i64p, cd, u16p, u16p, ci]),
             "oracle_jacobi": (None, [ci, i64p, cd, dp, dp, dp, cd, ci, ci]),
-            "oracle_residual": (None, [ci, i64p, cd, dp, dp, dp, dp]),
+            "oracle_residual": (None, [ci, i64p, cd, dp, dp, dp, dp, ci]),
             "oracle_ir_solve": (ci, [ci, i64p, cd, dp, dp, cd, ci, ci, ci, dp, dp,
                                      ctypes.POINTER(ctypes.c_int)]),
             "oracle_patch_halo_fill": (None, [i32p, i32p, i64p, dp]),
@@ -138,7 +138,7 @@ def jacobi(u, f, h, omega, sweeps, nthreads=1):
     return u
 
 
-def residual(u, f, h):
+def residual(u, f, h, nthreads=1):
     """Returns (r, [sum r^2, sum f^2])."""
     u = _f64(u)
     f = _f64(f)
@@ -147,7 +147,7 @@ def residual(u, f, h):
     dim, n = _grid(u.shape)
     lib().oracle_residual(dim, _ptr(n, ctypes.c_int64), h, _ptr(u, ctypes.c_double),
                           _ptr(f, ctypes.c_double), _ptr(r, ctypes.c_double),
-                          _ptr(nrm, ctypes.c_double))
+                          _ptr(nrm, ctypes.c_double), nthreads)
     return r, nrm
 
 

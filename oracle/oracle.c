@@ -320,25 +320,35 @@ void oracle_jacobi(int dim, const int64_t *n, double h, double *u,
 /* ------------------------------------------------------------------- residual */
 
 void oracle_residual(int dim, const int64_t *n, double h, const double *u,
-                     const double *f, double *r, double *norms2) {
+                     const double *f, double *r, double *norms2, int nthreads) {
   const int64_t nzc = nz_cells(dim, n);
+  const int64_t np = num_points(dim, n);
   const double h2 = h * h;
-  double rr = 0.0, ff = 0.0;
+  double *res = r ? r : (double *)malloc((size_t)np * sizeof(double));
+  set_threads(nthreads);
+  /* r_i = f_i - (S u)_i / h^2, independent per vertex */
+#pragma omp parallel for schedule(static) if (nthreads > 1)
   for (int64_t k = 0; k <= nzc; ++k)
     for (int64_t j = 0; j <= n[1]; ++j)
       for (int64_t i = 0; i <= n[0]; ++i) {
         const int64_t p = vidx(n, i, j, k);
-        if (!is_interior(dim, n, i, j, k)) {
-          if (r) r[p] = 0.0;
-          continue;
-        }
-        const double ri = f[p] - stencil_sum(dim, n, u, i, j, k, 0) / h2;
-        if (r) r[p] = ri;
-        rr += ri * ri;
+        res[p] = is_interior(dim, n, i, j, k)
+                     ? f[p] - stencil_sum(dim, n, u, i, j, k, 0) / h2
+                     : 0.0;
+      }
+  /* both sums in lexicographic order over interior vertices, one thread */
+  double rr = 0.0, ff = 0.0;
+  for (int64_t k = 0; k <= nzc; ++k)
+    for (int64_t j = 0; j <= n[1]; ++j)
+      for (int64_t i = 0; i <= n[0]; ++i) {
+        if (!is_interior(dim, n, i, j, k)) continue;
+        const int64_t p = vidx(n, i, j, k);
+        rr += res[p] * res[p];
         ff += f[p] * f[p];
       }
   norms2[0] = rr;
   norms2[1] = ff;
+  if (!r) free(res);
 }
 
 /* ------------------------------------------------------ iterative refinement */
@@ -364,7 +374,7 @@ int oracle_ir_solve(int dim, const int64_t *n, double h, double *x,
   *converged = 0;
   for (;;) {
     double nrm[2];
-    oracle_residual(dim, n, h, x, f, r, nrm);
+    oracle_residual(dim, n, h, x, f, r, nrm, 1);
     const double rho = sqrt(nrm[0]) / sqrt(nrm[1]);
     if (relres) relres[k] = rho;
     if (rho <= tol) {

@@ -73,9 +73,10 @@ void oracle_jacobi(int dim, const int64_t *n, double h, double *u,
 
 /* r = f - A u on interior vertices (0 on the boundary; r may be NULL) and
  * norms2[0] = sum r_i^2, norms2[1] = sum f_i^2 over interior vertices,
- * summed in lexicographic order. */
+ * summed in lexicographic order by one thread (r itself may be computed by
+ * nthreads threads; the result does not depend on nthreads). */
 void oracle_residual(int dim, const int64_t *n, double h, const double *u,
-                     const double *f, double *r, double *norms2);
+                     const double *f, double *r, double *norms2, int nthreads);
 
 /* Mixed-precision iterative refinement (see oracle.c for the steps).
  * inner_prec: 0 = FP64, 1 = FP32, 2 = bf16 storage / FP32 arithmetic.

@@ -1,0 +1,176 @@
+"""Python binding of libstencil_gb300 (the C ABI in include/stencil.h).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.  Functions
+carry the C names and take torch CUDA tensors laid out x fastest, shape
+(nz+1, ny+1, nx+1) in 3D or (ny+1, nx+1) in 2D, unit stride in x and a row stride
+(pitch) >= nx+1; the z stride must equal pitch * (ny+1).  Work is queued on the current
+torch stream unless `stream` is given.  There is no CPU fallback: if the library
+cannot be built or loaded, every call raises.
+"""
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+F64, F32, BF16 = 0, 1, 2
+FORM_ELEMENTWISE, FORM_STENCIL = 0, 1
+
+STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "EADMIT", -4: "ETIMEDOUT", -5: "ECUDA",
+          -6: "ENOTCONV", -7: "ENOTFOUND", -8: "EBUSY"}
+
+_DTYPES = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
+
+
+class StencilError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("n", ctypes.c_int64 * 3), ("pitch", ctypes.c_int64), ("h", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Loads (building first if needed) the shared library; raises if impossible."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        vp, ci, cd = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        gp = ctypes.POINTER(Grid)
+        sigs = {
+            "stencil_version": (ci, []),
+            "stencil_last_error": (ctypes.c_char_p, []),
+            "stencil_release_workspace": (ci, []),
+            "stencil_apply": (ci, [gp, vp, vp, ci, vp]),
+            "stencil_smooth_coloured": (ci, [gp, vp, vp, ci, vp]),
+            "stencil_smooth_jacobi": (ci, [gp, vp, vp, vp, ci, cd, vp]),
+            "stencil_residual": (ci, [gp, vp, vp, vp, vp, vp]),
+            "stencil_jacobi_step": (ci, [gp, vp, vp, vp, cd, vp]),
+        }
+        for name, (res, args) in sigs.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise StencilError(rc, lib().stencil_last_error().decode())
+
+
+def grid_for(t: torch.Tensor, h: float) -> Grid:
+    """Grid descriptor for a vertex tensor (validates layout, not device residency)."""
+    if t.dim() not in (2, 3):
+        raise ValueError("expected a 2D or 3D vertex tensor")
+    if t.dtype not in _DTYPES:
+        raise ValueError("unsupported dtype %s" % t.dtype)
+    if t.stride(-1) != 1:
+        raise ValueError("x must have unit stride")
+    g = Grid()
+    g.dim = t.dim()
+    g.dtype = _DTYPES[t.dtype]
+    if t.dim() == 3:
+        nz, ny, nx = (s - 1 for s in t.shape)
+        pitch = t.stride(1)
+        if t.shape[0] > 1 and t.stride(0) != pitch * t.shape[1]:
+            raise ValueError("z stride must be pitch * (ny+1)")
+        g.n[0], g.n[1], g.n[2] = nx, ny, nz
+    else:
+        ny, nx = (s - 1 for s in t.shape)
+        pitch = t.stride(0)
+        g.n[0], g.n[1], g.n[2] = nx, ny, 0
+    g.pitch = pitch
+    g.h = float(h)
+    return g
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _same_layout(a, b):
+    if a.shape != b.shape or a.stride() != b.stride() or a.dtype != b.dtype:
+        raise ValueError("arrays must share shape, strides and dtype")
+    if a.device != b.device or a.device.type != "cuda":
+        raise ValueError("arrays must be CUDA tensors on the same device")
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def stencil_version() -> int:
+    return lib().stencil_version()
+
+
+def stencil_apply(u, y, h, form=FORM_STENCIL, stream=None):
+    """y = A u (boundary rows of y set to 0)."""
+    _same_layout(u, y)
+    g = grid_for(u, h)
+    _check(lib().stencil_apply(ctypes.byref(g), _ptr(u), _ptr(y), int(form), _stream(stream)))
+    return y
+
+
+def stencil_smooth_coloured(u, f, h, sweeps, stream=None):
+    """`sweeps` coloured Gauss-Seidel sweeps on A u = f, in place on u."""
+    _same_layout(u, f)
+    g = grid_for(u, h)
+    _check(lib().stencil_smooth_coloured(ctypes.byref(g), _ptr(u), _ptr(f), int(sweeps),
+                                         _stream(stream)))
+    return u
+
+
+def stencil_smooth_jacobi(u, f, work, h, sweeps, omega=2.0 / 3.0, stream=None):
+    """`sweeps` damped Jacobi sweeps; result in u, work is scratch of u's layout."""
+    _same_layout(u, f)
+    _same_layout(u, work)
+    g = grid_for(u, h)
+    _check(lib().stencil_smooth_jacobi(ctypes.byref(g), _ptr(u), _ptr(f), _ptr(work),
+                                       int(sweeps), float(omega), _stream(stream)))
+    return u
+
+
+def stencil_jacobi_step(u_in, f, u_out, h, omega=2.0 / 3.0, stream=None):
+    """One damped Jacobi sweep from u_in into u_out (boundary copied)."""
+    _same_layout(u_in, f)
+    _same_layout(u_in, u_out)
+    g = grid_for(u_in, h)
+    _check(lib().stencil_jacobi_step(ctypes.byref(g), _ptr(u_in), _ptr(f), _ptr(u_out),
+                                     float(omega), _stream(stream)))
+    return u_out
+
+
+def stencil_residual(u, f, h, r=None, norms2=None, stream=None):
+    """r = f - A u (if r given) and norms2 = [sum r^2, sum f^2] (device float64[2])."""
+    _same_layout(u, f)
+    if r is not None:
+        _same_layout(u, r)
+    if norms2 is None:
+        norms2 = torch.empty(2, dtype=torch.float64, device=u.device)
+    g = grid_for(u, h)
+    _check(lib().stencil_residual(ctypes.byref(g), _ptr(u), _ptr(f),
+                                  _ptr(r) if r is not None else ctypes.c_void_p(0),
+                                  _ptr(norms2), _stream(stream)))
+    return norms2
+
+
+def stencil_release_workspace():
+    _check(lib().stencil_release_workspace())

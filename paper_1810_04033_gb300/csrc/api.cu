@@ -1,0 +1,240 @@
+// C ABI entry points of libstencil_gb300: argument checks, scratch management and
+// dispatch to the kernels.  See include/stencil.h for the contract of each call.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <cmath>
+#include <mutex>
+#include <string>
+
+#include "internal.h"
+
+namespace stencil {
+
+static thread_local std::string g_last_error;
+
+int set_error(int code, const std::string &msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int check_launch(const char *what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return set_error(STENCIL_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return STENCIL_OK;
+}
+
+// ------------------------------------------------------------ per-device scratch
+namespace {
+constexpr int kMaxDevices = 64;
+struct Scratch {
+  void *ptr[SCRATCH_SLOTS] = {nullptr};
+  size_t bytes[SCRATCH_SLOTS] = {0};
+};
+std::mutex g_scratch_mu;
+Scratch g_scratch[kMaxDevices];
+}  // namespace
+
+void *device_scratch(int slot, size_t bytes) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  Scratch &s = g_scratch[dev];
+  if (s.bytes[slot] >= bytes && s.ptr[slot]) return s.ptr[slot];
+  if (s.ptr[slot]) {
+    // the old buffer may still be in use by queued work on any stream
+    cudaDeviceSynchronize();
+    cudaFree(s.ptr[slot]);
+    s.ptr[slot] = nullptr;
+    s.bytes[slot] = 0;
+  }
+  void *p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  // reduction counters must start at zero
+  if (cudaMemset(p, 0, bytes) != cudaSuccess) {
+    cudaFree(p);
+    return nullptr;
+  }
+  s.ptr[slot] = p;
+  s.bytes[slot] = bytes;
+  return p;
+}
+
+static int release_scratch() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return set_error(STENCIL_ECUDA, "cudaGetDevice failed");
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  cudaDeviceSynchronize();
+  Scratch &s = g_scratch[dev];
+  for (int i = 0; i < SCRATCH_SLOTS; ++i) {
+    if (s.ptr[i]) cudaFree(s.ptr[i]);
+    s.ptr[i] = nullptr;
+    s.bytes[i] = 0;
+  }
+  return STENCIL_OK;
+}
+
+// ------------------------------------------------------------ argument checks
+static size_t elem_size(int dtype) {
+  switch (dtype) {
+    case STENCIL_F64: return 8;
+    case STENCIL_F32: return 4;
+    case STENCIL_BF16: return 2;
+    default: return 0;
+  }
+}
+
+int check_grid(const stencil_grid_t *g) {
+  if (!g) return set_error(STENCIL_EINVAL, "grid descriptor is NULL");
+  if (g->dim != 2 && g->dim != 3) return set_error(STENCIL_EINVAL, "dim must be 2 or 3");
+  if (!elem_size(g->dtype)) return set_error(STENCIL_EINVAL, "unknown dtype");
+  const int64_t lim = (int64_t)1 << 31;
+  for (int a = 0; a < g->dim; ++a)
+    if (g->n[a] < 1 || g->n[a] >= lim)
+      return set_error(STENCIL_EINVAL, "cells per axis must be in [1, 2^31)");
+  const int64_t pitch = g->pitch ? g->pitch : g->n[0] + 1;
+  if (pitch < g->n[0] + 1) return set_error(STENCIL_EINVAL, "pitch < n[0] + 1");
+  if (!(g->h > 0.0) || !std::isfinite(g->h))
+    return set_error(STENCIL_EINVAL, "h must be finite and > 0");
+  // total span must fit comfortably in int64 element offsets
+  const double span = (double)pitch * (double)(g->n[1] + 1) *
+                      (double)(g->dim == 3 ? g->n[2] + 1 : 1);
+  if (span > 9.0e15) return set_error(STENCIL_EINVAL, "array too large");
+  return STENCIL_OK;
+}
+
+static int check_ptr(const void *p, const stencil_grid_t *g, const char *name) {
+  if (!p) return set_error(STENCIL_EINVAL, std::string(name) + " is NULL");
+  if ((uintptr_t)p % elem_size(g->dtype))
+    return set_error(STENCIL_EINVAL, std::string(name) + " is not aligned to its element size");
+  return STENCIL_OK;
+}
+
+static bool overlap(const void *a, const void *b, size_t bytes) {
+  const char *x = (const char *)a, *y = (const char *)b;
+  return x < y + bytes && y < x + bytes;
+}
+
+}  // namespace stencil
+
+using namespace stencil;
+
+extern "C" {
+
+int stencil_version(void) { return 10000; }
+
+const char *stencil_last_error(void) { return g_last_error.c_str(); }
+
+int stencil_release_workspace(void) { return release_scratch(); }
+
+int stencil_apply(const stencil_grid_t *g, const void *u, void *y, int form, void *stream) {
+  int rc = check_grid(g);
+  if (rc) return rc;
+  if ((rc = check_ptr(u, g, "u")) || (rc = check_ptr(y, g, "y"))) return rc;
+  if (form != STENCIL_FORM_ELEMENTWISE && form != STENCIL_FORM_STENCIL)
+    return set_error(STENCIL_EINVAL, "unknown apply form");
+  if (g->dtype != STENCIL_F64) return set_error(STENCIL_EINVAL, "apply supports F64 only");
+  const Geo q = make_geo(*g);
+  if (overlap(u, y, (size_t)span_elems(q) * 8))
+    return set_error(STENCIL_EINVAL, "u and y overlap");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = form == STENCIL_FORM_STENCIL
+                      ? launch_apply_stencil_f64(q, g->dim, (const double *)u, (double *)y, s)
+                      : launch_apply_elementwise_f64(q, g->dim, (const double *)u, (double *)y, s);
+  if (e != cudaSuccess) return set_error(STENCIL_ECUDA, std::string("apply: ") + cudaGetErrorString(e));
+  return STENCIL_OK;
+}
+
+int stencil_smooth_coloured(const stencil_grid_t *g, void *u, const void *f, int sweeps,
+                            void *stream) {
+  int rc = check_grid(g);
+  if (rc) return rc;
+  if ((rc = check_ptr(u, g, "u")) || (rc = check_ptr(f, g, "f"))) return rc;
+  if (sweeps < 0) return set_error(STENCIL_EINVAL, "sweeps < 0");
+  if (g->dtype != STENCIL_F64) return set_error(STENCIL_EINVAL, "smooth_coloured supports F64 only");
+  const Geo q = make_geo(*g);
+  if (overlap(u, f, (size_t)span_elems(q) * 8)) return set_error(STENCIL_EINVAL, "u and f overlap");
+  if (sweeps == 0) return STENCIL_OK;
+  cudaError_t e = launch_gs_sweeps_f64(q, g->dim, (double *)u, (const double *)f, sweeps,
+                                       (cudaStream_t)stream);
+  if (e != cudaSuccess)
+    return set_error(STENCIL_ECUDA, std::string("smooth_coloured: ") + cudaGetErrorString(e));
+  return STENCIL_OK;
+}
+
+int stencil_smooth_jacobi(const stencil_grid_t *g, void *u, const void *f, void *work,
+                          int sweeps, double omega, void *stream) {
+  int rc = check_grid(g);
+  if (rc) return rc;
+  if ((rc = check_ptr(u, g, "u")) || (rc = check_ptr(f, g, "f")) ||
+      (rc = check_ptr(work, g, "work")))
+    return rc;
+  if (sweeps < 0) return set_error(STENCIL_EINVAL, "sweeps < 0");
+  if (!std::isfinite(omega)) return set_error(STENCIL_EINVAL, "omega must be finite");
+  if (g->dtype != STENCIL_F64) return set_error(STENCIL_EINVAL, "jacobi supports F64 only");
+  const Geo q = make_geo(*g);
+  const size_t bytes = (size_t)span_elems(q) * 8;
+  if (overlap(u, f, bytes) || overlap(u, work, bytes) || overlap(f, work, bytes))
+    return set_error(STENCIL_EINVAL, "u, f and work must not overlap");
+  cudaStream_t s = (cudaStream_t)stream;
+  double *a = (double *)u, *b = (double *)work;
+  for (int it = 0; it < sweeps; ++it) {
+    cudaError_t e = launch_jacobi_sweep_f64(q, g->dim, a, (const double *)f, b, omega, s);
+    if (e != cudaSuccess) return set_error(STENCIL_ECUDA, std::string("jacobi: ") + cudaGetErrorString(e));
+    double *t = a;
+    a = b;
+    b = t;
+  }
+  if (a != (double *)u) {
+    cudaError_t e = cudaMemcpyAsync(u, a, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return set_error(STENCIL_ECUDA, std::string("jacobi copy: ") + cudaGetErrorString(e));
+  }
+  return STENCIL_OK;
+}
+
+int stencil_jacobi_step(const stencil_grid_t *g, const void *u_in, const void *f, void *u_out,
+                        double omega, void *stream) {
+  int rc = check_grid(g);
+  if (rc) return rc;
+  if ((rc = check_ptr(u_in, g, "u_in")) || (rc = check_ptr(f, g, "f")) ||
+      (rc = check_ptr(u_out, g, "u_out")))
+    return rc;
+  if (!std::isfinite(omega)) return set_error(STENCIL_EINVAL, "omega must be finite");
+  if (g->dtype != STENCIL_F64) return set_error(STENCIL_EINVAL, "jacobi supports F64 only");
+  const Geo q = make_geo(*g);
+  const size_t bytes = (size_t)span_elems(q) * 8;
+  if (overlap(u_out, u_in, bytes) || overlap(u_out, f, bytes))
+    return set_error(STENCIL_EINVAL, "u_out overlaps an input");
+  cudaError_t e = launch_jacobi_sweep_f64(q, g->dim, (const double *)u_in, (const double *)f,
+                                          (double *)u_out, omega, (cudaStream_t)stream);
+  if (e != cudaSuccess) return set_error(STENCIL_ECUDA, std::string("jacobi: ") + cudaGetErrorString(e));
+  return STENCIL_OK;
+}
+
+int stencil_residual(const stencil_grid_t *g, const void *u, const void *f, void *r,
+                     double *d_norms2, void *stream) {
+  int rc = check_grid(g);
+  if (rc) return rc;
+  if ((rc = check_ptr(u, g, "u")) || (rc = check_ptr(f, g, "f"))) return rc;
+  if (r && (rc = check_ptr(r, g, "r"))) return rc;
+  if (!d_norms2 || (uintptr_t)d_norms2 % 8) return set_error(STENCIL_EINVAL, "d_norms2 NULL or misaligned");
+  if (g->dtype != STENCIL_F64) return set_error(STENCIL_EINVAL, "residual supports F64 only");
+  const Geo q = make_geo(*g);
+  const size_t bytes = (size_t)span_elems(q) * 8;
+  if (r && (overlap(r, u, bytes) || overlap(r, f, bytes)))
+    return set_error(STENCIL_EINVAL, "r overlaps u or f");
+  void *scratch = device_scratch(SCRATCH_REDUCE, reduce_scratch_bytes());
+  if (!scratch) return set_error(STENCIL_ENOMEM, "residual scratch allocation failed");
+  cudaError_t e = launch_residual_f64(q, g->dim, (const double *)u, (const double *)f,
+                                      (double *)r, d_norms2, scratch, (cudaStream_t)stream);
+  if (e != cudaSuccess) return set_error(STENCIL_ECUDA, std::string("residual: ") + cudaGetErrorString(e));
+  return STENCIL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,59 @@
+// Internal declarations shared by the translation units of libstencil_gb300.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "stencil.h"
+
+namespace stencil {
+
+// Grid geometry as the kernels see it (element strides, not bytes).
+struct Geo {
+  int64_t nx, ny, nz;  // cells per axis; nz == 0 for 2D
+  int64_t pitch;       // elements between x-rows
+  int64_t plane;       // elements between z-planes (pitch * (ny + 1))
+  double h;
+};
+
+inline Geo make_geo(const stencil_grid_t &g) {
+  Geo q;
+  q.nx = g.n[0];
+  q.ny = g.n[1];
+  q.nz = g.dim == 3 ? g.n[2] : 0;
+  q.pitch = g.pitch ? g.pitch : g.n[0] + 1;
+  q.plane = q.pitch * (q.ny + 1);
+  q.h = g.h;
+  return q;
+}
+
+// Number of elements spanned by an array of this geometry (last element + 1).
+inline int64_t span_elems(const Geo &q) { return q.plane * (q.nz + 1); }
+
+// Error plumbing (api.cu).
+int set_error(int code, const std::string &msg);
+int check_launch(const char *what);
+
+// Library-owned per-device scratch (api.cu): returns a device pointer with at least
+// `bytes` bytes for slot `slot`, growing with cudaMalloc when needed; nullptr on OOM.
+enum ScratchSlot { SCRATCH_REDUCE = 0, SCRATCH_PINGPONG = 1, SCRATCH_SLOTS = 4 };
+void *device_scratch(int slot, size_t bytes);
+
+// Kernel launchers (kernels_*.cu).  Return cudaGetLastError() of the launch.
+cudaError_t launch_apply_stencil_f64(const Geo &q, int dim, const double *u, double *y,
+                                     cudaStream_t s);
+cudaError_t launch_apply_elementwise_f64(const Geo &q, int dim, const double *u, double *y,
+                                         cudaStream_t s);
+cudaError_t launch_gs_sweeps_f64(const Geo &q, int dim, double *u, const double *f,
+                                 int sweeps, cudaStream_t s);
+cudaError_t launch_jacobi_sweep_f64(const Geo &q, int dim, const double *u, const double *f,
+                                    double *unew, double omega, cudaStream_t s);
+// Residual with norms; partials must hold 2 * kReduceBlocks doubles plus one
+// unsigned counter (zero before the first call; the kernel leaves it zero).
+constexpr int kReduceBlocks = 1216;  // 8 per SM on 152 SMs: fixed => fixed sum order
+size_t reduce_scratch_bytes();
+cudaError_t launch_residual_f64(const Geo &q, int dim, const double *u, const double *f,
+                                double *r, double *norms2, void *scratch, cudaStream_t s);
+
+}  // namespace stencil
