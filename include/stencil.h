@@ -137,6 +137,27 @@ int stencil_jacobi_step(const stencil_grid_t *g, const void *u_in, const void *f
 int stencil_residual(const stencil_grid_t *g, const void *u, const void *f, void *r,
                      double *d_norms2, void *stream);
 
+/*
+ * Allocation-free variant of stencil_residual, for callers that cannot let a library
+ * allocate device memory: cudaMalloc/cudaFree may synchronise the whole device, which a
+ * latency-bound loop driving several streams cannot afford; a caching allocator may
+ * already own nearly all device memory; some deployments forbid device allocation
+ * after start-up.  The paper has no counterpart; it is a service of this library.
+ * Same results as stencil_residual up to the summation order of the norms (r is
+ * identical in exact arithmetic; both are within the library's FP64 tolerance).
+ * Scratch: a fixed 128 KiB array in the library's device image (present on every GPU
+ * that loads the library, until process exit); nothing is allocated by the call.
+ * Limit: at most 524288 x-rows, i.e. (n[2]+1)*(n[1]+1) in 3D or n[1]+1 in 2D; larger
+ * grids return STENCIL_EINVAL.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ * capture.  Every call reuses the same array (its counter is cleared on the stream at
+ * the start of each call), so calls that overlap on the GPU race and must be ordered by
+ * the caller.  Arguments as for stencil_residual; dtype F64.
+ * Returns STENCIL_EINVAL, STENCIL_ECUDA.
+ */
+int stencil_residual_noalloc(const stencil_grid_t *g, const void *u, const void *f, void *r,
+                             double *d_norms2, void *stream);
+
 /* Frees the internal workspaces of the current device (not thread-safe against
  * concurrent calls on that device). */
 int stencil_release_workspace(void);

@@ -58,6 +58,7 @@ def lib():
             "stencil_smooth_jacobi": (ci, [gp, vp, vp, vp, ci, cd, vp]),
             "stencil_residual": (ci, [gp, vp, vp, vp, vp, vp]),
             "stencil_jacobi_step": (ci, [gp, vp, vp, vp, cd, vp]),
+            "stencil_residual_noalloc": (ci, [gp, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name)
@@ -169,6 +170,19 @@ def stencil_residual(u, f, h, r=None, norms2=None, stream=None):
     _check(lib().stencil_residual(ctypes.byref(g), _ptr(u), _ptr(f),
                                   _ptr(r) if r is not None else ctypes.c_void_p(0),
                                   _ptr(norms2), _stream(stream)))
+    return norms2
+
+
+def stencil_residual_noalloc(u, f, h, norms2, r=None, stream=None):
+    """stencil_residual without any device allocation: the caller supplies norms2
+    (device float64[2]) and optionally r; the library's fixed scratch array is used."""
+    _same_layout(u, f)
+    if r is not None:
+        _same_layout(u, r)
+    g = grid_for(u, h)
+    _check(lib().stencil_residual_noalloc(ctypes.byref(g), _ptr(u), _ptr(f),
+                                          _ptr(r) if r is not None else ctypes.c_void_p(0),
+                                          _ptr(norms2), _stream(stream)))
     return norms2
 
 
