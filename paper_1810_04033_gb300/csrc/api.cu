@@ -7,6 +7,7 @@
 #include <cmath>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "internal.h"
 
@@ -26,29 +27,37 @@ int check_launch(const char *what) {
   return STENCIL_OK;
 }
 
-// ------------------------------------------------------------ per-device scratch
+// ------------------------------------------------------------ per-stream scratch
 namespace {
 constexpr int kMaxDevices = 64;
 struct Scratch {
-  void *ptr[SCRATCH_SLOTS] = {nullptr};
-  size_t bytes[SCRATCH_SLOTS] = {0};
+  int device;
+  cudaStream_t stream;
+  void *ptr[SCRATCH_SLOTS];
+  size_t bytes[SCRATCH_SLOTS];
 };
 std::mutex g_scratch_mu;
-Scratch g_scratch[kMaxDevices];
+std::vector<Scratch> g_scratch;
 }  // namespace
 
-void *device_scratch(int slot, size_t bytes) {
+void *device_scratch(int slot, size_t bytes, cudaStream_t stream) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
   std::lock_guard<std::mutex> lk(g_scratch_mu);
-  Scratch &s = g_scratch[dev];
-  if (s.bytes[slot] >= bytes && s.ptr[slot]) return s.ptr[slot];
-  if (s.ptr[slot]) {
-    // the old buffer may still be in use by queued work on any stream
-    cudaDeviceSynchronize();
-    cudaFree(s.ptr[slot]);
-    s.ptr[slot] = nullptr;
-    s.bytes[slot] = 0;
+  Scratch *s = nullptr;
+  for (auto &e : g_scratch)
+    if (e.device == dev && e.stream == stream) s = &e;
+  if (!s) {
+    g_scratch.push_back(Scratch{dev, stream, {nullptr}, {0}});
+    s = &g_scratch.back();
+  }
+  if (s->bytes[slot] >= bytes && s->ptr[slot]) return s->ptr[slot];
+  if (s->ptr[slot]) {
+    // the old buffer may still be in use by work queued on this stream
+    cudaStreamSynchronize(stream);
+    cudaFree(s->ptr[slot]);
+    s->ptr[slot] = nullptr;
+    s->bytes[slot] = 0;
   }
   void *p = nullptr;
   if (cudaMalloc(&p, bytes) != cudaSuccess) {
@@ -60,8 +69,8 @@ void *device_scratch(int slot, size_t bytes) {
     cudaFree(p);
     return nullptr;
   }
-  s.ptr[slot] = p;
-  s.bytes[slot] = bytes;
+  s->ptr[slot] = p;
+  s->bytes[slot] = bytes;
   return p;
 }
 
@@ -71,11 +80,14 @@ static int release_scratch() {
     return set_error(STENCIL_ECUDA, "cudaGetDevice failed");
   std::lock_guard<std::mutex> lk(g_scratch_mu);
   cudaDeviceSynchronize();
-  Scratch &s = g_scratch[dev];
-  for (int i = 0; i < SCRATCH_SLOTS; ++i) {
-    if (s.ptr[i]) cudaFree(s.ptr[i]);
-    s.ptr[i] = nullptr;
-    s.bytes[i] = 0;
+  for (auto it = g_scratch.begin(); it != g_scratch.end();) {
+    if (it->device == dev) {
+      for (int i = 0; i < SCRATCH_SLOTS; ++i)
+        if (it->ptr[i]) cudaFree(it->ptr[i]);
+      it = g_scratch.erase(it);
+    } else {
+      ++it;
+    }
   }
   return STENCIL_OK;
 }
@@ -161,8 +173,16 @@ int stencil_smooth_coloured(const stencil_grid_t *g, void *u, const void *f, int
   const Geo q = make_geo(*g);
   if (overlap(u, f, (size_t)span_elems(q) * 8)) return set_error(STENCIL_EINVAL, "u and f overlap");
   if (sweeps == 0) return STENCIL_OK;
-  cudaError_t e = launch_gs_sweeps_f64(q, g->dim, (double *)u, (const double *)f, sweeps,
-                                       (cudaStream_t)stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (g->dim == 3) {
+    void *work = device_scratch(SCRATCH_PINGPONG, (size_t)span_elems(q) * 8, s);
+    void *bnd = device_scratch(SCRATCH_BOUNDS, gs_fx_bounds_bytes(), s);
+    if (!work || !bnd) return set_error(STENCIL_ENOMEM, "smooth_coloured workspace allocation failed");
+    e = launch_gs_sweeps_fx3(q, (double *)u, (const double *)f, sweeps, (double *)work, bnd, s);
+  } else {
+    e = launch_gs_sweeps_f64(q, g->dim, (double *)u, (const double *)f, sweeps, s);
+  }
   if (e != cudaSuccess)
     return set_error(STENCIL_ECUDA, std::string("smooth_coloured: ") + cudaGetErrorString(e));
   return STENCIL_OK;
@@ -229,7 +249,7 @@ int stencil_residual(const stencil_grid_t *g, const void *u, const void *f, void
   const size_t bytes = (size_t)span_elems(q) * 8;
   if (r && (overlap(r, u, bytes) || overlap(r, f, bytes)))
     return set_error(STENCIL_EINVAL, "r overlaps u or f");
-  void *scratch = device_scratch(SCRATCH_REDUCE, reduce_scratch_bytes());
+  void *scratch = device_scratch(SCRATCH_REDUCE, reduce_scratch_bytes(), (cudaStream_t)stream);
   if (!scratch) return set_error(STENCIL_ENOMEM, "residual scratch allocation failed");
   cudaError_t e = launch_residual_f64(q, g->dim, (const double *)u, (const double *)f,
                                       (double *)r, d_norms2, scratch, (cudaStream_t)stream);

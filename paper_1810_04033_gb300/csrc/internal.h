@@ -35,10 +35,12 @@ inline int64_t span_elems(const Geo &q) { return q.plane * (q.nz + 1); }
 int set_error(int code, const std::string &msg);
 int check_launch(const char *what);
 
-// Library-owned per-device scratch (api.cu): returns a device pointer with at least
-// `bytes` bytes for slot `slot`, growing with cudaMalloc when needed; nullptr on OOM.
-enum ScratchSlot { SCRATCH_REDUCE = 0, SCRATCH_PINGPONG = 1, SCRATCH_SLOTS = 4 };
-void *device_scratch(int slot, size_t bytes);
+// Library-owned scratch (api.cu), one set per (device, stream): returns a device
+// pointer with at least `bytes` bytes for slot `slot`, growing with cudaMalloc when
+// needed (zero-filled when allocated); nullptr on failure.  Work queued on one stream
+// therefore never shares scratch with work on another stream.
+enum ScratchSlot { SCRATCH_REDUCE = 0, SCRATCH_PINGPONG = 1, SCRATCH_BOUNDS = 2, SCRATCH_SLOTS = 4 };
+void *device_scratch(int slot, size_t bytes, cudaStream_t stream);
 
 // Kernel launchers (kernels_*.cu).  Return cudaGetLastError() of the launch.
 cudaError_t launch_apply_stencil_f64(const Geo &q, int dim, const double *u, double *y,
@@ -53,6 +55,12 @@ cudaError_t launch_jacobi_sweep_f64(const Geo &q, int dim, const double *u, cons
 // unsigned counter (zero before the first call; the kernel leaves it zero).
 constexpr int kReduceBlocks = 1216;  // 8 per SM on 152 SMs: fixed => fixed sum order
 size_t reduce_scratch_bytes();
+
+// Fixed-point FP64 paths (gs_fx.cu): 3D coloured GS, two launches per sweep, out of
+// place between u and work (same layout); result always ends in u.
+size_t gs_fx_bounds_bytes();
+cudaError_t launch_gs_sweeps_fx3(const Geo &q, double *u, const double *f, int sweeps,
+                                 double *work, void *bounds, cudaStream_t s);
 cudaError_t launch_residual_f64(const Geo &q, int dim, const double *u, const double *f,
                                 double *r, double *norms2, void *scratch, cudaStream_t s);
 

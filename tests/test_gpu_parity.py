@@ -153,3 +153,48 @@ def test_jacobi_step_out_of_place(dim, n):
     torch.cuda.synchronize()
     assert rel_err(to_host(od), ref) <= TOL_F64
     assert np.array_equal(to_host(ud), u0)
+
+
+@pytest.mark.parametrize("n", [(20, 70, 6), (10, 10, 70), (130, 33, 35), (59, 31, 5)])
+def test_gs_multi_tile_and_chunk(n):
+    """Grids spanning several (x, y) tiles and several z chunks of the fused sweep."""
+    h = 1.0 / max(n)
+    shape = synth.grid_shape(3, n)
+    u0 = synth.uniform_field(shape, 1000 + sum(n), zero_bc=False)
+    f = synth.uniform_field(shape, 1100 + sum(n))
+    for sweeps in (1, 2, 5):
+        ref = oracle.gs_coloured(u0, f, h, sweeps)
+        ud, fd = to_dev(u0), to_dev(f)
+        st.stencil_smooth_coloured(ud, fd, h, sweeps)
+        torch.cuda.synchronize()
+        assert rel_err(to_host(ud), ref) <= TOL_F64, sweeps
+
+
+@pytest.mark.parametrize("scale", [1e305, 1e-280, 1e-5, 1e12])
+def test_gs_extreme_magnitudes(scale):
+    """Magnitudes outside the fixed-point range take the kernel's FP64 branch; the
+    others exercise the tracked bound at unusual scales."""
+    n = (12, 9, 14)
+    h = 1.0 / 14
+    shape = synth.grid_shape(3, n)
+    u0 = synth.uniform_field(shape, 77, zero_bc=False) * scale
+    f = synth.uniform_field(shape, 78) * scale
+    ref = oracle.gs_coloured(u0, f, h, 3)
+    ud, fd = to_dev(u0), to_dev(f)
+    st.stencil_smooth_coloured(ud, fd, h, 3)
+    torch.cuda.synchronize()
+    assert rel_err(to_host(ud), ref) <= TOL_F64
+
+
+def test_gs_shrinking_iterate_keeps_relative_accuracy():
+    """f = 0: the iterate decays over the sweeps; the tracked bound follows it."""
+    n = (16, 16, 16)
+    h = 1.0 / 16
+    shape = synth.grid_shape(3, n)
+    u0 = synth.uniform_field(shape, 91)
+    f = np.zeros(shape)
+    ref = oracle.gs_coloured(u0, f, h, 40)
+    ud, fd = to_dev(u0), to_dev(f)
+    st.stencil_smooth_coloured(ud, fd, h, 40)
+    torch.cuda.synchronize()
+    assert rel_err(to_host(ud), ref) <= TOL_F64
