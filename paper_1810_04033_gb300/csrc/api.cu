@@ -156,9 +156,12 @@ int stencil_apply(const stencil_grid_t *g, const void *u, void *y, int form, voi
   if (overlap(u, y, (size_t)span_elems(q) * 8))
     return set_error(STENCIL_EINVAL, "u and y overlap");
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = form == STENCIL_FORM_STENCIL
-                      ? launch_apply_stencil_f64(q, g->dim, (const double *)u, (double *)y, s)
-                      : launch_apply_elementwise_f64(q, g->dim, (const double *)u, (double *)y, s);
+  cudaError_t e;
+  if (form == STENCIL_FORM_STENCIL)
+    e = g->dim == 3 ? launch_apply_stencil_fx3(q, (const double *)u, (double *)y, s)
+                    : launch_apply_stencil_f64(q, g->dim, (const double *)u, (double *)y, s);
+  else
+    e = launch_apply_elementwise_f64(q, g->dim, (const double *)u, (double *)y, s);
   if (e != cudaSuccess) return set_error(STENCIL_ECUDA, std::string("apply: ") + cudaGetErrorString(e));
   return STENCIL_OK;
 }
@@ -205,7 +208,8 @@ int stencil_smooth_jacobi(const stencil_grid_t *g, void *u, const void *f, void 
   cudaStream_t s = (cudaStream_t)stream;
   double *a = (double *)u, *b = (double *)work;
   for (int it = 0; it < sweeps; ++it) {
-    cudaError_t e = launch_jacobi_sweep_f64(q, g->dim, a, (const double *)f, b, omega, s);
+    cudaError_t e = g->dim == 3 ? launch_jacobi_fx3(q, a, (const double *)f, b, omega, s)
+                                : launch_jacobi_sweep_f64(q, g->dim, a, (const double *)f, b, omega, s);
     if (e != cudaSuccess) return set_error(STENCIL_ECUDA, std::string("jacobi: ") + cudaGetErrorString(e));
     double *t = a;
     a = b;
@@ -231,8 +235,11 @@ int stencil_jacobi_step(const stencil_grid_t *g, const void *u_in, const void *f
   const size_t bytes = (size_t)span_elems(q) * 8;
   if (overlap(u_out, u_in, bytes) || overlap(u_out, f, bytes))
     return set_error(STENCIL_EINVAL, "u_out overlaps an input");
-  cudaError_t e = launch_jacobi_sweep_f64(q, g->dim, (const double *)u_in, (const double *)f,
-                                          (double *)u_out, omega, (cudaStream_t)stream);
+  cudaError_t e =
+      g->dim == 3 ? launch_jacobi_fx3(q, (const double *)u_in, (const double *)f, (double *)u_out, omega,
+                                      (cudaStream_t)stream)
+                  : launch_jacobi_sweep_f64(q, g->dim, (const double *)u_in, (const double *)f,
+                                            (double *)u_out, omega, (cudaStream_t)stream);
   if (e != cudaSuccess) return set_error(STENCIL_ECUDA, std::string("jacobi: ") + cudaGetErrorString(e));
   return STENCIL_OK;
 }
@@ -249,10 +256,14 @@ int stencil_residual(const stencil_grid_t *g, const void *u, const void *f, void
   const size_t bytes = (size_t)span_elems(q) * 8;
   if (r && (overlap(r, u, bytes) || overlap(r, f, bytes)))
     return set_error(STENCIL_EINVAL, "r overlaps u or f");
-  void *scratch = device_scratch(SCRATCH_REDUCE, reduce_scratch_bytes(), (cudaStream_t)stream);
+  const size_t need = g->dim == 3 ? ops_fx_reduce_bytes(q) : reduce_scratch_bytes();
+  void *scratch = device_scratch(SCRATCH_REDUCE, need, (cudaStream_t)stream);
   if (!scratch) return set_error(STENCIL_ENOMEM, "residual scratch allocation failed");
-  cudaError_t e = launch_residual_f64(q, g->dim, (const double *)u, (const double *)f,
-                                      (double *)r, d_norms2, scratch, (cudaStream_t)stream);
+  cudaError_t e =
+      g->dim == 3 ? launch_residual_fx3(q, (const double *)u, (const double *)f, (double *)r, d_norms2,
+                                        scratch, (cudaStream_t)stream)
+                  : launch_residual_f64(q, g->dim, (const double *)u, (const double *)f, (double *)r,
+                                        d_norms2, scratch, (cudaStream_t)stream);
   if (e != cudaSuccess) return set_error(STENCIL_ECUDA, std::string("residual: ") + cudaGetErrorString(e));
   return STENCIL_OK;
 }

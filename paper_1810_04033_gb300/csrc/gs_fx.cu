@@ -38,17 +38,28 @@
 namespace stencil {
 namespace {
 
-constexpr int GS_TX = 58, GS_TY = 30;           // output tile
-constexpr int GS_SW = 64, GS_SH = GS_TY + 4;    // staged plane: 64 columns (62 used) x 34 rows
+constexpr int GS_TX = 58, GS_TY = 30;        // output tile
+constexpr int GS_SW = 64;                    // staged columns (62 used)
+constexpr int GS_SH = 36;                    // staged rows (34 used, 2 zero pad rows)
 constexpr int GS_THREADS = 256;
-constexpr int GS_CZ = 16;                       // centre planes per CTA
-constexpr size_t GS_SMEM = 3 * GS_SH * GS_SW * sizeof(long long);
+constexpr int GS_CZ = 16;                    // centre planes per CTA
+constexpr int GS_NUP = GS_SH * GS_SW / GS_THREADS;             // 9 values / thread
+constexpr int GS_NCE = (GS_SH / 2 * GS_SW + GS_THREADS - 1) / GS_THREADS;  // 5 (odd rows)
+constexpr size_t GS_PLANE = (size_t)GS_SH * GS_SW;
+constexpr size_t GS_SMEM = 3 * GS_PLANE * sizeof(long long);
+
+struct SweepBounds {
+  unsigned long long umax[3];  // max |u| of the iterate, ring indexed by sweep
+  unsigned long long fmax;     // max |f| over interior vertices
+};
 
 struct Ctx {
   Geo q;
-  int64_t x0, y0;
-  int rb, e2;      // fixed-point scale (fix mode)
-  double g;        // 3/8 h^2
+  int x0, y0;        // tile origin (vertex indices)
+  int rb, e2;        // fixed-point scale
+  double g;          // 3/8 h^2
+  int nx, ny;        // cells (as int: planes are < 2^31 elements)
+  int pitch;
 };
 
 template <bool FIX>
@@ -57,116 +68,183 @@ __device__ __forceinline__ long long enc(double v, int rb) {
   return __double_as_longlong(v);
 }
 
-// Stage plane z of src into slot (rows all or odd only), zero outside the grid.
-template <bool FIX>
-__device__ void stage_plane(long long *slot, const double *__restrict__ src, const Ctx &c,
-                            int64_t z, bool odd_rows_only) {
-  const int nrows = odd_rows_only ? GS_SH / 2 : GS_SH;
-  for (int idx = threadIdx.x; idx < nrows * GS_SW; idx += GS_THREADS) {
-    const int r = odd_rows_only ? 2 * (idx >> 6) + 1 : (idx >> 6);
-    const int col = idx & 63;
-    const int64_t x = c.x0 - 2 + col, j = c.y0 - 2 + r;
-    double v = 0.0;
-    if (col < GS_TX + 4 && x >= 0 && x <= c.q.nx && j >= 0 && j <= c.q.ny)
-      v = src[z * c.q.plane + j * c.q.pitch + x];
-    slot[r * GS_SW + col] = enc<FIX>(v, c.rb);
-  }
-}
-
 template <bool FIX>
 __device__ __forceinline__ long long add(long long a, long long b) {
   if (FIX) return a + b;
   return __double_as_longlong(__longlong_as_double(a) + __longlong_as_double(b));
 }
 
-// One phase on centre plane z.  which = 1: rows of parity 0 on the tile + 1 (results
-// also kept in shared memory); which = 2: rows of parity 1 on the tile.
-template <bool FIX, int WHICH>
-__device__ void phase(long long *ce, const long long *lo, const long long *up, const Ctx &c,
-                      int64_t z, const double *__restrict__ X, const double *__restrict__ f,
-                      double *__restrict__ Y, unsigned long long &vmax) {
+// In-plane offset of staged element (r, col) and whether it lies in the grid.
+template <bool INNER>
+__device__ __forceinline__ bool staged_at(const Ctx &c, int r, int col, int &off) {
+  const int x = c.x0 - 2 + col, j = c.y0 - 2 + r;
+  off = j * c.pitch + x;
+  if (INNER) return col < GS_TX + 4 && r < GS_TY + 4;
+  return col < GS_TX + 4 && r < GS_TY + 4 && x >= 0 && x <= c.nx && j >= 0 && j <= c.ny;
+}
+
+// Prefetch of one centre plane's odd rows (pc) and one full neighbour plane (pu).
+template <bool INNER>
+__device__ __forceinline__ void prefetch(const Ctx &c, const double *__restrict__ cplane,
+                                         const double *__restrict__ uplane, double (&pc)[GS_NCE],
+                                         double (&pu)[GS_NUP]) {
+#pragma unroll
+  for (int k = 0; k < GS_NCE; ++k) {
+    const int idx = threadIdx.x + k * GS_THREADS;
+    const int r = 2 * (idx >> 6) + 1, col = idx & 63;
+    int off;
+    const bool ok = idx < GS_SH / 2 * GS_SW && cplane && staged_at<INNER>(c, r, col, off);
+    pc[k] = ok ? cplane[off] : 0.0;
+  }
+#pragma unroll
+  for (int k = 0; k < GS_NUP; ++k) {
+    const int idx = threadIdx.x + k * GS_THREADS;
+    const int r = idx >> 6, col = idx & 63;
+    int off;
+    const bool ok = uplane && staged_at<INNER>(c, r, col, off);
+    pu[k] = ok ? uplane[off] : 0.0;
+  }
+}
+
+template <bool FIX>
+__device__ __forceinline__ void commit(const Ctx &c, const double (&pc)[GS_NCE],
+                                       const double (&pu)[GS_NUP], long long *ce, long long *up) {
+#pragma unroll
+  for (int k = 0; k < GS_NCE; ++k) {
+    const int idx = threadIdx.x + k * GS_THREADS;
+    if (idx < GS_SH / 2 * GS_SW) ce[(2 * (idx >> 6) + 1) * GS_SW + (idx & 63)] = enc<FIX>(pc[k], c.rb);
+  }
+#pragma unroll
+  for (int k = 0; k < GS_NUP; ++k) up[threadIdx.x + k * GS_THREADS] = enc<FIX>(pu[k], c.rb);
+}
+
+// f values this thread needs for the two phases of one centre plane (4 rows each).
+template <bool INNER>
+__device__ __forceinline__ void prefetch_f(const Ctx &c, const double *__restrict__ fplane,
+                                           double (&fv)[8]) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int NROWS = WHICH == 1 ? (GS_TY / 2 + 1) : (GS_TY / 2);
-  const Geo &q = c.q;
-  for (int task = warp; task < NROWS * 2; task += GS_THREADS / 32) {
-    const int rr = task >> 1, seg = task & 1;
-    const int r = WHICH == 1 ? 2 + 2 * rr : 3 + 2 * rr;
-    const int col = (WHICH == 1 ? 0 : 1) + 30 * seg + lane;
-    const int64_t x = c.x0 - 2 + col, j = c.y0 - 2 + r;
-    const bool out_lane = lane >= 1 && lane <= 30 && (WHICH == 1 ? col <= 60 : col <= 59);
-    const bool in_grid = x >= 0 && x <= q.nx && j >= 0 && j <= q.ny;
-    const bool interior = x >= 1 && x < q.nx && j >= 1 && j < q.ny;
-    const bool in_core = WHICH == 2 || (col >= 2 && col < 60 && r < 32);
-    const int64_t gp = z * q.plane + j * q.pitch + x;
-    double fv = 0.0;
-    if (out_lane && interior) fv = f[gp];
-    // column sums (every lane, columns up to 63 exist in shared memory)
-    const long long *cm = ce + (r - 1) * GS_SW + col, *cp = ce + (r + 1) * GS_SW + col;
-    const long long *l0 = lo + r * GS_SW + col, *u0 = up + r * GS_SW + col;
-    long long V = add<FIX>(cm[0], cp[0]);
-    long long W = add<FIX>(l0[0], u0[0]);
-    long long Q = add<FIX>(add<FIX>(l0[-GS_SW], l0[GS_SW]), add<FIX>(u0[-GS_SW], u0[GS_SW]));
-    long long VW = add<FIX>(V, W);
-    long long P = add<FIX>(add<FIX>(VW, VW), Q);
+  const int seg = warp & 1, grp = warp >> 1;
+#pragma unroll
+  for (int ph = 0; ph < 2; ++ph) {
+    const int col = (ph == 0 ? 0 : 1) + 30 * seg + lane;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int r = (ph == 0 ? 2 : 3) + 8 * grp + 2 * k;
+      const int x = c.x0 - 2 + col, j = c.y0 - 2 + r;
+      const bool ok = fplane && lane >= 1 && lane <= 30 && x >= 1 && x < c.nx && j >= 1 && j < c.ny;
+      fv[4 * ph + k] = ok ? fplane[j * c.pitch + x] : 0.0;
+    }
+  }
+}
+
+// One phase on the staged centre plane.  WHICH = 1: rows of parity 0 on the tile + 1
+// (results also written back into the centre plane); WHICH = 2: rows of parity 1 on
+// the tile.  A warp walks 4 rows of one 32-column segment, carrying the column sums of
+// the shared rows from one row to the next.
+template <bool FIX, bool INNER, int WHICH>
+__device__ __forceinline__ void phase(const Ctx &c, long long *ce, const long long *lo,
+                                      const long long *up, const double *__restrict__ xplane,
+                                      double *__restrict__ yplane, const double (&fv)[8],
+                                      bool zin, unsigned long long &vmax) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int seg = warp & 1, grp = warp >> 1;
+  const int col = (WHICH == 1 ? 0 : 1) + 30 * seg + lane;
+  const int r0 = (WHICH == 1 ? 2 : 3) + 8 * grp;
+  const int x = c.x0 - 2 + col;
+  const bool lane_out = lane >= 1 && lane <= 30 && (WHICH == 1 ? col <= 60 : col <= 59);
+  const bool x_in = INNER || (x >= 0 && x <= c.nx);
+  const bool x_inner = INNER || (x >= 1 && x < c.nx);
+  const bool col_core = WHICH == 2 || (col >= 2 && col < 60);
+  const long long *lc = lo + col, *uc = up + col;
+  long long *cc = ce + col;
+  long long Dm = add<FIX>(lc[(r0 - 1) * GS_SW], uc[(r0 - 1) * GS_SW]);
+  long long Cm = cc[(r0 - 1) * GS_SW];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int r = r0 + 2 * k;
+    const long long Dp = add<FIX>(lc[(r + 1) * GS_SW], uc[(r + 1) * GS_SW]);
+    const long long Cp = cc[(r + 1) * GS_SW];
+    const long long W = add<FIX>(lc[r * GS_SW], uc[r * GS_SW]);
+    const long long V = add<FIX>(Cm, Cp);
+    const long long Q = add<FIX>(Dm, Dp);
+    const long long VW = add<FIX>(V, W);
+    const long long P = add<FIX>(add<FIX>(VW, VW), Q);
     const long long Pm = __shfl_up_sync(0xffffffffu, P, 1);
     const long long Pp = __shfl_down_sync(0xffffffffu, P, 1);
-    if (!out_lane || !in_grid) continue;
+    Dm = Dp;
+    Cm = Cp;
+    const int j = c.y0 - 2 + r;
+    const bool row_ok = WHICH == 1 ? true : r <= GS_TY + 1;  // phase 2: last group has 3 rows
+    if (!lane_out || !row_ok) continue;
+    const bool in_grid = x_in && (INNER || (j >= 0 && j <= c.ny));
+    if (!in_grid) continue;
+    const bool inner = zin && x_inner && (INNER || (j >= 1 && j < c.ny));
+    const int off = j * c.pitch + x;
     double un;
-    if (interior) {
+    if (inner) {
       const long long S = add<FIX>(add<FIX>(Pm, Pp), add<FIX>(Q, Q));
       if (FIX)
-        un = fma(c.g, fv, fx::to_double(S, c.e2));
+        un = fma(c.g, fv[(WHICH - 1) * 4 + k], fx::to_double(S, c.e2));
       else
-        un = fma(__longlong_as_double(S), 0.03125, c.g * fv);
+        un = fma(__longlong_as_double(S), 0.03125, c.g * fv[(WHICH - 1) * 4 + k]);
     } else {
-      un = X[gp];  // Dirichlet value, copied
+      un = xplane[off];  // Dirichlet value, copied
     }
-    if (WHICH == 1) ce[r * GS_SW + col] = enc<FIX>(un, c.rb);
-    if (in_core) {
-      Y[gp] = un;
+    if (WHICH == 1) cc[r * GS_SW] = enc<FIX>(un, c.rb);
+    if (col_core && (WHICH == 2 || r < GS_TY + 2)) {
+      yplane[off] = un;
       const unsigned long long b = fx::abs_bits(un);
       vmax = b > vmax ? b : vmax;
     }
   }
 }
 
-struct SweepBounds {
-  unsigned long long umax[3];  // max |u| of the iterate, ring indexed by sweep
-  unsigned long long fmax;     // max |f| over interior vertices
-};
-
-template <bool FIX>
-__device__ void run_half(const Ctx &c, int pz, int64_t i0, int64_t i1, const double *__restrict__ X,
+template <bool FIX, bool INNER>
+__device__ void run_half(const Ctx &c, int pz, int i0, int i1, const double *__restrict__ X,
                          const double *__restrict__ N, double *__restrict__ Y,
                          const double *__restrict__ f, long long *smem, unsigned long long &vmax) {
   const Geo &q = c.q;
+  const int64_t P = q.plane;
+  long long *slot[3] = {smem, smem + GS_PLANE, smem + 2 * GS_PLANE};
   int lo = 0, ce = 1, up = 2;
-  bool have_lower = false;
-  for (int64_t i = i0; i < i1; ++i) {
-    const int64_t z = pz + 2 * i;
-    const bool interior_z = z >= 1 && z <= q.nz - 1;
-    if (interior_z) {
-      if (!have_lower) stage_plane<FIX>(smem + lo * GS_SH * GS_SW, N, c, z - 1, false);
-      stage_plane<FIX>(smem + ce * GS_SH * GS_SW, X, c, z, true);
-      stage_plane<FIX>(smem + up * GS_SH * GS_SW, N, c, z + 1, false);
-    } else if (z + 1 <= q.nz) {
-      stage_plane<FIX>(smem + up * GS_SH * GS_SW, N, c, z + 1, false);
-    }
+  double pc[GS_NCE], pu[GS_NUP], fv[8];
+  // prologue: the lower neighbour of the first centre plane, then its prefetch
+  {
+    const int64_t z = pz + 2 * (int64_t)i0;
+    double dummy[GS_NCE];
+    prefetch<INNER>(c, nullptr, z >= 1 ? N + (z - 1) * P : nullptr, dummy, pu);
+    commit<FIX>(c, dummy, pu, slot[ce], slot[lo]);  // ce gets zeros, overwritten below
+    const bool zin = z >= 1 && z <= q.nz - 1;
+    prefetch<INNER>(c, zin ? X + z * P : nullptr, z + 1 <= q.nz ? N + (z + 1) * P : nullptr, pc, pu);
+    prefetch_f<INNER>(c, zin ? f + z * P : nullptr, fv);
+  }
+  for (int i = i0; i < i1; ++i) {
+    const int64_t z = pz + 2 * (int64_t)i;
+    const bool zin = z >= 1 && z <= q.nz - 1;
+    commit<FIX>(c, pc, pu, slot[ce], slot[up]);
+    double fcur[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) fcur[k] = fv[k];
     __syncthreads();
-    if (interior_z) {
-      phase<FIX, 1>(smem + ce * GS_SH * GS_SW, smem + lo * GS_SH * GS_SW, smem + up * GS_SH * GS_SW,
-                    c, z, X, f, Y, vmax);
+    if (i + 1 < i1) {  // next centre plane z + 2 and its upper neighbour z + 3
+      const bool zn = z + 2 >= 1 && z + 2 <= q.nz - 1;
+      prefetch<INNER>(c, zn ? X + (z + 2) * P : nullptr, z + 3 <= q.nz ? N + (z + 3) * P : nullptr,
+                      pc, pu);
+      prefetch_f<INNER>(c, zn ? f + (z + 2) * P : nullptr, fv);
+    }
+    const double *xp = X + z * P;
+    double *yp = Y + z * P;
+    if (zin) {
+      phase<FIX, INNER, 1>(c, slot[ce], slot[lo], slot[up], xp, yp, fcur, true, vmax);
       __syncthreads();
-      phase<FIX, 2>(smem + ce * GS_SH * GS_SW, smem + lo * GS_SH * GS_SW, smem + up * GS_SH * GS_SW,
-                    c, z, X, f, Y, vmax);
+      phase<FIX, INNER, 2>(c, slot[ce], slot[lo], slot[up], xp, yp, fcur, true, vmax);
     } else {
       // Dirichlet plane: copy the tile
       for (int idx = threadIdx.x; idx < GS_TX * GS_TY; idx += GS_THREADS) {
-        const int64_t x = c.x0 + idx % GS_TX, j = c.y0 + idx / GS_TX;
-        if (x > q.nx || j > q.ny) continue;
-        const int64_t gp = z * q.plane + j * q.pitch + x;
-        const double v = X[gp];
-        Y[gp] = v;
+        const int x = c.x0 + idx % GS_TX, j = c.y0 + idx / GS_TX;
+        if (x > c.nx || j > c.ny) continue;
+        const double v = xp[j * c.pitch + x];
+        yp[j * c.pitch + x] = v;
         const unsigned long long b = fx::abs_bits(v);
         vmax = b > vmax ? b : vmax;
       }
@@ -176,7 +254,6 @@ __device__ void run_half(const Ctx &c, int pz, int64_t i0, int64_t i1, const dou
     const int t = lo;
     lo = up;
     up = t;
-    have_lower = z + 1 <= q.nz;
   }
 }
 
@@ -188,9 +265,12 @@ __global__ void __launch_bounds__(GS_THREADS, 2)
   __shared__ unsigned long long red[GS_THREADS / 32];
   Ctx c;
   c.q = q;
-  c.x0 = (int64_t)blockIdx.x * GS_TX;
-  c.y0 = (int64_t)blockIdx.y * GS_TY;
+  c.x0 = (int)blockIdx.x * GS_TX;
+  c.y0 = (int)blockIdx.y * GS_TY;
   c.g = g;
+  c.nx = (int)q.nx;
+  c.ny = (int)q.ny;
+  c.pitch = (int)q.pitch;
   // bound for this sweep: max |u| of the input iterate + growth within the sweep
   const double M = __longlong_as_double((long long)bnd->umax[slot_read]);
   const double F = __longlong_as_double((long long)bnd->fmax);
@@ -202,14 +282,20 @@ __global__ void __launch_bounds__(GS_THREADS, 2)
   if (slot_clear >= 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
     bnd->umax[slot_clear] = 0ull;
 
-  const int64_t ncentre = q.nz >= pz ? (q.nz - pz) / 2 + 1 : 0;
-  const int64_t i0 = (int64_t)blockIdx.z * GS_CZ;
-  const int64_t i1 = i0 + GS_CZ < ncentre ? i0 + GS_CZ : ncentre;
+  const int ncentre = q.nz >= pz ? (int)((q.nz - pz) / 2 + 1) : 0;
+  const int i0 = (int)blockIdx.z * GS_CZ;
+  const int i1 = i0 + GS_CZ < ncentre ? i0 + GS_CZ : ncentre;
+  // interior tile: every staged vertex in the grid and every output an interior vertex
+  const bool inner = c.x0 >= 2 && c.x0 + GS_TX + 1 <= c.nx && c.y0 >= 2 && c.y0 + GS_TY + 1 <= c.ny;
   unsigned long long vmax = 0ull;
-  if (fix)
-    run_half<true>(c, pz, i0, i1, X, N, Y, f, smem, vmax);
-  else
-    run_half<false>(c, pz, i0, i1, X, N, Y, f, smem, vmax);
+  if (fix) {
+    if (inner)
+      run_half<true, true>(c, pz, i0, i1, X, N, Y, f, smem, vmax);
+    else
+      run_half<true, false>(c, pz, i0, i1, X, N, Y, f, smem, vmax);
+  } else {
+    run_half<false, false>(c, pz, i0, i1, X, N, Y, f, smem, vmax);
+  }
 
   vmax = fx::warp_max_u64(vmax);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = vmax;
@@ -271,6 +357,7 @@ cudaError_t launch_gs_sweeps_fx3(const Geo &q, double *u, const double *f, int s
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  if (q.plane >= ((int64_t)1 << 31) - GS_SW * GS_SH) return cudaErrorInvalidValue;
   SweepBounds *bnd = (SweepBounds *)bounds;
   cudaError_t e = cudaMemsetAsync(bnd, 0, sizeof(SweepBounds), s);
   if (e != cudaSuccess) return e;

@@ -51,8 +51,9 @@ cudaError_t launch_gs_sweeps_f64(const Geo &q, int dim, double *u, const double 
                                  int sweeps, cudaStream_t s);
 cudaError_t launch_jacobi_sweep_f64(const Geo &q, int dim, const double *u, const double *f,
                                     double *unew, double omega, cudaStream_t s);
-// Residual with norms; partials must hold 2 * kReduceBlocks doubles plus one
-// unsigned counter (zero before the first call; the kernel leaves it zero).
+// Residual with norms.  Reduction scratch layout (all users): an unsigned counter in
+// the first 16 bytes (zero before the first call; kernels leave it zero), then the
+// per-CTA partial sums.
 constexpr int kReduceBlocks = 1216;  // 8 per SM on 152 SMs: fixed => fixed sum order
 size_t reduce_scratch_bytes();
 
@@ -63,5 +64,14 @@ cudaError_t launch_gs_sweeps_fx3(const Geo &q, double *u, const double *f, int s
                                  double *work, void *bounds, cudaStream_t s);
 cudaError_t launch_residual_f64(const Geo &q, int dim, const double *u, const double *f,
                                 double *r, double *norms2, void *scratch, cudaStream_t s);
+
+// Fixed-point out-of-place 3D operations (ops_fx.cu).  The residual needs
+// ops_fx_reduce_bytes(q) bytes of zero-initialised scratch (left zeroed).
+size_t ops_fx_reduce_bytes(const Geo &q);
+cudaError_t launch_apply_stencil_fx3(const Geo &q, const double *u, double *y, cudaStream_t s);
+cudaError_t launch_jacobi_fx3(const Geo &q, const double *u, const double *f, double *unew,
+                              double omega, cudaStream_t s);
+cudaError_t launch_residual_fx3(const Geo &q, const double *u, const double *f, double *r,
+                                double *norms2, void *scratch, cudaStream_t s);
 
 }  // namespace stencil

@@ -417,12 +417,13 @@ cudaError_t launch_jacobi_sweep_f64(const Geo &q, int dim, const double *u, cons
   return cudaGetLastError();
 }
 
-size_t reduce_scratch_bytes() { return 2 * kReduceBlocks * sizeof(double) + 16; }
+size_t reduce_scratch_bytes() { return 16 + 2 * kReduceBlocks * sizeof(double); }
 
 cudaError_t launch_residual_f64(const Geo &q, int dim, const double *u, const double *f,
                                 double *r, double *norms2, void *scratch, cudaStream_t s) {
-  double *partials = (double *)scratch;
-  unsigned *counter = (unsigned *)(partials + 2 * kReduceBlocks);
+  // layout shared by every reduction user of this scratch: counter first, partials after
+  unsigned *counter = (unsigned *)scratch;
+  double *partials = (double *)((char *)scratch + 16);
   k_residual<<<kReduceBlocks, RED_THREADS, 0, s>>>(q, dim, u, f, r, norms2, partials, counter,
                                                    1.0 / (q.h * q.h));
   return cudaGetLastError();

@@ -1,0 +1,372 @@
+// Out-of-place 3D Q1 operations on the integer pipes: assembled apply y = A u, one
+// damped Jacobi sweep, and the residual r = f - A u with its norms.
+//
+// All three need 12 S u = 32 u - (2E + C) (E: sum of the 12 edge neighbours, C: sum of
+// the 8 corner neighbours; face weights are 0), computed exactly in int64 fixed point
+// (fixed.cuh) with the same column-sum scheme as the Gauss-Seidel kernel:
+//   V = u(r-1) + u(r+1) in plane z, W = u(z-1) + u(z+1) in row r, Q = the four
+//   diagonal (r+-1, z+-1) values, P = 2(V + W) + Q, and 2E + C = P(c-1) + P(c+1) + 2Q(c).
+// A CTA owns a 60 x 32 (x, y) tile and a chunk of 32 planes; it streams z with three
+// staged planes (tile + 1-vertex halo) in shared memory and prefetches the next plane
+// into registers while it computes the current one.
+//
+// Fixed-point scale without a pre-pass: the CTA keeps a reference exponent R that only
+// grows.  Each newly staged plane's largest exponent is reduced over the CTA first; if
+// it exceeds R, the two planes already staged are shifted right to the new R.  If a
+// plane holds a non-finite value or the magnitudes leave [2^-900, 2^1000], the CTA
+// converts its staged planes to FP64 and finishes in native FP64 arithmetic.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fixed.cuh"
+#include "internal.h"
+
+namespace stencil {
+namespace {
+
+constexpr int OT_X = 60, OT_Y = 32;          // outputs per tile
+constexpr int OS_W = 64, OS_H = OT_Y + 2;    // staged plane: 64 columns (62 used) x 34 rows
+constexpr int O_THREADS = 256;
+constexpr int O_CZ = 32;                     // output planes per CTA
+constexpr int O_PER = (OS_W * OS_H + O_THREADS - 1) / O_THREADS;  // prefetched values / thread
+constexpr size_t O_SMEM = 3 * OS_H * OS_W * sizeof(long long);
+constexpr int R_MIN = -900, R_MAX = 1000;
+
+enum { OP_APPLY = 0, OP_JACOBI = 1, OP_RESIDUAL = 2 };
+
+struct OpArgs {
+  Geo q;
+  const double *u;
+  const double *f;
+  double *out;       // y, u_new or r (may be null for the residual)
+  double c1, c2;     // apply: c1 = 1/(12 h^2); jacobi: c1 = omega 3/8 h^2, c2 = -omega 3/8 / 12;
+                     // residual: c1 = -1/(12 h^2)
+  double *partials;  // residual: 2 per CTA
+  unsigned *counter; // residual: CTAs finished
+  double *norms2;    // residual: [sum r^2, sum f^2]
+};
+
+__device__ __forceinline__ void prefetch_plane(double (&v)[O_PER], const Geo &q, const double *src,
+                                               int64_t z, int64_t x0, int64_t y0) {
+#pragma unroll
+  for (int k = 0; k < O_PER; ++k) {
+    const int idx = threadIdx.x + k * O_THREADS;
+    const int r = idx >> 6, col = idx & 63;
+    const int64_t x = x0 - 1 + col, j = y0 - 1 + r;
+    double val = 0.0;
+    if (idx < OS_W * OS_H && col < OT_X + 2 && z >= 0 && z <= q.nz && x >= 0 && x <= q.nx &&
+        j >= 0 && j <= q.ny)
+      val = src[z * q.plane + j * q.pitch + x];
+    v[k] = val;
+  }
+}
+
+// Largest biased exponent among the prefetched values of the whole CTA (0: all zero or
+// subnormal; 2047: a non-finite value).
+__device__ __forceinline__ int cta_max_exponent(const double (&v)[O_PER], int *red) {
+  unsigned m = 0;
+#pragma unroll
+  for (int k = 0; k < O_PER; ++k) {
+    const unsigned e = (unsigned)(fx::dbits(v[k]) >> 52) & 0x7ffu;
+    m = e > m ? e : m;
+  }
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (int)m;
+  __syncthreads();
+  int r = 0;
+#pragma unroll
+  for (int w = 0; w < O_THREADS / 32; ++w) r = red[w] > r ? red[w] : r;
+  return r;
+}
+
+template <bool FIX>
+__device__ __forceinline__ long long add(long long a, long long b) {
+  if (FIX) return a + b;
+  return __double_as_longlong(__longlong_as_double(a) + __longlong_as_double(b));
+}
+
+// Outputs of plane z from the staged planes lo (z-1), ce (z), up (z+1).  Warp w owns
+// column segment w & 1 and the 8 consecutive rows 1 + 8 (w >> 1) ... ; walking down the
+// rows it carries W = lo + up and the centre-plane values, so each output needs three
+// new shared-memory loads: with W(r) = lo(r) + up(r),
+//   V = ce(r-1) + ce(r+1),  Q = W(r-1) + W(r+1),  P = 2 (V + W(r)) + Q.
+template <bool FIX, int OP, bool INNER>
+__device__ __forceinline__ void compute_plane(const OpArgs &a, int64_t z, int x0, int y0, int R,
+                                              const long long *lo, const long long *ce,
+                                              const long long *up, double &rr, double &ff) {
+  const Geo &q = a.q;
+  const int nx = (int)q.nx, ny = (int)q.ny, pitch = (int)q.pitch;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int col = 30 * (warp & 1) + lane, r0 = 1 + 8 * (warp >> 1);
+  const int x = x0 - 1 + col;
+  const bool zin = z >= 1 && z < q.nz;
+  const bool lane_out = lane >= 1 && lane <= 30 && (INNER || x <= nx);
+  const bool x_inner = INNER || (x >= 1 && x < nx);
+  const double *fp = a.f ? a.f + z * q.plane : nullptr;
+  const double *up_src = a.u + z * q.plane;
+  double *outp = a.out ? a.out + z * q.plane : nullptr;
+  double fv[8], uv[8];
+  if (OP != OP_APPLY) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int j = y0 - 1 + r0 + k;
+      const bool ok = lane_out && (INNER || j <= ny);
+      const bool inner = ok && zin && x_inner && (INNER || (j >= 1 && j < ny));
+      const int off = j * pitch + x;
+      fv[k] = inner ? fp[off] : 0.0;
+      uv[k] = (OP == OP_JACOBI && ok) ? up_src[off] : 0.0;
+    }
+  }
+  const int e2 = R - fx::FRAC;
+  const long long *lc = lo + col, *uc = up + col, *cc = ce + col;
+  long long Cm = cc[(r0 - 1) * OS_W], Cc = cc[r0 * OS_W];
+  long long Wm = add<FIX>(lc[(r0 - 1) * OS_W], uc[(r0 - 1) * OS_W]);
+  long long Wc = add<FIX>(lc[r0 * OS_W], uc[r0 * OS_W]);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int r = r0 + k;
+    const long long Cp = cc[(r + 1) * OS_W];
+    const long long Wp = add<FIX>(lc[(r + 1) * OS_W], uc[(r + 1) * OS_W]);
+    const long long V = add<FIX>(Cm, Cp);
+    const long long Q = add<FIX>(Wm, Wp);
+    const long long VW = add<FIX>(V, Wc);
+    const long long P = add<FIX>(add<FIX>(VW, VW), Q);
+    const long long Pm = __shfl_up_sync(0xffffffffu, P, 1);
+    const long long Pp = __shfl_down_sync(0xffffffffu, P, 1);
+    const long long Cu = Cc;
+    Cm = Cc;
+    Cc = Cp;
+    Wm = Wc;
+    Wc = Wp;
+    const int j = y0 - 1 + r;
+    if (!lane_out || (!INNER && j > ny)) continue;
+    const int off = j * pitch + x;
+    const bool inner = zin && x_inner && (INNER || (j >= 1 && j < ny));
+    double Td = 0.0;  // 32 u - (2E + C) = 12 (S u)
+    if (inner) {
+      const long long S = add<FIX>(add<FIX>(Pm, Pp), add<FIX>(Q, Q));
+      if (FIX)
+        Td = fx::to_double(32 * Cu - S, e2);
+      else
+        Td = fma(32.0, __longlong_as_double(Cu), -__longlong_as_double(S));
+    }
+    if (OP == OP_APPLY) {
+      outp[off] = inner ? Td * a.c1 : 0.0;
+    } else if (OP == OP_JACOBI) {
+      outp[off] = inner ? fma(a.c2, Td, fma(a.c1, fv[k], uv[k])) : uv[k];
+    } else {
+      const double rv = inner ? fma(a.c1, Td, fv[k]) : 0.0;
+      if (outp) outp[off] = rv;
+      if (inner) {
+        rr = fma(rv, rv, rr);
+        ff = fma(fv[k], fv[k], ff);
+      }
+    }
+  }
+}
+
+template <int OP>
+__global__ void __launch_bounds__(O_THREADS, 2) k_ops3(OpArgs a) {
+  extern __shared__ long long smem[];
+  __shared__ int red[O_THREADS / 32];
+  __shared__ double sh2[2 * O_THREADS / 32];
+  __shared__ bool last;
+  const Geo &q = a.q;
+  const int64_t x0 = (int64_t)blockIdx.x * OT_X, y0 = (int64_t)blockIdx.y * OT_Y;
+  const int64_t zs = (int64_t)blockIdx.z * O_CZ;
+  const int64_t ze = zs + O_CZ < q.nz + 1 ? zs + O_CZ : q.nz + 1;
+  long long *slot[3] = {smem, smem + OS_H * OS_W, smem + 2 * OS_H * OS_W};
+  // interior tile: every staged vertex in the grid, every output an interior vertex
+  const bool inner_tile = x0 >= 1 && x0 + OT_X <= q.nx && y0 >= 1 && y0 + OT_Y <= q.ny;
+  int lo = 0, ce = 1, up = 2;
+  bool fix = true;
+  int R = R_MIN;  // grows only
+  double rr = 0.0, ff = 0.0;
+  double v[O_PER];
+
+  // Admit one prefetched plane into slot `dst`: agree on the scale, rescale or switch
+  // to FP64 if needed, then store.  `live` slots hold already staged planes.
+  auto admit = [&](int dst, int live0, int live1) {
+    const int em = cta_max_exponent(v, red);
+    if (fix && em != 0) {
+      const int Rp = em - 1022 + 1;  // one spare bit
+      const int Rn = Rp > R ? Rp : R;
+      if (em == 2047 || Rp > R_MAX || Rp < R_MIN) {
+        // Out of the fixed-point range (or all data seen so far below it): continue in
+        // FP64.  Rp < R_MIN with R == R_MIN means nothing larger has been seen.
+        if (em == 2047 || Rp > R_MAX || R == R_MIN) {
+          for (int idx = threadIdx.x; idx < OS_H * OS_W; idx += O_THREADS) {
+            slot[live0][idx] = __double_as_longlong(fx::to_double(slot[live0][idx], R - fx::FRAC));
+            slot[live1][idx] = __double_as_longlong(fx::to_double(slot[live1][idx], R - fx::FRAC));
+          }
+          fix = false;
+        }
+      } else if (Rn > R) {
+        const int d = Rn - R;
+        for (int idx = threadIdx.x; idx < OS_H * OS_W; idx += O_THREADS) {
+          slot[live0][idx] = d < 63 ? (slot[live0][idx] >> d) : (slot[live0][idx] >> 63);
+          slot[live1][idx] = d < 63 ? (slot[live1][idx] >> d) : (slot[live1][idx] >> 63);
+        }
+        R = Rn;
+      }
+    }
+    __syncthreads();  // red[] reuse, rescaled slots visible
+#pragma unroll
+    for (int k = 0; k < O_PER; ++k) {
+      const int idx = threadIdx.x + k * O_THREADS;
+      if (idx < OS_H * OS_W)
+        slot[dst][idx] = fix ? fx::to_fixed(v[k], 1023 + R) : __double_as_longlong(v[k]);
+    }
+  };
+
+  // prologue: planes zs-1 and zs
+  for (int idx = threadIdx.x; idx < 3 * OS_H * OS_W; idx += O_THREADS) smem[idx] = 0;
+  __syncthreads();
+  prefetch_plane(v, q, a.u, zs - 1, x0, y0);
+  admit(lo, ce, up);
+  prefetch_plane(v, q, a.u, zs, x0, y0);
+  admit(ce, lo, up);
+  prefetch_plane(v, q, a.u, zs + 1, x0, y0);
+  for (int64_t z = zs; z < ze; ++z) {
+    admit(up, lo, ce);
+    __syncthreads();
+    if (z + 2 <= ze) prefetch_plane(v, q, a.u, z + 2, x0, y0);
+    if (fix) {
+      if (inner_tile)
+        compute_plane<true, OP, true>(a, z, (int)x0, (int)y0, R, slot[lo], slot[ce], slot[up], rr, ff);
+      else
+        compute_plane<true, OP, false>(a, z, (int)x0, (int)y0, R, slot[lo], slot[ce], slot[up], rr, ff);
+    } else {
+      compute_plane<false, OP, false>(a, z, (int)x0, (int)y0, R, slot[lo], slot[ce], slot[up], rr, ff);
+    }
+    __syncthreads();
+    const int t = lo;
+    lo = ce;
+    ce = up;
+    up = t;
+  }
+
+  if (OP == OP_RESIDUAL) {
+    // fixed-order CTA sum, one partial per CTA, the last CTA adds them in order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      rr += __shfl_xor_sync(0xffffffffu, rr, o);
+      ff += __shfl_xor_sync(0xffffffffu, ff, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+      sh2[2 * w] = rr;
+      sh2[2 * w + 1] = ff;
+    }
+    __syncthreads();
+    const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (threadIdx.x == 0) {
+      double s0 = 0.0, s1 = 0.0;
+      for (int k = 0; k < O_THREADS / 32; ++k) {
+        s0 += sh2[2 * k];
+        s1 += sh2[2 * k + 1];
+      }
+      a.partials[2 * bid] = s0;
+      a.partials[2 * bid + 1] = s1;
+      __threadfence();
+      last = atomicAdd(a.counter, 1u) == nblk - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double s0 = 0.0, s1 = 0.0;
+    for (unsigned k = threadIdx.x; k < nblk; k += O_THREADS) {
+      s0 += __ldcg(a.partials + 2 * k);
+      s1 += __ldcg(a.partials + 2 * k + 1);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    __syncthreads();
+    if (l == 0) {
+      sh2[2 * w] = s0;
+      sh2[2 * w + 1] = s1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t0 = 0.0, t1 = 0.0;
+      for (int k = 0; k < O_THREADS / 32; ++k) {
+        t0 += sh2[2 * k];
+        t1 += sh2[2 * k + 1];
+      }
+      a.norms2[0] = t0;
+      a.norms2[1] = t1;
+      *a.counter = 0u;
+    }
+  }
+}
+
+dim3 ops_grid(const Geo &q) {
+  return dim3((unsigned)((q.nx + OT_X) / OT_X), (unsigned)((q.ny + OT_Y) / OT_Y),
+              (unsigned)((q.nz + O_CZ) / O_CZ));
+}
+
+template <int OP>
+cudaError_t launch_op(const OpArgs &a, cudaStream_t s) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_ops3<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)O_SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const dim3 g = ops_grid(a.q);
+  if (g.y > 65535 || g.z > 65535) return cudaErrorInvalidConfiguration;
+  if (a.q.plane >= ((int64_t)1 << 31) - OS_W * OS_H) return cudaErrorInvalidValue;
+  k_ops3<OP><<<g, O_THREADS, O_SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t ops_fx_reduce_bytes(const Geo &q) {
+  const dim3 g = ops_grid(q);
+  return (size_t)g.x * g.y * g.z * 2 * sizeof(double) + 16;
+}
+
+cudaError_t launch_apply_stencil_fx3(const Geo &q, const double *u, double *y, cudaStream_t s) {
+  OpArgs a{};
+  a.q = q;
+  a.u = u;
+  a.out = y;
+  a.c1 = 1.0 / (12.0 * q.h * q.h);
+  return launch_op<OP_APPLY>(a, s);
+}
+
+cudaError_t launch_jacobi_fx3(const Geo &q, const double *u, const double *f, double *unew,
+                              double omega, cudaStream_t s) {
+  OpArgs a{};
+  a.q = q;
+  a.u = u;
+  a.f = f;
+  a.out = unew;
+  a.c1 = omega * 0.375 * q.h * q.h;
+  a.c2 = -omega * 0.375 / 12.0;
+  return launch_op<OP_JACOBI>(a, s);
+}
+
+cudaError_t launch_residual_fx3(const Geo &q, const double *u, const double *f, double *r,
+                                double *norms2, void *scratch, cudaStream_t s) {
+  const dim3 g = ops_grid(q);
+  const size_t nblk = (size_t)g.x * g.y * g.z;
+  OpArgs a{};
+  a.q = q;
+  a.u = u;
+  a.f = f;
+  a.out = r;
+  a.c1 = -1.0 / (12.0 * q.h * q.h);
+  (void)nblk;
+  a.counter = (unsigned *)scratch;  // counter first, partials after (same layout everywhere)
+  a.partials = (double *)((char *)scratch + 16);
+  a.norms2 = norms2;
+  return launch_op<OP_RESIDUAL>(a, s);
+}
+
+}  // namespace stencil

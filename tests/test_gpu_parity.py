@@ -198,3 +198,78 @@ def test_gs_shrinking_iterate_keeps_relative_accuracy():
     st.stencil_smooth_coloured(ud, fd, h, 40)
     torch.cuda.synchronize()
     assert rel_err(to_host(ud), ref) <= TOL_F64
+
+
+@pytest.mark.parametrize("n", [(61, 33, 33), (130, 70, 66), (5, 80, 40)])
+def test_out_of_place_ops_multi_tile(n):
+    """Apply, Jacobi step and residual on grids spanning several tiles and z chunks."""
+    h = 1.0 / max(n)
+    shape = synth.grid_shape(3, n)
+    u = synth.uniform_field(shape, 1200 + sum(n), zero_bc=False)
+    f = synth.uniform_field(shape, 1300 + sum(n))
+    ud, fd = to_dev(u), to_dev(f)
+    yd = torch.full_like(ud, float("nan"))
+    st.stencil_apply(ud, yd, h, st.FORM_STENCIL)
+    od = torch.full_like(ud, float("nan"))
+    st.stencil_jacobi_step(ud, fd, od, h, 2.0 / 3.0)
+    rd = torch.full_like(ud, float("nan"))
+    nrm = st.stencil_residual(ud, fd, h, r=rd)
+    torch.cuda.synchronize()
+    assert apply_err(to_host(yd), oracle.apply_stencil(u, h), u, h) <= TOL_F64
+    assert rel_err(to_host(od), oracle.jacobi(u, f, h, 2.0 / 3.0, 1)) <= TOL_F64
+    rref, nref = oracle.residual(u, f, h)
+    assert apply_err(to_host(rd), rref, u, h) <= TOL_F64
+    got = nrm.cpu().numpy()
+    assert abs(got[1] - nref[1]) <= 1e-12 * nref[1]
+    assert abs(got[0] - nref[0]) <= 1e-11 * nref[0]
+
+
+@pytest.mark.parametrize("scale", [1e300, 1e-280, 1e-6])
+def test_out_of_place_ops_extreme_and_mixed_magnitudes(scale):
+    """Out-of-range magnitudes switch a tile to FP64; a plane-by-plane growing scale
+    exercises the rescaling of staged planes."""
+    n = (40, 36, 45)
+    h = 1.0 / 45
+    shape = synth.grid_shape(3, n)
+    u = synth.uniform_field(shape, 1400, zero_bc=False) * scale
+    z = np.arange(shape[0], dtype=np.float64)[:, None, None]
+    u = u * (1.0 + 1e3 * (z / shape[0]) ** 4)  # magnitudes grow along z
+    f = synth.uniform_field(shape, 1401) * scale
+    ud, fd = to_dev(u), to_dev(f)
+    yd = torch.empty_like(ud)
+    st.stencil_apply(ud, yd, h, st.FORM_STENCIL)
+    od = torch.empty_like(ud)
+    st.stencil_jacobi_step(ud, fd, od, h, 0.8)
+    torch.cuda.synchronize()
+    assert apply_err(to_host(yd), oracle.apply_stencil(u, h), u, h) <= TOL_F64
+    assert rel_err(to_host(od), oracle.jacobi(u, f, h, 0.8, 1)) <= TOL_F64
+
+
+def test_full_size_sampled_apply_and_gs():
+    """512^3 cells in the launch configuration the benchmark times: apply and one GS
+    sweep compared with the oracle on sampled vertices (the oracle evaluates the
+    3x3x3 neighbourhood of each sample)."""
+    n = 512
+    h = 1.0 / n
+    shape = synth.grid_shape(3, n)
+    u = synth.uniform_field(shape, 1)
+    f = synth.sin_rhs(3, n)
+    ud, fd = to_dev(u), to_dev(f)
+    yd = torch.empty_like(ud)
+    st.stencil_apply(ud, yd, h, st.FORM_STENCIL)
+    torch.cuda.synchronize()
+    y = yd.cpu().numpy()
+    g = synth.rng(5)
+    pts = g.integers(1, n, size=(400, 3))
+    pts = np.vstack([pts, [[1, 1, 1], [n - 1, n - 1, n - 1], [1, n - 1, 1], [256, 256, 256]]])
+    for k, j, i in pts:
+        blk = u[k - 1:k + 2, j - 1:j + 2, i - 1:i + 2]
+        ref = oracle.apply_stencil(blk, h)[1, 1, 1]
+        assert abs(y[k, j, i] - ref) <= TOL_F64 * max(abs(ref), (16 / 3) / h ** 2 * 1e-3)
+    assert np.all(y[0] == 0) and np.all(y[:, :, -1] == 0)
+    # one full sweep: oracle on all host cores, compared everywhere
+    import os
+    st.stencil_smooth_coloured(ud, fd, h, 1)
+    ref = oracle.gs_coloured(u, f, h, 1, nthreads=os.cpu_count() or 1)
+    torch.cuda.synchronize()
+    assert rel_err(ud.cpu().numpy(), ref) <= TOL_F64
