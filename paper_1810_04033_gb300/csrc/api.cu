@@ -161,7 +161,8 @@ int stencil_apply(const stencil_grid_t *g, const void *u, void *y, int form, voi
     e = g->dim == 3 ? launch_apply_stencil_fx3(q, (const double *)u, (double *)y, s)
                     : launch_apply_stencil_f64(q, g->dim, (const double *)u, (double *)y, s);
   else
-    e = launch_apply_elementwise_f64(q, g->dim, (const double *)u, (double *)y, s);
+    e = g->dim == 3 ? launch_apply_elementwise_fx3(q, (const double *)u, (double *)y, s)
+                    : launch_apply_elementwise_f64(q, g->dim, (const double *)u, (double *)y, s);
   if (e != cudaSuccess) return set_error(STENCIL_ECUDA, std::string("apply: ") + cudaGetErrorString(e));
   return STENCIL_OK;
 }

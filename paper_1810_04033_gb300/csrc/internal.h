@@ -69,6 +69,7 @@ cudaError_t launch_residual_f64(const Geo &q, int dim, const double *u, const do
 // ops_fx_reduce_bytes(q) bytes of zero-initialised scratch (left zeroed).
 size_t ops_fx_reduce_bytes(const Geo &q);
 cudaError_t launch_apply_stencil_fx3(const Geo &q, const double *u, double *y, cudaStream_t s);
+cudaError_t launch_apply_elementwise_fx3(const Geo &q, const double *u, double *y, cudaStream_t s);
 cudaError_t launch_jacobi_fx3(const Geo &q, const double *u, const double *f, double *unew,
                               double omega, cudaStream_t s);
 cudaError_t launch_residual_fx3(const Geo &q, const double *u, const double *f, double *r,
