@@ -157,12 +157,12 @@ int stencil_apply(const stencil_grid_t *g, const void *u, void *y, int form, voi
     return set_error(STENCIL_EINVAL, "u and y overlap");
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
-  if (form == STENCIL_FORM_STENCIL)
-    e = g->dim == 3 ? launch_apply_stencil_fx3(q, (const double *)u, (double *)y, s)
-                    : launch_apply_stencil_f64(q, g->dim, (const double *)u, (double *)y, s);
+  if (g->dim == 2)
+    e = launch_apply_fx2(q, (const double *)u, (double *)y, form == STENCIL_FORM_ELEMENTWISE, s);
+  else if (form == STENCIL_FORM_STENCIL)
+    e = launch_apply_stencil_fx3(q, (const double *)u, (double *)y, s);
   else
-    e = g->dim == 3 ? launch_apply_elementwise_fx3(q, (const double *)u, (double *)y, s)
-                    : launch_apply_elementwise_f64(q, g->dim, (const double *)u, (double *)y, s);
+    e = launch_apply_elementwise_fx3(q, (const double *)u, (double *)y, s);
   if (e != cudaSuccess) return set_error(STENCIL_ECUDA, std::string("apply: ") + cudaGetErrorString(e));
   return STENCIL_OK;
 }
@@ -180,12 +180,14 @@ int stencil_smooth_coloured(const stencil_grid_t *g, void *u, const void *f, int
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
   if (g->dim == 3) {
-    void *work = device_scratch(SCRATCH_PINGPONG, (size_t)span_elems(q) * 8, s);
+    void *work = device_scratch(SCRATCH_PINGPONG, 3 * (size_t)span_elems(q) * 8, s);
     void *bnd = device_scratch(SCRATCH_BOUNDS, gs_fx_bounds_bytes(), s);
     if (!work || !bnd) return set_error(STENCIL_ENOMEM, "smooth_coloured workspace allocation failed");
     e = launch_gs_sweeps_fx3(q, (double *)u, (const double *)f, sweeps, (double *)work, bnd, s);
   } else {
-    e = launch_gs_sweeps_f64(q, g->dim, (double *)u, (const double *)f, sweeps, s);
+    void *work = device_scratch(SCRATCH_PINGPONG, (size_t)span_elems(q) * 8, s);
+    if (!work) return set_error(STENCIL_ENOMEM, "smooth_coloured workspace allocation failed");
+    e = launch_gs_sweeps_fx2(q, (double *)u, (const double *)f, sweeps, (double *)work, s);
   }
   if (e != cudaSuccess)
     return set_error(STENCIL_ECUDA, std::string("smooth_coloured: ") + cudaGetErrorString(e));
@@ -210,7 +212,7 @@ int stencil_smooth_jacobi(const stencil_grid_t *g, void *u, const void *f, void 
   double *a = (double *)u, *b = (double *)work;
   for (int it = 0; it < sweeps; ++it) {
     cudaError_t e = g->dim == 3 ? launch_jacobi_fx3(q, a, (const double *)f, b, omega, s)
-                                : launch_jacobi_sweep_f64(q, g->dim, a, (const double *)f, b, omega, s);
+                                : launch_jacobi_fx2(q, a, (const double *)f, b, omega, s);
     if (e != cudaSuccess) return set_error(STENCIL_ECUDA, std::string("jacobi: ") + cudaGetErrorString(e));
     double *t = a;
     a = b;
@@ -239,8 +241,8 @@ int stencil_jacobi_step(const stencil_grid_t *g, const void *u_in, const void *f
   cudaError_t e =
       g->dim == 3 ? launch_jacobi_fx3(q, (const double *)u_in, (const double *)f, (double *)u_out, omega,
                                       (cudaStream_t)stream)
-                  : launch_jacobi_sweep_f64(q, g->dim, (const double *)u_in, (const double *)f,
-                                            (double *)u_out, omega, (cudaStream_t)stream);
+                  : launch_jacobi_fx2(q, (const double *)u_in, (const double *)f, (double *)u_out, omega,
+                                      (cudaStream_t)stream);
   if (e != cudaSuccess) return set_error(STENCIL_ECUDA, std::string("jacobi: ") + cudaGetErrorString(e));
   return STENCIL_OK;
 }
@@ -257,14 +259,14 @@ int stencil_residual(const stencil_grid_t *g, const void *u, const void *f, void
   const size_t bytes = (size_t)span_elems(q) * 8;
   if (r && (overlap(r, u, bytes) || overlap(r, f, bytes)))
     return set_error(STENCIL_EINVAL, "r overlaps u or f");
-  const size_t need = g->dim == 3 ? ops_fx_reduce_bytes(q) : reduce_scratch_bytes();
+  const size_t need = g->dim == 3 ? ops_fx_reduce_bytes(q) : ops2_reduce_bytes(q);
   void *scratch = device_scratch(SCRATCH_REDUCE, need, (cudaStream_t)stream);
   if (!scratch) return set_error(STENCIL_ENOMEM, "residual scratch allocation failed");
   cudaError_t e =
       g->dim == 3 ? launch_residual_fx3(q, (const double *)u, (const double *)f, (double *)r, d_norms2,
                                         scratch, (cudaStream_t)stream)
-                  : launch_residual_f64(q, g->dim, (const double *)u, (const double *)f, (double *)r,
-                                        d_norms2, scratch, (cudaStream_t)stream);
+                  : launch_residual_fx2(q, (const double *)u, (const double *)f, (double *)r, d_norms2,
+                                        scratch, (cudaStream_t)stream);
   if (e != cudaSuccess) return set_error(STENCIL_ECUDA, std::string("residual: ") + cudaGetErrorString(e));
   return STENCIL_OK;
 }

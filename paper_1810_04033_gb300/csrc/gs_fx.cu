@@ -48,33 +48,75 @@ constexpr int GS_NCE = (GS_SH / 2 * GS_SW + GS_THREADS - 1) / GS_THREADS;  // 5 
 constexpr size_t GS_PLANE = (size_t)GS_SH * GS_SW;
 constexpr size_t GS_SMEM = 3 * GS_PLANE * sizeof(long long);
 
+enum { F64 = 0, FXP = 1 };  // storage format of an array: FP64, or int64 fixed point
+
+// Sweep s reads umax[s % 4] (its bound) and umax[(s + 3) % 4] (the previous sweep's,
+// for the scale of its input), accumulates umax[(s + 1) % 4] and clears umax[(s + 2) % 4],
+// which no kernel of sweep s reads.
 struct SweepBounds {
-  unsigned long long umax[3];  // max |u| of the iterate, ring indexed by sweep
-  unsigned long long fmax;     // max |f| over interior vertices
+  unsigned long long umax[4];  // max |u| of the iterate (FP64 bits), ring indexed by sweep
+  unsigned long long fmax;     // max |f| over interior vertices (FP64 bits)
+  unsigned long long m0;       // max |u| of the input (FP64 bits), never cleared
 };
 
 struct Ctx {
   Geo q;
   int x0, y0;        // tile origin (vertex indices)
-  int rb, e2;        // fixed-point scale
+  int R;             // scale of this sweep: values are multiples of 2^(R - 52), |v| < 2^R
+  int dx, dn, df;    // right shifts taking X, N and GF to this sweep's scale
   double g;          // 3/8 h^2
-  int nx, ny;        // cells (as int: planes are < 2^31 elements)
-  int pitch;
+  int nx, ny, pitch;
+  bool write_bnd;    // write Dirichlet copies into Y (false when Y is the caller's u)
 };
 
-template <bool FIX>
-__device__ __forceinline__ long long enc(double v, int rb) {
-  if (FIX) return fx::to_fixed(v, rb);
-  return __double_as_longlong(v);
+// Per-call fixed-point plan, recomputed identically by every CTA from the bounds.
+struct Plan {
+  bool fix;
+  int Rf;            // scale of GF = 3/8 h^2 f
+};
+
+__device__ __forceinline__ double bits_to_d(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+__device__ __forceinline__ Plan make_plan(const SweepBounds *bnd, double g, int sweeps) {
+  Plan p;
+  const double M0 = bits_to_d(bnd->m0);
+  const double gF = g * bits_to_d(bnd->fmax);
+  // |u| after s sweeps <= M0 + 4 s g max|f|: every value of the call stays in range
+  const double B = M0 + 4.0 * (double)(sweeps + 1) * gF;
+  p.fix = fx::bound_ok(B) && fx::bound_ok(gF);
+  p.Rf = gF > 0.0 ? fx::bound_exponent(gF) + 1 : -900;
+  return p;
 }
 
-template <bool FIX>
+__device__ __forceinline__ int sweep_R(const SweepBounds *bnd, int slot, double g) {
+  const double B = bits_to_d(bnd->umax[slot]) + 4.0 * g * bits_to_d(bnd->fmax);
+  const int R = fx::bound_exponent(B) + 1;  // one spare bit: rounding can never reach 2^R
+  return R < -900 ? -900 : R;
+}
+
+__device__ __forceinline__ long long shr(long long v, int d) {
+  return d >= 63 ? (v >> 63) : (d >= 0 ? (v >> d) : (v << (-d)));
+}
+
+// Raw 64-bit load (FP64 bits or int64) of element `off` of plane pointer p.
+__device__ __forceinline__ long long ld64(const void *p, int off) {
+  return ((const long long *)p)[off];
+}
+
+// Convert a raw staged value of format SF into this sweep's representation.
+template <bool FIXA, int SF>
+__device__ __forceinline__ long long to_rep(long long raw, int rb, int d) {
+  if (!FIXA) return raw;                                    // FP64 arithmetic: keep the bits
+  if (SF == F64) return fx::to_fixed(__longlong_as_double(raw), rb);
+  return d ? shr(raw, d) : raw;
+}
+
+template <bool FIXA>
 __device__ __forceinline__ long long add(long long a, long long b) {
-  if (FIX) return a + b;
+  if (FIXA) return a + b;
   return __double_as_longlong(__longlong_as_double(a) + __longlong_as_double(b));
 }
 
-// In-plane offset of staged element (r, col) and whether it lies in the grid.
 template <bool INNER>
 __device__ __forceinline__ bool staged_at(const Ctx &c, int r, int col, int &off) {
   const int x = c.x0 - 2 + col, j = c.y0 - 2 + r;
@@ -83,18 +125,17 @@ __device__ __forceinline__ bool staged_at(const Ctx &c, int r, int col, int &off
   return col < GS_TX + 4 && r < GS_TY + 4 && x >= 0 && x <= c.nx && j >= 0 && j <= c.ny;
 }
 
-// Prefetch of one centre plane's odd rows (pc) and one full neighbour plane (pu).
+// Prefetch (raw 64-bit) of one centre plane's odd rows and one full neighbour plane.
 template <bool INNER>
-__device__ __forceinline__ void prefetch(const Ctx &c, const double *__restrict__ cplane,
-                                         const double *__restrict__ uplane, double (&pc)[GS_NCE],
-                                         double (&pu)[GS_NUP]) {
+__device__ __forceinline__ void prefetch(const Ctx &c, const void *cplane, const void *uplane,
+                                         long long (&pc)[GS_NCE], long long (&pu)[GS_NUP]) {
 #pragma unroll
   for (int k = 0; k < GS_NCE; ++k) {
     const int idx = threadIdx.x + k * GS_THREADS;
     const int r = 2 * (idx >> 6) + 1, col = idx & 63;
     int off;
     const bool ok = idx < GS_SH / 2 * GS_SW && cplane && staged_at<INNER>(c, r, col, off);
-    pc[k] = ok ? cplane[off] : 0.0;
+    pc[k] = ok ? ld64(cplane, off) : 0ll;
   }
 #pragma unroll
   for (int k = 0; k < GS_NUP; ++k) {
@@ -102,26 +143,29 @@ __device__ __forceinline__ void prefetch(const Ctx &c, const double *__restrict_
     const int r = idx >> 6, col = idx & 63;
     int off;
     const bool ok = uplane && staged_at<INNER>(c, r, col, off);
-    pu[k] = ok ? uplane[off] : 0.0;
+    pu[k] = ok ? ld64(uplane, off) : 0ll;
   }
 }
 
-template <bool FIX>
-__device__ __forceinline__ void commit(const Ctx &c, const double (&pc)[GS_NCE],
-                                       const double (&pu)[GS_NUP], long long *ce, long long *up) {
+template <bool FIXA, int CF, int UF>
+__device__ __forceinline__ void commit(const Ctx &c, const long long (&pc)[GS_NCE],
+                                       const long long (&pu)[GS_NUP], long long *ce, long long *up,
+                                       int dup) {
+  const int rb = 1023 + c.R;
 #pragma unroll
   for (int k = 0; k < GS_NCE; ++k) {
     const int idx = threadIdx.x + k * GS_THREADS;
-    if (idx < GS_SH / 2 * GS_SW) ce[(2 * (idx >> 6) + 1) * GS_SW + (idx & 63)] = enc<FIX>(pc[k], c.rb);
+    if (idx < GS_SH / 2 * GS_SW)
+      ce[(2 * (idx >> 6) + 1) * GS_SW + (idx & 63)] = to_rep<FIXA, CF>(pc[k], rb, c.dx);
   }
 #pragma unroll
-  for (int k = 0; k < GS_NUP; ++k) up[threadIdx.x + k * GS_THREADS] = enc<FIX>(pu[k], c.rb);
+  for (int k = 0; k < GS_NUP; ++k) up[threadIdx.x + k * GS_THREADS] = to_rep<FIXA, UF>(pu[k], rb, dup);
 }
 
-// f values this thread needs for the two phases of one centre plane (4 rows each).
+// Right-hand side values for the two phases of one centre plane (4 rows each): GF
+// (int64, 3/8 h^2 f in fixed point) in fixed arithmetic, f itself otherwise.
 template <bool INNER>
-__device__ __forceinline__ void prefetch_f(const Ctx &c, const double *__restrict__ fplane,
-                                           double (&fv)[8]) {
+__device__ __forceinline__ void prefetch_f(const Ctx &c, const void *fplane, long long (&fv)[8]) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int seg = warp & 1, grp = warp >> 1;
 #pragma unroll
@@ -132,7 +176,7 @@ __device__ __forceinline__ void prefetch_f(const Ctx &c, const double *__restric
       const int r = (ph == 0 ? 2 : 3) + 8 * grp + 2 * k;
       const int x = c.x0 - 2 + col, j = c.y0 - 2 + r;
       const bool ok = fplane && lane >= 1 && lane <= 30 && x >= 1 && x < c.nx && j >= 1 && j < c.ny;
-      fv[4 * ph + k] = ok ? fplane[j * c.pitch + x] : 0.0;
+      fv[4 * ph + k] = ok ? ld64(fplane, j * c.pitch + x) : 0ll;
     }
   }
 }
@@ -141,11 +185,10 @@ __device__ __forceinline__ void prefetch_f(const Ctx &c, const double *__restric
 // (results also written back into the centre plane); WHICH = 2: rows of parity 1 on
 // the tile.  A warp walks 4 rows of one 32-column segment, carrying the column sums of
 // the shared rows from one row to the next.
-template <bool FIX, bool INNER, int WHICH>
+template <bool FIXA, int XF, int YF, bool INNER, int WHICH>
 __device__ __forceinline__ void phase(const Ctx &c, long long *ce, const long long *lo,
-                                      const long long *up, const double *__restrict__ xplane,
-                                      double *__restrict__ yplane, const double (&fv)[8],
-                                      bool zin, unsigned long long &vmax) {
+                                      const long long *up, const void *xplane, void *yplane,
+                                      const long long (&fv)[8], long long &vmax) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int seg = warp & 1, grp = warp >> 1;
   const int col = (WHICH == 1 ? 0 : 1) + 30 * seg + lane;
@@ -157,18 +200,18 @@ __device__ __forceinline__ void phase(const Ctx &c, long long *ce, const long lo
   const bool col_core = WHICH == 2 || (col >= 2 && col < 60);
   const long long *lc = lo + col, *uc = up + col;
   long long *cc = ce + col;
-  long long Dm = add<FIX>(lc[(r0 - 1) * GS_SW], uc[(r0 - 1) * GS_SW]);
+  long long Dm = add<FIXA>(lc[(r0 - 1) * GS_SW], uc[(r0 - 1) * GS_SW]);
   long long Cm = cc[(r0 - 1) * GS_SW];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int r = r0 + 2 * k;
-    const long long Dp = add<FIX>(lc[(r + 1) * GS_SW], uc[(r + 1) * GS_SW]);
+    const long long Dp = add<FIXA>(lc[(r + 1) * GS_SW], uc[(r + 1) * GS_SW]);
     const long long Cp = cc[(r + 1) * GS_SW];
-    const long long W = add<FIX>(lc[r * GS_SW], uc[r * GS_SW]);
-    const long long V = add<FIX>(Cm, Cp);
-    const long long Q = add<FIX>(Dm, Dp);
-    const long long VW = add<FIX>(V, W);
-    const long long P = add<FIX>(add<FIX>(VW, VW), Q);
+    const long long W = add<FIXA>(lc[r * GS_SW], uc[r * GS_SW]);
+    const long long V = add<FIXA>(Cm, Cp);
+    const long long Q = add<FIXA>(Dm, Dp);
+    const long long VW = add<FIXA>(V, W);
+    const long long P = add<FIXA>(add<FIXA>(VW, VW), Q);
     const long long Pm = __shfl_up_sync(0xffffffffu, P, 1);
     const long long Pp = __shfl_down_sync(0xffffffffu, P, 1);
     Dm = Dp;
@@ -178,75 +221,100 @@ __device__ __forceinline__ void phase(const Ctx &c, long long *ce, const long lo
     if (!lane_out || !row_ok) continue;
     const bool in_grid = x_in && (INNER || (j >= 0 && j <= c.ny));
     if (!in_grid) continue;
-    const bool inner = zin && x_inner && (INNER || (j >= 1 && j < c.ny));
+    const bool inner = x_inner && (INNER || (j >= 1 && j < c.ny));
     const int off = j * c.pitch + x;
-    double un;
+    const bool core = col_core && (WHICH == 2 || r < GS_TY + 2);
+    long long rep;  // new value in this sweep's representation
     if (inner) {
-      const long long S = add<FIX>(add<FIX>(Pm, Pp), add<FIX>(Q, Q));
-      if (FIX)
-        un = fma(c.g, fv[(WHICH - 1) * 4 + k], fx::to_double(S, c.e2));
+      const long long S = add<FIXA>(add<FIXA>(Pm, Pp), add<FIXA>(Q, Q));  // 2E + C
+      if (FIXA)
+        rep = shr(fv[(WHICH - 1) * 4 + k], c.df) + (S >> 5);
       else
-        un = fma(__longlong_as_double(S), 0.03125, c.g * fv[(WHICH - 1) * 4 + k]);
+        rep = __double_as_longlong(fma(__longlong_as_double(S), 0.03125,
+                                       c.g * __longlong_as_double(fv[(WHICH - 1) * 4 + k])));
     } else {
-      un = xplane[off];  // Dirichlet value, copied
+      // Dirichlet value, carried through
+      rep = to_rep<FIXA, XF>(ld64(xplane, off), 1023 + c.R, c.dx);
+      if (!c.write_bnd) {
+        if (WHICH == 1) cc[r * GS_SW] = rep;
+        continue;
+      }
     }
-    if (WHICH == 1) cc[r * GS_SW] = enc<FIX>(un, c.rb);
-    if (col_core && (WHICH == 2 || r < GS_TY + 2)) {
-      yplane[off] = un;
-      const unsigned long long b = fx::abs_bits(un);
-      vmax = b > vmax ? b : vmax;
+    if (WHICH == 1) cc[r * GS_SW] = rep;
+    if (core) {
+      if (YF == FXP && FIXA) {
+        ((long long *)yplane)[off] = rep;
+      } else if (FIXA) {
+        ((double *)yplane)[off] = inner ? fx::to_double(rep, c.R - fx::FRAC) : __longlong_as_double(ld64(xplane, off));
+      } else {
+        ((long long *)yplane)[off] = rep;  // FP64 bits
+      }
+      const long long a = FIXA ? (rep < 0 ? -rep : rep) : (long long)fx::abs_bits(__longlong_as_double(rep));
+      vmax = a > vmax ? a : vmax;
     }
   }
 }
 
-template <bool FIX, bool INNER>
-__device__ void run_half(const Ctx &c, int pz, int i0, int i1, const double *__restrict__ X,
-                         const double *__restrict__ N, double *__restrict__ Y,
-                         const double *__restrict__ f, long long *smem, unsigned long long &vmax) {
+template <bool FIXA, int XF, int NF, int YF, bool INNER>
+__device__ void run_half(Ctx &c, int pz, int i0, int i1, const void *X, const void *N, void *Y,
+                         const void *F, long long *smem, long long &vmax) {
   const Geo &q = c.q;
   const int64_t P = q.plane;
   long long *slot[3] = {smem, smem + GS_PLANE, smem + 2 * GS_PLANE};
   int lo = 0, ce = 1, up = 2;
-  double pc[GS_NCE], pu[GS_NUP], fv[8];
-  // prologue: the lower neighbour of the first centre plane, then its prefetch
+  long long pc[GS_NCE], pu[GS_NUP], fv[8];
+  const char *Xc = (const char *)X, *Nc = (const char *)N, *Fc = (const char *)F;
+  char *Yc = (char *)Y;
   {
     const int64_t z = pz + 2 * (int64_t)i0;
-    double dummy[GS_NCE];
-    prefetch<INNER>(c, nullptr, z >= 1 ? N + (z - 1) * P : nullptr, dummy, pu);
-    commit<FIX>(c, dummy, pu, slot[ce], slot[lo]);  // ce gets zeros, overwritten below
+    long long dummy[GS_NCE];
+    prefetch<INNER>(c, nullptr, z >= 1 ? Nc + (z - 1) * P * 8 : nullptr, dummy, pu);
+    commit<FIXA, XF, NF>(c, dummy, pu, slot[ce], slot[lo], c.dn);
     const bool zin = z >= 1 && z <= q.nz - 1;
-    prefetch<INNER>(c, zin ? X + z * P : nullptr, z + 1 <= q.nz ? N + (z + 1) * P : nullptr, pc, pu);
-    prefetch_f<INNER>(c, zin ? f + z * P : nullptr, fv);
+    prefetch<INNER>(c, zin ? Xc + z * P * 8 : nullptr, z + 1 <= q.nz ? Nc + (z + 1) * P * 8 : nullptr, pc, pu);
+    prefetch_f<INNER>(c, zin ? Fc + z * P * 8 : nullptr, fv);
   }
   for (int i = i0; i < i1; ++i) {
     const int64_t z = pz + 2 * (int64_t)i;
     const bool zin = z >= 1 && z <= q.nz - 1;
-    commit<FIX>(c, pc, pu, slot[ce], slot[up]);
-    double fcur[8];
+    commit<FIXA, XF, NF>(c, pc, pu, slot[ce], slot[up], c.dn);
+    long long fcur[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) fcur[k] = fv[k];
     __syncthreads();
     if (i + 1 < i1) {  // next centre plane z + 2 and its upper neighbour z + 3
       const bool zn = z + 2 >= 1 && z + 2 <= q.nz - 1;
-      prefetch<INNER>(c, zn ? X + (z + 2) * P : nullptr, z + 3 <= q.nz ? N + (z + 3) * P : nullptr,
+      prefetch<INNER>(c, zn ? Xc + (z + 2) * P * 8 : nullptr, z + 3 <= q.nz ? Nc + (z + 3) * P * 8 : nullptr,
                       pc, pu);
-      prefetch_f<INNER>(c, zn ? f + (z + 2) * P : nullptr, fv);
+      prefetch_f<INNER>(c, zn ? Fc + (z + 2) * P * 8 : nullptr, fv);
     }
-    const double *xp = X + z * P;
-    double *yp = Y + z * P;
+    const void *xp = Xc + z * P * 8;
+    void *yp = Yc + z * P * 8;
     if (zin) {
-      phase<FIX, INNER, 1>(c, slot[ce], slot[lo], slot[up], xp, yp, fcur, true, vmax);
+      phase<FIXA, XF, YF, INNER, 1>(c, slot[ce], slot[lo], slot[up], xp, yp, fcur, vmax);
       __syncthreads();
-      phase<FIX, INNER, 2>(c, slot[ce], slot[lo], slot[up], xp, yp, fcur, true, vmax);
-    } else {
-      // Dirichlet plane: copy the tile
+      phase<FIXA, XF, YF, INNER, 2>(c, slot[ce], slot[lo], slot[up], xp, yp, fcur, vmax);
+    } else if (c.write_bnd) {
+      // Dirichlet plane: carry the tile through
       for (int idx = threadIdx.x; idx < GS_TX * GS_TY; idx += GS_THREADS) {
         const int x = c.x0 + idx % GS_TX, j = c.y0 + idx / GS_TX;
         if (x > c.nx || j > c.ny) continue;
-        const double v = xp[j * c.pitch + x];
-        yp[j * c.pitch + x] = v;
-        const unsigned long long b = fx::abs_bits(v);
-        vmax = b > vmax ? b : vmax;
+        const int off = j * c.pitch + x;
+        const long long raw = ld64(xp, off);
+        long long out, a;
+        if (FIXA && YF == FXP) {
+          out = to_rep<FIXA, XF>(raw, 1023 + c.R, c.dx);
+          a = out < 0 ? -out : out;
+        } else if (FIXA) {  // FP64 output of an FP64 or fixed input
+          out = XF == F64 ? raw : __double_as_longlong(fx::to_double(shr(raw, c.dx), c.R - fx::FRAC));
+          a = XF == F64 ? to_rep<true, F64>(raw, 1023 + c.R, 0) : shr(raw, c.dx);
+          a = a < 0 ? -a : a;
+        } else {
+          out = raw;
+          a = (long long)fx::abs_bits(__longlong_as_double(raw));
+        }
+        ((long long *)yp)[off] = out;
+        vmax = a > vmax ? a : vmax;
       }
     }
     __syncthreads();
@@ -257,12 +325,13 @@ __device__ void run_half(const Ctx &c, int pz, int i0, int i1, const double *__r
   }
 }
 
+template <int XF, int NF, int YF>
 __global__ void __launch_bounds__(GS_THREADS, 2)
-    k_gs_half_sweep(Geo q, int pz, const double *__restrict__ X, const double *__restrict__ N,
-                    double *__restrict__ Y, const double *__restrict__ f, SweepBounds *bnd,
-                    int slot_read, int slot_write, int slot_clear, double g) {
+    k_gs_half_sweep(Geo q, int pz, const void *X, const void *N, void *Y, const double *f, const long long *GF,
+                    SweepBounds *bnd, int sweep, int sweeps, double g, int n_even_odd_sweeps_unused,
+                    bool write_bnd) {
   extern __shared__ long long smem[];
-  __shared__ unsigned long long red[GS_THREADS / 32];
+  __shared__ long long red[GS_THREADS / 32];
   Ctx c;
   c.q = q;
   c.x0 = (int)blockIdx.x * GS_TX;
@@ -271,39 +340,61 @@ __global__ void __launch_bounds__(GS_THREADS, 2)
   c.nx = (int)q.nx;
   c.ny = (int)q.ny;
   c.pitch = (int)q.pitch;
-  // bound for this sweep: max |u| of the input iterate + growth within the sweep
-  const double M = __longlong_as_double((long long)bnd->umax[slot_read]);
-  const double F = __longlong_as_double((long long)bnd->fmax);
-  const double B = M + 4.0 * g * F;
-  const bool fix = fx::bound_ok(B);
-  const int R = fx::bound_exponent(B) + 1;  // one spare bit: rounding can never reach 2^R
-  c.rb = 1023 + R;
-  c.e2 = R - fx::FRAC - 5;  // (2E + C) / 32
-  if (slot_clear >= 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
-    bnd->umax[slot_clear] = 0ull;
+  c.write_bnd = write_bnd;
+  const Plan plan = make_plan(bnd, g, sweeps);
+  const int rd = sweep % 4, wr = (sweep + 1) % 4, cl = (sweep + 2) % 4;
+  c.R = sweep_R(bnd, rd, g);
+  const int Rx = sweep > 0 ? sweep_R(bnd, (sweep + 3) % 4, g) : c.R;  // scale of the previous sweep
+  c.dx = XF == FXP ? c.R - Rx : 0;
+  c.dn = NF == FXP ? (pz == 0 ? c.dx : 0) : 0;  // odd launch: N is this sweep's output
+  c.df = c.R - plan.Rf;
+  if (pz == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
+    bnd->umax[cl] = 0ull;  // to be accumulated by sweep s + 1
+  (void)n_even_odd_sweeps_unused;
 
   const int ncentre = q.nz >= pz ? (int)((q.nz - pz) / 2 + 1) : 0;
   const int i0 = (int)blockIdx.z * GS_CZ;
   const int i1 = i0 + GS_CZ < ncentre ? i0 + GS_CZ : ncentre;
-  // interior tile: every staged vertex in the grid and every output an interior vertex
   const bool inner = c.x0 >= 2 && c.x0 + GS_TX + 1 <= c.nx && c.y0 >= 2 && c.y0 + GS_TY + 1 <= c.ny;
-  unsigned long long vmax = 0ull;
-  if (fix) {
+  long long vmax = 0;
+  if (plan.fix) {
     if (inner)
-      run_half<true, true>(c, pz, i0, i1, X, N, Y, f, smem, vmax);
+      run_half<true, XF, NF, YF, true>(c, pz, i0, i1, X, N, Y, GF, smem, vmax);
     else
-      run_half<true, false>(c, pz, i0, i1, X, N, Y, f, smem, vmax);
+      run_half<true, XF, NF, YF, false>(c, pz, i0, i1, X, N, Y, GF, smem, vmax);
   } else {
-    run_half<false, false>(c, pz, i0, i1, X, N, Y, f, smem, vmax);
+    run_half<false, F64, F64, F64, false>(c, pz, i0, i1, X, N, Y, f, smem, vmax);
   }
-
-  vmax = fx::warp_max_u64(vmax);
+  // block max of |new values| -> FP64 bits -> the next sweep's bound
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long w = __shfl_xor_sync(0xffffffffu, vmax, o);
+    vmax = w > vmax ? w : vmax;
+  }
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = vmax;
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned long long m = 0;
+    long long m = 0;
     for (int w = 0; w < GS_THREADS / 32; ++w) m = red[w] > m ? red[w] : m;
-    atomicMax(&bnd->umax[slot_write], m);
+    const unsigned long long mb =
+        plan.fix ? fx::abs_bits(fx::to_double(m, c.R - fx::FRAC) * (1.0 + 0x1p-50)) : (unsigned long long)m;
+    atomicMax(&bnd->umax[wr], mb);
+  }
+}
+
+// 3/8 h^2 f in fixed point (scale Rf of the plan) on interior vertices, 0 elsewhere.
+__global__ void __launch_bounds__(256) k_prep_gf(Geo q, const double *__restrict__ f, long long *__restrict__ GF,
+                                                 const SweepBounds *bnd, double g, int sweeps) {
+  const Plan plan = make_plan(bnd, g, sweeps);
+  if (!plan.fix) return;
+  const int rb = 1023 + plan.Rf;
+  const int64_t nrows = (q.nz + 1) * (q.ny + 1);
+  for (int64_t row = blockIdx.x; row < nrows; row += gridDim.x) {
+    const int64_t k = row / (q.ny + 1), j = row % (q.ny + 1);
+    const bool row_inner = j > 0 && j < q.ny && k > 0 && k < q.nz;
+    const int64_t base = k * q.plane + j * q.pitch;
+    for (int64_t i = threadIdx.x; i <= q.nx; i += blockDim.x)
+      GF[base + i] = (row_inner && i > 0 && i < q.nx) ? fx::to_fixed(g * f[base + i], rb) : 0ll;
   }
 }
 
@@ -340,6 +431,7 @@ __global__ void __launch_bounds__(256) k_absmax_uf(Geo q, int dim, const double 
       mf = rf[w] > mf ? rf[w] : mf;
     }
     atomicMax(&bnd->umax[0], mu);
+    atomicMax(&bnd->m0, mu);
     atomicMax(&bnd->fmax, mf);
   }
 }
@@ -348,46 +440,67 @@ __global__ void __launch_bounds__(256) k_absmax_uf(Geo q, int dim, const double 
 
 size_t gs_fx_bounds_bytes() { return sizeof(SweepBounds); }
 
-cudaError_t launch_gs_sweeps_fx3(const Geo &q, double *u, const double *f, int sweeps,
-                                 double *work, void *bounds, cudaStream_t s) {
-  static bool attr_set = false;  // per process; harmless to repeat
+template <int XF, int NF, int YF>
+static cudaError_t launch_half(const Geo &q, int pz, const void *X, const void *N, void *Y, const double *f,
+                               const long long *GF, SweepBounds *bnd, int sweep, int sweeps, double g,
+                               bool write_bnd, cudaStream_t s) {
+  static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_gs_half_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_gs_half_sweep<XF, NF, YF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)GS_SMEM);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  const unsigned tx = (unsigned)((q.nx + 1 + GS_TX - 1) / GS_TX);
+  const unsigned ty = (unsigned)((q.ny + 1 + GS_TY - 1) / GS_TY);
+  const int64_t ncentre = (q.nz - pz) / 2 + 1;
+  const unsigned tz = (unsigned)((ncentre + GS_CZ - 1) / GS_CZ);
+  if (ty > 65535 || tz > 65535) return cudaErrorInvalidConfiguration;
+  k_gs_half_sweep<XF, NF, YF><<<dim3(tx, ty, tz), GS_THREADS, GS_SMEM, s>>>(q, pz, X, N, Y, f, GF, bnd, sweep,
+                                                                            sweeps, g, 0, write_bnd);
+  return cudaGetLastError();
+}
+
+// work: 3 arrays of u's span (8 bytes per element): two ping-pong buffers and GF.
+cudaError_t launch_gs_sweeps_fx3(const Geo &q, double *u, const double *f, int sweeps, double *work,
+                                 void *bounds, cudaStream_t s) {
   if (q.plane >= ((int64_t)1 << 31) - GS_SW * GS_SH) return cudaErrorInvalidValue;
+  const int64_t span = span_elems(q);
+  void *A = work, *B = work + span;
+  long long *GF = (long long *)(work + 2 * span);
   SweepBounds *bnd = (SweepBounds *)bounds;
   cudaError_t e = cudaMemsetAsync(bnd, 0, sizeof(SweepBounds), s);
   if (e != cudaSuccess) return e;
   k_absmax_uf<<<1216, 256, 0, s>>>(q, 3, u, f, bnd);
   const double g = 0.375 * q.h * q.h;
-  const unsigned tx = (unsigned)((q.nx + 1 + GS_TX - 1) / GS_TX);
-  const unsigned ty = (unsigned)((q.ny + 1 + GS_TY - 1) / GS_TY);
-  if (ty > 65535) return cudaErrorInvalidConfiguration;
-  double *cur = u, *nxt = work;
-  for (int it = 0; it < sweeps; ++it) {
-    const int rd = it % 3, wr = (it + 1) % 3, cl = (it + 2) % 3;
-    for (int pz = 0; pz < 2; ++pz) {
-      const int64_t ncentre = (q.nz - pz) / 2 + 1;
-      const unsigned tz = (unsigned)((ncentre + GS_CZ - 1) / GS_CZ);
-      if (tz > 65535) return cudaErrorInvalidConfiguration;
-      dim3 grid(tx, ty, tz);
-      k_gs_half_sweep<<<grid, GS_THREADS, GS_SMEM, s>>>(q, pz, cur, pz == 0 ? cur : nxt, nxt, f, bnd,
-                                                        rd, wr, pz == 0 ? cl : -1, g);
+  k_prep_gf<<<1216, 256, 0, s>>>(q, f, GF, bnd, g, sweeps);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (sweeps == 1) {
+    // u -> A in FP64 (boundary carried), then back into u
+    e = launch_half<F64, F64, F64>(q, 0, u, u, A, f, GF, bnd, 0, 1, g, true, s);
+    if (!e) e = launch_half<F64, F64, F64>(q, 1, u, A, A, f, GF, bnd, 0, 1, g, true, s);
+    if (!e) e = cudaMemcpyAsync(u, A, (size_t)span * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    return e;
+  }
+  const void *X = u;
+  for (int it = 0; it < sweeps && !e; ++it) {
+    const bool first = it == 0, last = it == sweeps - 1;
+    void *Y = last ? (void *)u : (it % 2 == 0 ? A : B);
+    if (first) {
+      e = launch_half<F64, F64, FXP>(q, 0, X, X, Y, f, GF, bnd, it, sweeps, g, true, s);
+      if (!e) e = launch_half<F64, FXP, FXP>(q, 1, X, Y, Y, f, GF, bnd, it, sweeps, g, true, s);
+    } else if (!last) {
+      e = launch_half<FXP, FXP, FXP>(q, 0, X, X, Y, f, GF, bnd, it, sweeps, g, true, s);
+      if (!e) e = launch_half<FXP, FXP, FXP>(q, 1, X, Y, Y, f, GF, bnd, it, sweeps, g, true, s);
+    } else {
+      // the caller's u: its Dirichlet values were never overwritten, leave them
+      e = launch_half<FXP, FXP, F64>(q, 0, X, X, Y, f, GF, bnd, it, sweeps, g, false, s);
+      if (!e) e = launch_half<FXP, F64, F64>(q, 1, X, Y, Y, f, GF, bnd, it, sweeps, g, false, s);
     }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    double *t = cur;
-    cur = nxt;
-    nxt = t;
+    X = Y;
   }
-  if (cur != u) {
-    e = cudaMemcpyAsync(u, cur, (size_t)span_elems(q) * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaGetLastError();
+  return e ? e : cudaGetLastError();
 }
 
 }  // namespace stencil

@@ -57,8 +57,9 @@ cudaError_t launch_jacobi_sweep_f64(const Geo &q, int dim, const double *u, cons
 constexpr int kReduceBlocks = 1216;  // 8 per SM on 152 SMs: fixed => fixed sum order
 size_t reduce_scratch_bytes();
 
-// Fixed-point FP64 paths (gs_fx.cu): 3D coloured GS, two launches per sweep, out of
-// place between u and work (same layout); result always ends in u.
+// Fixed-point FP64 paths (gs_fx.cu): 3D coloured GS, two launches per sweep.  work
+// holds 3 arrays of u's span (two int64 ping-pong buffers and 3/8 h^2 f in fixed point);
+// the result always ends in u, whose boundary values are never written.
 size_t gs_fx_bounds_bytes();
 cudaError_t launch_gs_sweeps_fx3(const Geo &q, double *u, const double *f, int sweeps,
                                  double *work, void *bounds, cudaStream_t s);
@@ -72,6 +73,15 @@ cudaError_t launch_apply_stencil_fx3(const Geo &q, const double *u, double *y, c
 cudaError_t launch_apply_elementwise_fx3(const Geo &q, const double *u, double *y, cudaStream_t s);
 cudaError_t launch_jacobi_fx3(const Geo &q, const double *u, const double *f, double *unew,
                               double omega, cudaStream_t s);
+// 2D (ops2d_fx.cu)
+size_t ops2_reduce_bytes(const Geo &q);
+cudaError_t launch_apply_fx2(const Geo &q, const double *u, double *y, bool elementwise, cudaStream_t s);
+cudaError_t launch_jacobi_fx2(const Geo &q, const double *u, const double *f, double *unew, double omega,
+                              cudaStream_t s);
+cudaError_t launch_residual_fx2(const Geo &q, const double *u, const double *f, double *r, double *norms2,
+                                void *scratch, cudaStream_t s);
+cudaError_t launch_gs_sweeps_fx2(const Geo &q, double *u, const double *f, int sweeps, double *work,
+                                 cudaStream_t s);
 cudaError_t launch_residual_fx3(const Geo &q, const double *u, const double *f, double *r,
                                 double *norms2, void *scratch, cudaStream_t s);
 

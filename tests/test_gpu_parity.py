@@ -273,3 +273,60 @@ def test_full_size_sampled_apply_and_gs():
     ref = oracle.gs_coloured(u, f, h, 1, nthreads=os.cpu_count() or 1)
     torch.cuda.synchronize()
     assert rel_err(ud.cpu().numpy(), ref) <= TOL_F64
+
+
+@pytest.mark.parametrize("n", [(200, 150), (61, 300), (29, 29), (31, 130)])
+def test_2d_ops_multi_segment(n):
+    """2D apply (both forms), GS, Jacobi step and residual over several warp segments
+    and row chunks."""
+    h = 1.0 / max(n)
+    shape = synth.grid_shape(2, n)
+    u = synth.uniform_field(shape, 1500 + sum(n), zero_bc=False)
+    f = synth.uniform_field(shape, 1600 + sum(n))
+    ud, fd = to_dev(u, pad=5), to_dev(f, pad=5)
+    for form, ref in ((st.FORM_ELEMENTWISE, oracle.apply_elementwise(u, h)),
+                      (st.FORM_STENCIL, oracle.apply_stencil(u, h))):
+        yd = to_dev(np.full(shape, np.nan), pad=5)
+        st.stencil_apply(ud, yd, h, form)
+        torch.cuda.synchronize()
+        assert apply_err(to_host(yd), ref, u, h) <= TOL_F64, form
+    od = to_dev(np.full(shape, np.nan), pad=5)
+    st.stencil_jacobi_step(ud, fd, od, h, 2.0 / 3.0)
+    rd = to_dev(np.full(shape, np.nan), pad=5)
+    nrm = st.stencil_residual(ud, fd, h, r=rd)
+    torch.cuda.synchronize()
+    assert rel_err(to_host(od), oracle.jacobi(u, f, h, 2.0 / 3.0, 1)) <= TOL_F64
+    rref, nref = oracle.residual(u, f, h)
+    assert apply_err(to_host(rd), rref, u, h) <= TOL_F64
+    got = nrm.cpu().numpy()
+    assert abs(got[1] - nref[1]) <= 1e-12 * nref[1]
+    assert abs(got[0] - nref[0]) <= 1e-11 * nref[0]
+    for sweeps in (1, 2, 3):
+        gd = to_dev(u, pad=5)
+        st.stencil_smooth_coloured(gd, fd, h, sweeps)
+        torch.cuda.synchronize()
+        assert rel_err(to_host(gd), oracle.gs_coloured(u, f, h, sweeps)) <= TOL_F64, sweeps
+
+
+@pytest.mark.parametrize("scale", [1e300, 1e-280, 1e-7])
+def test_2d_extreme_and_growing_magnitudes(scale):
+    n = (70, 90)
+    h = 1.0 / 90
+    shape = synth.grid_shape(2, n)
+    yy = np.arange(shape[0], dtype=np.float64)[:, None]
+    u = synth.uniform_field(shape, 1700, zero_bc=False) * scale * (1.0 + 1e3 * (yy / shape[0]) ** 4)
+    f = synth.uniform_field(shape, 1701) * scale
+    ud, fd = to_dev(u), to_dev(f)
+    for form, ref in ((st.FORM_ELEMENTWISE, oracle.apply_elementwise(u, h)),
+                      (st.FORM_STENCIL, oracle.apply_stencil(u, h))):
+        yd = torch.empty_like(ud)
+        st.stencil_apply(ud, yd, h, form)
+        torch.cuda.synchronize()
+        assert apply_err(to_host(yd), ref, u, h) <= TOL_F64
+    gd = ud.clone()
+    st.stencil_smooth_coloured(gd, fd, h, 2)
+    od = torch.empty_like(ud)
+    st.stencil_jacobi_step(ud, fd, od, h, 0.9)
+    torch.cuda.synchronize()
+    assert rel_err(to_host(gd), oracle.gs_coloured(u, f, h, 2)) <= TOL_F64
+    assert rel_err(to_host(od), oracle.jacobi(u, f, h, 0.9, 1)) <= TOL_F64
