@@ -98,7 +98,9 @@ int stencil_apply(const stencil_grid_t *g, const void *u, void *y, int form, voi
  * inside a colour).  Each interior vertex i of the current colour becomes
  *   u_i = (h^2 f_i - sum_{j != i} S_ij u_j) / S_ii.
  * Boundary values of u are read, never written; f on the boundary is ignored.
- * u: device array (in/out); f: device array, may not alias u.  dtype F64 or F32.
+ * u: device array (in/out); f: device array, may not alias u.  dtype F64 (2D, 3D);
+ * F32 or BF16 (3D): values stored in that type, arithmetic in FP32, every store of a
+ * bf16 value rounded to nearest even.
  * The call may use an internal device workspace of the size of u (allocated on first
  * use and kept; see stencil_release_workspace).
  * Returns STENCIL_EINVAL, STENCIL_ENOMEM, STENCIL_ECUDA.
@@ -157,6 +159,83 @@ int stencil_residual(const stencil_grid_t *g, const void *u, const void *f, void
  */
 int stencil_residual_noalloc(const stencil_grid_t *g, const void *u, const void *f, void *r,
                              double *d_norms2, void *stream);
+
+/* Options and report of stencil_solve. */
+typedef struct stencil_solve_opts {
+  double rel_tol;   /* stop when ||f - A u||_2 / ||f||_2 <= rel_tol (interior vertices) */
+  int max_outer;    /* at most this many corrections */
+  int inner_sweeps; /* coloured GS sweeps per correction, from a zero correction */
+  int inner_dtype;  /* STENCIL_F64, STENCIL_F32 or STENCIL_BF16 (the last two: 3D only) */
+} stencil_solve_opts_t;
+
+typedef struct stencil_solve_info {
+  int iterations;          /* corrections applied */
+  int converged;           /* 1 if rel_tol was reached */
+  double relres;           /* relative residual of the returned u */
+  double *relres_history;  /* optional host array of max_outer + 1 entries (or NULL):
+                              relative residual before each correction and at the end */
+} stencil_solve_info_t;
+
+/*
+ * Iterative refinement for A u = f with the coloured Gauss-Seidel smoother as inner
+ * solver (the multigrid-smoother use of Section 1; the precision split is this
+ * library's).  Each outer iteration: r = f - A u and both norms in FP64 (fixed-order
+ * reduction); stop when ||r|| / ||f|| <= rel_tol; round r to inner_dtype (bf16 via FP32,
+ * nearest even); from e = 0 run inner_sweeps coloured GS sweeps on A e = r, stored and
+ * computed in inner_dtype (bf16: FP32 arithmetic, every store rounded); u += e in FP64.
+ * u: device F64 array (in: initial guess and Dirichlet data; out: result); f: device
+ * F64.  g->dtype must be STENCIL_F64.  Host-synchronous: returns after the last
+ * iteration (it synchronises `stream` once per outer iteration to read the norm).
+ * Uses library workspaces of a few arrays of u's size (kept per stream).
+ * Returns STENCIL_OK, STENCIL_ENOTCONV (u holds the last iterate), STENCIL_EINVAL,
+ * STENCIL_ENOMEM, STENCIL_ECUDA.
+ */
+int stencil_solve(const stencil_grid_t *g, double *u, const double *f, const stencil_solve_opts_t *opts,
+                  stencil_solve_info_t *info, void *stream);
+
+/* ------------------------------------------------------------ patch batches */
+/* One cubic patch of a batch: a dense (n+1)^3 vertex array, x fastest, at element
+ * offset `offset` of the packed FP64 buffers.  Its boundary shell is a halo. */
+typedef struct stencil_patch_desc {
+  int32_t n;        /* cells per edge, 2..64 */
+  int32_t reserved; /* 0 */
+  int64_t offset;   /* element offset of the patch in the packed arrays */
+  double h;         /* mesh width; 0 selects 1/n (a unit cube per patch) */
+} stencil_patch_desc_t;
+
+typedef struct stencil_batch stencil_batch_t; /* opaque */
+
+/*
+ * Creates a batch of `npatch` cubic patches, the regular patches of a block-structured
+ * mesh (Section 2).  neighbours: host array of 27 int32 per patch, entry
+ * (dx+1) + 3(dy+1) + 9(dz+1) naming the patch across the face/edge/corner in direction
+ * (dx,dy,dz) (the centre entry is ignored), or -1 at the outer boundary.  Halo rule,
+ * applied before every sweep: a shell vertex of p with outward direction d takes, from
+ * q = neighbour(d), per axis the vertex of q nearest to its position (ties to the lower
+ * index) clamped into [1, n_q - 1]; with no neighbour the value is 0.  Copies the
+ * tables to the current device.  Returns STENCIL_EINVAL, STENCIL_ENOMEM.
+ */
+int stencil_patch_batch_create(const stencil_patch_desc_t *patches, int32_t npatch, const int32_t *neighbours,
+                               stencil_batch_t **out);
+
+/*
+ * `sweeps` repetitions of [halo fill of every patch, one coloured Gauss-Seidel sweep of
+ * every patch (colours as in stencil_smooth_coloured, each patch on its own grid with
+ * f_all)].  All patches of a sweep run in one persistent launch; CTAs take patches
+ * largest first.  u_all (in/out), f_all: device FP64 packed arrays.  Asynchronous.
+ */
+int stencil_patch_batch_smooth(stencil_batch_t *b, double *u_all, const double *f_all, int sweeps, void *stream);
+
+/* Times a few launch shapes (threads per CTA x CTAs per SM) on a scratch copy of u_all
+ * and keeps the fastest for later smooth calls.  Host-synchronous; u_all is not
+ * modified.  Returns STENCIL_ENOMEM if the scratch copy cannot be allocated. */
+int stencil_patch_batch_autotune(stencil_batch_t *b, const double *u_all, const double *f_all, void *stream);
+
+/* The launch shape the batch uses (after autotuning, or the default 256 x 4). */
+int stencil_patch_batch_config(const stencil_batch_t *b, int32_t *threads, int32_t *ctas_per_sm);
+
+/* Frees the batch's device tables (not the caller's arrays). */
+int stencil_patch_batch_destroy(stencil_batch_t *b);
 
 /* Frees the internal workspaces of the current device (not thread-safe against
  * concurrent calls on that device). */

@@ -34,6 +34,16 @@ class Grid(ctypes.Structure):
                 ("n", ctypes.c_int64 * 3), ("pitch", ctypes.c_int64), ("h", ctypes.c_double)]
 
 
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("rel_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
+                ("inner_sweeps", ctypes.c_int), ("inner_dtype", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("relres", ctypes.c_double), ("relres_history", ctypes.POINTER(ctypes.c_double))]
+
+
 _lib = None
 
 
@@ -59,6 +69,7 @@ def lib():
             "stencil_residual": (ci, [gp, vp, vp, vp, vp, vp]),
             "stencil_jacobi_step": (ci, [gp, vp, vp, vp, cd, vp]),
             "stencil_residual_noalloc": (ci, [gp, vp, vp, vp, vp, vp]),
+            "stencil_solve": (ci, [gp, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name)
@@ -184,6 +195,31 @@ def stencil_residual_noalloc(u, f, h, norms2, r=None, stream=None):
                                           _ptr(r) if r is not None else ctypes.c_void_p(0),
                                           _ptr(norms2), _stream(stream)))
     return norms2
+
+
+def stencil_solve(u, f, h, rel_tol=1e-10, max_outer=100000, inner_sweeps=8, inner_dtype=F32,
+                  stream=None, history=True):
+    """Iterative refinement on A u = f (u, f float64; u updated in place).  Returns a
+    dict with iterations, converged, relres and (optionally) the relative-residual
+    history.  Raises StencilError except for the not-converged status (-6)."""
+    _same_layout(u, f)
+    if u.dtype != torch.float64:
+        raise ValueError("solve needs float64 u and f")
+    g = grid_for(u, h)
+    opts = SolveOpts(float(rel_tol), int(max_outer), int(inner_sweeps), int(inner_dtype))
+    info = SolveInfo()
+    hist = None
+    if history:
+        hist = (ctypes.c_double * (int(max_outer) + 1))()
+        info.relres_history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
+    rc = lib().stencil_solve(ctypes.byref(g), _ptr(u), _ptr(f), ctypes.byref(opts), ctypes.byref(info),
+                             _stream(stream))
+    if rc not in (0, -6):
+        _check(rc)
+    out = {"iterations": info.iterations, "converged": bool(info.converged), "relres": info.relres}
+    if history:
+        out["history"] = list(hist[:info.iterations + 1])
+    return out
 
 
 def stencil_release_workspace():

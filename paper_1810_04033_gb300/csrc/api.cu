@@ -35,6 +35,8 @@ struct Scratch {
   cudaStream_t stream;
   void *ptr[SCRATCH_SLOTS];
   size_t bytes[SCRATCH_SLOTS];
+  void *host;
+  size_t host_bytes;
 };
 std::mutex g_scratch_mu;
 std::vector<Scratch> g_scratch;
@@ -48,7 +50,7 @@ void *device_scratch(int slot, size_t bytes, cudaStream_t stream) {
   for (auto &e : g_scratch)
     if (e.device == dev && e.stream == stream) s = &e;
   if (!s) {
-    g_scratch.push_back(Scratch{dev, stream, {nullptr}, {0}});
+    g_scratch.push_back(Scratch{dev, stream, {nullptr}, {0}, nullptr, 0});
     s = &g_scratch.back();
   }
   if (s->bytes[slot] >= bytes && s->ptr[slot]) return s->ptr[slot];
@@ -74,6 +76,31 @@ void *device_scratch(int slot, size_t bytes, cudaStream_t stream) {
   return p;
 }
 
+void *host_scratch(size_t bytes, cudaStream_t stream) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  // make sure the set exists
+  if (!device_scratch(SCRATCH_NORMS, 64, stream)) return nullptr;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  for (auto &e : g_scratch) {
+    if (e.device != dev || e.stream != stream) continue;
+    if (e.host && e.host_bytes >= bytes) return e.host;
+    if (e.host) {
+      cudaStreamSynchronize(stream);
+      cudaFreeHost(e.host);
+      e.host = nullptr;
+    }
+    if (cudaMallocHost(&e.host, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      e.host = nullptr;
+      return nullptr;
+    }
+    e.host_bytes = bytes;
+    return e.host;
+  }
+  return nullptr;
+}
+
 static int release_scratch() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
@@ -84,6 +111,7 @@ static int release_scratch() {
     if (it->device == dev) {
       for (int i = 0; i < SCRATCH_SLOTS; ++i)
         if (it->ptr[i]) cudaFree(it->ptr[i]);
+      if (it->host) cudaFreeHost(it->host);
       it = g_scratch.erase(it);
     } else {
       ++it;
@@ -173,13 +201,21 @@ int stencil_smooth_coloured(const stencil_grid_t *g, void *u, const void *f, int
   if (rc) return rc;
   if ((rc = check_ptr(u, g, "u")) || (rc = check_ptr(f, g, "f"))) return rc;
   if (sweeps < 0) return set_error(STENCIL_EINVAL, "sweeps < 0");
-  if (g->dtype != STENCIL_F64) return set_error(STENCIL_EINVAL, "smooth_coloured supports F64 only");
+  if (g->dtype != STENCIL_F64 && g->dim != 3)
+    return set_error(STENCIL_EINVAL, "smooth_coloured: F32/BF16 storage is 3D only");
   const Geo q = make_geo(*g);
-  if (overlap(u, f, (size_t)span_elems(q) * 8)) return set_error(STENCIL_EINVAL, "u and f overlap");
+  const size_t esz = elem_size(g->dtype);
+  if (overlap(u, f, (size_t)span_elems(q) * esz)) return set_error(STENCIL_EINVAL, "u and f overlap");
   if (sweeps == 0) return STENCIL_OK;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
-  if (g->dim == 3) {
+  if (g->dtype != STENCIL_F64) {
+    void *work = device_scratch(SCRATCH_LP, (size_t)span_elems(q) * esz, s);
+    if (!work) return set_error(STENCIL_ENOMEM, "smooth_coloured workspace allocation failed");
+    e = g->dtype == STENCIL_F32
+            ? launch_gs_sweeps_f32_3d(q, (float *)u, (const float *)f, sweeps, (float *)work, s)
+            : launch_gs_sweeps_bf16_3d(q, u, f, sweeps, work, s);
+  } else if (g->dim == 3) {
     void *work = device_scratch(SCRATCH_PINGPONG, 3 * (size_t)span_elems(q) * 8, s);
     void *bnd = device_scratch(SCRATCH_BOUNDS, gs_fx_bounds_bytes(), s);
     if (!work || !bnd) return set_error(STENCIL_ENOMEM, "smooth_coloured workspace allocation failed");
@@ -268,6 +304,82 @@ int stencil_residual(const stencil_grid_t *g, const void *u, const void *f, void
                   : launch_residual_fx2(q, (const double *)u, (const double *)f, (double *)r, d_norms2,
                                         scratch, (cudaStream_t)stream);
   if (e != cudaSuccess) return set_error(STENCIL_ECUDA, std::string("residual: ") + cudaGetErrorString(e));
+  return STENCIL_OK;
+}
+
+int stencil_solve(const stencil_grid_t *g, double *u, const double *f, const stencil_solve_opts_t *opts,
+                  stencil_solve_info_t *info, void *stream) {
+  int rc = check_grid(g);
+  if (rc) return rc;
+  if (g->dtype != STENCIL_F64) return set_error(STENCIL_EINVAL, "solve: u and f must be F64");
+  if ((rc = check_ptr(u, g, "u")) || (rc = check_ptr(f, g, "f"))) return rc;
+  if (!opts) return set_error(STENCIL_EINVAL, "solve: opts is NULL");
+  if (!(opts->rel_tol >= 0.0) || opts->max_outer < 0 || opts->inner_sweeps < 1)
+    return set_error(STENCIL_EINVAL, "solve: need rel_tol >= 0, max_outer >= 0, inner_sweeps >= 1");
+  const int inner = opts->inner_dtype;
+  if (inner != STENCIL_F64 && inner != STENCIL_F32 && inner != STENCIL_BF16)
+    return set_error(STENCIL_EINVAL, "solve: unknown inner_dtype");
+  if (inner != STENCIL_F64 && g->dim != 3)
+    return set_error(STENCIL_EINVAL, "solve: FP32/BF16 inner sweeps are 3D only");
+  const Geo q = make_geo(*g);
+  const size_t span = (size_t)span_elems(q);
+  if (overlap(u, f, span * 8)) return set_error(STENCIL_EINVAL, "u and f overlap");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t esz = elem_size(inner);
+  void *r = device_scratch(SCRATCH_SOLVE_R, span * esz, s);
+  void *e = device_scratch(SCRATCH_SOLVE_E, span * esz, s);
+  double *dn = (double *)device_scratch(SCRATCH_NORMS, 64, s);
+  const size_t red = g->dim == 3 ? ops_fx_reduce_bytes(q) : ops2_reduce_bytes(q);
+  void *red_scr = device_scratch(SCRATCH_REDUCE, red, s);
+  double *hn = (double *)host_scratch(64, s);
+  void *work = nullptr;
+  if (inner == STENCIL_F64)
+    work = device_scratch(SCRATCH_PINGPONG, (g->dim == 3 ? 3 : 1) * span * 8, s);
+  else
+    work = device_scratch(SCRATCH_LP, span * esz, s);
+  void *bnd = g->dim == 3 ? device_scratch(SCRATCH_BOUNDS, gs_fx_bounds_bytes(), s) : (void *)1;
+  if (!r || !e || !dn || !red_scr || !hn || !work || !bnd)
+    return set_error(STENCIL_ENOMEM, "solve: workspace allocation failed");
+  const int out_kind = inner == STENCIL_F64 ? 0 : (inner == STENCIL_F32 ? 1 : 2);
+  int k = 0;
+  double rho = 0.0;
+  bool conv = false;
+  for (;;) {
+    cudaError_t ce = g->dim == 3
+                         ? launch_residual_fx3(q, u, f, (double *)r, dn, red_scr, s, out_kind)
+                         : launch_residual_fx2(q, u, f, (double *)r, dn, red_scr, s);
+    if (!ce) ce = cudaMemcpyAsync(hn, dn, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (!ce) ce = cudaStreamSynchronize(s);
+    if (ce) return set_error(STENCIL_ECUDA, std::string("solve: ") + cudaGetErrorString(ce));
+    rho = hn[1] > 0.0 ? std::sqrt(hn[0]) / std::sqrt(hn[1]) : std::sqrt(hn[0]);
+    if (info && info->relres_history) info->relres_history[k] = rho;
+    if (rho <= opts->rel_tol) {
+      conv = true;
+      break;
+    }
+    if (k >= opts->max_outer) break;
+    ce = cudaMemsetAsync(e, 0, span * esz, s);
+    if (!ce) {
+      if (inner == STENCIL_F64)
+        ce = g->dim == 3 ? launch_gs_sweeps_fx3(q, (double *)e, (const double *)r, opts->inner_sweeps,
+                                                (double *)work, bnd, s)
+                         : launch_gs_sweeps_fx2(q, (double *)e, (const double *)r, opts->inner_sweeps,
+                                                (double *)work, s);
+      else if (inner == STENCIL_F32)
+        ce = launch_gs_sweeps_f32_3d(q, (float *)e, (const float *)r, opts->inner_sweeps, (float *)work, s);
+      else
+        ce = launch_gs_sweeps_bf16_3d(q, e, r, opts->inner_sweeps, work, s);
+    }
+    if (!ce) ce = launch_add_correction(q, g->dim, u, e, inner, s);
+    if (ce) return set_error(STENCIL_ECUDA, std::string("solve: ") + cudaGetErrorString(ce));
+    ++k;
+  }
+  if (info) {
+    info->iterations = k;
+    info->converged = conv ? 1 : 0;
+    info->relres = rho;
+  }
+  if (!conv) return set_error(STENCIL_ENOTCONV, "solve: max_outer reached before rel_tol");
   return STENCIL_OK;
 }
 

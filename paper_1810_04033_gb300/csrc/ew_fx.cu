@@ -13,11 +13,12 @@
 // A CTA owns 60 x 32 (x, y) output vertices and a chunk of 32 vertex planes.  It streams
 // cell layers k = z0-1, z0, ...: layer k lies between vertex planes k and k+1, whose
 // values sit in shared memory (with a 1-vertex halo), together with two int64
-// accumulator planes.  Inside a layer the cells are processed in four colour passes
-// (x parity, y parity; the layer fixes the z parity), separated by barriers: cells of
-// one colour share no vertex, so the read-modify-write of the accumulators needs no
-// atomics.  After layer k, vertex plane k has received all 8 contributions and is
-// written out.  The fixed-point reference is the per-CTA monotone scheme of ops_fx.cu.
+// accumulator planes.  The race of the scatter is resolved by colours: the z parity by
+// processing layers in order, the y parity by two passes per layer separated by
+// barriers, the x parity inside each warp (neighbouring cells' shared vertices are
+// combined through a shuffle, see scatter_layer).  After layer k, vertex plane k has
+// received all 8 contributions and is written out.  The fixed-point reference is the
+// per-CTA monotone scheme of ops_fx.cu.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -56,9 +57,9 @@ __device__ __forceinline__ long long sub(long long a, long long b) {
 }
 
 template <bool FIX>
-__device__ __forceinline__ long long times5(long long a) {
-  if (FIX) return (a << 2) + a;
-  return __double_as_longlong(5.0 * __longlong_as_double(a));
+__device__ __forceinline__ long long times4(long long a) {
+  if (FIX) return a << 2;
+  return __double_as_longlong(4.0 * __longlong_as_double(a));
 }
 
 __device__ __forceinline__ void prefetch_vplane(double (&v)[E_PER], const Geo &q, const double *src,
@@ -91,48 +92,59 @@ __device__ __forceinline__ int cta_max_exponent(const double (&v)[E_PER], int *r
   return r;
 }
 
-// The four colour passes of cell layer k (between vertex planes k and k+1).
+// Cell layer k (between vertex planes k and k+1).  A warp takes one row of 32
+// consecutive cells (local cells lcx = 30 seg + lane); each lane computes its cell's 8
+// contributions: with bottom-face values b_i (plane k) and top-face values t_i (plane
+// k+1), i = 0 (x,y), 1 (x+1,y), 2 (x,y+1), 3 (x+1,y+1), and face sums Sb, St,
+//   12 (K u)_{b_i} = 4 b_i - b_{i^3} + t_i - St,   12 (K u)_{t_i} = 4 t_i - t_{i^3} + b_i - Sb.
+// The right-hand vertices' contributions move to the next lane by a shuffle (the two x
+// colours of the row meet in registers), so each output lane adds the sums for its own
+// vertex column into the shared accumulators of vertex rows y and y+1 of both planes.
+// Cell rows of one y parity share no vertex row: the two y colours are separate
+// passes with a barrier between them; layers run in z order.
 template <bool FIX>
 __device__ void scatter_layer(const Geo &q, int64_t k, int x0, int y0, const long long *ulo,
                               const long long *uhi, long long *alo, long long *ahi) {
   if (k < 0 || k >= q.nz) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int colour = 0; colour < 4; ++colour) {
-    const int px = colour & 1, py = colour >> 1;
-    // local cell (lcx, lcy) covers local vertices (lcx..lcx+1, lcy..lcy+1); its global
-    // cell index is (x0 - 1 + lcx, y0 - 1 + lcy)
-    const int lcx0 = ((x0 - 1) & 1) == px ? 0 : 1;
+  for (int py = 0; py < 2; ++py) {
     const int lcy0 = ((y0 - 1) & 1) == py ? 0 : 1;
-    const int lcx = lcx0 + 2 * lane;  // lanes 0..30 cover local cells up to 61
-    const int cx = x0 - 1 + lcx;
-    const bool xok = lcx < ET_X + 1 && cx >= 0 && cx < q.nx;
-    for (int lcy = lcy0 + 2 * warp; lcy < ET_Y + 1; lcy += 2 * (E_THREADS / 32)) {
-      const int cy = y0 - 1 + lcy;
-      if (!xok || cy < 0 || cy >= q.ny) continue;
-      const int i00 = lcy * ES_W + lcx, i10 = i00 + ES_W;
-      long long v[8];
-      v[0] = ulo[i00];
-      v[1] = ulo[i00 + 1];
-      v[2] = ulo[i10];
-      v[3] = ulo[i10 + 1];
-      v[4] = uhi[i00];
-      v[5] = uhi[i00 + 1];
-      v[6] = uhi[i10];
-      v[7] = uhi[i10 + 1];
-      const long long T = add<FIX>(add<FIX>(add<FIX>(v[0], v[1]), add<FIX>(v[2], v[3])),
-                                   add<FIX>(add<FIX>(v[4], v[5]), add<FIX>(v[6], v[7])));
-      long long c[8];
-#pragma unroll
-      for (int w = 0; w < 8; ++w)
-        c[w] = sub<FIX>(add<FIX>(times5<FIX>(v[w]), add<FIX>(add<FIX>(v[w ^ 1], v[w ^ 2]), v[w ^ 4])), T);
-      alo[i00] = add<FIX>(alo[i00], c[0]);
-      alo[i00 + 1] = add<FIX>(alo[i00 + 1], c[1]);
-      alo[i10] = add<FIX>(alo[i10], c[2]);
-      alo[i10 + 1] = add<FIX>(alo[i10 + 1], c[3]);
-      ahi[i00] = add<FIX>(ahi[i00], c[4]);
-      ahi[i00 + 1] = add<FIX>(ahi[i00 + 1], c[5]);
-      ahi[i10] = add<FIX>(ahi[i10], c[6]);
-      ahi[i10 + 1] = add<FIX>(ahi[i10 + 1], c[7]);
+    // tasks: (cell row, segment); rows lcy = lcy0, lcy0 + 2, ... < ET_Y + 1
+    const int nrows = (ET_Y + 1 - lcy0 + 1) / 2;
+    for (int task = warp; task < 2 * nrows; task += E_THREADS / 32) {
+      const int lcy = lcy0 + 2 * (task >> 1), seg = task & 1;
+      const int lcx = 30 * seg + lane;  // local cell; covers vertex columns lcx, lcx+1
+      const int cx = x0 - 1 + lcx, cy = y0 - 1 + lcy;
+      const int i0 = lcy * ES_W + lcx, i1 = i0 + ES_W;
+      const long long b0 = ulo[i0], b2 = ulo[i1], t0 = uhi[i0], t2 = uhi[i1];
+      const long long b1 = __shfl_down_sync(0xffffffffu, b0, 1);
+      const long long b3 = __shfl_down_sync(0xffffffffu, b2, 1);
+      const long long t1 = __shfl_down_sync(0xffffffffu, t0, 1);
+      const long long t3 = __shfl_down_sync(0xffffffffu, t2, 1);
+      const bool cell = lane <= 30 && cx >= 0 && cx < q.nx && cy >= 0 && cy < q.ny;
+      long long cb0 = 0, cb1 = 0, cb2 = 0, cb3 = 0, ct0 = 0, ct1 = 0, ct2 = 0, ct3 = 0;
+      if (cell) {
+        const long long Sb = add<FIX>(add<FIX>(b0, b1), add<FIX>(b2, b3));
+        const long long St = add<FIX>(add<FIX>(t0, t1), add<FIX>(t2, t3));
+        cb0 = add<FIX>(sub<FIX>(times4<FIX>(b0), b3), sub<FIX>(t0, St));
+        cb1 = add<FIX>(sub<FIX>(times4<FIX>(b1), b2), sub<FIX>(t1, St));
+        cb2 = add<FIX>(sub<FIX>(times4<FIX>(b2), b1), sub<FIX>(t2, St));
+        cb3 = add<FIX>(sub<FIX>(times4<FIX>(b3), b0), sub<FIX>(t3, St));
+        ct0 = add<FIX>(sub<FIX>(times4<FIX>(t0), t3), sub<FIX>(b0, Sb));
+        ct1 = add<FIX>(sub<FIX>(times4<FIX>(t1), t2), sub<FIX>(b1, Sb));
+        ct2 = add<FIX>(sub<FIX>(times4<FIX>(t2), t1), sub<FIX>(b2, Sb));
+        ct3 = add<FIX>(sub<FIX>(times4<FIX>(t3), t0), sub<FIX>(b3, Sb));
+      }
+      // the left neighbour's right-hand contributions land on this lane's column
+      const long long lb1 = __shfl_up_sync(0xffffffffu, cb1, 1);
+      const long long lb3 = __shfl_up_sync(0xffffffffu, cb3, 1);
+      const long long lt1 = __shfl_up_sync(0xffffffffu, ct1, 1);
+      const long long lt3 = __shfl_up_sync(0xffffffffu, ct3, 1);
+      if (lane < 1 || lane > 30) continue;
+      alo[i0] = add<FIX>(alo[i0], add<FIX>(cb0, lb1));
+      alo[i1] = add<FIX>(alo[i1], add<FIX>(cb2, lb3));
+      ahi[i0] = add<FIX>(ahi[i0], add<FIX>(ct0, lt1));
+      ahi[i1] = add<FIX>(ahi[i1], add<FIX>(ct2, lt3));
     }
     __syncthreads();
   }

@@ -39,7 +39,18 @@ int check_launch(const char *what);
 // pointer with at least `bytes` bytes for slot `slot`, growing with cudaMalloc when
 // needed (zero-filled when allocated); nullptr on failure.  Work queued on one stream
 // therefore never shares scratch with work on another stream.
-enum ScratchSlot { SCRATCH_REDUCE = 0, SCRATCH_PINGPONG = 1, SCRATCH_BOUNDS = 2, SCRATCH_SLOTS = 4 };
+enum ScratchSlot {
+  SCRATCH_REDUCE = 0,
+  SCRATCH_PINGPONG = 1,
+  SCRATCH_BOUNDS = 2,
+  SCRATCH_LP = 3,      // reduced-precision GS ping-pong
+  SCRATCH_SOLVE_R = 4, // refinement: residual in the inner type
+  SCRATCH_SOLVE_E = 5, // refinement: correction
+  SCRATCH_NORMS = 6,   // refinement: device norms
+  SCRATCH_SLOTS = 8
+};
+// Pinned host scratch of the (device, stream) set.
+void *host_scratch(size_t bytes, cudaStream_t stream);
 void *device_scratch(int slot, size_t bytes, cudaStream_t stream);
 
 // Kernel launchers (kernels_*.cu).  Return cudaGetLastError() of the launch.
@@ -82,7 +93,18 @@ cudaError_t launch_residual_fx2(const Geo &q, const double *u, const double *f, 
                                 void *scratch, cudaStream_t s);
 cudaError_t launch_gs_sweeps_fx2(const Geo &q, double *u, const double *f, int sweeps, double *work,
                                  cudaStream_t s);
+// out_kind: r stored as 0 = FP64, 1 = FP32, 2 = bf16 (r is an element pointer of that
+// type passed as double*; the layout is u's).
 cudaError_t launch_residual_fx3(const Geo &q, const double *u, const double *f, double *r,
-                                double *norms2, void *scratch, cudaStream_t s);
+                                double *norms2, void *scratch, cudaStream_t s, int out_kind = 0);
+
+// Reduced-precision coloured GS, 3D (gs_lp.cu): work has u's span of the same type.
+cudaError_t launch_gs_sweeps_f32_3d(const Geo &q, float *u, const float *f, int sweeps, float *work,
+                                    cudaStream_t s);
+cudaError_t launch_gs_sweeps_bf16_3d(const Geo &q, void *u, const void *f, int sweeps, void *work,
+                                     cudaStream_t s);
+
+// x += e on interior vertices, e of element type dtype (solve.cu).
+cudaError_t launch_add_correction(const Geo &q, int dim, double *x, const void *e, int dtype, cudaStream_t s);
 
 }  // namespace stencil

@@ -91,6 +91,169 @@ __device__ __forceinline__ long long eight_u_minus_n(long long m, long long c, l
   return __double_as_longlong(fma(8.0, __longlong_as_double(c), -__longlong_as_double(N)));
 }
 
+constexpr int PF = 3;  // rows in flight per warp
+
+// Per-warp streaming state of k_ops2.
+struct Stream2 {
+  int64_t x;
+  bool xok, xin, out_lane;
+  int lane;
+  long long um, uc, up;  // converted rows j-1, j, j+1 (element-wise: ua = uc, acc = um/up)
+  double rc, rp;         // raw rows j, j+1
+  double rr, ff;
+};
+
+// Element-wise apply: cell rows cj in [cj0, je); returns the first row not done (a
+// switch to FP64 was requested) or je.
+template <bool FIX>
+__device__ __forceinline__ int64_t ew2_rows(const Op2Args &a, WarpScale &w, Stream2 &s, int64_t cj0, int64_t js,
+                                            int64_t je) {
+  const Geo &q = a.q;
+  const double *ucol = a.u + (s.xok ? s.x : 0);
+  long long &ua = s.uc, &alo = s.um, &ahi = s.up;
+  double qb[PF];  // qb[t]: raw vertex row cj + 1 for the iteration cj = cb + t
+#pragma unroll
+  for (int t = 0; t < PF; ++t)
+    qb[t] = (s.xok && cj0 + 1 + t <= q.ny && cj0 + 1 + t >= 0) ? ucol[(cj0 + 1 + t) * q.pitch] : 0.0;
+  for (int64_t cb = cj0; cb < je; cb += PF) {
+#pragma unroll
+    for (int t = 0; t < PF; ++t) {
+      const int64_t cj = cb + t;
+      if (cj >= je) return je;
+      const int slot = t;
+      const double rb = qb[slot];
+      const unsigned em = __reduce_max_sync(0xffffffffu, biased_exp(rb));
+      if (FIX) {
+        const int d = admit_row(w, em, 1);
+        if (d < 0) {  // leave this row to the FP64 loop
+          ua = to_f64_bits(ua, w.R);
+          alo = to_f64_bits(alo, w.R);
+          ahi = to_f64_bits(ahi, w.R);
+          w.fix = false;
+          return cj;
+        }
+        if (d > 0) {
+          ua = shr(ua, d);
+          alo = shr(alo, d);
+          ahi = shr(ahi, d);
+        }
+      }
+      qb[slot] = (cj + 1 + PF <= je && s.xok && cj + 1 + PF <= q.ny) ? ucol[(cj + 1 + PF) * q.pitch] : 0.0;
+      const long long ub = FIX ? fx::to_fixed(rb, 1023 + w.R) : __double_as_longlong(rb);
+      // cell with lower-left vertex (x, cj): v0 = (x,cj), v1 = (x+1,cj), v2 = (x,cj+1),
+      // v3 = (x+1,cj+1); 6 (K u)_w = 4 u_w - (face-adjacent pair) - 2 u_opposite
+      const long long v1 = __shfl_down_sync(0xffffffffu, ua, 1);
+      const long long v3 = __shfl_down_sync(0xffffffffu, ub, 1);
+      const bool cell = s.lane <= 30 && s.x >= 0 && s.x < q.nx && cj >= 0 && cj < q.ny;
+      // two colour passes over the x parity; the right-hand vertices' shares move to
+      // the next lane
+#pragma unroll
+      for (int px = 0; px < 2; ++px) {
+        const bool mine = cell && (int)(s.x & 1) == px;
+        long long c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+        if (mine) {
+          if (FIX) {
+            c0 = 4 * ua - (v1 + ub) - 2 * v3;
+            c1 = 4 * v1 - (ua + v3) - 2 * ub;
+            c2 = 4 * ub - (ua + v3) - 2 * v1;
+            c3 = 4 * v3 - (v1 + ub) - 2 * ua;
+          } else {
+            const double A0 = __longlong_as_double(ua), A1 = __longlong_as_double(v1),
+                         A2 = __longlong_as_double(ub), A3 = __longlong_as_double(v3);
+            c0 = __double_as_longlong(4.0 * A0 - (A1 + A2) - 2.0 * A3);
+            c1 = __double_as_longlong(4.0 * A1 - (A0 + A3) - 2.0 * A2);
+            c2 = __double_as_longlong(4.0 * A2 - (A0 + A3) - 2.0 * A1);
+            c3 = __double_as_longlong(4.0 * A3 - (A1 + A2) - 2.0 * A0);
+          }
+        }
+        const long long c1l = __shfl_up_sync(0xffffffffu, c1, 1);
+        const long long c3l = __shfl_up_sync(0xffffffffu, c3, 1);
+        alo = add<FIX>(alo, add<FIX>(c0, s.lane >= 1 ? c1l : 0));
+        ahi = add<FIX>(ahi, add<FIX>(c2, s.lane >= 1 ? c3l : 0));
+      }
+      if (cj >= js && s.out_lane) {
+        const bool inner = s.xin && cj >= 1 && cj < q.ny;
+        const double sv = FIX ? fx::to_double(alo, w.R - fx::FRAC) : __longlong_as_double(alo);
+        a.out[cj * q.pitch + s.x] = inner ? sv * a.c1 : 0.0;
+      }
+      alo = ahi;
+      ahi = 0;
+      ua = ub;
+    }
+  }
+  return je;
+}
+
+// Assembled apply / Jacobi / residual: output rows j in [j0, je).
+template <bool FIX, int OP>
+__device__ __forceinline__ int64_t op2_rows(const Op2Args &a, WarpScale &w, Stream2 &s, int64_t j0, int64_t js,
+                                            int64_t je) {
+  const Geo &q = a.q;
+  const double *ucol = a.u + (s.xok ? s.x : 0);
+  const double *fcol = a.f ? a.f + (s.xok ? s.x : 0) : nullptr;
+  double *ocol = a.out ? a.out + (s.xok ? s.x : 0) : nullptr;
+  double qb[PF];  // qb[t]: raw row j + 2 for the iteration j = jb + t
+#pragma unroll
+  for (int t = 0; t < PF; ++t) qb[t] = (s.xok && j0 + 2 + t <= q.ny) ? ucol[(j0 + 2 + t) * q.pitch] : 0.0;
+  for (int64_t jb = j0; jb < je; jb += PF) {
+#pragma unroll
+    for (int t = 0; t < PF; ++t) {
+      const int64_t j = jb + t;
+      if (j >= je) return je;
+      const int slot = t;
+      const double rn = qb[slot];  // row j + 2
+      const unsigned em = __reduce_max_sync(0xffffffffu, biased_exp(rn));
+      const bool inner = s.xin && j >= 1 && j < q.ny;
+      double fv = 0.0;
+      if (OP != O2_APPLY && s.out_lane && inner) fv = fcol[j * q.pitch];
+      const long long T = eight_u_minus_n<FIX>(s.um, s.uc, s.up);
+      if (s.out_lane) {
+        const double Td = inner ? (FIX ? fx::to_double(T, w.R - fx::FRAC) : __longlong_as_double(T)) : 0.0;
+        const int64_t go = j * q.pitch;
+        if (OP == O2_APPLY) {
+          ocol[go] = inner ? Td * a.c1 : 0.0;
+        } else if (OP == O2_JACOBI) {
+          ocol[go] = inner ? fma(a.c2, Td, fma(a.c1, fv, s.rc)) : s.rc;
+        } else {
+          const double r = inner ? fma(a.c1, Td, fv) : 0.0;
+          if (ocol) ocol[go] = r;
+          if (inner) {
+            s.rr = fma(r, r, s.rr);
+            s.ff = fma(fv, fv, s.ff);
+          }
+        }
+      }
+      // admit row j + 2 (after row j is done)
+      if (FIX) {
+        const int d = admit_row(w, em, 1);
+        if (d < 0) {
+          s.uc = to_f64_bits(s.uc, w.R);
+          s.up = to_f64_bits(s.up, w.R);
+          w.fix = false;
+          // row j is finished; rows j+1, j+2 continue in FP64 (rn still in the queue)
+          s.um = s.uc;
+          s.uc = s.up;
+          s.up = __double_as_longlong(rn);
+          s.rc = s.rp;
+          s.rp = rn;
+          return j + 1;
+        }
+        if (d > 0) {
+          s.uc = shr(s.uc, d);
+          s.up = shr(s.up, d);
+        }
+      }
+      qb[slot] = (j + 2 + PF <= je && s.xok && j + 2 + PF <= q.ny) ? ucol[(j + 2 + PF) * q.pitch] : 0.0;
+      s.um = s.uc;
+      s.uc = s.up;
+      s.up = FIX ? fx::to_fixed(rn, 1023 + w.R) : __double_as_longlong(rn);
+      s.rc = s.rp;
+      s.rp = rn;
+    }
+  }
+  return je;
+}
+
 template <int OP>
 __global__ void __launch_bounds__(W2_THREADS) k_ops2(Op2Args a) {
   __shared__ double sh[2 * W2_THREADS / 32];
@@ -102,131 +265,44 @@ __global__ void __launch_bounds__(W2_THREADS) k_ops2(Op2Args a) {
   const int64_t seg = gw % nseg, chunk = gw / nseg;
   const int64_t js = chunk * W2_ROWS;
   const int64_t je = js + W2_ROWS < q.ny + 1 ? js + W2_ROWS : q.ny + 1;
-  const int64_t x = seg * 30 + lane - 1;  // lanes 1..30 produce outputs
-  const bool xok = x >= 0 && x <= q.nx;
-  const bool xin = x >= 1 && x < q.nx;
-  const bool out_lane = lane >= 1 && lane <= 30 && xok;
-  double rr = 0.0, ff = 0.0;
+  Stream2 s;
+  s.lane = lane;
+  s.x = seg * 30 + lane - 1;  // lanes 1..30 produce outputs
+  s.xok = s.x >= 0 && s.x <= q.nx;
+  s.xin = s.x >= 1 && s.x < q.nx;
+  s.out_lane = lane >= 1 && lane <= 30 && s.xok;
+  s.rr = 0.0;
+  s.ff = 0.0;
   WarpScale w;
   if (js <= q.ny) {
-    auto load = [&](int64_t j) -> double {
-      return (xok && j >= 0 && j <= q.ny) ? a.u[j * q.pitch + x] : 0.0;
-    };
+    const double *ucol = a.u + (s.xok ? s.x : 0);
+    auto load = [&](int64_t j) -> double { return (s.xok && j >= 0 && j <= q.ny) ? ucol[j * q.pitch] : 0.0; };
     if (OP == O2_ELEMENTWISE) {
-      // stream cell rows cj = js-1 .. je-1; vertex row cj is complete after cell row cj
-      double ra = load(js - 1);
-      int d = admit_row(w, __reduce_max_sync(0xffffffffu, biased_exp(ra)), 1);
-      if (d < 0) w.fix = false;
-      long long ua = enc(w, ra), alo = 0, ahi = 0;
-      double rb_next = load(js);
-      for (int64_t cj = js - 1; cj < je; ++cj) {
-        const double rb = rb_next;
-        if (cj + 2 <= je) rb_next = load(cj + 2);
-        d = admit_row(w, __reduce_max_sync(0xffffffffu, biased_exp(rb)), 1);
-        if (d < 0) {
-          ua = to_f64_bits(ua, w.R);
-          alo = to_f64_bits(alo, w.R);
-          ahi = to_f64_bits(ahi, w.R);
-          w.fix = false;
-        } else if (d > 0) {
-          ua = shr(ua, d);
-          alo = shr(alo, d);
-          ahi = shr(ahi, d);
-        }
-        const long long ub = enc(w, rb);
-        // the cell with lower-left vertex (x, cj): v0 = (x,cj), v1 = (x+1,cj),
-        // v2 = (x,cj+1), v3 = (x+1,cj+1); two colour passes over the x parity
-        const long long v1 = __shfl_down_sync(0xffffffffu, ua, 1);
-        const long long v3 = __shfl_down_sync(0xffffffffu, ub, 1);
-        const bool cell = lane <= 30 && x >= 0 && x < q.nx && cj >= 0 && cj < q.ny;
-        for (int px = 0; px < 2; ++px) {
-          const bool mine = cell && (int)(x & 1) == px;
-          long long c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-          if (mine) {
-            if (w.fix) {
-              c0 = 4 * ua - (v1 + ub) - 2 * v3;
-              c1 = 4 * v1 - (ua + v3) - 2 * ub;
-              c2 = 4 * ub - (ua + v3) - 2 * v1;
-              c3 = 4 * v3 - (v1 + ub) - 2 * ua;
-            } else {
-              const double A0 = __longlong_as_double(ua), A1 = __longlong_as_double(v1),
-                           A2 = __longlong_as_double(ub), A3 = __longlong_as_double(v3);
-              c0 = __double_as_longlong(4.0 * A0 - (A1 + A2) - 2.0 * A3);
-              c1 = __double_as_longlong(4.0 * A1 - (A0 + A3) - 2.0 * A2);
-              c2 = __double_as_longlong(4.0 * A2 - (A0 + A3) - 2.0 * A1);
-              c3 = __double_as_longlong(4.0 * A3 - (A1 + A2) - 2.0 * A0);
-            }
-          }
-          // contributions to the right-hand vertices go to the next lane
-          const long long c1l = __shfl_up_sync(0xffffffffu, c1, 1);
-          const long long c3l = __shfl_up_sync(0xffffffffu, c3, 1);
-          if (w.fix) {
-            alo += c0 + (lane >= 1 ? c1l : 0);
-            ahi += c2 + (lane >= 1 ? c3l : 0);
-          } else {
-            alo = add<false>(alo, add<false>(c0, lane >= 1 ? c1l : 0));
-            ahi = add<false>(ahi, add<false>(c2, lane >= 1 ? c3l : 0));
-          }
-        }
-        if (cj >= js && out_lane) {
-          const bool inner = xin && cj >= 1 && cj < q.ny;
-          const double s = w.fix ? fx::to_double(alo, w.R - fx::FRAC) : __longlong_as_double(alo);
-          a.out[cj * q.pitch + x] = inner ? s * a.c1 : 0.0;
-        }
-        alo = ahi;
-        ahi = 0;
-        ua = ub;
-      }
+      const double ra = load(js - 1);
+      if (admit_row(w, __reduce_max_sync(0xffffffffu, biased_exp(ra)), 1) < 0) w.fix = false;
+      s.uc = w.fix ? fx::to_fixed(ra, 1023 + w.R) : __double_as_longlong(ra);
+      s.um = 0;
+      s.up = 0;
+      int64_t cj = js - 1;
+      if (w.fix) cj = ew2_rows<true>(a, w, s, cj, js, je);
+      if (cj < je) ew2_rows<false>(a, w, s, cj, js, je);
     } else {
-      // rows j-1, j, j+1 in registers; j+2 in flight
-      double rm = load(js - 1), rc = load(js), rp = load(js + 1);
+      s.rc = load(js);
+      s.rp = load(js + 1);
+      const double rm = load(js - 1);
       unsigned em = __reduce_max_sync(0xffffffffu, biased_exp(rm));
-      em = max(em, __reduce_max_sync(0xffffffffu, biased_exp(rc)));
-      em = max(em, __reduce_max_sync(0xffffffffu, biased_exp(rp)));
+      em = max(em, __reduce_max_sync(0xffffffffu, biased_exp(s.rc)));
+      em = max(em, __reduce_max_sync(0xffffffffu, biased_exp(s.rp)));
       if (admit_row(w, em, 1) < 0) w.fix = false;
-      long long um = enc(w, rm), uc = enc(w, rc), up = enc(w, rp);
-      double rn = load(js + 2);
-      for (int64_t j = js; j < je; ++j) {
-        double fv = 0.0;
-        const bool inner = xin && j >= 1 && j < q.ny;
-        if (OP != O2_APPLY && out_lane && inner) fv = a.f[j * q.pitch + x];
-        const long long T = w.fix ? eight_u_minus_n<true>(um, uc, up) : eight_u_minus_n<false>(um, uc, up);
-        if (out_lane) {
-          const double Td = inner ? (w.fix ? fx::to_double(T, w.R - fx::FRAC) : __longlong_as_double(T)) : 0.0;
-          const int64_t gp = j * q.pitch + x;
-          if (OP == O2_APPLY) {
-            a.out[gp] = inner ? Td * a.c1 : 0.0;
-          } else if (OP == O2_JACOBI) {
-            a.out[gp] = inner ? fma(a.c2, Td, fma(a.c1, fv, rc)) : rc;
-          } else {
-            const double r = inner ? fma(a.c1, Td, fv) : 0.0;
-            if (a.out) a.out[gp] = r;
-            if (inner) {
-              rr = fma(r, r, rr);
-              ff = fma(fv, fv, ff);
-            }
-          }
-        }
-        // advance: admit row j+2
-        const double rnn = (j + 3 <= je) ? load(j + 3) : 0.0;
-        const int d = admit_row(w, __reduce_max_sync(0xffffffffu, biased_exp(rn)), 1);
-        if (d < 0) {
-          uc = to_f64_bits(uc, w.R);
-          up = to_f64_bits(up, w.R);
-          w.fix = false;
-        } else if (d > 0) {
-          uc = shr(uc, d);
-          up = shr(up, d);
-        }
-        um = uc;
-        uc = up;
-        up = enc(w, rn);
-        rc = rp;
-        rp = rn;
-        rn = rnn;
-      }
+      s.um = w.fix ? fx::to_fixed(rm, 1023 + w.R) : __double_as_longlong(rm);
+      s.uc = w.fix ? fx::to_fixed(s.rc, 1023 + w.R) : __double_as_longlong(s.rc);
+      s.up = w.fix ? fx::to_fixed(s.rp, 1023 + w.R) : __double_as_longlong(s.rp);
+      int64_t j = js;
+      if (w.fix) j = op2_rows<true, OP>(a, w, s, j, js, je);
+      if (j < je) op2_rows<false, OP>(a, w, s, j, js, je);
     }
   }
+  double rr = s.rr, ff = s.ff;
   if (OP == O2_RESIDUAL) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -294,6 +370,89 @@ unsigned ops2_blocks(const Geo &q) {
 // Inside a row the even-x colour is updated first; the odd-x colour then reads it
 // through shuffles, so a warp produces columns for lanes 2..29 (28 per segment).
 // u_new = 3/8 h^2 f + N/8.
+struct GsLane {
+  int64_t x;
+  bool xok, xin, out_lane;
+  long long um;  // converted row j - 1
+};
+
+template <bool FIX>
+__device__ __forceinline__ int64_t gs2_rows(const Geo &q, int pr, const double *__restrict__ X,
+                                            const double *__restrict__ N, double *__restrict__ Y,
+                                            const double *__restrict__ f, double g, WarpScale &w, GsLane &L,
+                                            int64_t i0, int64_t i1) {
+  constexpr int PG = 3;  // centre rows in flight
+  auto ld = [&](const double *p, int64_t j) -> double {
+    return (L.xok && j >= 0 && j <= q.ny) ? p[j * q.pitch + L.x] : 0.0;
+  };
+  auto ldf = [&](int64_t j) -> double { return (L.xin && j >= 1 && j < q.ny) ? f[j * q.pitch + L.x] : 0.0; };
+  double qx[PG], qn[PG], qf[PG];
+#pragma unroll
+  for (int t = 0; t < PG; ++t) {
+    const int64_t j = pr + 2 * (i0 + t);
+    const bool ok = i0 + t < i1;
+    qx[t] = ok ? ld(X, j) : 0.0;
+    qn[t] = ok ? ld(N, j + 1) : 0.0;
+    qf[t] = ok ? ldf(j) : 0.0;
+  }
+  for (int64_t ib = i0; ib < i1; ib += PG) {
+#pragma unroll
+    for (int t = 0; t < PG; ++t) {
+      const int64_t i = ib + t;
+      if (i >= i1) return i1;
+      const int64_t j = pr + 2 * i;
+      const double rc = qx[t], rp = qn[t], fv = qf[t];
+      if (FIX) {
+        unsigned em = __reduce_max_sync(0xffffffffu, biased_exp(rc));
+        em = max(em, __reduce_max_sync(0xffffffffu, biased_exp(rp)));
+        // exponent bound of g * f from the exponents (no FP64 multiply): |g f| < 2^(eg + ef)
+        const unsigned ef = __reduce_max_sync(0xffffffffu, biased_exp(fv));
+        if (ef) em = max(em, (unsigned)max(1, (int)ef + (int)biased_exp(g) - 1023 + 1));
+        const int d = admit_row(w, em, 2);  // new values <= max|u| + g max|f|: two spare bits
+        if (d < 0) {
+          L.um = to_f64_bits(L.um, w.R);
+          w.fix = false;
+          return i;  // redo this row in FP64
+        }
+        if (d > 0) L.um = shr(L.um, d);
+      }
+      if (i + PG < i1) {
+        const int64_t jn = j + 2 * PG;
+        qx[t] = ld(X, jn);
+        qn[t] = ld(N, jn + 1);
+        qf[t] = ldf(jn);
+      }
+      long long uc = FIX ? fx::to_fixed(rc, 1023 + w.R) : __double_as_longlong(rc);
+      const long long up = FIX ? fx::to_fixed(rp, 1023 + w.R) : __double_as_longlong(rp);
+      double out = rc;
+      if (j >= 1 && j < q.ny) {
+        const long long V = add<FIX>(L.um, up);
+#pragma unroll
+        for (int px = 0; px < 2; ++px) {
+          const long long T = add<FIX>(V, uc);
+          const long long Tm = __shfl_up_sync(0xffffffffu, T, 1);
+          const long long Tp = __shfl_down_sync(0xffffffffu, T, 1);
+          if (L.xin && (int)(L.x & 1) == px) {
+            const long long Nn = add<FIX>(add<FIX>(Tm, Tp), V);
+            double un;
+            if (FIX) {
+              un = fma(g, fv, fx::to_double(Nn, w.R - fx::FRAC - 3));
+              uc = fx::to_fixed(un, 1023 + w.R);
+            } else {
+              un = fma(__longlong_as_double(Nn), 0.125, g * fv);
+              uc = __double_as_longlong(un);
+            }
+            out = un;
+          }
+        }
+      }
+      if (L.out_lane) Y[j * q.pitch + L.x] = out;
+      L.um = up;
+    }
+  }
+  return i1;
+}
+
 __global__ void __launch_bounds__(W2_THREADS) k_gs2_half(Geo q, int pr, const double *__restrict__ X,
                                                          const double *__restrict__ N, double *__restrict__ Y,
                                                          const double *__restrict__ f, double g) {
@@ -305,61 +464,19 @@ __global__ void __launch_bounds__(W2_THREADS) k_gs2_half(Geo q, int pr, const do
   const int64_t i0 = chunk * (W2_ROWS / 2);
   if (i0 >= ncentre) return;
   const int64_t i1 = i0 + W2_ROWS / 2 < ncentre ? i0 + W2_ROWS / 2 : ncentre;
-  const int64_t x = seg * 28 + lane - 2;
-  const bool xok = x >= 0 && x <= q.nx;
-  const bool xin = x >= 1 && x < q.nx;
-  const bool out_lane = lane >= 2 && lane <= 29 && xok;
+  GsLane L;
+  L.x = seg * 28 + lane - 2;
+  L.xok = L.x >= 0 && L.x <= q.nx;
+  L.xin = L.x >= 1 && L.x < q.nx;
+  L.out_lane = lane >= 2 && lane <= 29 && L.xok;
   WarpScale w;
-  auto ld = [&](const double *p, int64_t j) -> double {
-    return (xok && j >= 0 && j <= q.ny) ? p[j * q.pitch + x] : 0.0;
-  };
   const int64_t jf = pr + 2 * i0;
-  double rm = ld(N, jf - 1);
+  const double rm = (L.xok && jf - 1 >= 0) ? N[(jf - 1) * q.pitch + L.x] : 0.0;
   if (admit_row(w, __reduce_max_sync(0xffffffffu, biased_exp(rm)), 2) < 0) w.fix = false;
-  long long um = enc(w, rm);
-  for (int64_t i = i0; i < i1; ++i) {
-    const int64_t j = pr + 2 * i;
-    const bool jin = j >= 1 && j < q.ny;
-    const double rc = ld(X, j), rp = ld(N, j + 1);
-    const double fv = (jin && xin) ? f[j * q.pitch + x] : 0.0;
-    unsigned em = __reduce_max_sync(0xffffffffu, biased_exp(rc));
-    em = max(em, __reduce_max_sync(0xffffffffu, biased_exp(rp)));
-    em = max(em, __reduce_max_sync(0xffffffffu, biased_exp(g * fv)));
-    const int d = admit_row(w, em, 2);  // new values <= max|u| + g max|f|: two spare bits
-    if (d < 0) {
-      um = to_f64_bits(um, w.R);
-      w.fix = false;
-    } else if (d > 0) {
-      um = shr(um, d);
-    }
-    long long uc = enc(w, rc);
-    const long long up = enc(w, rp);
-    double out = rc;
-    if (jin) {
-      for (int px = 0; px < 2; ++px) {
-        const long long V = w.fix ? um + up : add<false>(um, up);
-        const long long T = w.fix ? V + uc : add<false>(V, uc);
-        const long long Tm = __shfl_up_sync(0xffffffffu, T, 1);
-        const long long Tp = __shfl_down_sync(0xffffffffu, T, 1);
-        const bool mine = xin && (int)(x & 1) == px;
-        if (mine) {
-          double un;
-          if (w.fix) {
-            const long long Nn = Tm + Tp + V;
-            un = fma(g, fv, fx::to_double(Nn, w.R - fx::FRAC - 3));
-            uc = fx::to_fixed(un, 1023 + w.R);
-          } else {
-            const double Nn = __longlong_as_double(Tm) + __longlong_as_double(Tp) + __longlong_as_double(V);
-            un = fma(Nn, 0.125, g * fv);
-            uc = __double_as_longlong(un);
-          }
-          out = un;
-        }
-      }
-    }
-    if (out_lane) Y[j * q.pitch + x] = out;
-    um = up;
-  }
+  L.um = w.fix ? fx::to_fixed(rm, 1023 + w.R) : __double_as_longlong(rm);
+  int64_t i = i0;
+  if (w.fix) i = gs2_rows<true>(q, pr, X, N, Y, f, g, w, L, i, i1);
+  if (i < i1) gs2_rows<false>(q, pr, X, N, Y, f, g, w, L, i, i1);
 }
 
 }  // namespace

@@ -15,6 +15,7 @@
 // it exceeds R, the two planes already staged are shifted right to the new R.  If a
 // plane holds a non-finite value or the magnitudes leave [2^-900, 2^1000], the CTA
 // converts its staged planes to FP64 and finishes in native FP64 arithmetic.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -44,6 +45,7 @@ struct OpArgs {
   double *partials;  // residual: 2 per CTA
   unsigned *counter; // residual: CTAs finished
   double *norms2;    // residual: [sum r^2, sum f^2]
+  int out_kind;      // residual: 0 = r in FP64, 1 = FP32, 2 = bf16 (FP64 -> FP32 -> bf16)
 };
 
 __device__ __forceinline__ void prefetch_plane(double (&v)[O_PER], const Geo &q, const double *src,
@@ -156,7 +158,15 @@ __device__ __forceinline__ void compute_plane(const OpArgs &a, int64_t z, int x0
       outp[off] = inner ? fma(a.c2, Td, fma(a.c1, fv[k], uv[k])) : uv[k];
     } else {
       const double rv = inner ? fma(a.c1, Td, fv[k]) : 0.0;
-      if (outp) outp[off] = rv;
+      if (a.out) {
+        const int64_t e = z * q.plane + off;  // element index
+        if (a.out_kind == 0)
+          a.out[e] = rv;
+        else if (a.out_kind == 1)
+          ((float *)a.out)[e] = (float)rv;
+        else
+          ((__nv_bfloat16 *)a.out)[e] = __float2bfloat16_rn((float)rv);
+      }
       if (inner) {
         rr = fma(rv, rv, rr);
         ff = fma(fv[k], fv[k], ff);
@@ -353,7 +363,7 @@ cudaError_t launch_jacobi_fx3(const Geo &q, const double *u, const double *f, do
 }
 
 cudaError_t launch_residual_fx3(const Geo &q, const double *u, const double *f, double *r,
-                                double *norms2, void *scratch, cudaStream_t s) {
+                                double *norms2, void *scratch, cudaStream_t s, int out_kind) {
   const dim3 g = ops_grid(q);
   const size_t nblk = (size_t)g.x * g.y * g.z;
   OpArgs a{};
@@ -366,6 +376,7 @@ cudaError_t launch_residual_fx3(const Geo &q, const double *u, const double *f, 
   a.counter = (unsigned *)scratch;  // counter first, partials after (same layout everywhere)
   a.partials = (double *)((char *)scratch + 16);
   a.norms2 = norms2;
+  a.out_kind = out_kind;
   return launch_op<OP_RESIDUAL>(a, s);
 }
 
