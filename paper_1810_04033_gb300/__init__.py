@@ -34,6 +34,11 @@ class Grid(ctypes.Structure):
                 ("n", ctypes.c_int64 * 3), ("pitch", ctypes.c_int64), ("h", ctypes.c_double)]
 
 
+class PatchDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("reserved", ctypes.c_int32), ("offset", ctypes.c_int64),
+                ("h", ctypes.c_double)]
+
+
 class SolveOpts(ctypes.Structure):
     _fields_ = [("rel_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("inner_sweeps", ctypes.c_int), ("inner_dtype", ctypes.c_int)]
@@ -70,6 +75,12 @@ def lib():
             "stencil_jacobi_step": (ci, [gp, vp, vp, vp, cd, vp]),
             "stencil_residual_noalloc": (ci, [gp, vp, vp, vp, vp, vp]),
             "stencil_solve": (ci, [gp, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]),
+            "stencil_patch_batch_create": (ci, [ctypes.POINTER(PatchDesc), ctypes.c_int32,
+                                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(vp)]),
+            "stencil_patch_batch_smooth": (ci, [vp, vp, vp, ci, vp]),
+            "stencil_patch_batch_autotune": (ci, [vp, vp, vp, vp]),
+            "stencil_patch_batch_config": (ci, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+            "stencil_patch_batch_destroy": (ci, [vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name)
@@ -220,6 +231,52 @@ def stencil_solve(u, f, h, rel_tol=1e-10, max_outer=100000, inner_sweeps=8, inne
     if history:
         out["history"] = list(hist[:info.iterations + 1])
     return out
+
+
+class PatchBatch:
+    """Handle of a patch batch (stencil_patch_batch_*).  sizes: cells per edge per
+    patch; offsets: element offsets in the packed arrays; neighbours: (npatch, 27) int32."""
+
+    def __init__(self, sizes, offsets, neighbours):
+        import numpy as np
+        sizes = np.asarray(sizes, dtype=np.int32)
+        offsets = np.asarray(offsets, dtype=np.int64)
+        nb = np.ascontiguousarray(neighbours, dtype=np.int32)
+        n = len(sizes)
+        descs = (PatchDesc * n)()
+        for i in range(n):
+            descs[i].n = int(sizes[i])
+            descs[i].reserved = 0
+            descs[i].offset = int(offsets[i])
+            descs[i].h = 0.0
+        self._h = ctypes.c_void_p()
+        _check(lib().stencil_patch_batch_create(descs, n, nb.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                                ctypes.byref(self._h)))
+        self.npatch = n
+
+    def smooth(self, u_all, f_all, sweeps, stream=None):
+        _check(lib().stencil_patch_batch_smooth(self._h, _ptr(u_all), _ptr(f_all), int(sweeps), _stream(stream)))
+        return u_all
+
+    def autotune(self, u_all, f_all, stream=None):
+        _check(lib().stencil_patch_batch_autotune(self._h, _ptr(u_all), _ptr(f_all), _stream(stream)))
+        return self.config()
+
+    def config(self):
+        t, c = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().stencil_patch_batch_config(self._h, ctypes.byref(t), ctypes.byref(c)))
+        return t.value, c.value
+
+    def close(self):
+        if self._h:
+            lib().stencil_patch_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def stencil_release_workspace():

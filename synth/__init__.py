@@ -113,6 +113,22 @@ class PatchLattice:
         o = int(self.offsets[p])
         return a[o:o + (n + 1) ** 3].reshape((n + 1,) * 3)
 
+    def neighbours27(self) -> np.ndarray:
+        """(npatch, 27) int32 table: entry (dx+1) + 3(dy+1) + 9(dz+1) is the patch at
+        lattice offset (dx, dy, dz), -1 outside the lattice (the centre entry is p)."""
+        lx, ly, lz = (int(v) for v in self.lat)
+        npatch = lx * ly * lz
+        nb = np.full((npatch, 27), -1, dtype=np.int32)
+        for p in range(npatch):
+            px, py, pz = p % lx, (p // lx) % ly, p // (lx * ly)
+            for dz in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dx in (-1, 0, 1):
+                        qx, qy, qz = px + dx, py + dy, pz + dz
+                        if 0 <= qx < lx and 0 <= qy < ly and 0 <= qz < lz:
+                            nb[p, (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] = qx + lx * (qy + ly * qz)
+        return nb
+
     @property
     def interior_updates_per_sweep(self) -> int:
         return int(((self.np_sizes.astype(np.int64) - 1) ** 3).sum())
