@@ -79,6 +79,12 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--n3", type=int, default=N3, help="3D cells per edge (0: no 3D grid)")
     ap.add_argument("--n2", type=int, default=N2, help="2D cells per edge (0: no 2D grid)")
+    ap.add_argument("--workload", default="cfg1", choices=["cfg0", "cfg1", "cfg2", "cfg3", "cfg4"],
+                    help="cfg1 (default): the 512^3 op mix above; cfg0: 32^3 apply + 10 GS sweeps; "
+                         "cfg2: 4096 patches x 20 sweeps; cfg3: refinement to 1e-10 at 256^3 "
+                         "(FP32 / bf16 inner) vs plain FP64 GS; cfg4: request server")
+    ap.add_argument("--requests", type=int, default=400, help="cfg4: requests per arrival rate")
+    ap.add_argument("--rates", default="200,1000,5000", help="cfg4: arrival rates (req/s)")
     return ap.parse_args()
 
 
@@ -423,10 +429,153 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+# ------------------------------------------------------------------ other workloads
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_cfg0(args):
+    """32^3 cells: one element-wise apply on u ~ U[-1,1] (seed 0), then 10 coloured GS
+    sweeps on A u = f, f = 3 pi^2 sin sin sin, u0 = 0."""
+    import torch
+    import paper_1810_04033_gb300 as st
+    n, h = 32, 1.0 / 32
+    s3 = synth.grid_shape(3, n)
+    u = torch.from_numpy(synth.uniform_field(s3, 0)).cuda()
+    f = torch.from_numpy(synth.sin_rhs(3, n)).cuda()
+    y, g = torch.empty_like(u), torch.zeros_like(u)
+
+    def step():
+        st.stencil_apply(u, y, h, st.FORM_ELEMENTWISE)
+        g.zero_()
+        st.stencil_smooth_coloured(g, f, h, 10)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    upd = 11 * (n - 1) ** 3
+    return {"metric": "Mupdates/s (32^3 Q1: 1 element-wise apply + 10 coloured GS sweeps)", "workload": "cfg0",
+            "value": round(upd / ms / 1e3, 1), "unit": "Mupdates/s", "ms_per_step": round(ms, 4),
+            "steps": args.steps, "dtype": "f64", "note": "launch-bound size (30K interior vertices)"}
+
+
+def run_cfg2(args):
+    """4096 patches in a 16^3 lattice, edges from {8,12,16,24,32} (seed 2), f ~ U[-1,1],
+    u0 = 0, 20 coloured GS sweeps with a halo fill before each; launch shape autotuned."""
+    import torch
+    import paper_1810_04033_gb300 as st
+    L = synth.PatchLattice(lat=(16, 16, 16), seed=2)
+    b = st.PatchBatch(L.np_sizes, L.offsets, L.neighbours27())
+    u = torch.from_numpy(L.u).cuda()
+    f = torch.from_numpy(L.f).cuda()
+    tuned = b.autotune(u, f)
+    for _ in range(args.warmup):
+        b.smooth(u, f, 20)
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch)
+    e0.record()
+    for _ in range(args.steps):
+        b.smooth(u, f, 20)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    upd = 20 * L.interior_updates_per_sweep
+    return {"metric": "Mupdates/s (4096 uneven patches, 20 GS sweeps with halo fill)", "workload": "cfg2",
+            "value": round(upd / ms / 1e3, 1), "unit": "Mupdates/s", "ms_per_step": round(ms, 3),
+            "algorithmic_gbs": round(24 * upd / ms / 1e6, 1), "hbm_frac": round(24 * upd / ms / 1e6 / 6683.2, 4),
+            "autotuned_launch": {"threads": tuned[0], "ctas_per_sm": tuned[1]}, "dtype": "f64",
+            "patches": int(L.np_sizes.size), "vertices": L.total}
+
+
+def run_cfg3(args):
+    """256^3, f from u* = sin(2 pi x) sin(3 pi y) sin(pi z): refinement to a relative
+    residual of 1e-10 with 8 inner GS sweeps in FP32 and in bf16 storage, against plain
+    FP64 coloured GS (inner FP64, same loop) to the same residual; error of each result
+    against the closed-form discrete solution."""
+    import torch
+    import paper_1810_04033_gb300 as st
+    n, h = 256, 1.0 / 256
+    modes = (2, 3, 1)
+    f = synth.sin_rhs(3, n, modes)
+    lam = 0.0
+    a = [2 - 2 * math.cos(m * math.pi * h) for m in modes]
+    mm = [(2 + math.cos(m * math.pi * h)) / 3 for m in modes]
+    lam = a[0] * mm[1] * mm[2] + mm[0] * a[1] * mm[2] + mm[0] * mm[1] * a[2]
+    uh = h * h * f / lam
+    fd = torch.from_numpy(f).cuda()
+    out = {}
+    for name, prec in (("fp64", st.F64), ("fp32", st.F32), ("bf16", st.BF16)):
+        ud = torch.zeros_like(fd)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        res = st.stencil_solve(ud, fd, h, rel_tol=1e-10, max_outer=20000, inner_sweeps=8, inner_dtype=prec,
+                               history=False)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t
+        err = float(np.max(np.abs(ud.cpu().numpy() - uh)) / np.max(np.abs(uh)))
+        out[name] = {"seconds": round(sec, 3), "corrections": res["iterations"], "sweeps": 8 * res["iterations"],
+                     "relres": res["relres"], "converged": res["converged"], "rel_err_vs_closed_form": err}
+    return {"metric": "time to relative residual 1e-10, 256^3 (speedup of mixed precision over FP64)",
+            "workload": "cfg3", "value": round(out["fp64"]["seconds"] / out["fp32"]["seconds"], 3),
+            "unit": "x (FP64 time / FP32-inner time)", "bf16_speedup": round(out["fp64"]["seconds"] /
+                                                                             out["bf16"]["seconds"], 3),
+            "runs": out}
+
+
+def run_cfg4(args):
+    """Request server: per arrival rate, `requests` requests from the seeded stream
+    (edge log-uniform in [16, 256], SMOOTH = 20 GS sweeps or SOLVE to 1e-8 with FP32
+    inner sweeps, f drawn on the device from each request's seed), Poisson arrivals;
+    p50 / p99 latency (submit to done) and aggregate Mupdates/s."""
+    import torch
+    import paper_1810_04033_gb300 as st
+    lines = []
+    for rate in [float(r) for r in args.rates.split(",")]:
+        reqs = synth.request_stream(args.requests, rate, seed=3)
+        srv = st.Server(64 << 30, streams=8, max_inflight=64, inner_dtype=st.F32)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tickets = []
+        for r in reqs:
+            while time.perf_counter() - t0 < r["t"]:
+                time.sleep(0.0002)
+            kind = st.REQ_SOLVE if r["kind"] == "solve" else st.REQ_SMOOTH
+            tickets.append((srv.submit(kind, r["edge"], sweeps=20, rel_tol=1e-8, f_seed=r["seed"]), r))
+        lat, upd = [], 0
+        for t, r in tickets:
+            res = srv.wait(t)
+            lat.append(res["t_done"] - res["t_submit"])
+            sweeps = 20 if r["kind"] == "smooth" else 8 * res["iterations"]
+            upd += sweeps * (r["edge"] - 1) ** 3
+            srv.release(t)
+        wall = time.perf_counter() - t0
+        srv.close()
+        lat = np.array(lat)
+        lines.append({"rate_req_s": rate, "requests": len(reqs), "p50_s": round(float(np.percentile(lat, 50)), 4),
+                      "p99_s": round(float(np.percentile(lat, 99)), 4), "wall_s": round(wall, 2),
+                      "aggregate_mupdates_s": round(upd / wall / 1e6, 1)})
+    return {"metric": "serving: p50/p99 latency and aggregate Mupdates/s", "workload": "cfg4",
+            "value": lines[0]["aggregate_mupdates_s"], "unit": "Mupdates/s", "per_rate": lines}
+
+
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.workload != "cfg1" and args.impl == "gpu":
+        import torch
+        torch.cuda.set_device(0)
+        fn = {"cfg0": run_cfg0, "cfg2": run_cfg2, "cfg3": run_cfg3, "cfg4": run_cfg4}[args.workload]
+        if rank == 0:
+            print(json.dumps(fn(args)))
+        return
     if args.impl == "reference":
         out = run_reference(args, rank, world)
         if out is not None:

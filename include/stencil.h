@@ -237,6 +237,71 @@ int stencil_patch_batch_config(const stencil_batch_t *b, int32_t *threads, int32
 /* Frees the batch's device tables (not the caller's arrays). */
 int stencil_patch_batch_destroy(stencil_batch_t *b);
 
+/* ------------------------------------------------------------ request server */
+#define STENCIL_REQ_SMOOTH 0
+#define STENCIL_REQ_SOLVE 1
+
+typedef struct stencil_server stencil_server_t; /* opaque */
+
+typedef struct stencil_server_opts {
+  int32_t streams;      /* CUDA streams requests are spread over (0: 8) */
+  int32_t max_inflight; /* requests resident and in progress at once (0: 64) */
+  int32_t inner_sweeps; /* SOLVE: coloured GS sweeps per correction (0: 8) */
+  int32_t inner_dtype;  /* SOLVE: STENCIL_F32 (default), STENCIL_BF16 or STENCIL_F64 */
+  int32_t max_outer;    /* SOLVE: at most this many corrections (0: 100000) */
+  int32_t reserved;
+} stencil_server_opts_t;
+
+typedef struct stencil_request {
+  int32_t kind;      /* STENCIL_REQ_SMOOTH or STENCIL_REQ_SOLVE */
+  int32_t n;         /* cells per edge of the unit-cube grid (h = 1/n), 2..2048 */
+  int32_t sweeps;    /* SMOOTH: coloured GS sweeps */
+  int32_t reserved;
+  double rel_tol;    /* SOLVE: stop when ||f - A u|| / ||f|| <= rel_tol */
+  const double *f;   /* host (n+1)^3 FP64 right-hand side, copied by submit; or NULL: */
+  uint64_t f_seed;   /*   f_i = U[-1,1) from SplitMix64 at counter i (interior), 0 on the boundary */
+  const double *u0;  /* host (n+1)^3 initial guess incl. Dirichlet data, or NULL (zeros) */
+} stencil_request_t;
+
+typedef struct stencil_result {
+  int32_t status;    /* STENCIL_OK, STENCIL_ENOTCONV (solve hit max_outer), STENCIL_ECUDA */
+  int32_t iterations; /* SMOOTH: sweeps; SOLVE: corrections */
+  double relres;     /* SOLVE: relative residual of the result */
+  double t_submit, t_admit, t_done; /* seconds since the server was created */
+} stencil_result_t;
+
+typedef struct stencil_server_stats {
+  int64_t submitted, completed, pending, inflight;
+  uint64_t hbm_used, hbm_budget;
+} stencil_server_stats_t;
+
+/*
+ * Creates a request server on the current device with a device-memory budget.  A host
+ * engine thread admits queued requests in arrival order (looking past a blocked head
+ * at the next few) whenever a request's footprint fits the remaining budget and an
+ * in-flight slot is free, keeps its grids resident on the device and advances all
+ * admitted requests concurrently on several streams (continuous batching): SMOOTH =
+ * `sweeps` coloured GS sweeps (as stencil_smooth_coloured); SOLVE = the refinement of
+ * stencil_solve, one correction per step.  A request's result does not depend on the
+ * other requests.  The paper's use case is the multigrid smoother (Section 1); the
+ * serving loop is this library's.  Returns STENCIL_EINVAL, STENCIL_ECUDA.
+ */
+int stencil_server_create(size_t hbm_budget_bytes, const stencil_server_opts_t *opts, stencil_server_t **out);
+/* Queues a request (copies its host arrays).  STENCIL_EADMIT if its footprint exceeds
+ * the whole budget (it could never be admitted). */
+int stencil_server_submit(stencil_server_t *s, const stencil_request_t *req, uint64_t *ticket);
+/* Non-blocking: STENCIL_OK with the result once done, STENCIL_EBUSY before. */
+int stencil_server_poll(stencil_server_t *s, uint64_t ticket, stencil_result_t *res);
+/* Blocks until done or timeout_us (negative: no limit): STENCIL_ETIMEDOUT. */
+int stencil_server_wait(stencil_server_t *s, uint64_t ticket, int64_t timeout_us, stencil_result_t *res);
+/* Copies a finished request's (n+1)^3 FP64 result to host memory and releases it. */
+int stencil_server_fetch(stencil_server_t *s, uint64_t ticket, double *u_host);
+/* Releases a finished request without copying its result. */
+int stencil_server_release(stencil_server_t *s, uint64_t ticket);
+int stencil_server_stats(stencil_server_t *s, stencil_server_stats_t *st);
+/* Stops the engine (waits for work in flight) and frees everything. */
+int stencil_server_destroy(stencil_server_t *s);
+
 /* Frees the internal workspaces of the current device (not thread-safe against
  * concurrent calls on that device). */
 int stencil_release_workspace(void);

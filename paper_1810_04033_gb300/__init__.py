@@ -39,6 +39,32 @@ class PatchDesc(ctypes.Structure):
                 ("h", ctypes.c_double)]
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("streams", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
+                ("inner_sweeps", ctypes.c_int32), ("inner_dtype", ctypes.c_int32),
+                ("max_outer", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n", ctypes.c_int32), ("sweeps", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("rel_tol", ctypes.c_double),
+                ("f", ctypes.POINTER(ctypes.c_double)), ("f_seed", ctypes.c_uint64),
+                ("u0", ctypes.POINTER(ctypes.c_double))]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("relres", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("pending", ctypes.c_int64),
+                ("inflight", ctypes.c_int64), ("hbm_used", ctypes.c_uint64), ("hbm_budget", ctypes.c_uint64)]
+
+
+REQ_SMOOTH, REQ_SOLVE = 0, 1
+
+
 class SolveOpts(ctypes.Structure):
     _fields_ = [("rel_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("inner_sweeps", ctypes.c_int), ("inner_dtype", ctypes.c_int)]
@@ -81,6 +107,14 @@ def lib():
             "stencil_patch_batch_autotune": (ci, [vp, vp, vp, vp]),
             "stencil_patch_batch_config": (ci, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
             "stencil_patch_batch_destroy": (ci, [vp]),
+            "stencil_server_create": (ci, [ctypes.c_size_t, ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)]),
+            "stencil_server_submit": (ci, [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+            "stencil_server_poll": (ci, [vp, ctypes.c_uint64, ctypes.POINTER(Result)]),
+            "stencil_server_wait": (ci, [vp, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(Result)]),
+            "stencil_server_fetch": (ci, [vp, ctypes.c_uint64, vp]),
+            "stencil_server_release": (ci, [vp, ctypes.c_uint64]),
+            "stencil_server_stats": (ci, [vp, ctypes.POINTER(ServerStats)]),
+            "stencil_server_destroy": (ci, [vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name)
@@ -270,6 +304,79 @@ class PatchBatch:
     def close(self):
         if self._h:
             lib().stencil_patch_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Handle of a request server (stencil_server_*), host-array interface."""
+
+    def __init__(self, hbm_budget_bytes, streams=0, max_inflight=0, inner_sweeps=0, inner_dtype=F32,
+                 max_outer=0):
+        o = ServerOpts(int(streams), int(max_inflight), int(inner_sweeps), int(inner_dtype), int(max_outer), 0)
+        self._h = ctypes.c_void_p()
+        _check(lib().stencil_server_create(int(hbm_budget_bytes), ctypes.byref(o), ctypes.byref(self._h)))
+        self._keep = {}
+
+    def submit(self, kind, n, sweeps=20, rel_tol=1e-8, f=None, f_seed=0, u0=None):
+        """f / u0: host float64 arrays of (n+1)^3 or None (f: drawn from f_seed)."""
+        import numpy as np
+        r = Request()
+        r.kind, r.n, r.sweeps, r.reserved, r.rel_tol = int(kind), int(n), int(sweeps), 0, float(rel_tol)
+        keep = []
+        if f is not None:
+            fa = np.ascontiguousarray(f, dtype=np.float64)
+            keep.append(fa)
+            r.f = fa.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        r.f_seed = int(f_seed) & 0xFFFFFFFFFFFFFFFF
+        if u0 is not None:
+            ua = np.ascontiguousarray(u0, dtype=np.float64)
+            keep.append(ua)
+            r.u0 = ua.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        t = ctypes.c_uint64()
+        _check(lib().stencil_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        return t.value
+
+    @staticmethod
+    def _res(r):
+        return {"status": r.status, "iterations": r.iterations, "relres": r.relres, "t_submit": r.t_submit,
+                "t_admit": r.t_admit, "t_done": r.t_done}
+
+    def poll(self, ticket):
+        r = Result()
+        rc = lib().stencil_server_poll(self._h, ticket, ctypes.byref(r))
+        if rc == -8:
+            return None
+        _check(rc)
+        return self._res(r)
+
+    def wait(self, ticket, timeout_us=-1):
+        r = Result()
+        _check(lib().stencil_server_wait(self._h, ticket, int(timeout_us), ctypes.byref(r)))
+        return self._res(r)
+
+    def fetch(self, ticket, n):
+        import numpy as np
+        out = np.empty((n + 1,) * 3, dtype=np.float64)
+        _check(lib().stencil_server_fetch(self._h, ticket, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def release(self, ticket):
+        _check(lib().stencil_server_release(self._h, ticket))
+
+    def stats(self):
+        st = ServerStats()
+        _check(lib().stencil_server_stats(self._h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            lib().stencil_server_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

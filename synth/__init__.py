@@ -134,6 +134,29 @@ class PatchLattice:
         return int(((self.np_sizes.astype(np.int64) - 1) ** 3).sum())
 
 
+# ------------------------------------------------------------------ SplitMix64 fields
+
+_GOLDEN = 0x9E3779B97F4A7C15
+
+
+def splitmix_field(n: int, seed: int) -> np.ndarray:
+    """(n+1)^3 field whose interior value at flat index i (x fastest) is the top 53
+    bits of SplitMix64 (Steele, Lea & Flood, 2014) evaluated at counter
+    seed + (i + 1) * 0x9E3779B97F4A7C15 (mod 2^64), mapped to U[-1, 1); boundary 0.
+    The request server draws the same numbers on the device for seeded requests."""
+    W = n + 1
+    with np.errstate(over="ignore"):
+        i = np.arange(W ** 3, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + (i + np.uint64(1)) * np.uint64(_GOLDEN)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    v = (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53) * 2.0 - 1.0
+    v = np.ascontiguousarray(v.reshape(W, W, W))
+    zero_boundary(v)
+    return v
+
+
 # ------------------------------------------------------------------ request stream
 
 def request_stream(count: int, rate_per_s: float, seed: int = 3, edge_lo: int = 16,
