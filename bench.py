@@ -55,9 +55,9 @@ def pitch2(n2):
 
 def launches_per_step(n3, n2):
     """Kernel launches of the library per step (3D: GS two launches per sweep plus two
-    per-call pre-passes; 2D: two per sweep)."""
+    per-call pre-passes; 2D: one fused launch per sweep)."""
     d3 = 2 * N_APPLY + (2 * N_SWEEPS + 2) + N_SWEEPS + 1
-    d2 = 2 * N_APPLY + 2 * N_SWEEPS + N_SWEEPS + 1
+    d2 = 2 * N_APPLY + N_SWEEPS + N_SWEEPS + 1
     return (d3 if n3 else 0) + (d2 if n2 else 0)
 
 

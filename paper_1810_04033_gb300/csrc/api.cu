@@ -27,6 +27,18 @@ int check_launch(const char *what) {
   return STENCIL_OK;
 }
 
+int device_sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (!cached[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
 // ------------------------------------------------------------ per-stream scratch
 namespace {
 constexpr int kMaxDevices = 64;
@@ -221,9 +233,10 @@ int stencil_smooth_coloured(const stencil_grid_t *g, void *u, const void *f, int
     if (!work || !bnd) return set_error(STENCIL_ENOMEM, "smooth_coloured workspace allocation failed");
     e = launch_gs_sweeps_fx3(q, (double *)u, (const double *)f, sweeps, (double *)work, bnd, s);
   } else {
-    void *work = device_scratch(SCRATCH_PINGPONG, (size_t)span_elems(q) * 8, s);
-    if (!work) return set_error(STENCIL_ENOMEM, "smooth_coloured workspace allocation failed");
-    e = launch_gs_sweeps_fx2(q, (double *)u, (const double *)f, sweeps, (double *)work, s);
+    void *work = device_scratch(SCRATCH_PINGPONG, 3 * (size_t)span_elems(q) * 8, s);
+    void *bnd = device_scratch(SCRATCH_BOUNDS, gs_fx_bounds_bytes(), s);
+    if (!work || !bnd) return set_error(STENCIL_ENOMEM, "smooth_coloured workspace allocation failed");
+    e = launch_gs_sweeps_fx2(q, (double *)u, (const double *)f, sweeps, (double *)work, bnd, s);
   }
   if (e != cudaSuccess)
     return set_error(STENCIL_ECUDA, std::string("smooth_coloured: ") + cudaGetErrorString(e));
@@ -334,10 +347,10 @@ int stencil_solve(const stencil_grid_t *g, double *u, const double *f, const ste
   double *hn = (double *)host_scratch(64, s);
   void *work = nullptr;
   if (inner == STENCIL_F64)
-    work = device_scratch(SCRATCH_PINGPONG, (g->dim == 3 ? 3 : 1) * span * 8, s);
+    work = device_scratch(SCRATCH_PINGPONG, 3 * span * 8, s);
   else
     work = device_scratch(SCRATCH_LP, span * esz, s);
-  void *bnd = g->dim == 3 ? device_scratch(SCRATCH_BOUNDS, gs_fx_bounds_bytes(), s) : (void *)1;
+  void *bnd = device_scratch(SCRATCH_BOUNDS, gs_fx_bounds_bytes(), s);
   if (!r || !e || !dn || !red_scr || !hn || !work || !bnd)
     return set_error(STENCIL_ENOMEM, "solve: workspace allocation failed");
   const int out_kind = inner == STENCIL_F64 ? 0 : (inner == STENCIL_F32 ? 1 : 2);
@@ -364,7 +377,7 @@ int stencil_solve(const stencil_grid_t *g, double *u, const double *f, const ste
         ce = g->dim == 3 ? launch_gs_sweeps_fx3(q, (double *)e, (const double *)r, opts->inner_sweeps,
                                                 (double *)work, bnd, s)
                          : launch_gs_sweeps_fx2(q, (double *)e, (const double *)r, opts->inner_sweeps,
-                                                (double *)work, s);
+                                                (double *)work, bnd, s);
       else if (inner == STENCIL_F32)
         ce = launch_gs_sweeps_f32_3d(q, (float *)e, (const float *)r, opts->inner_sweeps, (float *)work, s);
       else

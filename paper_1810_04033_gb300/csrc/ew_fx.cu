@@ -42,6 +42,7 @@ struct EwArgs {
   const double *u;
   double *y;
   double scale;  // 1 / (12 h^2)
+  int cz;        // planes per CTA
 };
 
 template <bool FIX>
@@ -173,8 +174,8 @@ __global__ void __launch_bounds__(E_THREADS, 2) k_apply_elementwise_fx3(EwArgs a
   __shared__ int red[E_THREADS / 32];
   const Geo &q = a.q;
   const int x0 = (int)blockIdx.x * ET_X, y0 = (int)blockIdx.y * ET_Y;
-  const int64_t zs = (int64_t)blockIdx.z * E_CZ;
-  const int64_t ze = zs + E_CZ < q.nz + 1 ? zs + E_CZ : q.nz + 1;
+  const int64_t zs = (int64_t)blockIdx.z * a.cz;
+  const int64_t ze = zs + a.cz < q.nz + 1 ? zs + a.cz : q.nz + 1;
   long long *slot[4] = {smem, smem + E_PLANE, smem + 2 * E_PLANE, smem + 3 * E_PLANE};
   int ulo = 0, uhi = 1, alo = 2, ahi = 3;
   bool fix = true;
@@ -252,14 +253,16 @@ cudaError_t launch_apply_elementwise_fx3(const Geo &q, const double *u, double *
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const dim3 g((unsigned)((q.nx + ET_X) / ET_X), (unsigned)((q.ny + ET_Y) / ET_Y),
-               (unsigned)((q.nz + E_CZ) / E_CZ));
+  const int64_t txy = ((q.nx + ET_X) / ET_X) * ((q.ny + ET_Y) / ET_Y);
+  const int cz = z_chunk(txy, q.nz + 1, E_CZ, 4, 2);
+  const dim3 g((unsigned)((q.nx + ET_X) / ET_X), (unsigned)((q.ny + ET_Y) / ET_Y), (unsigned)((q.nz + cz) / cz));
   if (g.y > 65535 || g.z > 65535) return cudaErrorInvalidConfiguration;
   EwArgs a;
   a.q = q;
   a.u = u;
   a.y = y;
   a.scale = 1.0 / (12.0 * q.h * q.h);
+  a.cz = cz;
   k_apply_elementwise_fx3<<<g, E_THREADS, E_SMEM, s>>>(a);
   return cudaGetLastError();
 }

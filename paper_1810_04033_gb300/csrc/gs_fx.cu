@@ -34,6 +34,7 @@
 
 #include "fixed.cuh"
 #include "internal.h"
+#include "sweep_bounds.cuh"
 
 namespace stencil {
 namespace {
@@ -42,22 +43,13 @@ constexpr int GS_TX = 58, GS_TY = 30;        // output tile
 constexpr int GS_SW = 64;                    // staged columns (62 used)
 constexpr int GS_SH = 36;                    // staged rows (34 used, 2 zero pad rows)
 constexpr int GS_THREADS = 256;
-constexpr int GS_CZ = 16;                    // centre planes per CTA
+constexpr int GS_CZ = 16;                    // centre planes per CTA (at most)
 constexpr int GS_NUP = GS_SH * GS_SW / GS_THREADS;             // 9 values / thread
 constexpr int GS_NCE = (GS_SH / 2 * GS_SW + GS_THREADS - 1) / GS_THREADS;  // 5 (odd rows)
 constexpr size_t GS_PLANE = (size_t)GS_SH * GS_SW;
 constexpr size_t GS_SMEM = 3 * GS_PLANE * sizeof(long long);
 
 enum { F64 = 0, FXP = 1 };  // storage format of an array: FP64, or int64 fixed point
-
-// Sweep s reads umax[s % 4] (its bound) and umax[(s + 3) % 4] (the previous sweep's,
-// for the scale of its input), accumulates umax[(s + 1) % 4] and clears umax[(s + 2) % 4],
-// which no kernel of sweep s reads.
-struct SweepBounds {
-  unsigned long long umax[4];  // max |u| of the iterate (FP64 bits), ring indexed by sweep
-  unsigned long long fmax;     // max |f| over interior vertices (FP64 bits)
-  unsigned long long m0;       // max |u| of the input (FP64 bits), never cleared
-};
 
 struct Ctx {
   Geo q;
@@ -69,34 +61,7 @@ struct Ctx {
   bool write_bnd;    // write Dirichlet copies into Y (false when Y is the caller's u)
 };
 
-// Per-call fixed-point plan, recomputed identically by every CTA from the bounds.
-struct Plan {
-  bool fix;
-  int Rf;            // scale of GF = 3/8 h^2 f
-};
-
-__device__ __forceinline__ double bits_to_d(unsigned long long b) { return __longlong_as_double((long long)b); }
-
-__device__ __forceinline__ Plan make_plan(const SweepBounds *bnd, double g, int sweeps) {
-  Plan p;
-  const double M0 = bits_to_d(bnd->m0);
-  const double gF = g * bits_to_d(bnd->fmax);
-  // |u| after s sweeps <= M0 + 4 s g max|f|: every value of the call stays in range
-  const double B = M0 + 4.0 * (double)(sweeps + 1) * gF;
-  p.fix = fx::bound_ok(B) && fx::bound_ok(gF);
-  p.Rf = gF > 0.0 ? fx::bound_exponent(gF) + 1 : -900;
-  return p;
-}
-
-__device__ __forceinline__ int sweep_R(const SweepBounds *bnd, int slot, double g) {
-  const double B = bits_to_d(bnd->umax[slot]) + 4.0 * g * bits_to_d(bnd->fmax);
-  const int R = fx::bound_exponent(B) + 1;  // one spare bit: rounding can never reach 2^R
-  return R < -900 ? -900 : R;
-}
-
-__device__ __forceinline__ long long shr(long long v, int d) {
-  return d >= 63 ? (v >> 63) : (d >= 0 ? (v >> d) : (v << (-d)));
-}
+__device__ __forceinline__ long long shr(long long v, int d) { return shr_any(v, d); }
 
 // Raw 64-bit load (FP64 bits or int64) of element `off` of plane pointer p.
 __device__ __forceinline__ long long ld64(const void *p, int off) {
@@ -328,7 +293,7 @@ __device__ void run_half(Ctx &c, int pz, int i0, int i1, const void *X, const vo
 template <int XF, int NF, int YF>
 __global__ void __launch_bounds__(GS_THREADS, 2)
     k_gs_half_sweep(Geo q, int pz, const void *X, const void *N, void *Y, const double *f, const long long *GF,
-                    SweepBounds *bnd, int sweep, int sweeps, double g, int n_even_odd_sweeps_unused,
+                    SweepBounds *bnd, int sweep, int sweeps, double g, int cz,
                     bool write_bnd) {
   extern __shared__ long long smem[];
   __shared__ long long red[GS_THREADS / 32];
@@ -350,11 +315,10 @@ __global__ void __launch_bounds__(GS_THREADS, 2)
   c.df = c.R - plan.Rf;
   if (pz == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
     bnd->umax[cl] = 0ull;  // to be accumulated by sweep s + 1
-  (void)n_even_odd_sweeps_unused;
 
   const int ncentre = q.nz >= pz ? (int)((q.nz - pz) / 2 + 1) : 0;
-  const int i0 = (int)blockIdx.z * GS_CZ;
-  const int i1 = i0 + GS_CZ < ncentre ? i0 + GS_CZ : ncentre;
+  const int i0 = (int)blockIdx.z * cz;
+  const int i1 = i0 + cz < ncentre ? i0 + cz : ncentre;
   const bool inner = c.x0 >= 2 && c.x0 + GS_TX + 1 <= c.nx && c.y0 >= 2 && c.y0 + GS_TY + 1 <= c.ny;
   long long vmax = 0;
   if (plan.fix) {
@@ -383,15 +347,16 @@ __global__ void __launch_bounds__(GS_THREADS, 2)
 }
 
 // 3/8 h^2 f in fixed point (scale Rf of the plan) on interior vertices, 0 elsewhere.
-__global__ void __launch_bounds__(256) k_prep_gf(Geo q, const double *__restrict__ f, long long *__restrict__ GF,
-                                                 const SweepBounds *bnd, double g, int sweeps) {
+__global__ void __launch_bounds__(256) k_prep_gf(Geo q, int dim, const double *__restrict__ f,
+                                                 long long *__restrict__ GF, const SweepBounds *bnd, double g,
+                                                 int sweeps) {
   const Plan plan = make_plan(bnd, g, sweeps);
   if (!plan.fix) return;
   const int rb = 1023 + plan.Rf;
   const int64_t nrows = (q.nz + 1) * (q.ny + 1);
   for (int64_t row = blockIdx.x; row < nrows; row += gridDim.x) {
     const int64_t k = row / (q.ny + 1), j = row % (q.ny + 1);
-    const bool row_inner = j > 0 && j < q.ny && k > 0 && k < q.nz;
+    const bool row_inner = j > 0 && j < q.ny && (dim == 2 || (k > 0 && k < q.nz));
     const int64_t base = k * q.plane + j * q.pitch;
     for (int64_t i = threadIdx.x; i <= q.nx; i += blockDim.x)
       GF[base + i] = (row_inner && i > 0 && i < q.nx) ? fx::to_fixed(g * f[base + i], rb) : 0ll;
@@ -440,6 +405,17 @@ __global__ void __launch_bounds__(256) k_absmax_uf(Geo q, int dim, const double 
 
 size_t gs_fx_bounds_bytes() { return sizeof(SweepBounds); }
 
+cudaError_t launch_gs_prepass(const Geo &q, int dim, const double *u, const double *f, long long *GF, void *bounds,
+                              int sweeps, cudaStream_t s) {
+  SweepBounds *bnd = (SweepBounds *)bounds;
+  cudaError_t e = cudaMemsetAsync(bnd, 0, sizeof(SweepBounds), s);
+  if (e != cudaSuccess) return e;
+  const unsigned nb = (unsigned)(8 * device_sm_count());
+  k_absmax_uf<<<nb, 256, 0, s>>>(q, dim, u, f, bnd);
+  k_prep_gf<<<nb, 256, 0, s>>>(q, dim, f, GF, bnd, 0.375 * q.h * q.h, sweeps);
+  return cudaGetLastError();
+}
+
 template <int XF, int NF, int YF>
 static cudaError_t launch_half(const Geo &q, int pz, const void *X, const void *N, void *Y, const double *f,
                                const long long *GF, SweepBounds *bnd, int sweep, int sweeps, double g,
@@ -454,10 +430,11 @@ static cudaError_t launch_half(const Geo &q, int pz, const void *X, const void *
   const unsigned tx = (unsigned)((q.nx + 1 + GS_TX - 1) / GS_TX);
   const unsigned ty = (unsigned)((q.ny + 1 + GS_TY - 1) / GS_TY);
   const int64_t ncentre = (q.nz - pz) / 2 + 1;
-  const unsigned tz = (unsigned)((ncentre + GS_CZ - 1) / GS_CZ);
+  const int cz = z_chunk((int64_t)tx * ty, ncentre, GS_CZ, 2, 4);
+  const unsigned tz = (unsigned)((ncentre + cz - 1) / cz);
   if (ty > 65535 || tz > 65535) return cudaErrorInvalidConfiguration;
   k_gs_half_sweep<XF, NF, YF><<<dim3(tx, ty, tz), GS_THREADS, GS_SMEM, s>>>(q, pz, X, N, Y, f, GF, bnd, sweep,
-                                                                            sweeps, g, 0, write_bnd);
+                                                                            sweeps, g, cz, write_bnd);
   return cudaGetLastError();
 }
 
@@ -469,13 +446,9 @@ cudaError_t launch_gs_sweeps_fx3(const Geo &q, double *u, const double *f, int s
   void *A = work, *B = work + span;
   long long *GF = (long long *)(work + 2 * span);
   SweepBounds *bnd = (SweepBounds *)bounds;
-  cudaError_t e = cudaMemsetAsync(bnd, 0, sizeof(SweepBounds), s);
+  cudaError_t e = launch_gs_prepass(q, 3, u, f, GF, bounds, sweeps, s);
   if (e != cudaSuccess) return e;
-  k_absmax_uf<<<1216, 256, 0, s>>>(q, 3, u, f, bnd);
   const double g = 0.375 * q.h * q.h;
-  k_prep_gf<<<1216, 256, 0, s>>>(q, f, GF, bnd, g, sweeps);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
   if (sweeps == 1) {
     // u -> A in FP64 (boundary carried), then back into u
     e = launch_half<F64, F64, F64>(q, 0, u, u, A, f, GF, bnd, 0, 1, g, true, s);

@@ -19,7 +19,7 @@ namespace {
 constexpr int LP_TX = 58, LP_TY = 30;
 constexpr int LP_SW = 64, LP_SH = 36;
 constexpr int LP_THREADS = 256;
-constexpr int LP_CZ = 16;
+constexpr int LP_CZ = 16;  // centre planes per CTA (at most)
 constexpr int LP_PLANE = LP_SW * LP_SH;
 
 template <typename S>
@@ -107,13 +107,13 @@ __device__ void lp_phase(const Geo &q, int x0, int y0, float *ce, const float *l
 
 template <typename S>
 __global__ void __launch_bounds__(LP_THREADS) k_gs_lp_half(Geo q, int pz, const S *X, const S *N, S *Y, const S *f,
-                                                           float g) {
+                                                           float g, int cz) {
   extern __shared__ float lps[];
   float *slot[3] = {lps, lps + LP_PLANE, lps + 2 * LP_PLANE};
   const int x0 = (int)blockIdx.x * LP_TX, y0 = (int)blockIdx.y * LP_TY;
   const int64_t ncentre = (q.nz - pz) / 2 + 1;
-  const int64_t i0 = (int64_t)blockIdx.z * LP_CZ;
-  const int64_t i1 = i0 + LP_CZ < ncentre ? i0 + LP_CZ : ncentre;
+  const int64_t i0 = (int64_t)blockIdx.z * cz;
+  const int64_t i1 = i0 + cz < ncentre ? i0 + cz : ncentre;
   int lo = 0, ce = 1, up = 2;
   bool have_lower = false;
   for (int64_t i = i0; i < i1; ++i) {
@@ -166,8 +166,9 @@ static cudaError_t gs_lp_sweeps(const Geo &q, S *u, const S *f, int sweeps, S *w
   for (int it = 0; it < sweeps; ++it) {
     for (int pz = 0; pz < 2; ++pz) {
       const int64_t ncentre = (q.nz - pz) / 2 + 1;
-      const unsigned tz = (unsigned)((ncentre + LP_CZ - 1) / LP_CZ);
-      k_gs_lp_half<S><<<dim3(tx, ty, tz), LP_THREADS, smem, s>>>(q, pz, X, pz == 0 ? X : Y, Y, f, g);
+      const int cz = z_chunk((int64_t)tx * ty, ncentre, LP_CZ, 2, 8);
+      const unsigned tz = (unsigned)((ncentre + cz - 1) / cz);
+      k_gs_lp_half<S><<<dim3(tx, ty, tz), LP_THREADS, smem, s>>>(q, pz, X, pz == 0 ? X : Y, Y, f, g, cz);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -31,6 +31,21 @@ inline Geo make_geo(const stencil_grid_t &g) {
 // Number of elements spanned by an array of this geometry (last element + 1).
 inline int64_t span_elems(const Geo &q) { return q.plane * (q.nz + 1); }
 
+// Streaming multiprocessors of the current device (cached per device; 152 on GB300).
+int device_sm_count();
+
+// Planes (or centre planes) per CTA for kernels that tile x-y and stream through z in
+// chunks: the largest chunk up to cz_max that still gives about two waves of
+// `ctas_per_sm` CTAs on every SM, but not below cz_min (each chunk restages its
+// first neighbour plane).  Small grids thus get short chunks and more CTAs.
+inline int z_chunk(int64_t tiles_xy, int64_t units, int cz_max, int cz_min, int ctas_per_sm) {
+  const int64_t target = 2ll * device_sm_count() * ctas_per_sm;
+  int64_t cz = (units * tiles_xy + target - 1) / target;
+  if (cz > cz_max) cz = cz_max;
+  if (cz < cz_min) cz = cz_min;
+  return (int)cz;
+}
+
 // Error plumbing (api.cu).
 int set_error(int code, const std::string &msg);
 int check_launch(const char *what);
@@ -72,6 +87,10 @@ size_t reduce_scratch_bytes();
 // holds 3 arrays of u's span (two int64 ping-pong buffers and 3/8 h^2 f in fixed point);
 // the result always ends in u, whose boundary values are never written.
 size_t gs_fx_bounds_bytes();
+// Per-call pre-pass of the multi-sweep GS drivers: clears the bounds, takes max |u| and
+// max |f| (interior), and writes GF = 3/8 h^2 f as fixed point (0 off the interior).
+cudaError_t launch_gs_prepass(const Geo &q, int dim, const double *u, const double *f, long long *GF,
+                              void *bounds, int sweeps, cudaStream_t s);
 cudaError_t launch_gs_sweeps_fx3(const Geo &q, double *u, const double *f, int sweeps,
                                  double *work, void *bounds, cudaStream_t s);
 cudaError_t launch_residual_f64(const Geo &q, int dim, const double *u, const double *f,
@@ -91,8 +110,9 @@ cudaError_t launch_jacobi_fx2(const Geo &q, const double *u, const double *f, do
                               cudaStream_t s);
 cudaError_t launch_residual_fx2(const Geo &q, const double *u, const double *f, double *r, double *norms2,
                                 void *scratch, cudaStream_t s);
+// 2D coloured GS, one launch per sweep; work and bounds as for the 3D form.
 cudaError_t launch_gs_sweeps_fx2(const Geo &q, double *u, const double *f, int sweeps, double *work,
-                                 cudaStream_t s);
+                                 void *bounds, cudaStream_t s);
 // out_kind: r stored as 0 = FP64, 1 = FP32, 2 = bf16 (r is an element pointer of that
 // type passed as double*; the layout is u's).
 cudaError_t launch_residual_fx3(const Geo &q, const double *u, const double *f, double *r,

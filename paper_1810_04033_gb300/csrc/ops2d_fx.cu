@@ -1,6 +1,6 @@
 // 2D Q1 (bilinear, 9-point stencil of Fig. 1) operations on the integer pipes:
 // assembled apply, element-wise apply with colour passes, damped Jacobi sweep,
-// residual with norms, and the coloured Gauss-Seidel half sweeps.
+// residual with norms, and the coloured Gauss-Seidel sweep (one pass per sweep).
 //
 //   3 S u = 8 u - N,  N = sum of the 8 neighbours;   6 K_e (element matrix, h-free) has
 //   entries 4 (same vertex), -1 (differ in one coordinate), -2 (opposite corner).
@@ -9,9 +9,10 @@
 //
 // Each warp owns a segment of 32 consecutive columns and streams down a chunk of rows,
 // keeping the rows it needs in registers and reaching x-neighbours by shuffles; no
-// shared memory and no block barriers.  The fixed-point reference R is per warp and
-// only grows: every newly loaded row is reduced to its largest exponent first, and when
-// that exceeds R the rows held so far are shifted to the new scale.  A warp that meets
+// shared memory and no block barriers.  For the single-pass operations the fixed-point
+// reference R is per warp and only grows: every newly loaded row is reduced to its
+// largest exponent first, and when that exceeds R the rows held so far are shifted to
+// the new scale.  A warp that meets
 // a non-finite value or magnitudes outside [2^-900, 2^1000] converts what it holds to
 // FP64 and continues in native FP64 arithmetic.
 #include <cuda_runtime.h>
@@ -19,6 +20,7 @@
 
 #include "fixed.cuh"
 #include "internal.h"
+#include "sweep_bounds.cuh"
 
 namespace stencil {
 namespace {
@@ -73,10 +75,6 @@ template <bool FIX>
 __device__ __forceinline__ long long add(long long a, long long b) {
   if (FIX) return a + b;
   return __double_as_longlong(__longlong_as_double(a) + __longlong_as_double(b));
-}
-
-__device__ __forceinline__ long long enc(const WarpScale &w, double v) {
-  return w.fix ? fx::to_fixed(v, 1023 + w.R) : __double_as_longlong(v);
 }
 
 // 8u - N at this lane's column (3 S u), from the rows above (m), at (c) and below (p).
@@ -364,119 +362,268 @@ unsigned ops2_blocks(const Geo &q) {
 }
 
 // ------------------------------------------------------------------ Gauss-Seidel
-// Half sweep over the rows of parity pr (0: colours 0, 1; 1: colours 2, 3), out of place
-// from X into Y: the centre row comes from X, the rows above and below from N (X for
-// the even-row pass, Y for the odd-row pass, which then holds the new even rows).
-// Inside a row the even-x colour is updated first; the odd-x colour then reads it
-// through shuffles, so a warp produces columns for lanes 2..29 (28 per segment).
 // u_new = 3/8 h^2 f + N/8.
-struct GsLane {
+// Whole sweep in one pass (row wavefront inside a warp).  For even row j: colours 0
+// (x even) and 1 (x odd) from the old rows j-1, j+1; then odd row j-1: colours 2 and 3
+// from the new rows j-2 and j.  Every value read is the one the sequential colour
+// order would read.  Lanes cover 32 columns; each colour step consumes one lane of
+// halo, so lanes 4..27 produce outputs (24 per segment).  A chunk of rows [js, je]
+// (js even) also recomputes its last even row je (which the next chunk owns) so that
+// its last odd row can be finished; chunks are therefore independent.
+struct Gs2Lane {
   int64_t x;
   bool xok, xin, out_lane;
-  long long um;  // converted row j - 1
+  long long ev_new;  // converted new even row j-2
+  long long od_old;  // converted old odd row j-1
+  double od_raw;     // raw old odd row j-1 (for Dirichlet copies)
 };
 
 template <bool FIX>
-__device__ __forceinline__ int64_t gs2_rows(const Geo &q, int pr, const double *__restrict__ X,
-                                            const double *__restrict__ N, double *__restrict__ Y,
-                                            const double *__restrict__ f, double g, WarpScale &w, GsLane &L,
-                                            int64_t i0, int64_t i1) {
-  constexpr int PG = 3;  // centre rows in flight
-  auto ld = [&](const double *p, int64_t j) -> double {
-    return (L.xok && j >= 0 && j <= q.ny) ? p[j * q.pitch + L.x] : 0.0;
+__device__ __forceinline__ void colour_pair(long long &uc, long long V, double fv, double g, const WarpScale &w,
+                                            bool xin, int64_t x, double &out0) {
+#pragma unroll
+  for (int px = 0; px < 2; ++px) {
+    const long long T = add<FIX>(V, uc);
+    const long long Tm = __shfl_up_sync(0xffffffffu, T, 1);
+    const long long Tp = __shfl_down_sync(0xffffffffu, T, 1);
+    if (xin && (int)(x & 1) == px) {
+      const long long Nn = add<FIX>(add<FIX>(Tm, Tp), V);
+      double un;
+      if (FIX) {
+        un = fma(g, fv, fx::to_double(Nn, w.R - fx::FRAC - 3));
+        uc = fx::to_fixed(un, 1023 + w.R);
+      } else {
+        un = fma(__longlong_as_double(Nn), 0.125, g * fv);
+        uc = __double_as_longlong(un);
+      }
+      out0 = un;
+    }
+  }
+}
+
+template <bool FIX>
+__device__ __forceinline__ int64_t gs2f_rows(const Geo &q, const double *__restrict__ X, double *__restrict__ Y,
+                                             const double *__restrict__ f, double g, WarpScale &w, Gs2Lane &L,
+                                             int64_t j0, int64_t js, int64_t je) {
+  auto ldx = [&](int64_t j) -> double { return (L.xok && j >= 0 && j <= q.ny) ? X[j * q.pitch + L.x] : 0.0; };
+  auto ldf = [&](int64_t j) -> double {
+    return (L.xin && j >= 1 && j < q.ny) ? f[j * q.pitch + L.x] : 0.0;
   };
-  auto ldf = [&](int64_t j) -> double { return (L.xin && j >= 1 && j < q.ny) ? f[j * q.pitch + L.x] : 0.0; };
-  double qx[PG], qn[PG], qf[PG];
+  constexpr int PG = 2;
+  double qe[PG], qo[PG], qfe[PG], qfo[PG];  // X rows j, j+1 and f rows j, j-1 for even j
 #pragma unroll
   for (int t = 0; t < PG; ++t) {
-    const int64_t j = pr + 2 * (i0 + t);
-    const bool ok = i0 + t < i1;
-    qx[t] = ok ? ld(X, j) : 0.0;
-    qn[t] = ok ? ld(N, j + 1) : 0.0;
-    qf[t] = ok ? ldf(j) : 0.0;
+    const int64_t j = j0 + 2 * t;
+    qe[t] = ldx(j);
+    qo[t] = ldx(j + 1);
+    qfe[t] = ldf(j);
+    qfo[t] = ldf(j - 1);
   }
-  for (int64_t ib = i0; ib < i1; ib += PG) {
+  for (int64_t jb = j0; jb <= je; jb += 2 * PG) {
 #pragma unroll
     for (int t = 0; t < PG; ++t) {
-      const int64_t i = ib + t;
-      if (i >= i1) return i1;
-      const int64_t j = pr + 2 * i;
-      const double rc = qx[t], rp = qn[t], fv = qf[t];
+      const int64_t j = jb + 2 * t;
+      if (j > je) return je + 2;
+      const double rc = qe[t], rp = qo[t], fe = qfe[t], fo = qfo[t];
       if (FIX) {
         unsigned em = __reduce_max_sync(0xffffffffu, biased_exp(rc));
         em = max(em, __reduce_max_sync(0xffffffffu, biased_exp(rp)));
-        // exponent bound of g * f from the exponents (no FP64 multiply): |g f| < 2^(eg + ef)
-        const unsigned ef = __reduce_max_sync(0xffffffffu, biased_exp(fv));
+        const unsigned ef = max(__reduce_max_sync(0xffffffffu, biased_exp(fe)),
+                                __reduce_max_sync(0xffffffffu, biased_exp(fo)));
         if (ef) em = max(em, (unsigned)max(1, (int)ef + (int)biased_exp(g) - 1023 + 1));
-        const int d = admit_row(w, em, 2);  // new values <= max|u| + g max|f|: two spare bits
+        const int d = admit_row(w, em, 2);
         if (d < 0) {
-          L.um = to_f64_bits(L.um, w.R);
+          L.ev_new = to_f64_bits(L.ev_new, w.R);
+          L.od_old = to_f64_bits(L.od_old, w.R);
           w.fix = false;
-          return i;  // redo this row in FP64
+          return j;  // redo from this even row in FP64
         }
-        if (d > 0) L.um = shr(L.um, d);
+        if (d > 0) {
+          L.ev_new = shr(L.ev_new, d);
+          L.od_old = shr(L.od_old, d);
+        }
       }
-      if (i + PG < i1) {
+      {
         const int64_t jn = j + 2 * PG;
-        qx[t] = ld(X, jn);
-        qn[t] = ld(N, jn + 1);
-        qf[t] = ldf(jn);
+        qe[t] = jn <= je ? ldx(jn) : 0.0;
+        qo[t] = jn <= je ? ldx(jn + 1) : 0.0;
+        qfe[t] = jn <= je ? ldf(jn) : 0.0;
+        qfo[t] = jn <= je ? ldf(jn - 1) : 0.0;
       }
-      long long uc = FIX ? fx::to_fixed(rc, 1023 + w.R) : __double_as_longlong(rc);
-      const long long up = FIX ? fx::to_fixed(rp, 1023 + w.R) : __double_as_longlong(rp);
-      double out = rc;
-      if (j >= 1 && j < q.ny) {
-        const long long V = add<FIX>(L.um, up);
-#pragma unroll
-        for (int px = 0; px < 2; ++px) {
-          const long long T = add<FIX>(V, uc);
-          const long long Tm = __shfl_up_sync(0xffffffffu, T, 1);
-          const long long Tp = __shfl_down_sync(0xffffffffu, T, 1);
-          if (L.xin && (int)(L.x & 1) == px) {
-            const long long Nn = add<FIX>(add<FIX>(Tm, Tp), V);
-            double un;
-            if (FIX) {
-              un = fma(g, fv, fx::to_double(Nn, w.R - fx::FRAC - 3));
-              uc = fx::to_fixed(un, 1023 + w.R);
-            } else {
-              un = fma(__longlong_as_double(Nn), 0.125, g * fv);
-              uc = __double_as_longlong(un);
-            }
-            out = un;
-          }
-        }
+      // even row j: colours 0 and 1 from the old rows j-1 (od_old) and j+1
+      long long ue = FIX ? fx::to_fixed(rc, 1023 + w.R) : __double_as_longlong(rc);
+      const long long up_old = FIX ? fx::to_fixed(rp, 1023 + w.R) : __double_as_longlong(rp);
+      double oute = rc;
+      if (j >= 1 && j < q.ny) colour_pair<FIX>(ue, add<FIX>(L.od_old, up_old), fe, g, w, L.xin, L.x, oute);
+      // odd row j-1: colours 2 and 3 from the new rows j-2 (ev_new) and j (ue)
+      if (j - 1 >= js + 1) {
+        long long uo = L.od_old;
+        double outo = L.od_raw;
+        if (j - 1 < q.ny) colour_pair<FIX>(uo, add<FIX>(L.ev_new, ue), fo, g, w, L.xin, L.x, outo);
+        if (L.out_lane) Y[(j - 1) * q.pitch + L.x] = outo;
       }
-      if (L.out_lane) Y[j * q.pitch + L.x] = out;
-      L.um = up;
+      if (L.out_lane && (j < je || je == q.ny)) Y[j * q.pitch + L.x] = oute;
+      L.ev_new = ue;
+      L.od_old = up_old;
+      L.od_raw = rp;
     }
   }
-  return i1;
+  return je + 2;
 }
 
-__global__ void __launch_bounds__(W2_THREADS) k_gs2_half(Geo q, int pr, const double *__restrict__ X,
-                                                         const double *__restrict__ N, double *__restrict__ Y,
-                                                         const double *__restrict__ f, double g) {
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int64_t gw = (int64_t)blockIdx.x * (W2_THREADS / 32) + wib;
-  const int64_t nseg = (q.nx + 28) / 28;
-  const int64_t seg = gw % nseg, chunk = gw / nseg;
-  const int64_t ncentre = (q.ny - pr) / 2 + 1;
-  const int64_t i0 = chunk * (W2_ROWS / 2);
-  if (i0 >= ncentre) return;
-  const int64_t i1 = i0 + W2_ROWS / 2 < ncentre ? i0 + W2_ROWS / 2 : ncentre;
-  GsLane L;
-  L.x = seg * 28 + lane - 2;
+// One warp's share of a sweep on FP64 data with the per-warp adaptive scale.
+__device__ __forceinline__ void gs2_fused_warp(const Geo &q, const double *__restrict__ X, double *__restrict__ Y,
+                                               const double *__restrict__ f, double g, int64_t seg, int64_t js,
+                                               int lane) {
+  // last even row of the chunk (recomputed; the next chunk writes it) or the grid end
+  int64_t je = js + W2_ROWS;
+  if (je > q.ny) je = (q.ny & 1) ? q.ny + 1 : q.ny;
+  Gs2Lane L;
+  L.x = seg * 24 + lane - 4;
   L.xok = L.x >= 0 && L.x <= q.nx;
   L.xin = L.x >= 1 && L.x < q.nx;
-  L.out_lane = lane >= 2 && lane <= 29 && L.xok;
+  L.out_lane = lane >= 4 && lane <= 27 && L.xok;
   WarpScale w;
-  const int64_t jf = pr + 2 * i0;
-  const double rm = (L.xok && jf - 1 >= 0) ? N[(jf - 1) * q.pitch + L.x] : 0.0;
+  const double rm = (L.xok && js - 1 >= 0) ? X[(js - 1) * q.pitch + L.x] : 0.0;
   if (admit_row(w, __reduce_max_sync(0xffffffffu, biased_exp(rm)), 2) < 0) w.fix = false;
-  L.um = w.fix ? fx::to_fixed(rm, 1023 + w.R) : __double_as_longlong(rm);
-  int64_t i = i0;
-  if (w.fix) i = gs2_rows<true>(q, pr, X, N, Y, f, g, w, L, i, i1);
-  if (i < i1) gs2_rows<false>(q, pr, X, N, Y, f, g, w, L, i, i1);
+  L.od_old = w.fix ? fx::to_fixed(rm, 1023 + w.R) : __double_as_longlong(rm);
+  L.od_raw = rm;
+  L.ev_new = 0;
+  int64_t j = js;
+  if (w.fix) j = gs2f_rows<true>(q, X, Y, f, g, w, L, j, js, je);
+  if (j <= je) gs2f_rows<false>(q, X, Y, f, g, w, L, j, js, je);
+}
+
+__global__ void __launch_bounds__(W2_THREADS) k_gs2_fused(Geo q, const double *__restrict__ X,
+                                                          double *__restrict__ Y, const double *__restrict__ f,
+                                                          double g) {
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * (W2_THREADS / 32) + wib;
+  const int64_t nseg = (q.nx + 24) / 24;
+  const int64_t seg = gw % nseg, chunk = gw / nseg;
+  const int64_t js = chunk * W2_ROWS;  // even
+  if (js > q.ny) return;
+  gs2_fused_warp(q, X, Y, f, g, seg, js, lane);
+}
+
+// ------------------------------------------------------------------ multi-sweep form
+// Intermediate sweeps of one call keep the iterate as int64 fixed point in HBM at a
+// scale shared by the whole grid and tracked on the device (sweep_bounds.cuh), and
+// 3/8 h^2 f is precomputed once per call as fixed point (GF).  A sweep is then integer
+// arithmetic only: no conversion per element except on the first load from u and the
+// last store into u.  Same row wavefront as above.
+enum { SF_F64 = 0, SF_FXP = 1 };  // storage format: FP64, or int64 fixed point
+
+__device__ __forceinline__ void colour_pair_gs(long long &uc, long long V, long long gv, bool xin, int64_t x) {
+#pragma unroll
+  for (int px = 0; px < 2; ++px) {
+    const long long T = V + uc;
+    const long long Tm = __shfl_up_sync(0xffffffffu, T, 1);
+    const long long Tp = __shfl_down_sync(0xffffffffu, T, 1);
+    if (xin && (int)(x & 1) == px) uc = gv + ((Tm + Tp + V) >> 3);  // 3/8 h^2 f + N / 8
+  }
+}
+
+template <int XF, int YF>
+__global__ void __launch_bounds__(W2_THREADS) k_gs2_sweep(Geo q, const void *__restrict__ X, void *__restrict__ Y,
+                                                          const double *__restrict__ f,
+                                                          const long long *__restrict__ GF, SweepBounds *bnd,
+                                                          int sweep, int sweeps, double g, bool write_bnd) {
+  __shared__ long long red[W2_THREADS / 32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * (W2_THREADS / 32) + wib;
+  const int64_t nseg = (q.nx + 24) / 24;
+  const int64_t seg = gw % nseg, chunk = gw / nseg;
+  const int64_t js = chunk * W2_ROWS;  // even
+  const Plan plan = make_plan(bnd, g, sweeps);
+  if (!plan.fix) {
+    // bound unusable for fixed point: every sweep of the call keeps FP64 buffers
+    if (js <= q.ny) gs2_fused_warp(q, (const double *)X, (double *)Y, f, g, seg, js, lane);
+    return;
+  }
+  const int R = sweep_R(bnd, sweep % 4, g);
+  const int Rx = sweep > 0 ? sweep_R(bnd, (sweep + 3) % 4, g) : R;
+  const int dx = XF == SF_FXP ? R - Rx : 0, df = R - plan.Rf, rb = 1023 + R;
+  if (blockIdx.x == 0 && threadIdx.x == 0) bnd->umax[(sweep + 2) % 4] = 0ull;
+  long long vmax = 0;
+  if (js <= q.ny) {
+    int64_t je = js + W2_ROWS;
+    if (je > q.ny) je = (q.ny & 1) ? q.ny + 1 : q.ny;
+    const int64_t x = seg * 24 + lane - 4;
+    const bool xok = x >= 0 && x <= q.nx, xin = x >= 1 && x < q.nx;
+    const bool out_lane = lane >= 4 && lane <= 27 && xok;
+    const long long *Xl = (const long long *)X;
+    auto rawx = [&](int64_t j) -> long long { return (xok && j >= 0 && j <= q.ny) ? Xl[j * q.pitch + x] : 0ll; };
+    auto rawg = [&](int64_t j) -> long long { return (xin && j >= 1 && j < q.ny) ? GF[j * q.pitch + x] : 0ll; };
+    auto cvx = [&](long long raw) -> long long {
+      return XF == SF_F64 ? fx::to_fixed(__longlong_as_double(raw), rb) : shr_any(raw, dx);
+    };
+    auto put = [&](int64_t j, long long v) {
+      if (!out_lane) return;
+      const bool inner = xin && j >= 1 && j < q.ny;
+      if (!inner && !write_bnd) return;
+      if (YF == SF_FXP)
+        ((long long *)Y)[j * q.pitch + x] = v;
+      else
+        ((double *)Y)[j * q.pitch + x] = fx::to_double(v, R - fx::FRAC);
+      const long long a = v < 0 ? -v : v;
+      vmax = a > vmax ? a : vmax;
+    };
+    long long od_old = cvx(rawx(js - 1)), ev_new = 0;
+    constexpr int PG = 2;
+    long long qe[PG], qo[PG], qge[PG], qgo[PG];  // raw X rows j, j+1 and GF rows j, j-1
+#pragma unroll
+    for (int t = 0; t < PG; ++t) {
+      const int64_t j = js + 2 * t;
+      const bool ok = j <= je;
+      qe[t] = ok ? rawx(j) : 0ll;
+      qo[t] = ok ? rawx(j + 1) : 0ll;
+      qge[t] = ok ? rawg(j) : 0ll;
+      qgo[t] = ok ? rawg(j - 1) : 0ll;
+    }
+    for (int64_t jb = js; jb <= je; jb += 2 * PG) {
+#pragma unroll
+      for (int t = 0; t < PG; ++t) {
+        const int64_t j = jb + 2 * t;
+        if (j > je) break;
+        const long long rc = cvx(qe[t]), rp = cvx(qo[t]);
+        const long long ge = shr_any(qge[t], df), go = shr_any(qgo[t], df);
+        {
+          const int64_t jn = j + 2 * PG;
+          const bool ok = jn <= je;
+          qe[t] = ok ? rawx(jn) : 0ll;
+          qo[t] = ok ? rawx(jn + 1) : 0ll;
+          qge[t] = ok ? rawg(jn) : 0ll;
+          qgo[t] = ok ? rawg(jn - 1) : 0ll;
+        }
+        // even row j: colours 0 and 1 from the old rows j-1 and j+1
+        long long ue = rc;
+        if (j >= 1 && j < q.ny) colour_pair_gs(ue, od_old + rp, ge, xin, x);
+        // odd row j-1: colours 2 and 3 from the new rows j-2 and j
+        if (j - 1 >= js + 1) {
+          long long uo = od_old;
+          if (j - 1 < q.ny) colour_pair_gs(uo, ev_new + ue, go, xin, x);
+          put(j - 1, uo);
+        }
+        if (j < je || je == q.ny) put(j, ue);
+        ev_new = ue;
+        od_old = rp;
+      }
+    }
+  }
+  // block max of |new values| -> FP64 bits -> the next sweep's bound
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long w = __shfl_xor_sync(0xffffffffu, vmax, o);
+    vmax = w > vmax ? w : vmax;
+  }
+  if (lane == 0) red[wib] = vmax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long m = 0;
+    for (int w = 0; w < W2_THREADS / 32; ++w) m = red[w] > m ? red[w] : m;
+    atomicMax(&bnd->umax[(sweep + 1) % 4], fx::abs_bits(fx::to_double(m, R - fx::FRAC) * (1.0 + 0x1p-50)));
+  }
 }
 
 }  // namespace
@@ -529,26 +676,40 @@ cudaError_t launch_residual_fx2(const Geo &q, const double *u, const double *f, 
   return launch_ops2(O2_RESIDUAL, a, s);
 }
 
-// Coloured GS in 2D: per sweep an even-row pass (X -> Y) and an odd-row pass (new even
-// rows from Y); work has u's span.  The result ends in u.
-cudaError_t launch_gs_sweeps_fx2(const Geo &q, double *u, const double *f, int sweeps, double *work,
+// work: 3 arrays of u's span (8 bytes per element): two int64 ping-pong buffers and
+// GF; bounds: gs_fx_bounds_bytes() bytes.  The result always ends in u, whose boundary
+// values are never written.
+cudaError_t launch_gs_sweeps_fx2(const Geo &q, double *u, const double *f, int sweeps, double *work, void *bounds,
                                  cudaStream_t s) {
   const double g = 0.375 * q.h * q.h;
-  const int64_t nseg = (q.nx + 28) / 28;
-  const int64_t nchunk = (q.ny + 1 + W2_ROWS - 1) / W2_ROWS + 1;
+  const int64_t nseg = (q.nx + 24) / 24;
+  const int64_t nchunk = (q.ny + W2_ROWS) / W2_ROWS;
   const unsigned nb = (unsigned)((nseg * nchunk + W2_THREADS / 32 - 1) / (W2_THREADS / 32));
-  double *X = u, *Y = work;
-  for (int it = 0; it < sweeps; ++it) {
-    k_gs2_half<<<nb, W2_THREADS, 0, s>>>(q, 0, X, X, Y, f, g);
-    k_gs2_half<<<nb, W2_THREADS, 0, s>>>(q, 1, X, Y, Y, f, g);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    double *t = X;
-    X = Y;
-    Y = t;
+  const int64_t span = span_elems(q);
+  cudaError_t e;
+  if (sweeps == 1) {
+    k_gs2_fused<<<nb, W2_THREADS, 0, s>>>(q, u, work, f, g);
+    e = cudaGetLastError();
+    return e ? e : cudaMemcpyAsync(u, work, (size_t)span * sizeof(double), cudaMemcpyDeviceToDevice, s);
   }
-  if (X != u) return cudaMemcpyAsync(u, X, (size_t)span_elems(q) * sizeof(double), cudaMemcpyDeviceToDevice, s);
-  return cudaSuccess;
+  void *A = work, *B = work + span;
+  long long *GF = (long long *)(work + 2 * span);
+  SweepBounds *bnd = (SweepBounds *)bounds;
+  e = launch_gs_prepass(q, 2, u, f, GF, bounds, sweeps, s);
+  const void *X = u;
+  for (int it = 0; it < sweeps && !e; ++it) {
+    const bool first = it == 0, last = it == sweeps - 1;
+    void *Y = last ? (void *)u : (it % 2 == 0 ? A : B);
+    if (first)
+      k_gs2_sweep<SF_F64, SF_FXP><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, true);
+    else if (!last)
+      k_gs2_sweep<SF_FXP, SF_FXP><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, true);
+    else  // the caller's u: its Dirichlet values were never overwritten, leave them
+      k_gs2_sweep<SF_FXP, SF_F64><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, false);
+    e = cudaGetLastError();
+    X = Y;
+  }
+  return e;
 }
 
 }  // namespace stencil

@@ -28,7 +28,7 @@ namespace {
 constexpr int OT_X = 60, OT_Y = 32;          // outputs per tile
 constexpr int OS_W = 64, OS_H = OT_Y + 2;    // staged plane: 64 columns (62 used) x 34 rows
 constexpr int O_THREADS = 256;
-constexpr int O_CZ = 32;                     // output planes per CTA
+constexpr int O_CZ = 32;                     // output planes per CTA (at most)
 constexpr int O_PER = (OS_W * OS_H + O_THREADS - 1) / O_THREADS;  // prefetched values / thread
 constexpr size_t O_SMEM = 3 * OS_H * OS_W * sizeof(long long);
 constexpr int R_MIN = -900, R_MAX = 1000;
@@ -46,6 +46,7 @@ struct OpArgs {
   unsigned *counter; // residual: CTAs finished
   double *norms2;    // residual: [sum r^2, sum f^2]
   int out_kind;      // residual: 0 = r in FP64, 1 = FP32, 2 = bf16 (FP64 -> FP32 -> bf16)
+  int cz;            // output planes per CTA
 };
 
 __device__ __forceinline__ void prefetch_plane(double (&v)[O_PER], const Geo &q, const double *src,
@@ -183,8 +184,8 @@ __global__ void __launch_bounds__(O_THREADS, 2) k_ops3(OpArgs a) {
   __shared__ bool last;
   const Geo &q = a.q;
   const int64_t x0 = (int64_t)blockIdx.x * OT_X, y0 = (int64_t)blockIdx.y * OT_Y;
-  const int64_t zs = (int64_t)blockIdx.z * O_CZ;
-  const int64_t ze = zs + O_CZ < q.nz + 1 ? zs + O_CZ : q.nz + 1;
+  const int64_t zs = (int64_t)blockIdx.z * a.cz;
+  const int64_t ze = zs + a.cz < q.nz + 1 ? zs + a.cz : q.nz + 1;
   long long *slot[3] = {smem, smem + OS_H * OS_W, smem + 2 * OS_H * OS_W};
   // interior tile: every staged vertex in the grid, every output an interior vertex
   const bool inner_tile = x0 >= 1 && x0 + OT_X <= q.nx && y0 >= 1 && y0 + OT_Y <= q.ny;
@@ -314,9 +315,15 @@ __global__ void __launch_bounds__(O_THREADS, 2) k_ops3(OpArgs a) {
   }
 }
 
+int ops_cz(const Geo &q) {
+  const int64_t txy = ((q.nx + OT_X) / OT_X) * ((q.ny + OT_Y) / OT_Y);
+  return z_chunk(txy, q.nz + 1, O_CZ, 4, 2);
+}
+
 dim3 ops_grid(const Geo &q) {
+  const int cz = ops_cz(q);
   return dim3((unsigned)((q.nx + OT_X) / OT_X), (unsigned)((q.ny + OT_Y) / OT_Y),
-              (unsigned)((q.nz + O_CZ) / O_CZ));
+              (unsigned)((q.nz + cz) / cz));
 }
 
 template <int OP>
@@ -330,7 +337,9 @@ cudaError_t launch_op(const OpArgs &a, cudaStream_t s) {
   const dim3 g = ops_grid(a.q);
   if (g.y > 65535 || g.z > 65535) return cudaErrorInvalidConfiguration;
   if (a.q.plane >= ((int64_t)1 << 31) - OS_W * OS_H) return cudaErrorInvalidValue;
-  k_ops3<OP><<<g, O_THREADS, O_SMEM, s>>>(a);
+  OpArgs b = a;
+  b.cz = ops_cz(a.q);
+  k_ops3<OP><<<g, O_THREADS, O_SMEM, s>>>(b);
   return cudaGetLastError();
 }
 
@@ -364,15 +373,12 @@ cudaError_t launch_jacobi_fx3(const Geo &q, const double *u, const double *f, do
 
 cudaError_t launch_residual_fx3(const Geo &q, const double *u, const double *f, double *r,
                                 double *norms2, void *scratch, cudaStream_t s, int out_kind) {
-  const dim3 g = ops_grid(q);
-  const size_t nblk = (size_t)g.x * g.y * g.z;
   OpArgs a{};
   a.q = q;
   a.u = u;
   a.f = f;
   a.out = r;
   a.c1 = -1.0 / (12.0 * q.h * q.h);
-  (void)nblk;
   a.counter = (unsigned *)scratch;  // counter first, partials after (same layout everywhere)
   a.partials = (double *)((char *)scratch + 16);
   a.norms2 = norms2;
