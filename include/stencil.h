@@ -101,8 +101,8 @@ int stencil_apply(const stencil_grid_t *g, const void *u, void *y, int form, voi
  * u: device array (in/out); f: device array, may not alias u.  dtype F64 (2D, 3D);
  * F32 or BF16 (3D): values stored in that type, arithmetic in FP32, every store of a
  * bf16 value rounded to nearest even.
- * The call may use an internal device workspace of the size of u (allocated on first
- * use and kept; see stencil_release_workspace).
+ * The call may use an internal device workspace of up to three times the size of u
+ * (allocated on first use and kept; see stencil_release_workspace).
  * Returns STENCIL_EINVAL, STENCIL_ENOMEM, STENCIL_ECUDA.
  */
 int stencil_smooth_coloured(const stencil_grid_t *g, void *u, const void *f, int sweeps,
@@ -112,9 +112,11 @@ int stencil_smooth_coloured(const stencil_grid_t *g, void *u, const void *f, int
  * `sweeps` damped Jacobi sweeps, out of place:
  *   u_i <- u_i + omega * (h^2 f_i - (S u)_i) / S_ii   on interior vertices,
  * every new value computed from the previous sweep's array (the contrast to the
- * in-situ update of Section 2).  work: caller-owned device array with the layout of u;
- * its boundary is overwritten with u's.  The result of the last sweep is in u.
- * dtype F64.  Returns STENCIL_EINVAL, STENCIL_ECUDA.
+ * in-situ update of Section 2).  work: caller-owned device array with the layout of u,
+ * used as scratch (its contents on return are unspecified).  The result of the last
+ * sweep is in u; boundary values of u are never changed.  The call may use an internal
+ * device workspace of twice the size of u (allocated on first use and kept).
+ * dtype F64.  Returns STENCIL_EINVAL, STENCIL_ENOMEM, STENCIL_ECUDA.
  */
 int stencil_smooth_jacobi(const stencil_grid_t *g, void *u, const void *f, void *work,
                           int sweeps, double omega, void *stream);

@@ -113,6 +113,10 @@ cudaError_t launch_residual_fx2(const Geo &q, const double *u, const double *f, 
 // 2D coloured GS, one launch per sweep; work and bounds as for the 3D form.
 cudaError_t launch_gs_sweeps_fx2(const Geo &q, double *u, const double *f, int sweeps, double *work,
                                  void *bounds, cudaStream_t s);
+// Multi-sweep damped Jacobi, 2D, 0 < omega <= 1, int64 fixed point between sweeps.
+// A: one u-sized buffer; scratch: two; bounds: gs_fx_bounds_bytes().  Result in u.
+cudaError_t launch_jacobi_sweeps_fx2(const Geo &q, double *u, const double *f, int sweeps, double omega, double *A,
+                                     double *scratch, void *bounds, cudaStream_t s);
 // out_kind: r stored as 0 = FP64, 1 = FP32, 2 = bf16 (r is an element pointer of that
 // type passed as double*; the layout is u's).
 cudaError_t launch_residual_fx3(const Geo &q, const double *u, const double *f, double *r,

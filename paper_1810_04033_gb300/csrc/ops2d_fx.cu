@@ -26,7 +26,8 @@ namespace stencil {
 namespace {
 
 constexpr int W2_THREADS = 128;
-constexpr int W2_ROWS = 64;  // rows per warp
+constexpr int W2_ROWS = 64;   // rows per warp (single-pass operations)
+constexpr int S2_ROWS = 256;  // rows per warp (multi-sweep GS and Jacobi)
 constexpr int R_MIN = -900, R_MAX = 1000;
 
 enum { O2_APPLY = 0, O2_JACOBI = 1, O2_RESIDUAL = 2, O2_ELEMENTWISE = 3 };
@@ -143,31 +144,36 @@ __device__ __forceinline__ int64_t ew2_rows(const Op2Args &a, WarpScale &w, Stre
       const long long v1 = __shfl_down_sync(0xffffffffu, ua, 1);
       const long long v3 = __shfl_down_sync(0xffffffffu, ub, 1);
       const bool cell = s.lane <= 30 && s.x >= 0 && s.x < q.nx && cj >= 0 && cj < q.ny;
-      // two colour passes over the x parity; the right-hand vertices' shares move to
-      // the next lane
-#pragma unroll
-      for (int px = 0; px < 2; ++px) {
-        const bool mine = cell && (int)(s.x & 1) == px;
-        long long c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-        if (mine) {
-          if (FIX) {
-            c0 = 4 * ua - (v1 + ub) - 2 * v3;
-            c1 = 4 * v1 - (ua + v3) - 2 * ub;
-            c2 = 4 * ub - (ua + v3) - 2 * v1;
-            c3 = 4 * v3 - (v1 + ub) - 2 * ua;
-          } else {
-            const double A0 = __longlong_as_double(ua), A1 = __longlong_as_double(v1),
-                         A2 = __longlong_as_double(ub), A3 = __longlong_as_double(v3);
-            c0 = __double_as_longlong(4.0 * A0 - (A1 + A2) - 2.0 * A3);
-            c1 = __double_as_longlong(4.0 * A1 - (A0 + A3) - 2.0 * A2);
-            c2 = __double_as_longlong(4.0 * A2 - (A0 + A3) - 2.0 * A1);
-            c3 = __double_as_longlong(4.0 * A3 - (A1 + A2) - 2.0 * A0);
-          }
+      // Every lane forms its own cell's four contributions; each vertex column is owned
+      // by one lane, which adds the share of its own cell and (by shuffle) that of the
+      // cell on its left, so the scatter has no write conflicts.  In fixed point the
+      // sums are exact, so the order of the two x colours is immaterial; the FP64 path
+      // adds the even-x colour's share first.
+      long long c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+      if (cell) {
+        if (FIX) {
+          const long long s1 = v1 + ub, s2 = ua + v3;
+          c0 = 4 * ua - s1 - 2 * v3;
+          c1 = 4 * v1 - s2 - 2 * ub;
+          c2 = 4 * ub - s2 - 2 * v1;
+          c3 = 4 * v3 - s1 - 2 * ua;
+        } else {
+          const double A0 = __longlong_as_double(ua), A1 = __longlong_as_double(v1),
+                       A2 = __longlong_as_double(ub), A3 = __longlong_as_double(v3);
+          c0 = __double_as_longlong(4.0 * A0 - (A1 + A2) - 2.0 * A3);
+          c1 = __double_as_longlong(4.0 * A1 - (A0 + A3) - 2.0 * A2);
+          c2 = __double_as_longlong(4.0 * A2 - (A0 + A3) - 2.0 * A1);
+          c3 = __double_as_longlong(4.0 * A3 - (A1 + A2) - 2.0 * A0);
         }
-        const long long c1l = __shfl_up_sync(0xffffffffu, c1, 1);
-        const long long c3l = __shfl_up_sync(0xffffffffu, c3, 1);
-        alo = add<FIX>(alo, add<FIX>(c0, s.lane >= 1 ? c1l : 0));
-        ahi = add<FIX>(ahi, add<FIX>(c2, s.lane >= 1 ? c3l : 0));
+      }
+      long long c1l = __shfl_up_sync(0xffffffffu, c1, 1), c3l = __shfl_up_sync(0xffffffffu, c3, 1);
+      if (s.lane == 0) c1l = c3l = 0;
+      if (FIX || (s.x & 1) == 0) {  // own cell has the even-x colour: it goes first
+        alo = add<FIX>(add<FIX>(alo, c0), c1l);
+        ahi = add<FIX>(add<FIX>(ahi, c2), c3l);
+      } else {
+        alo = add<FIX>(add<FIX>(alo, c1l), c0);
+        ahi = add<FIX>(add<FIX>(ahi, c3l), c2);
       }
       if (cj >= js && s.out_lane) {
         const bool inner = s.xin && cj >= 1 && cj < q.ny;
@@ -252,18 +258,14 @@ __device__ __forceinline__ int64_t op2_rows(const Op2Args &a, WarpScale &w, Stre
   return je;
 }
 
+// One warp's share of k_ops2: a segment of 30 output columns and a chunk of rows.
 template <int OP>
-__global__ void __launch_bounds__(W2_THREADS) k_ops2(Op2Args a) {
-  __shared__ double sh[2 * W2_THREADS / 32];
-  __shared__ bool last;
+__device__ __forceinline__ void ops2_warp(const Op2Args &a, int lane, int64_t gw, Stream2 &s, int rows) {
   const Geo &q = a.q;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int64_t gw = (int64_t)blockIdx.x * (W2_THREADS / 32) + wib;
   const int64_t nseg = (q.nx + 30) / 30;  // 30 outputs per segment
   const int64_t seg = gw % nseg, chunk = gw / nseg;
-  const int64_t js = chunk * W2_ROWS;
-  const int64_t je = js + W2_ROWS < q.ny + 1 ? js + W2_ROWS : q.ny + 1;
-  Stream2 s;
+  const int64_t js = chunk * rows;
+  const int64_t je = js + rows < q.ny + 1 ? js + rows : q.ny + 1;
   s.lane = lane;
   s.x = seg * 30 + lane - 1;  // lanes 1..30 produce outputs
   s.xok = s.x >= 0 && s.x <= q.nx;
@@ -300,6 +302,15 @@ __global__ void __launch_bounds__(W2_THREADS) k_ops2(Op2Args a) {
       if (j < je) op2_rows<false, OP>(a, w, s, j, js, je);
     }
   }
+}
+
+template <int OP>
+__global__ void __launch_bounds__(W2_THREADS) k_ops2(Op2Args a) {
+  __shared__ double sh[2 * W2_THREADS / 32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  Stream2 s;
+  ops2_warp<OP>(a, lane, (int64_t)blockIdx.x * (W2_THREADS / 32) + wib, s, W2_ROWS);
   double rr = s.rr, ff = s.ff;
   if (OP == O2_RESIDUAL) {
 #pragma unroll
@@ -474,9 +485,9 @@ __device__ __forceinline__ int64_t gs2f_rows(const Geo &q, const double *__restr
 // One warp's share of a sweep on FP64 data with the per-warp adaptive scale.
 __device__ __forceinline__ void gs2_fused_warp(const Geo &q, const double *__restrict__ X, double *__restrict__ Y,
                                                const double *__restrict__ f, double g, int64_t seg, int64_t js,
-                                               int lane) {
+                                               int lane, int rows) {
   // last even row of the chunk (recomputed; the next chunk writes it) or the grid end
-  int64_t je = js + W2_ROWS;
+  int64_t je = js + rows;
   if (je > q.ny) je = (q.ny & 1) ? q.ny + 1 : q.ny;
   Gs2Lane L;
   L.x = seg * 24 + lane - 4;
@@ -501,9 +512,9 @@ __global__ void __launch_bounds__(W2_THREADS) k_gs2_fused(Geo q, const double *_
   const int64_t gw = (int64_t)blockIdx.x * (W2_THREADS / 32) + wib;
   const int64_t nseg = (q.nx + 24) / 24;
   const int64_t seg = gw % nseg, chunk = gw / nseg;
-  const int64_t js = chunk * W2_ROWS;  // even
+  const int64_t js = chunk * S2_ROWS;  // even
   if (js > q.ny) return;
-  gs2_fused_warp(q, X, Y, f, g, seg, js, lane);
+  gs2_fused_warp(q, X, Y, f, g, seg, js, lane, S2_ROWS);
 }
 
 // ------------------------------------------------------------------ multi-sweep form
@@ -534,11 +545,11 @@ __global__ void __launch_bounds__(W2_THREADS) k_gs2_sweep(Geo q, const void *__r
   const int64_t gw = (int64_t)blockIdx.x * (W2_THREADS / 32) + wib;
   const int64_t nseg = (q.nx + 24) / 24;
   const int64_t seg = gw % nseg, chunk = gw / nseg;
-  const int64_t js = chunk * W2_ROWS;  // even
+  const int64_t js = chunk * S2_ROWS;  // even
   const Plan plan = make_plan(bnd, g, sweeps);
   if (!plan.fix) {
     // bound unusable for fixed point: every sweep of the call keeps FP64 buffers
-    if (js <= q.ny) gs2_fused_warp(q, (const double *)X, (double *)Y, f, g, seg, js, lane);
+    if (js <= q.ny) gs2_fused_warp(q, (const double *)X, (double *)Y, f, g, seg, js, lane, S2_ROWS);
     return;
   }
   const int R = sweep_R(bnd, sweep % 4, g);
@@ -547,7 +558,7 @@ __global__ void __launch_bounds__(W2_THREADS) k_gs2_sweep(Geo q, const void *__r
   if (blockIdx.x == 0 && threadIdx.x == 0) bnd->umax[(sweep + 2) % 4] = 0ull;
   long long vmax = 0;
   if (js <= q.ny) {
-    int64_t je = js + W2_ROWS;
+    int64_t je = js + S2_ROWS;
     if (je > q.ny) je = (q.ny & 1) ? q.ny + 1 : q.ny;
     const int64_t x = seg * 24 + lane - 4;
     const bool xok = x >= 0 && x <= q.nx, xin = x >= 1 && x < q.nx;
@@ -626,6 +637,112 @@ __global__ void __launch_bounds__(W2_THREADS) k_gs2_sweep(Geo q, const void *__r
   }
 }
 
+// Multi-sweep damped Jacobi in the same global-scale fixed point (0 < omega <= 1):
+//   u' = u + omega (3/8 h^2 f + N/8 - u),
+// with omega applied as an integer product: floor(D * Wq / 2^62), Wq = omega 2^62
+// rounded, exact to one unit of the last fixed-point place.  |u'| <= max|u| +
+// omega 3/8 h^2 max|f|, within the bound of sweep_bounds.cuh.  If the plan rules out
+// fixed point, every sweep of the call runs the FP64-capable single-sweep path on FP64
+// buffers.
+__device__ __forceinline__ long long omega_times(long long D, long long Wq) {
+  const long long hi = __mul64hi(D, Wq);
+  const unsigned long long lo = (unsigned long long)D * (unsigned long long)Wq;
+  return (long long)(((unsigned long long)hi << 2) | (lo >> 62));
+}
+
+template <int XF, int YF>
+__global__ void __launch_bounds__(W2_THREADS) k_jac2_sweep(Geo q, const void *__restrict__ X, void *__restrict__ Y,
+                                                           const double *__restrict__ f,
+                                                           const long long *__restrict__ GF, SweepBounds *bnd,
+                                                           int sweep, int sweeps, double g, double omega,
+                                                           long long Wq, bool write_bnd) {
+  __shared__ long long red[W2_THREADS / 32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * (W2_THREADS / 32) + wib;
+  const Plan plan = make_plan(bnd, g, sweeps);
+  if (!plan.fix) {
+    Op2Args a{};
+    a.q = q;
+    a.u = (const double *)X;
+    a.f = f;
+    a.out = (double *)Y;
+    a.c1 = omega * g;
+    a.c2 = -omega * 0.375 / 3.0;
+    Stream2 s;
+    ops2_warp<O2_JACOBI>(a, lane, gw, s, S2_ROWS);
+    return;
+  }
+  const int R = sweep_R(bnd, sweep % 4, g);
+  const int Rx = sweep > 0 ? sweep_R(bnd, (sweep + 3) % 4, g) : R;
+  const int dx = XF == SF_FXP ? R - Rx : 0, df = R - plan.Rf, rb = 1023 + R;
+  if (blockIdx.x == 0 && threadIdx.x == 0) bnd->umax[(sweep + 2) % 4] = 0ull;
+  const int64_t nseg = (q.nx + 30) / 30;
+  const int64_t seg = gw % nseg, chunk = gw / nseg;
+  const int64_t js = chunk * S2_ROWS;
+  long long vmax = 0;
+  if (js <= q.ny) {
+    const int64_t je = js + S2_ROWS < q.ny + 1 ? js + S2_ROWS : q.ny + 1;
+    const int64_t x = seg * 30 + lane - 1;
+    const bool xok = x >= 0 && x <= q.nx, xin = x >= 1 && x < q.nx;
+    const bool out_lane = lane >= 1 && lane <= 30 && xok;
+    const long long *Xl = (const long long *)X;
+    auto rawx = [&](int64_t j) -> long long { return (xok && j >= 0 && j <= q.ny) ? Xl[j * q.pitch + x] : 0ll; };
+    auto rawg = [&](int64_t j) -> long long { return (xin && j >= 1 && j < q.ny) ? GF[j * q.pitch + x] : 0ll; };
+    auto cvx = [&](long long raw) -> long long {
+      return XF == SF_F64 ? fx::to_fixed(__longlong_as_double(raw), rb) : shr_any(raw, dx);
+    };
+    long long um = cvx(rawx(js - 1)), uc = cvx(rawx(js)), up = cvx(rawx(js + 1));
+    constexpr int PQ = 3;
+    long long qx[PQ], qg[PQ];  // raw X row j + 2 and GF row j for the iteration j = jb + t
+#pragma unroll
+    for (int t = 0; t < PQ; ++t) {
+      qx[t] = rawx(js + 2 + t);
+      qg[t] = rawg(js + t);
+    }
+    for (int64_t jb = js; jb < je; jb += PQ) {
+#pragma unroll
+      for (int t = 0; t < PQ; ++t) {
+        const int64_t j = jb + t;
+        if (j >= je) break;
+        const long long rn = qx[t], gr = qg[t];
+        qx[t] = j + 2 + PQ <= je ? rawx(j + 2 + PQ) : 0ll;
+        qg[t] = j + PQ < je ? rawg(j + PQ) : 0ll;
+        const long long V = um + up, T = V + uc;
+        const long long Tm = __shfl_up_sync(0xffffffffu, T, 1);
+        const long long Tp = __shfl_down_sync(0xffffffffu, T, 1);
+        if (out_lane) {
+          const bool inner = xin && j >= 1 && j < q.ny;
+          long long un = uc;  // Dirichlet value carried
+          if (inner) un = uc + omega_times(shr_any(gr, df) + ((Tm + Tp + V) >> 3) - uc, Wq);
+          if (inner || write_bnd) {
+            if (YF == SF_FXP)
+              ((long long *)Y)[j * q.pitch + x] = un;
+            else
+              ((double *)Y)[j * q.pitch + x] = fx::to_double(un, R - fx::FRAC);
+            const long long aa = un < 0 ? -un : un;
+            vmax = aa > vmax ? aa : vmax;
+          }
+        }
+        um = uc;
+        uc = up;
+        up = cvx(rn);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long w = __shfl_xor_sync(0xffffffffu, vmax, o);
+    vmax = w > vmax ? w : vmax;
+  }
+  if (lane == 0) red[wib] = vmax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long m = 0;
+    for (int w = 0; w < W2_THREADS / 32; ++w) m = red[w] > m ? red[w] : m;
+    atomicMax(&bnd->umax[(sweep + 1) % 4], fx::abs_bits(fx::to_double(m, R - fx::FRAC) * (1.0 + 0x1p-50)));
+  }
+}
+
 }  // namespace
 
 size_t ops2_reduce_bytes(const Geo &q) { return 16 + (size_t)ops2_blocks(q) * 2 * sizeof(double); }
@@ -683,7 +800,7 @@ cudaError_t launch_gs_sweeps_fx2(const Geo &q, double *u, const double *f, int s
                                  cudaStream_t s) {
   const double g = 0.375 * q.h * q.h;
   const int64_t nseg = (q.nx + 24) / 24;
-  const int64_t nchunk = (q.ny + W2_ROWS) / W2_ROWS;
+  const int64_t nchunk = (q.ny + S2_ROWS) / S2_ROWS;
   const unsigned nb = (unsigned)((nseg * nchunk + W2_THREADS / 32 - 1) / (W2_THREADS / 32));
   const int64_t span = span_elems(q);
   cudaError_t e;
@@ -706,6 +823,45 @@ cudaError_t launch_gs_sweeps_fx2(const Geo &q, double *u, const double *f, int s
       k_gs2_sweep<SF_FXP, SF_FXP><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, true);
     else  // the caller's u: its Dirichlet values were never overwritten, leave them
       k_gs2_sweep<SF_FXP, SF_F64><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, false);
+    e = cudaGetLastError();
+    X = Y;
+  }
+  return e;
+}
+
+}  // namespace stencil
+
+namespace stencil {
+
+// Multi-sweep damped Jacobi, 2D, 0 < omega <= 1.  A: u-sized buffer (the caller's
+// work array); scratch: 2 u-sized buffers (second ping-pong buffer and GF); bounds:
+// gs_fx_bounds_bytes().  The result ends in u; u's boundary is never written.
+cudaError_t launch_jacobi_sweeps_fx2(const Geo &q, double *u, const double *f, int sweeps, double omega, double *A,
+                                     double *scratch, void *bounds, cudaStream_t s) {
+  const double g = 0.375 * q.h * q.h;
+  const int64_t nseg = (q.nx + 30) / 30;
+  const int64_t nchunk = (q.ny + S2_ROWS) / S2_ROWS;
+  const unsigned nb = (unsigned)((nseg * nchunk + W2_THREADS / 32 - 1) / (W2_THREADS / 32));
+  const int64_t span = span_elems(q);
+  void *B = scratch;
+  long long *GF = (long long *)(scratch + span);
+  SweepBounds *bnd = (SweepBounds *)bounds;
+  const long long Wq = (long long)llrint(omega * 0x1p62);
+  if (sweeps == 1) {  // u -> A (boundary copied), then back
+    cudaError_t e = launch_jacobi_fx2(q, u, f, A, omega, s);
+    return e ? e : cudaMemcpyAsync(u, A, (size_t)span * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  }
+  cudaError_t e = launch_gs_prepass(q, 2, u, f, GF, bounds, sweeps, s);
+  const void *X = u;
+  for (int it = 0; it < sweeps && !e; ++it) {
+    const bool first = it == 0, last = it == sweeps - 1;
+    void *Y = last ? (void *)u : (it % 2 == 0 ? (void *)A : B);
+    if (first)
+      k_jac2_sweep<SF_F64, SF_FXP><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, omega, Wq, true);
+    else if (!last)
+      k_jac2_sweep<SF_FXP, SF_FXP><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, omega, Wq, true);
+    else
+      k_jac2_sweep<SF_FXP, SF_F64><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, omega, Wq, false);
     e = cudaGetLastError();
     X = Y;
   }

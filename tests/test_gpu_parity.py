@@ -76,19 +76,33 @@ def test_gs_zero_sweeps_is_identity():
     assert np.array_equal(to_host(ud), u0)
 
 
+def _boundary(a):
+    """All boundary entries (first/last index on any axis), flattened."""
+    m = np.zeros(a.shape, dtype=bool)
+    for ax in range(a.ndim):
+        idx = [slice(None)] * a.ndim
+        idx[ax] = 0
+        m[tuple(idx)] = True
+        idx[ax] = -1
+        m[tuple(idx)] = True
+    return a[m]
+
+
 @pytest.mark.parametrize("dim,n", list(_cases()))
-@pytest.mark.parametrize("sweeps", [1, 2])
-def test_jacobi(dim, n, sweeps):
+@pytest.mark.parametrize("sweeps,omega", [(1, 2.0 / 3.0), (2, 2.0 / 3.0), (5, 2.0 / 3.0), (3, 1.0), (3, 1.3)])
+def test_jacobi(dim, n, sweeps, omega):
     h = 1.0 / max(n)
     shape = synth.grid_shape(dim, n)
     u0 = synth.uniform_field(shape, 400 + sum(n), zero_bc=False)
     f = synth.uniform_field(shape, 500 + sum(n))
-    ref = oracle.jacobi(u0, f, h, 2.0 / 3.0, sweeps)
+    ref = oracle.jacobi(u0, f, h, omega, sweeps)
     ud, fd = to_dev(u0), to_dev(f)
     wd = torch.empty_like(ud)
-    st.stencil_smooth_jacobi(ud, fd, wd, h, sweeps, 2.0 / 3.0)
+    st.stencil_smooth_jacobi(ud, fd, wd, h, sweeps, omega)
     torch.cuda.synchronize()
-    assert rel_err(to_host(ud), ref) <= TOL_F64
+    got = to_host(ud)
+    assert rel_err(got, ref) <= TOL_F64
+    assert np.array_equal(_boundary(got), _boundary(u0))  # Dirichlet data untouched
 
 
 @pytest.mark.parametrize("dim,n", list(_cases()))
@@ -275,7 +289,7 @@ def test_full_size_sampled_apply_and_gs():
     assert rel_err(ud.cpu().numpy(), ref) <= TOL_F64
 
 
-@pytest.mark.parametrize("n", [(200, 150), (61, 300), (29, 29), (31, 130)])
+@pytest.mark.parametrize("n", [(200, 150), (61, 300), (29, 29), (31, 130), (45, 601), (70, 514)])
 def test_2d_ops_multi_segment(n):
     """2D apply (both forms), GS, Jacobi step and residual over several warp segments
     and row chunks."""
@@ -304,8 +318,11 @@ def test_2d_ops_multi_segment(n):
     for sweeps in (1, 2, 3):
         gd = to_dev(u, pad=5)
         st.stencil_smooth_coloured(gd, fd, h, sweeps)
+        jd = to_dev(u, pad=5)
+        st.stencil_smooth_jacobi(jd, fd, to_dev(np.zeros(shape), pad=5), h, sweeps, 2.0 / 3.0)
         torch.cuda.synchronize()
         assert rel_err(to_host(gd), oracle.gs_coloured(u, f, h, sweeps)) <= TOL_F64, sweeps
+        assert rel_err(to_host(jd), oracle.jacobi(u, f, h, 2.0 / 3.0, sweeps)) <= TOL_F64, sweeps
 
 
 @pytest.mark.parametrize("scale", [1e300, 1e-280, 1e-7])
@@ -330,3 +347,12 @@ def test_2d_extreme_and_growing_magnitudes(scale):
     torch.cuda.synchronize()
     assert rel_err(to_host(gd), oracle.gs_coloured(u, f, h, 2)) <= TOL_F64
     assert rel_err(to_host(od), oracle.jacobi(u, f, h, 0.9, 1)) <= TOL_F64
+    # several sweeps per call: fixed point between sweeps where the bound allows it,
+    # FP64 buffers throughout where it does not (1e300)
+    gd = ud.clone()
+    st.stencil_smooth_coloured(gd, fd, h, 4)
+    jd = ud.clone()
+    st.stencil_smooth_jacobi(jd, fd, torch.empty_like(ud), h, 4, 0.9)
+    torch.cuda.synchronize()
+    assert rel_err(to_host(gd), oracle.gs_coloured(u, f, h, 4)) <= TOL_F64
+    assert rel_err(to_host(jd), oracle.jacobi(u, f, h, 0.9, 4)) <= TOL_F64
