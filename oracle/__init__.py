@@ -40,6 +40,12 @@ def lib():
                                      ctypes.POINTER(ctypes.c_int)]),
             "oracle_patch_halo_fill": (None, [i32p, i32p, i64p, dp]),
             "oracle_patch_smooth": (None, [i32p, i32p, i64p, dp, dp, ci, ci]),
+            "oracle_mg_levels": (ci, [ci, i64p, ci]),
+            "oracle_mg_restrict": (None, [ci, i64p, dp, dp]),
+            "oracle_mg_prolong_add": (None, [ci, i64p, dp, dp]),
+            "oracle_mg_vcycle": (None, [ci, i64p, cd, dp, dp, ci, ci, ci, ci]),
+            "oracle_mg_solve": (ci, [ci, i64p, cd, dp, dp, cd, ci, ci, ci, ci, ci, dp,
+                                     ctypes.POINTER(ctypes.c_int)]),
             "oracle_f32_to_bf16": (ctypes.c_uint16, [ctypes.c_float]),
             "oracle_bf16_to_f32": (ctypes.c_float, [ctypes.c_uint16]),
         }
@@ -168,6 +174,60 @@ def ir_solve(x0, f, h, tol, max_outer, inner_sweeps, inner_prec, keep_history=Fa
     if keep_history:
         out = out + (hist[:k],)
     return out
+
+
+def _coarse_shape(shape):
+    return tuple((m - 1) // 2 + 1 for m in shape)
+
+
+def mg_levels(shape, max_levels=64):
+    """Grids in the multigrid hierarchy of a vertex array of this shape."""
+    dim, n = _grid(shape)
+    return lib().oracle_mg_levels(dim, _ptr(n, ctypes.c_int64), max_levels)
+
+
+def mg_restrict(rf):
+    """Full-weighting restriction of a fine vertex array (even cells per axis)."""
+    rf = _f64(rf)
+    dim, nf = _grid(rf.shape)
+    nc = nf // 2
+    rc = np.zeros(_coarse_shape(rf.shape))
+    lib().oracle_mg_restrict(dim, _ptr(nc, ctypes.c_int64), _ptr(rf, ctypes.c_double),
+                             _ptr(rc, ctypes.c_double))
+    return rc
+
+
+def mg_prolong_add(ec, uf):
+    """uf + P ec on the fine interior (uf's boundary unchanged)."""
+    ec = _f64(ec)
+    u = _f64(uf).copy()
+    dim, nc = _grid(ec.shape)
+    lib().oracle_mg_prolong_add(dim, _ptr(nc, ctypes.c_int64), _ptr(ec, ctypes.c_double),
+                                _ptr(u, ctypes.c_double))
+    return u
+
+
+def mg_vcycle(u0, f, h, levels, pre=2, post=2, coarse_sweeps=20):
+    u = _f64(u0).copy()
+    f = _f64(f)
+    dim, n = _grid(u.shape)
+    lib().oracle_mg_vcycle(dim, _ptr(n, ctypes.c_int64), h, _ptr(u, ctypes.c_double),
+                           _ptr(f, ctypes.c_double), levels, pre, post, coarse_sweeps)
+    return u
+
+
+def mg_solve(u0, f, h, tol, max_cycles, levels=64, pre=2, post=2, coarse_sweeps=20):
+    """Returns (u, relres history, cycles, converged)."""
+    u = _f64(u0).copy()
+    f = _f64(f)
+    dim, n = _grid(u.shape)
+    levels = min(levels, mg_levels(u.shape))
+    relres = np.zeros(max_cycles + 1)
+    conv = ctypes.c_int(0)
+    k = lib().oracle_mg_solve(dim, _ptr(n, ctypes.c_int64), h, _ptr(u, ctypes.c_double),
+                              _ptr(f, ctypes.c_double), tol, max_cycles, levels, pre, post,
+                              coarse_sweeps, _ptr(relres, ctypes.c_double), ctypes.byref(conv))
+    return u, relres[:k + 1], k, bool(conv.value)
 
 
 def patch_halo_fill(lat, np_sizes, offsets, u_all):

@@ -28,6 +28,10 @@
  *   oracle_residual           pinned: dense brute force; zero at the discrete solution.
  *   oracle_ir_solve           pinned: converges to the closed-form discrete solution of
  *                             the manufactured problem; FP64 inner equals plain GS.
+ *   oracle_mg_*               pinned: Galerkin identity R A_h P = A_2h on random
+ *                             coarse vectors; P reproduces d-linear functions; R is
+ *                             P^T / 2^d (adjoint identity); the solve reaches the
+ *                             closed-form discrete solution; V-cycle contraction.
  *   oracle_patch_*            parity unpinned beyond: a single patch with zero
  *                             neighbours equals a plain Dirichlet GS; equal-size
  *                             neighbours copy the first interior layer (the halo rule
@@ -488,4 +492,140 @@ void oracle_patch_smooth(const int32_t *lat, const int32_t *np,
                          nthreads);
     }
   }
+}
+
+/* ------------------------------------------------------ geometric multigrid */
+
+/* The paper names smoothers of matrix-free multigrid codes as the use of its sweeps
+ * (Section 1).  A standard vertex-centred V-cycle with the coloured Gauss-Seidel as
+ * smoother, written out from its textbook definition:
+ *   coarse grid: every second vertex, n_c = n / 2 cells per axis, h_c = 2 h;
+ *   prolongation P: d-linear interpolation of the coarse values (coarse boundary 0);
+ *   restriction R = P^T / 2^d (full weighting: weight prod_a (1 - |o_a|/2) / 2^d at
+ *   fine offset o in {-1,0,1}^d), which for the Q1 operator A = S / h^2 gives the
+ *   Galerkin identity R A_h P = A_2h;
+ *   V-cycle(u, f): `pre` sweeps; r = f - A u; e_c = V-cycle(0, R r) on the coarse grid
+ *   (or `coarse_sweeps` sweeps on the coarsest grid); u += P e_c; `post` sweeps.
+ * Grids are coarsened while every n[a] is even and n[a] / 2 >= 2. */
+
+static int mg_can_coarsen(int dim, const int64_t *n) {
+  for (int a = 0; a < dim; ++a)
+    if (n[a] % 2 != 0 || n[a] / 2 < 2) return 0;
+  return 1;
+}
+
+/* Number of grids of the hierarchy starting at n (>= 1), at most max_levels. */
+int oracle_mg_levels(int dim, const int64_t *n, int max_levels) {
+  int64_t m[3] = {n[0], n[1], dim == 3 ? n[2] : 0};
+  int L = 1;
+  while (L < max_levels && mg_can_coarsen(dim, m)) {
+    for (int a = 0; a < dim; ++a) m[a] /= 2;
+    ++L;
+  }
+  return L;
+}
+
+/* 1D interpolation weight of fine offset o in {-1, 0, 1}: 1, 1/2. */
+static double hat(int o) { return o == 0 ? 1.0 : 0.5; }
+
+void oracle_mg_restrict(int dim, const int64_t *nc, const double *rf, double *rc) {
+  const int64_t nf[3] = {2 * nc[0], 2 * nc[1], dim == 3 ? 2 * nc[2] : 0};
+  const int64_t nzc = nz_cells(dim, nc);
+  const double scale = dim == 3 ? 0.125 : 0.25; /* 1 / 2^d */
+  const int zlo = dim == 3 ? -1 : 0, zhi = dim == 3 ? 1 : 0;
+  for (int64_t K = 0; K <= nzc; ++K)
+    for (int64_t J = 0; J <= nc[1]; ++J)
+      for (int64_t I = 0; I <= nc[0]; ++I) {
+        const int64_t pc = vidx(nc, I, J, K);
+        if (!is_interior(dim, nc, I, J, K)) {
+          rc[pc] = 0.0;
+          continue;
+        }
+        double acc = 0.0;
+        for (int dz = zlo; dz <= zhi; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              const double w = hat(dx) * hat(dy) * (dim == 3 ? hat(dz) : 1.0);
+              acc += w * rf[vidx(nf, 2 * I + dx, 2 * J + dy, dim == 3 ? 2 * K + dz : 0)];
+            }
+        rc[pc] = scale * acc;
+      }
+}
+
+void oracle_mg_prolong_add(int dim, const int64_t *nc, const double *ec, double *uf) {
+  const int64_t nf[3] = {2 * nc[0], 2 * nc[1], dim == 3 ? 2 * nc[2] : 0};
+  const int64_t nzf = nz_cells(dim, nf);
+  for (int64_t k = 0; k <= nzf; ++k)
+    for (int64_t j = 0; j <= nf[1]; ++j)
+      for (int64_t i = 0; i <= nf[0]; ++i) {
+        if (!is_interior(dim, nf, i, j, k)) continue;
+        /* average of the coarse vertices around the fine vertex: along each axis the
+           coarse index i/2 when i is even, the two neighbours (i +- 1)/2 when odd */
+        double acc = 0.0;
+        const int nzs = dim == 3 ? ((k & 1) ? 2 : 1) : 1;
+        for (int a = 0; a < nzs; ++a)
+          for (int b = 0; b < ((j & 1) ? 2 : 1); ++b)
+            for (int c = 0; c < ((i & 1) ? 2 : 1); ++c) {
+              const int64_t I = (i & 1) ? (i - 1) / 2 + c : i / 2;
+              const int64_t J = (j & 1) ? (j - 1) / 2 + b : j / 2;
+              const int64_t K = dim == 3 ? ((k & 1) ? (k - 1) / 2 + a : k / 2) : 0;
+              const double w = ((i & 1) ? 0.5 : 1.0) * ((j & 1) ? 0.5 : 1.0) *
+                               (dim == 3 && (k & 1) ? 0.5 : 1.0);
+              acc += w * ec[vidx(nc, I, J, K)];
+            }
+        uf[vidx(nf, i, j, k)] += acc;
+      }
+}
+
+static void mg_vcycle(int dim, const int64_t *n, double h, double *u, const double *f,
+                      int level, int levels, int pre, int post, int coarse_sweeps) {
+  if (level == levels - 1) {
+    oracle_gs_coloured(dim, n, h, u, f, coarse_sweeps, 1);
+    return;
+  }
+  const int64_t np = num_points(dim, n);
+  const int64_t nc[3] = {n[0] / 2, n[1] / 2, dim == 3 ? n[2] / 2 : 0};
+  const int64_t npc = num_points(dim, nc);
+  double *r = (double *)malloc((size_t)np * sizeof(double));
+  double *rc = (double *)malloc((size_t)npc * sizeof(double));
+  double *ec = (double *)calloc((size_t)npc, sizeof(double));
+  double nrm[2];
+  oracle_gs_coloured(dim, n, h, u, f, pre, 1);
+  oracle_residual(dim, n, h, u, f, r, nrm, 1);
+  oracle_mg_restrict(dim, nc, r, rc);
+  mg_vcycle(dim, nc, 2.0 * h, ec, rc, level + 1, levels, pre, post, coarse_sweeps);
+  oracle_mg_prolong_add(dim, nc, ec, u);
+  oracle_gs_coloured(dim, n, h, u, f, post, 1);
+  free(r);
+  free(rc);
+  free(ec);
+}
+
+void oracle_mg_vcycle(int dim, const int64_t *n, double h, double *u, const double *f,
+                      int levels, int pre, int post, int coarse_sweeps) {
+  mg_vcycle(dim, n, h, u, f, 0, levels, pre, post, coarse_sweeps);
+}
+
+int oracle_mg_solve(int dim, const int64_t *n, double h, double *u, const double *f,
+                    double tol, int max_cycles, int levels, int pre, int post,
+                    int coarse_sweeps, double *relres, int *converged) {
+  const int64_t np = num_points(dim, n);
+  double *r = (double *)malloc((size_t)np * sizeof(double));
+  int k = 0;
+  *converged = 0;
+  for (;;) {
+    double nrm[2];
+    oracle_residual(dim, n, h, u, f, r, nrm, 1);
+    const double rho = nrm[1] > 0.0 ? sqrt(nrm[0]) / sqrt(nrm[1]) : sqrt(nrm[0]);
+    if (relres) relres[k] = rho;
+    if (rho <= tol) {
+      *converged = 1;
+      break;
+    }
+    if (k >= max_cycles) break;
+    mg_vcycle(dim, n, h, u, f, 0, levels, pre, post, coarse_sweeps);
+    ++k;
+  }
+  free(r);
+  return k;
 }

@@ -101,6 +101,25 @@ void oracle_patch_smooth(const int32_t *lat, const int32_t *np,
                          const int64_t *off, double *u_all, const double *f_all,
                          int sweeps, int nthreads);
 
+/* Geometric multigrid (Section 1: the sweeps as smoothers of multigrid codes).
+ * Coarse grid nc = n / 2 (every second vertex).  Restriction of a fine residual
+ * (full weighting R = P^T / 2^d; coarse boundary 0) and d-linear prolongation added
+ * to the fine interior (uf += P ec, interpolating ec at every coarse vertex, boundary
+ * included: in the V-cycle the coarse correction's boundary is 0).
+ * oracle_mg_levels: grids in the hierarchy (coarsened while all n even and n/2 >= 2).
+ * oracle_mg_vcycle: one V(pre, post) cycle with coloured GS smoothing and
+ * `coarse_sweeps` sweeps on the coarsest of `levels` grids.
+ * oracle_mg_solve: V-cycles until ||f - A u|| / ||f|| <= tol (relres[k] before cycle
+ * k); returns the number of cycles. */
+int oracle_mg_levels(int dim, const int64_t *n, int max_levels);
+void oracle_mg_restrict(int dim, const int64_t *nc, const double *rf, double *rc);
+void oracle_mg_prolong_add(int dim, const int64_t *nc, const double *ec, double *uf);
+void oracle_mg_vcycle(int dim, const int64_t *n, double h, double *u, const double *f,
+                      int levels, int pre, int post, int coarse_sweeps);
+int oracle_mg_solve(int dim, const int64_t *n, double h, double *u, const double *f,
+                    double tol, int max_cycles, int levels, int pre, int post,
+                    int coarse_sweeps, double *relres, int *converged);
+
 /* Round-to-nearest-even conversion helpers exposed for tests. */
 uint16_t oracle_f32_to_bf16(float x);
 float oracle_bf16_to_f32(uint16_t b);
