@@ -79,12 +79,12 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--n3", type=int, default=N3, help="3D cells per edge (0: no 3D grid)")
     ap.add_argument("--n2", type=int, default=N2, help="2D cells per edge (0: no 2D grid)")
-    ap.add_argument("--workload", default="cfg1", choices=["cfg0", "cfg1", "cfg2", "cfg3", "cfg4"],
-                    help="cfg1 (default): the 512^3 op mix above; cfg0: 32^3 apply + 10 GS sweeps; "
-                         "cfg2: 4096 patches x 20 sweeps; cfg3: refinement to 1e-10 at 256^3 "
-                         "(FP32 / bf16 inner) vs plain FP64 GS; cfg4: request server")
-    ap.add_argument("--requests", type=int, default=400, help="cfg4: requests per arrival rate")
-    ap.add_argument("--rates", default="200,1000,5000", help="cfg4: arrival rates (req/s)")
+    ap.add_argument("--workload", default="grid", choices=["grid", "small", "patches", "refine", "serve"],
+                    help="grid (default): the 512^3 + 16384^2 op mix above; small: 32^3 apply + 10 GS "
+                         "sweeps; patches: 4096 uneven patches x 20 sweeps; refine: refinement to 1e-10 "
+                         "at 256^3 (FP32 / bf16 inner) vs FP64 inner; serve: request server")
+    ap.add_argument("--requests", type=int, default=400, help="serve: requests per arrival rate")
+    ap.add_argument("--rates", default="200,1000,5000", help="serve: arrival rates (req/s)")
     return ap.parse_args()
 
 
@@ -224,6 +224,16 @@ def traffic_from_profiles(kernel_key, units_per_launch):
     return None
 
 
+def workload_name(n3, n2):
+    parts = []
+    if n3:
+        parts.append("%d^3-cell 3D" % n3)
+    if n2:
+        parts.append("%d^2-cell 2D 9-point" % n2)
+    return ("FP64 Q1 grids: %s; per step and grid 50+50 applies, 50 GS sweeps, 50 Jacobi sweeps, "
+            "1 residual" % " + ".join(parts))
+
+
 def metric_name(n3, n2):
     parts = []
     if n3:
@@ -315,9 +325,7 @@ def run_gpu(args, rank, world):
            "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded U[-1,1] u0, manufactured sin RHS)",
-           "config": {"workload": "512^3-cell FP64 Q1 grid (configs[1]) plus its 2D 9-point "
-                                  "16384^2 variant; per step and grid 50+50 applies, 50 GS "
-                                  "sweeps, 50 Jacobi sweeps, 1 residual",
+           "config": {"workload": workload_name(n3, n2),
                       "grid_3d": [n3 + 1] * 3 if n3 else None,
                       "grid_2d": [n2 + 1, n2 + 1] if n2 else None, "pitch_2d": wl.p2 or None,
                       "l2": "inputs larger than L2 (no flush)" if n3 >= 256 or n2 >= 8192
@@ -421,7 +429,7 @@ def run_reference(args, rank, world):
             "value": round(val, 2), "unit": "Mupdates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(sec_tot / args.steps * 1e3, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "configs[1] op mix, oracle on host cores; "
+            "data": "synthetic", "config": {"workload": "grid op mix, oracle on host cores; "
                                                         "each step a bounded sample: 128^3 + 2048^2"},
             "cpu_baseline": {"value": round(val, 2), "unit": "Mupdates/s", "cores": nthreads,
                              "kind": "oracle", "sample": "per step: op mix on 128^3 and 2048^2"},
@@ -434,7 +442,7 @@ def _events(torch):
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def run_cfg0(args):
+def run_small(args):
     """32^3 cells: one element-wise apply on u ~ U[-1,1] (seed 0), then 10 coloured GS
     sweeps on A u = f, f = 3 pi^2 sin sin sin, u0 = 0."""
     import torch
@@ -461,12 +469,12 @@ def run_cfg0(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     upd = 11 * (n - 1) ** 3
-    return {"metric": "Mupdates/s (32^3 Q1: 1 element-wise apply + 10 coloured GS sweeps)", "workload": "cfg0",
+    return {"metric": "Mupdates/s (32^3 Q1: 1 element-wise apply + 10 coloured GS sweeps)", "workload": "small",
             "value": round(upd / ms / 1e3, 1), "unit": "Mupdates/s", "ms_per_step": round(ms, 4),
             "steps": args.steps, "dtype": "f64", "note": "launch-bound size (30K interior vertices)"}
 
 
-def run_cfg2(args):
+def run_patches(args):
     """4096 patches in a 16^3 lattice, edges from {8,12,16,24,32} (seed 2), f ~ U[-1,1],
     u0 = 0, 20 coloured GS sweeps with a halo fill before each; launch shape autotuned."""
     import torch
@@ -487,14 +495,14 @@ def run_cfg2(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     upd = 20 * L.interior_updates_per_sweep
-    return {"metric": "Mupdates/s (4096 uneven patches, 20 GS sweeps with halo fill)", "workload": "cfg2",
+    return {"metric": "Mupdates/s (4096 uneven patches, 20 GS sweeps with halo fill)", "workload": "patches",
             "value": round(upd / ms / 1e3, 1), "unit": "Mupdates/s", "ms_per_step": round(ms, 3),
             "algorithmic_gbs": round(24 * upd / ms / 1e6, 1), "hbm_frac": round(24 * upd / ms / 1e6 / 6683.2, 4),
             "autotuned_launch": {"threads": tuned[0], "ctas_per_sm": tuned[1]}, "dtype": "f64",
             "patches": int(L.np_sizes.size), "vertices": L.total}
 
 
-def run_cfg3(args):
+def run_refine(args):
     """256^3, f from u* = sin(2 pi x) sin(3 pi y) sin(pi z): refinement to a relative
     residual of 1e-10 with 8 inner GS sweeps in FP32 and in bf16 storage, against plain
     FP64 coloured GS (inner FP64, same loop) to the same residual; error of each result
@@ -523,13 +531,13 @@ def run_cfg3(args):
         out[name] = {"seconds": round(sec, 3), "corrections": res["iterations"], "sweeps": 8 * res["iterations"],
                      "relres": res["relres"], "converged": res["converged"], "rel_err_vs_closed_form": err}
     return {"metric": "time to relative residual 1e-10, 256^3 (speedup of mixed precision over FP64)",
-            "workload": "cfg3", "value": round(out["fp64"]["seconds"] / out["fp32"]["seconds"], 3),
+            "workload": "refine", "value": round(out["fp64"]["seconds"] / out["fp32"]["seconds"], 3),
             "unit": "x (FP64 time / FP32-inner time)", "bf16_speedup": round(out["fp64"]["seconds"] /
                                                                              out["bf16"]["seconds"], 3),
             "runs": out}
 
 
-def run_cfg4(args):
+def run_serve(args):
     """Request server: per arrival rate, `requests` requests from the seeded stream
     (edge log-uniform in [16, 256], SMOOTH = 20 GS sweeps or SOLVE to 1e-8 with FP32
     inner sweeps, f drawn on the device from each request's seed), Poisson arrivals;
@@ -561,7 +569,7 @@ def run_cfg4(args):
         lines.append({"rate_req_s": rate, "requests": len(reqs), "p50_s": round(float(np.percentile(lat, 50)), 4),
                       "p99_s": round(float(np.percentile(lat, 99)), 4), "wall_s": round(wall, 2),
                       "aggregate_mupdates_s": round(upd / wall / 1e6, 1)})
-    return {"metric": "serving: p50/p99 latency and aggregate Mupdates/s", "workload": "cfg4",
+    return {"metric": "serving: p50/p99 latency and aggregate Mupdates/s", "workload": "serve",
             "value": lines[0]["aggregate_mupdates_s"], "unit": "Mupdates/s", "per_rate": lines}
 
 
@@ -569,10 +577,10 @@ def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    if args.workload != "cfg1" and args.impl == "gpu":
+    if args.workload != "grid" and args.impl == "gpu":
         import torch
         torch.cuda.set_device(0)
-        fn = {"cfg0": run_cfg0, "cfg2": run_cfg2, "cfg3": run_cfg3, "cfg4": run_cfg4}[args.workload]
+        fn = {"small": run_small, "patches": run_patches, "refine": run_refine, "serve": run_serve}[args.workload]
         if rank == 0:
             print(json.dumps(fn(args)))
         return
