@@ -41,8 +41,8 @@ def lib():
             "oracle_patch_halo_fill": (None, [i32p, i32p, i64p, dp]),
             "oracle_patch_smooth": (None, [i32p, i32p, i64p, dp, dp, ci, ci]),
             "oracle_mg_levels": (ci, [ci, i64p, ci]),
-            "oracle_mg_restrict": (None, [ci, i64p, dp, dp]),
-            "oracle_mg_prolong_add": (None, [ci, i64p, dp, dp]),
+            "oracle_mg_restrict": (None, [ci, i64p, i64p, dp, dp]),
+            "oracle_mg_prolong_add": (None, [ci, i64p, i64p, dp, dp]),
             "oracle_mg_vcycle": (None, [ci, i64p, cd, dp, dp, ci, ci, ci, ci]),
             "oracle_mg_solve": (ci, [ci, i64p, cd, dp, dp, cd, ci, ci, ci, ci, ci, dp,
                                      ctypes.POINTER(ctypes.c_int)]),
@@ -176,8 +176,15 @@ def ir_solve(x0, f, h, tol, max_outer, inner_sweeps, inner_prec, keep_history=Fa
     return out
 
 
-def _coarse_shape(shape):
-    return tuple((m - 1) // 2 + 1 for m in shape)
+def coarse_shape(shape):
+    """Vertex-array shape of the coarse grid of the multigrid hierarchy (None if the
+    grid is the coarsest): n/2 when all n are even, ceil(n/2) when all n are equal."""
+    dim, n = _grid(shape)
+    n = [int(v) for v in n[:dim]]
+    if min(n) < 4 or (any(v % 2 for v in n) and len(set(n)) > 1):
+        return None
+    nc = [(v + 1) // 2 for v in n]
+    return tuple(v + 1 for v in reversed(nc))
 
 
 def mg_levels(shape, max_levels=64):
@@ -186,14 +193,15 @@ def mg_levels(shape, max_levels=64):
     return lib().oracle_mg_levels(dim, _ptr(n, ctypes.c_int64), max_levels)
 
 
-def mg_restrict(rf):
-    """Full-weighting restriction of a fine vertex array (even cells per axis)."""
+def mg_restrict(rf, coarse=None):
+    """Restriction R rf onto the coarse grid of rf's grid (or onto `coarse`, a shape)."""
     rf = _f64(rf)
     dim, nf = _grid(rf.shape)
-    nc = nf // 2
-    rc = np.zeros(_coarse_shape(rf.shape))
-    lib().oracle_mg_restrict(dim, _ptr(nc, ctypes.c_int64), _ptr(rf, ctypes.c_double),
-                             _ptr(rc, ctypes.c_double))
+    cs = coarse if coarse is not None else coarse_shape(rf.shape)
+    _, nc = _grid(cs)
+    rc = np.zeros(cs)
+    lib().oracle_mg_restrict(dim, _ptr(nf, ctypes.c_int64), _ptr(nc, ctypes.c_int64),
+                             _ptr(rf, ctypes.c_double), _ptr(rc, ctypes.c_double))
     return rc
 
 
@@ -201,9 +209,10 @@ def mg_prolong_add(ec, uf):
     """uf + P ec on the fine interior (uf's boundary unchanged)."""
     ec = _f64(ec)
     u = _f64(uf).copy()
-    dim, nc = _grid(ec.shape)
-    lib().oracle_mg_prolong_add(dim, _ptr(nc, ctypes.c_int64), _ptr(ec, ctypes.c_double),
-                                _ptr(u, ctypes.c_double))
+    dim, nf = _grid(u.shape)
+    _, nc = _grid(ec.shape)
+    lib().oracle_mg_prolong_add(dim, _ptr(nf, ctypes.c_int64), _ptr(nc, ctypes.c_int64),
+                                _ptr(ec, ctypes.c_double), _ptr(u, ctypes.c_double))
     return u
 
 

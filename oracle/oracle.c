@@ -29,9 +29,10 @@
  *   oracle_ir_solve           pinned: converges to the closed-form discrete solution of
  *                             the manufactured problem; FP64 inner equals plain GS.
  *   oracle_mg_*               pinned: Galerkin identity R A_h P = A_2h on random
- *                             coarse vectors; P reproduces d-linear functions; R is
- *                             P^T / 2^d (adjoint identity); the solve reaches the
- *                             closed-form discrete solution; V-cycle contraction.
+ *                             coarse vectors (nested grids); P reproduces d-linear
+ *                             functions (nested and not); R is (n_c/n)^d P^T (adjoint
+ *                             identity); the solve reaches the closed-form discrete
+ *                             solution for even and odd n; V-cycle contraction.
  *   oracle_patch_*            parity unpinned beyond: a single patch with zero
  *                             neighbours equals a plain Dirichlet GS; equal-size
  *                             neighbours copy the first interior layer (the halo rule
@@ -499,40 +500,61 @@ void oracle_patch_smooth(const int32_t *lat, const int32_t *np,
 /* The paper names smoothers of matrix-free multigrid codes as the use of its sweeps
  * (Section 1).  A standard vertex-centred V-cycle with the coloured Gauss-Seidel as
  * smoother, written out from its textbook definition:
- *   coarse grid: every second vertex, n_c = n / 2 cells per axis, h_c = 2 h;
- *   prolongation P: d-linear interpolation of the coarse values (coarse boundary 0);
- *   restriction R = P^T / 2^d (full weighting: weight prod_a (1 - |o_a|/2) / 2^d at
- *   fine offset o in {-1,0,1}^d), which for the Q1 operator A = S / h^2 gives the
- *   Galerkin identity R A_h P = A_2h;
+ *   coarse grid: n_c = n / 2 cells per axis when every n[a] is even (every second
+ *   vertex), otherwise, for a grid with the same n on every axis, n_c = ceil(n / 2) on
+ *   every axis (coarse vertices not nested in the fine ones); the coarse cells are
+ *   cubes of side h_c = h n / n_c.  Grids are coarsened while every n[a] >= 4.
+ *   prolongation P: d-linear interpolation of the coarse values at the fine vertex
+ *   positions x_i = i / n (in units of the domain side), coarse vertices at I / n_c;
+ *   restriction R = (n_c / n)^d P^T (full weighting when nested), which for the Q1
+ *   operator A = S / h^2 gives the Galerkin identity R A_h P = A_2h in the nested case;
  *   V-cycle(u, f): `pre` sweeps; r = f - A u; e_c = V-cycle(0, R r) on the coarse grid
- *   (or `coarse_sweeps` sweeps on the coarsest grid); u += P e_c; `post` sweeps.
- * Grids are coarsened while every n[a] is even and n[a] / 2 >= 2. */
+ *   (or `coarse_sweeps` sweeps on the coarsest grid); u += P e_c; `post` sweeps. */
 
-static int mg_can_coarsen(int dim, const int64_t *n) {
-  for (int a = 0; a < dim; ++a)
-    if (n[a] % 2 != 0 || n[a] / 2 < 2) return 0;
+/* Coarse grid of n (returns 0 when n is the coarsest grid). */
+static int mg_coarsen(int dim, const int64_t *n, int64_t *nc) {
+  int all_even = 1, all_equal = 1;
+  for (int a = 0; a < dim; ++a) {
+    if (n[a] < 4) return 0;
+    if (n[a] % 2) all_even = 0;
+    if (n[a] != n[0]) all_equal = 0;
+  }
+  if (!all_even && !all_equal) return 0;
+  for (int a = 0; a < 3; ++a) nc[a] = a < dim ? (n[a] + 1) / 2 : 0;
   return 1;
 }
 
-/* Number of grids of the hierarchy starting at n (>= 1), at most max_levels. */
 int oracle_mg_levels(int dim, const int64_t *n, int max_levels) {
-  int64_t m[3] = {n[0], n[1], dim == 3 ? n[2] : 0};
+  int64_t m[3] = {n[0], n[1], dim == 3 ? n[2] : 0}, c[3];
   int L = 1;
-  while (L < max_levels && mg_can_coarsen(dim, m)) {
-    for (int a = 0; a < dim; ++a) m[a] /= 2;
+  while (L < max_levels && mg_coarsen(dim, m, c)) {
+    for (int a = 0; a < 3; ++a) m[a] = c[a];
     ++L;
   }
   return L;
 }
 
-/* 1D interpolation weight of fine offset o in {-1, 0, 1}: 1, 1/2. */
-static double hat(int o) { return o == 0 ? 1.0 : 0.5; }
+/* 1D interpolation weight of coarse vertex I (of nc cells) at fine vertex i (of nf
+ * cells): 1 - |i nc / nf - I| where positive, else 0 (exact integer arithmetic for the
+ * distance, one division). */
+static double interp_w(int64_t i, int64_t nf, int64_t I, int64_t nc) {
+  int64_t d = i * nc - I * nf;
+  if (d < 0) d = -d;
+  return d >= nf ? 0.0 : (double)(nf - d) / (double)nf;
+}
 
-void oracle_mg_restrict(int dim, const int64_t *nc, const double *rf, double *rc) {
-  const int64_t nf[3] = {2 * nc[0], 2 * nc[1], dim == 3 ? 2 * nc[2] : 0};
+/* Fine indices i in [*lo, *hi] that can see coarse vertex I (|i nc - I nf| < nf). */
+static void fine_range(int64_t I, int64_t nf, int64_t nc, int64_t *lo, int64_t *hi) {
+  int64_t a = ((I - 1) * nf) / nc, b = ((I + 1) * nf + nc - 1) / nc;
+  *lo = a < 0 ? 0 : a;
+  *hi = b > nf ? nf : b;
+}
+
+void oracle_mg_restrict(int dim, const int64_t *nf, const int64_t *nc, const double *rf,
+                        double *rc) {
   const int64_t nzc = nz_cells(dim, nc);
-  const double scale = dim == 3 ? 0.125 : 0.25; /* 1 / 2^d */
-  const int zlo = dim == 3 ? -1 : 0, zhi = dim == 3 ? 1 : 0;
+  double scale = 1.0;
+  for (int a = 0; a < dim; ++a) scale *= (double)nc[a] / (double)nf[a];
   for (int64_t K = 0; K <= nzc; ++K)
     for (int64_t J = 0; J <= nc[1]; ++J)
       for (int64_t I = 0; I <= nc[0]; ++I) {
@@ -541,50 +563,67 @@ void oracle_mg_restrict(int dim, const int64_t *nc, const double *rf, double *rc
           rc[pc] = 0.0;
           continue;
         }
+        /* every fine vertex whose interpolation uses coarse vertex (I, J, K) */
         double acc = 0.0;
-        for (int dz = zlo; dz <= zhi; ++dz)
-          for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-              const double w = hat(dx) * hat(dy) * (dim == 3 ? hat(dz) : 1.0);
-              acc += w * rf[vidx(nf, 2 * I + dx, 2 * J + dy, dim == 3 ? 2 * K + dz : 0)];
+        int64_t klo = 0, khi = 0, jlo, jhi, ilo, ihi;
+        if (dim == 3) fine_range(K, nf[2], nc[2], &klo, &khi);
+        fine_range(J, nf[1], nc[1], &jlo, &jhi);
+        fine_range(I, nf[0], nc[0], &ilo, &ihi);
+        for (int64_t k = klo; k <= khi; ++k) {
+          const double wz = dim == 3 ? interp_w(k, nf[2], K, nc[2]) : 1.0;
+          if (wz == 0.0) continue;
+          for (int64_t j = jlo; j <= jhi; ++j) {
+            const double wy = interp_w(j, nf[1], J, nc[1]);
+            if (wy == 0.0) continue;
+            for (int64_t i = ilo; i <= ihi; ++i) {
+              const double wx = interp_w(i, nf[0], I, nc[0]);
+              if (wx == 0.0) continue;
+              acc += wx * wy * wz * rf[vidx(nf, i, j, k)];
             }
+          }
+        }
         rc[pc] = scale * acc;
       }
 }
 
-void oracle_mg_prolong_add(int dim, const int64_t *nc, const double *ec, double *uf) {
-  const int64_t nf[3] = {2 * nc[0], 2 * nc[1], dim == 3 ? 2 * nc[2] : 0};
-  const int64_t nzf = nz_cells(dim, nf);
+void oracle_mg_prolong_add(int dim, const int64_t *nf, const int64_t *nc, const double *ec,
+                           double *uf) {
+  const int64_t nzf = nz_cells(dim, nf), nzc = nz_cells(dim, nc);
   for (int64_t k = 0; k <= nzf; ++k)
     for (int64_t j = 0; j <= nf[1]; ++j)
       for (int64_t i = 0; i <= nf[0]; ++i) {
         if (!is_interior(dim, nf, i, j, k)) continue;
-        /* average of the coarse vertices around the fine vertex: along each axis the
-           coarse index i/2 when i is even, the two neighbours (i +- 1)/2 when odd */
+        /* the coarse vertices at or just left of the fine position, and the next */
         double acc = 0.0;
-        const int nzs = dim == 3 ? ((k & 1) ? 2 : 1) : 1;
-        for (int a = 0; a < nzs; ++a)
-          for (int b = 0; b < ((j & 1) ? 2 : 1); ++b)
-            for (int c = 0; c < ((i & 1) ? 2 : 1); ++c) {
-              const int64_t I = (i & 1) ? (i - 1) / 2 + c : i / 2;
-              const int64_t J = (j & 1) ? (j - 1) / 2 + b : j / 2;
-              const int64_t K = dim == 3 ? ((k & 1) ? (k - 1) / 2 + a : k / 2) : 0;
-              const double w = ((i & 1) ? 0.5 : 1.0) * ((j & 1) ? 0.5 : 1.0) *
-                               (dim == 3 && (k & 1) ? 0.5 : 1.0);
-              acc += w * ec[vidx(nc, I, J, K)];
+        const int64_t K0 = dim == 3 ? (k * nc[2]) / nf[2] : 0, J0 = (j * nc[1]) / nf[1],
+                      I0 = (i * nc[0]) / nf[0];
+        const int64_t K1 = dim == 3 && K0 < nzc ? K0 + 1 : K0, J1 = J0 < nc[1] ? J0 + 1 : J0,
+                      I1 = I0 < nc[0] ? I0 + 1 : I0;
+        for (int64_t K = K0; K <= K1; ++K) {
+          const double wz = dim == 3 ? interp_w(k, nf[2], K, nc[2]) : 1.0;
+          if (wz == 0.0) continue;
+          for (int64_t J = J0; J <= J1; ++J) {
+            const double wy = interp_w(j, nf[1], J, nc[1]);
+            if (wy == 0.0) continue;
+            for (int64_t I = I0; I <= I1; ++I) {
+              const double wx = interp_w(i, nf[0], I, nc[0]);
+              if (wx == 0.0) continue;
+              acc += wx * wy * wz * ec[vidx(nc, I, J, K)];
             }
+          }
+        }
         uf[vidx(nf, i, j, k)] += acc;
       }
 }
 
 static void mg_vcycle(int dim, const int64_t *n, double h, double *u, const double *f,
                       int level, int levels, int pre, int post, int coarse_sweeps) {
-  if (level == levels - 1) {
+  int64_t nc[3];
+  if (level == levels - 1 || !mg_coarsen(dim, n, nc)) {
     oracle_gs_coloured(dim, n, h, u, f, coarse_sweeps, 1);
     return;
   }
   const int64_t np = num_points(dim, n);
-  const int64_t nc[3] = {n[0] / 2, n[1] / 2, dim == 3 ? n[2] / 2 : 0};
   const int64_t npc = num_points(dim, nc);
   double *r = (double *)malloc((size_t)np * sizeof(double));
   double *rc = (double *)malloc((size_t)npc * sizeof(double));
@@ -592,9 +631,10 @@ static void mg_vcycle(int dim, const int64_t *n, double h, double *u, const doub
   double nrm[2];
   oracle_gs_coloured(dim, n, h, u, f, pre, 1);
   oracle_residual(dim, n, h, u, f, r, nrm, 1);
-  oracle_mg_restrict(dim, nc, r, rc);
-  mg_vcycle(dim, nc, 2.0 * h, ec, rc, level + 1, levels, pre, post, coarse_sweeps);
-  oracle_mg_prolong_add(dim, nc, ec, u);
+  oracle_mg_restrict(dim, n, nc, r, rc);
+  const double hc = h * (double)n[0] / (double)nc[0];
+  mg_vcycle(dim, nc, hc, ec, rc, level + 1, levels, pre, post, coarse_sweeps);
+  oracle_mg_prolong_add(dim, n, nc, ec, u);
   oracle_gs_coloured(dim, n, h, u, f, post, 1);
   free(r);
   free(rc);

@@ -102,18 +102,22 @@ void oracle_patch_smooth(const int32_t *lat, const int32_t *np,
                          int sweeps, int nthreads);
 
 /* Geometric multigrid (Section 1: the sweeps as smoothers of multigrid codes).
- * Coarse grid nc = n / 2 (every second vertex).  Restriction of a fine residual
- * (full weighting R = P^T / 2^d; coarse boundary 0) and d-linear prolongation added
- * to the fine interior (uf += P ec, interpolating ec at every coarse vertex, boundary
- * included: in the V-cycle the coarse correction's boundary is 0).
- * oracle_mg_levels: grids in the hierarchy (coarsened while all n even and n/2 >= 2).
+ * Coarse grid nc: n/2 per axis when all n are even, else ceil(n/2) when all n are equal
+ * (coarse vertices not nested); coarsened while every n >= 4.  Restriction of a fine
+ * residual (R = (nc/nf)^d P^T, full weighting when nested; coarse boundary 0) and
+ * d-linear prolongation added to the fine interior (uf += P ec, interpolating ec at
+ * every coarse vertex, boundary included: in the V-cycle the coarse correction's
+ * boundary is 0).
+ * oracle_mg_levels: grids in the hierarchy.
  * oracle_mg_vcycle: one V(pre, post) cycle with coloured GS smoothing and
  * `coarse_sweeps` sweeps on the coarsest of `levels` grids.
  * oracle_mg_solve: V-cycles until ||f - A u|| / ||f|| <= tol (relres[k] before cycle
  * k); returns the number of cycles. */
 int oracle_mg_levels(int dim, const int64_t *n, int max_levels);
-void oracle_mg_restrict(int dim, const int64_t *nc, const double *rf, double *rc);
-void oracle_mg_prolong_add(int dim, const int64_t *nc, const double *ec, double *uf);
+void oracle_mg_restrict(int dim, const int64_t *nf, const int64_t *nc, const double *rf,
+                        double *rc);
+void oracle_mg_prolong_add(int dim, const int64_t *nf, const int64_t *nc, const double *ec,
+                           double *uf);
 void oracle_mg_vcycle(int dim, const int64_t *n, double h, double *u, const double *f,
                       int levels, int pre, int post, int coarse_sweeps);
 int oracle_mg_solve(int dim, const int64_t *n, double h, double *u, const double *f,
