@@ -85,6 +85,8 @@ def parse_args():
                          "at 256^3 (FP32 / bf16 inner) vs FP64 inner; serve: request server")
     ap.add_argument("--requests", type=int, default=400, help="serve: requests per arrival rate")
     ap.add_argument("--rates", default="200,1000,5000", help="serve: arrival rates (req/s)")
+    ap.add_argument("--solver", default="mg", choices=["mg", "refine"],
+                    help="serve: SOLVE requests by multigrid V-cycles (mg) or by refinement with FP32 GS")
     return ap.parse_args()
 
 
@@ -530,8 +532,21 @@ def run_refine(args):
         err = float(np.max(np.abs(ud.cpu().numpy() - uh)) / np.max(np.abs(uh)))
         out[name] = {"seconds": round(sec, 3), "corrections": res["iterations"], "sweeps": 8 * res["iterations"],
                      "relres": res["relres"], "converged": res["converged"], "rel_err_vs_closed_form": err}
+    # the multigrid solver (FP64 V(2,2) cycles) on the same problem, for comparison
+    ud = torch.zeros_like(fd)
+    st.stencil_mg_solve(ud, fd, h, rel_tol=1e-10, max_cycles=50, history=False)  # workspace warm-up
+    ud.zero_()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    res = st.stencil_mg_solve(ud, fd, h, rel_tol=1e-10, max_cycles=50, history=False)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t
+    err = float(np.max(np.abs(ud.cpu().numpy() - uh)) / np.max(np.abs(uh)))
+    out["mg"] = {"seconds": round(sec, 4), "cycles": res["cycles"], "levels": res["levels"],
+                 "relres": res["relres"], "converged": res["converged"], "rel_err_vs_closed_form": err}
     return {"metric": "time to relative residual 1e-10, 256^3 (speedup of mixed precision over FP64)",
             "workload": "refine", "value": round(out["fp64"]["seconds"] / out["fp32"]["seconds"], 3),
+            "mg_speedup_over_fp64_refinement": round(out["fp64"]["seconds"] / out["mg"]["seconds"], 1),
             "unit": "x (FP64 time / FP32-inner time)", "bf16_speedup": round(out["fp64"]["seconds"] /
                                                                              out["bf16"]["seconds"], 3),
             "runs": out}
@@ -547,7 +562,8 @@ def run_serve(args):
     lines = []
     for rate in [float(r) for r in args.rates.split(",")]:
         reqs = synth.request_stream(args.requests, rate, seed=3)
-        srv = st.Server(64 << 30, streams=8, max_inflight=64, inner_dtype=st.F32)
+        solver = st.SOLVER_MG if args.solver == "mg" else st.SOLVER_REFINE
+        srv = st.Server(64 << 30, streams=8, max_inflight=64, inner_dtype=st.F32, solver=solver)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         tickets = []
@@ -560,17 +576,33 @@ def run_serve(args):
         for t, r in tickets:
             res = srv.wait(t)
             lat.append(res["t_done"] - res["t_submit"])
-            sweeps = 20 if r["kind"] == "smooth" else 8 * res["iterations"]
-            upd += sweeps * (r["edge"] - 1) ** 3
+            if r["kind"] == "smooth":
+                upd += 20 * (r["edge"] - 1) ** 3
+            elif args.solver == "mg":
+                upd += res["iterations"] * mg_cycle_updates(r["edge"])
+            else:
+                upd += 8 * res["iterations"] * (r["edge"] - 1) ** 3
             srv.release(t)
         wall = time.perf_counter() - t0
         srv.close()
         lat = np.array(lat)
         lines.append({"rate_req_s": rate, "requests": len(reqs), "p50_s": round(float(np.percentile(lat, 50)), 4),
                       "p99_s": round(float(np.percentile(lat, 99)), 4), "wall_s": round(wall, 2),
+                      "requests_per_s": round(len(reqs) / wall, 1),
                       "aggregate_mupdates_s": round(upd / wall / 1e6, 1)})
     return {"metric": "serving: p50/p99 latency and aggregate Mupdates/s", "workload": "serve",
-            "value": lines[0]["aggregate_mupdates_s"], "unit": "Mupdates/s", "per_rate": lines}
+            "value": lines[0]["aggregate_mupdates_s"], "unit": "Mupdates/s", "solver": args.solver,
+            "updates": "GS vertex updates (multigrid: smoothing sweeps on every level)", "per_rate": lines}
+
+
+def mg_cycle_updates(n, pre=2, post=2, coarse=20):
+    """GS vertex updates of one V(pre, post) cycle on an n^3 grid (coarsened while n is
+    even and n / 2 >= 2; `coarse` sweeps on the coarsest grid)."""
+    tot = 0
+    while n % 2 == 0 and n // 2 >= 2:
+        tot += (pre + post) * (n - 1) ** 3
+        n //= 2
+    return tot + coarse * (n - 1) ** 3
 
 
 def main():

@@ -195,6 +195,68 @@ typedef struct stencil_solve_info {
 int stencil_solve(const stencil_grid_t *g, double *u, const double *f, const stencil_solve_opts_t *opts,
                   stencil_solve_info_t *info, void *stream);
 
+/* ------------------------------------------------------------ geometric multigrid */
+/* The paper's sweeps are the smoothers of matrix-free multigrid codes (Section 1).
+ * Hierarchy: the coarse grid has n/2 cells per axis when every n[a] is even (every
+ * second vertex), or ceil(n/2) on every axis when all n[a] are equal (coarse vertices
+ * then not nested in the fine ones); coarse cells are cubes of side h n / n_c; grids are
+ * coarsened while every n[a] >= 4 (any other grid is its own coarsest grid).
+ * Prolongation P is d-linear interpolation at the fine vertex positions; restriction
+ * is R = (n_c/n)^d P^T (full weighting for nested grids, where R A_h P = A_2h holds for
+ * the Q1 operator).  V(pre, post) cycle: `pre` coloured GS sweeps; r = f - A u (FP64);
+ * coarse right-hand side R r; coarse correction from 0 by a V-cycle (on the coarsest
+ * grid: `coarse_sweeps` sweeps); u += P e; `post` sweeps. */
+typedef struct stencil_mg_opts {
+  double rel_tol;        /* solve: stop when ||f - A u||_2 / ||f||_2 <= rel_tol */
+  int32_t max_cycles;    /* solve: at most this many V-cycles */
+  int32_t pre;           /* GS sweeps before the coarse correction (>= 0) */
+  int32_t post;          /* GS sweeps after it (>= 0) */
+  int32_t coarse_sweeps; /* GS sweeps on the coarsest grid (>= 1) */
+  int32_t max_levels;    /* at most this many grids (0: as many as the sizes allow) */
+  int32_t reserved;      /* 0 */
+} stencil_mg_opts_t;
+
+typedef struct stencil_mg_info {
+  int32_t cycles;          /* V-cycles applied */
+  int32_t converged;       /* 1 if rel_tol was reached */
+  int32_t levels;          /* grids in the hierarchy used */
+  int32_t reserved;
+  double relres;           /* relative residual of the returned u */
+  double *relres_history;  /* optional host array of max_cycles + 1 entries (or NULL):
+                              relative residual before each cycle and at the end */
+} stencil_mg_info_t;
+
+/*
+ * V-cycles for A u = f until ||f - A u|| / ||f|| <= rel_tol.  u: device F64 array (in:
+ * initial guess and Dirichlet data, which are never changed; out: result); f: device F64
+ * of the same layout (boundary ignored).  g->dtype must be STENCIL_F64, 2D or 3D.
+ * Host-synchronous (synchronises `stream` once per cycle to read the norm).  Uses
+ * library workspaces (per stream, kept): the coarse-level arrays (about 3/7 (3D) or 1
+ * (2D) of u's size plus one u-sized residual) and the smoother's three u-sized arrays.
+ * Returns STENCIL_OK, STENCIL_ENOTCONV (u holds the last iterate), STENCIL_EINVAL,
+ * STENCIL_ENOMEM, STENCIL_ECUDA.
+ */
+int stencil_mg_solve(const stencil_grid_t *g, double *u, const double *f, const stencil_mg_opts_t *opts,
+                     stencil_mg_info_t *info, void *stream);
+
+/* One V-cycle on u, stream-ordered (no host synchronisation; rel_tol and max_cycles
+ * are ignored).  Same arrays, workspaces and errors as stencil_mg_solve. */
+int stencil_mg_vcycle(const stencil_grid_t *g, double *u, const double *f, const stencil_mg_opts_t *opts,
+                      void *stream);
+
+/* Restriction rc = R rf from a fine grid to its coarse grid in the hierarchy above (the
+ * coarse descriptor must have exactly those cell counts; any pitch; same dim; its h is
+ * not used): coarse interior vertices get the weighted sum, the coarse boundary 0.
+ * Device F64 arrays; rf and rc must not overlap.  Returns STENCIL_EINVAL, STENCIL_ECUDA. */
+int stencil_mg_restrict(const stencil_grid_t *fine, const double *rf, const stencil_grid_t *coarse, double *rc,
+                        void *stream);
+
+/* uf += P ec on the fine interior (d-linear interpolation of ec, all coarse vertices
+ * read, boundary included); the fine boundary is not written.  Grids as for
+ * stencil_mg_restrict.  Returns STENCIL_EINVAL, STENCIL_ECUDA. */
+int stencil_mg_prolong_add(const stencil_grid_t *fine, double *uf, const stencil_grid_t *coarse, const double *ec,
+                           void *stream);
+
 /* ------------------------------------------------------------ patch batches */
 /* One cubic patch of a batch: a dense (n+1)^3 vertex array, x fastest, at element
  * offset `offset` of the packed FP64 buffers.  Its boundary shell is a halo. */
@@ -250,9 +312,15 @@ typedef struct stencil_server_opts {
   int32_t max_inflight; /* requests resident and in progress at once (0: 64) */
   int32_t inner_sweeps; /* SOLVE: coloured GS sweeps per correction (0: 8) */
   int32_t inner_dtype;  /* SOLVE: STENCIL_F32 (default), STENCIL_BF16 or STENCIL_F64 */
-  int32_t max_outer;    /* SOLVE: at most this many corrections (0: 100000) */
-  int32_t reserved;
+  int32_t max_outer;    /* SOLVE: at most this many corrections or V-cycles (0: 100000) */
+  int32_t solver;       /* SOLVE: STENCIL_SOLVER_REFINE (0: iterative refinement with the
+                           GS inner solver above) or STENCIL_SOLVER_MG (FP64 multigrid
+                           V(2,2) cycles, 20 sweeps on the coarsest grid; a grid with
+                           an odd cell count is its own coarsest grid) */
 } stencil_server_opts_t;
+
+#define STENCIL_SOLVER_REFINE 0
+#define STENCIL_SOLVER_MG 1
 
 typedef struct stencil_request {
   int32_t kind;      /* STENCIL_REQ_SMOOTH or STENCIL_REQ_SOLVE */

@@ -23,6 +23,9 @@ STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "EADMIT", -4: "ETIMEDOUT", -5
 _DTYPES = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
 
 
+SOLVER_REFINE, SOLVER_MG = 0, 1
+
+
 class StencilError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("%s (%d): %s" % (STATUS.get(code, "?"), code, msg))
@@ -42,7 +45,7 @@ class PatchDesc(ctypes.Structure):
 class ServerOpts(ctypes.Structure):
     _fields_ = [("streams", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
                 ("inner_sweeps", ctypes.c_int32), ("inner_dtype", ctypes.c_int32),
-                ("max_outer", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("max_outer", ctypes.c_int32), ("solver", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -75,6 +78,18 @@ class SolveInfo(ctypes.Structure):
                 ("relres", ctypes.c_double), ("relres_history", ctypes.POINTER(ctypes.c_double))]
 
 
+class MgOpts(ctypes.Structure):
+    _fields_ = [("rel_tol", ctypes.c_double), ("max_cycles", ctypes.c_int32), ("pre", ctypes.c_int32),
+                ("post", ctypes.c_int32), ("coarse_sweeps", ctypes.c_int32), ("max_levels", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class MgInfo(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int32), ("converged", ctypes.c_int32), ("levels", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("relres", ctypes.c_double),
+                ("relres_history", ctypes.POINTER(ctypes.c_double))]
+
+
 _lib = None
 
 
@@ -101,6 +116,10 @@ def lib():
             "stencil_jacobi_step": (ci, [gp, vp, vp, vp, cd, vp]),
             "stencil_residual_noalloc": (ci, [gp, vp, vp, vp, vp, vp]),
             "stencil_solve": (ci, [gp, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]),
+            "stencil_mg_solve": (ci, [gp, vp, vp, ctypes.POINTER(MgOpts), ctypes.POINTER(MgInfo), vp]),
+            "stencil_mg_vcycle": (ci, [gp, vp, vp, ctypes.POINTER(MgOpts), vp]),
+            "stencil_mg_restrict": (ci, [gp, vp, gp, vp, vp]),
+            "stencil_mg_prolong_add": (ci, [gp, vp, gp, vp, vp]),
             "stencil_patch_batch_create": (ci, [ctypes.POINTER(PatchDesc), ctypes.c_int32,
                                                 ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(vp)]),
             "stencil_patch_batch_smooth": (ci, [vp, vp, vp, ci, vp]),
@@ -267,6 +286,59 @@ def stencil_solve(u, f, h, rel_tol=1e-10, max_outer=100000, inner_sweeps=8, inne
     return out
 
 
+def _mg_opts(rel_tol, max_cycles, pre, post, coarse_sweeps, max_levels):
+    return MgOpts(float(rel_tol), int(max_cycles), int(pre), int(post), int(coarse_sweeps), int(max_levels), 0)
+
+
+def stencil_mg_solve(u, f, h, rel_tol=1e-10, max_cycles=100, pre=2, post=2, coarse_sweeps=20, max_levels=0,
+                     stream=None, history=True):
+    """Multigrid V-cycles on A u = f (u, f float64; u updated in place).  Returns a dict
+    with cycles, converged, levels, relres and (optionally) the relative-residual
+    history.  Raises StencilError except for the not-converged status (-6)."""
+    _same_layout(u, f)
+    if u.dtype != torch.float64:
+        raise ValueError("multigrid needs float64 u and f")
+    g = grid_for(u, h)
+    opts = _mg_opts(rel_tol, max_cycles, pre, post, coarse_sweeps, max_levels)
+    info = MgInfo()
+    hist = None
+    if history:
+        hist = (ctypes.c_double * (int(max_cycles) + 1))()
+        info.relres_history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
+    rc = lib().stencil_mg_solve(ctypes.byref(g), _ptr(u), _ptr(f), ctypes.byref(opts), ctypes.byref(info),
+                                _stream(stream))
+    if rc not in (0, -6):
+        _check(rc)
+    out = {"cycles": info.cycles, "converged": bool(info.converged), "levels": info.levels,
+           "relres": info.relres}
+    if history:
+        out["history"] = list(hist[:info.cycles + 1])
+    return out
+
+
+def stencil_mg_vcycle(u, f, h, pre=2, post=2, coarse_sweeps=20, max_levels=0, stream=None):
+    """One V-cycle on u (in place), stream-ordered."""
+    _same_layout(u, f)
+    g = grid_for(u, h)
+    opts = _mg_opts(0.0, 0, pre, post, coarse_sweeps, max_levels)
+    _check(lib().stencil_mg_vcycle(ctypes.byref(g), _ptr(u), _ptr(f), ctypes.byref(opts), _stream(stream)))
+    return u
+
+
+def stencil_mg_restrict(rf, rc, h, stream=None):
+    """rc = R rf (full weighting); rc is a vertex array of the coarse grid."""
+    gf, gc = grid_for(rf, h), grid_for(rc, 2.0 * h)
+    _check(lib().stencil_mg_restrict(ctypes.byref(gf), _ptr(rf), ctypes.byref(gc), _ptr(rc), _stream(stream)))
+    return rc
+
+
+def stencil_mg_prolong_add(ec, uf, h, stream=None):
+    """uf += P ec on the fine interior; h is the fine mesh width."""
+    gf, gc = grid_for(uf, h), grid_for(ec, 2.0 * h)
+    _check(lib().stencil_mg_prolong_add(ctypes.byref(gf), _ptr(uf), ctypes.byref(gc), _ptr(ec), _stream(stream)))
+    return uf
+
+
 class PatchBatch:
     """Handle of a patch batch (stencil_patch_batch_*).  sizes: cells per edge per
     patch; offsets: element offsets in the packed arrays; neighbours: (npatch, 27) int32."""
@@ -317,8 +389,10 @@ class Server:
     """Handle of a request server (stencil_server_*), host-array interface."""
 
     def __init__(self, hbm_budget_bytes, streams=0, max_inflight=0, inner_sweeps=0, inner_dtype=F32,
-                 max_outer=0):
-        o = ServerOpts(int(streams), int(max_inflight), int(inner_sweeps), int(inner_dtype), int(max_outer), 0)
+                 max_outer=0, solver=0):
+        """solver: SOLVER_REFINE (0) or SOLVER_MG (1) for SOLVE requests."""
+        o = ServerOpts(int(streams), int(max_inflight), int(inner_sweeps), int(inner_dtype), int(max_outer),
+                       int(solver))
         self._h = ctypes.c_void_p()
         _check(lib().stencil_server_create(int(hbm_budget_bytes), ctypes.byref(o), ctypes.byref(self._h)))
         self._keep = {}

@@ -4,6 +4,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -402,6 +403,141 @@ int stencil_solve(const stencil_grid_t *g, double *u, const double *f, const ste
     info->relres = rho;
   }
   if (!conv) return set_error(STENCIL_ENOTCONV, "solve: max_outer reached before rel_tol");
+  return STENCIL_OK;
+}
+
+// ------------------------------------------------------------ multigrid
+
+static int check_mg_opts(const stencil_mg_opts_t *o) {
+  if (!o) return set_error(STENCIL_EINVAL, "mg: opts is NULL");
+  if (o->pre < 0 || o->post < 0 || o->coarse_sweeps < 1 || o->max_levels < 0 || o->max_cycles < 0 ||
+      !(o->rel_tol >= 0.0))
+    return set_error(STENCIL_EINVAL, "mg: need pre, post, max_levels, max_cycles >= 0, coarse_sweeps >= 1, "
+                                     "rel_tol >= 0");
+  return STENCIL_OK;
+}
+
+// Workspaces and cycle object for one multigrid call on stream s.
+static int mg_prepare(const stencil_grid_t *g, const stencil_mg_opts_t *o, cudaStream_t s, MgCycle &cyc,
+                      int &levels, double *&dn) {
+  const Geo q = make_geo(*g);
+  const int maxl = o->max_levels > 0 ? std::min(o->max_levels, MgCycle::kMaxLevels) : MgCycle::kMaxLevels;
+  levels = mg_levels(q, g->dim, maxl);
+  void *work = levels > 1 ? device_scratch(SCRATCH_MG, mg_work_bytes(q, g->dim, levels), s) : (void *)1;
+  void *gsw = device_scratch(SCRATCH_PINGPONG, 3 * (size_t)span_elems(q) * 8, s);
+  void *bnd = device_scratch(SCRATCH_BOUNDS, gs_fx_bounds_bytes(), s);
+  dn = (double *)device_scratch(SCRATCH_NORMS, 64, s);
+  void *red = device_scratch(SCRATCH_REDUCE, mg_reduce_bytes(q, g->dim, levels), s);
+  if (!work || !gsw || !bnd || !dn || !red) return set_error(STENCIL_ENOMEM, "mg: workspace allocation failed");
+  if (!cyc.setup(q, g->dim, levels, o->pre, o->post, o->coarse_sweeps, work, (double *)gsw, bnd, dn, red, s))
+    return set_error(STENCIL_EINVAL, "mg: bad hierarchy");
+  return STENCIL_OK;
+}
+
+static int mg_check_uf(const stencil_grid_t *g, const double *u, const double *f) {
+  int rc = check_grid(g);
+  if (rc) return rc;
+  if (g->dtype != STENCIL_F64) return set_error(STENCIL_EINVAL, "mg: u and f must be F64");
+  if ((rc = check_ptr(u, g, "u")) || (rc = check_ptr(f, g, "f"))) return rc;
+  if (overlap(u, f, (size_t)span_elems(make_geo(*g)) * 8)) return set_error(STENCIL_EINVAL, "u and f overlap");
+  return STENCIL_OK;
+}
+
+int stencil_mg_vcycle(const stencil_grid_t *g, double *u, const double *f, const stencil_mg_opts_t *opts,
+                      void *stream) {
+  int rc = mg_check_uf(g, u, f);
+  if (rc || (rc = check_mg_opts(opts))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  MgCycle cyc;
+  int levels;
+  double *dn;
+  if ((rc = mg_prepare(g, opts, s, cyc, levels, dn))) return rc;
+  cudaError_t e = cyc.run(u, f);
+  if (e) return set_error(STENCIL_ECUDA, std::string("mg_vcycle: ") + cudaGetErrorString(e));
+  return STENCIL_OK;
+}
+
+int stencil_mg_solve(const stencil_grid_t *g, double *u, const double *f, const stencil_mg_opts_t *opts,
+                     stencil_mg_info_t *info, void *stream) {
+  int rc = mg_check_uf(g, u, f);
+  if (rc || (rc = check_mg_opts(opts))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Geo q = make_geo(*g);
+  MgCycle cyc;
+  int levels;
+  double *dn;
+  if ((rc = mg_prepare(g, opts, s, cyc, levels, dn))) return rc;
+  double *hn = (double *)host_scratch(64, s);
+  // reduction scratch of the convergence test: the cycle's (sized for every level)
+  void *red = device_scratch(SCRATCH_REDUCE, mg_reduce_bytes(q, g->dim, levels), s);
+  if (!hn || !red) return set_error(STENCIL_ENOMEM, "mg: workspace allocation failed");
+  int k = 0;
+  double rho = 0.0;
+  bool conv = false;
+  for (;;) {
+    cudaError_t ce = g->dim == 3 ? launch_residual_fx3(q, u, f, nullptr, dn, red, s)
+                                 : launch_residual_fx2(q, u, f, nullptr, dn, red, s);
+    if (!ce) ce = cudaMemcpyAsync(hn, dn, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (!ce) ce = cudaStreamSynchronize(s);
+    if (ce) return set_error(STENCIL_ECUDA, std::string("mg_solve: ") + cudaGetErrorString(ce));
+    rho = hn[1] > 0.0 ? std::sqrt(hn[0]) / std::sqrt(hn[1]) : std::sqrt(hn[0]);
+    if (info && info->relres_history) info->relres_history[k] = rho;
+    if (rho <= opts->rel_tol) {
+      conv = true;
+      break;
+    }
+    if (k >= opts->max_cycles) break;
+    ce = cyc.run(u, f);
+    if (ce) return set_error(STENCIL_ECUDA, std::string("mg_solve: ") + cudaGetErrorString(ce));
+    ++k;
+  }
+  if (info) {
+    info->cycles = k;
+    info->converged = conv ? 1 : 0;
+    info->levels = levels;
+    info->relres = rho;
+  }
+  if (!conv) return set_error(STENCIL_ENOTCONV, "mg_solve: max_cycles reached before rel_tol");
+  return STENCIL_OK;
+}
+
+static int check_transfer(const stencil_grid_t *fine, const stencil_grid_t *coarse) {
+  int rc = check_grid(fine);
+  if (rc || (rc = check_grid(coarse))) return rc;
+  if (fine->dtype != STENCIL_F64 || coarse->dtype != STENCIL_F64)
+    return set_error(STENCIL_EINVAL, "mg transfer: F64 only");
+  if (fine->dim != coarse->dim) return set_error(STENCIL_EINVAL, "mg transfer: dim mismatch");
+  Geo qc;
+  if (!mg_coarse(make_geo(*fine), fine->dim, qc))
+    return set_error(STENCIL_EINVAL, "mg transfer: the fine grid has no coarse grid");
+  if (coarse->n[0] != qc.nx || coarse->n[1] != qc.ny || (fine->dim == 3 && coarse->n[2] != qc.nz))
+    return set_error(STENCIL_EINVAL, "mg transfer: coarse n must be the hierarchy's coarse grid of the fine n");
+  return STENCIL_OK;
+}
+
+int stencil_mg_restrict(const stencil_grid_t *fine, const double *rf, const stencil_grid_t *coarse, double *rc,
+                        void *stream) {
+  int r = check_transfer(fine, coarse);
+  if (r || (r = check_ptr(rf, fine, "rf")) || (r = check_ptr(rc, coarse, "rc"))) return r;
+  const Geo qf = make_geo(*fine), qc = make_geo(*coarse);
+  const size_t bf = (size_t)span_elems(qf) * 8, bc = (size_t)span_elems(qc) * 8;
+  if ((const char *)rf < (const char *)rc + bc && (const char *)rc < (const char *)rf + bf)
+    return set_error(STENCIL_EINVAL, "rf and rc overlap");
+  cudaError_t e = launch_mg_restrict(qf, qc, fine->dim, rf, rc, (cudaStream_t)stream);
+  if (e) return set_error(STENCIL_ECUDA, std::string("mg_restrict: ") + cudaGetErrorString(e));
+  return STENCIL_OK;
+}
+
+int stencil_mg_prolong_add(const stencil_grid_t *fine, double *uf, const stencil_grid_t *coarse, const double *ec,
+                           void *stream) {
+  int r = check_transfer(fine, coarse);
+  if (r || (r = check_ptr(uf, fine, "uf")) || (r = check_ptr(ec, coarse, "ec"))) return r;
+  const Geo qf = make_geo(*fine), qc = make_geo(*coarse);
+  const size_t bf = (size_t)span_elems(qf) * 8, bc = (size_t)span_elems(qc) * 8;
+  if ((const char *)ec < (const char *)uf + bf && (const char *)uf < (const char *)ec + bc)
+    return set_error(STENCIL_EINVAL, "uf and ec overlap");
+  cudaError_t e = launch_mg_prolong_add(qf, qc, fine->dim, ec, uf, (cudaStream_t)stream);
+  if (e) return set_error(STENCIL_ECUDA, std::string("mg_prolong_add: ") + cudaGetErrorString(e));
   return STENCIL_OK;
 }
 

@@ -62,6 +62,7 @@ enum ScratchSlot {
   SCRATCH_SOLVE_R = 4, // refinement: residual in the inner type
   SCRATCH_SOLVE_E = 5, // refinement: correction
   SCRATCH_NORMS = 6,   // refinement: device norms
+  SCRATCH_MG = 7,      // multigrid: coarse-level arrays
   SCRATCH_SLOTS = 8
 };
 // Pinned host scratch of the (device, stream) set.
@@ -87,7 +88,7 @@ size_t reduce_scratch_bytes();
 // holds 3 arrays of u's span (two int64 ping-pong buffers and 3/8 h^2 f in fixed point);
 // the result always ends in u, whose boundary values are never written.
 size_t gs_fx_bounds_bytes();
-// Per-call pre-pass of the multi-sweep GS drivers: clears the bounds, takes max |u| and
+// Per-call pre-pass of the multi-sweep GS and Jacobi launchers: clears the bounds, takes max |u| and
 // max |f| (interior), and writes GF = 3/8 h^2 f as fixed point (0 off the interior).
 cudaError_t launch_gs_prepass(const Geo &q, int dim, const double *u, const double *f, long long *GF,
                               void *bounds, int sweeps, cudaStream_t s);
@@ -130,5 +131,39 @@ cudaError_t launch_gs_sweeps_bf16_3d(const Geo &q, void *u, const void *f, int s
 
 // x += e on interior vertices, e of element type dtype (solve.cu).
 cudaError_t launch_add_correction(const Geo &q, int dim, double *x, const void *e, int dtype, cudaStream_t s);
+
+// Geometric multigrid (mg.cu).  Coarse grids are dense (pitch n_c + 1): n/2 per axis
+// when all n are even, ceil(n/2) when all n are equal; none (false) below n = 4.
+bool mg_coarse(const Geo &qf, int dim, Geo &qc);
+int mg_levels(const Geo &q, int dim, int max_levels);
+size_t mg_work_bytes(const Geo &q0, int dim, int levels);    // coarse-level arrays
+size_t mg_reduce_bytes(const Geo &q0, int dim, int levels);  // residual reduction scratch
+cudaError_t launch_mg_restrict(const Geo &qf, const Geo &qc, int dim, const double *rf, double *rc, cudaStream_t s);
+cudaError_t launch_mg_prolong_add(const Geo &qf, const Geo &qc, int dim, const double *ec, double *uf,
+                                  cudaStream_t s);
+
+// One V-cycle, stream-ordered.  setup() carves the coarse-level arrays out of `work`
+// (mg_work_bytes); gs_work / gs_bounds are the multi-sweep GS workspace of the finest
+// grid (reused on every level), norms 2 doubles and red the residual reduction scratch
+// (mg_reduce_bytes), both device.
+class MgCycle {
+ public:
+  static constexpr int kMaxLevels = 40;
+  bool setup(const Geo &q0, int dim, int levels, int pre, int post, int coarse_sweeps, void *work,
+             double *gs_work, void *gs_bounds, double *norms, void *red, cudaStream_t s);
+  cudaError_t run(double *u0, const double *f0);
+
+ private:
+  cudaError_t level(int l, double *u, const double *f);
+  cudaError_t smooth(const Geo &q, double *u, const double *f, int sweeps);
+  Geo q_[kMaxLevels];
+  double *u_[kMaxLevels], *f_[kMaxLevels], *r_[kMaxLevels];
+  int dim_ = 3, levels_ = 1, pre_ = 2, post_ = 2, coarse_sweeps_ = 20;
+  double *gs_work_ = nullptr;
+  void *gs_bounds_ = nullptr;
+  double *norms_ = nullptr;
+  void *red_ = nullptr;
+  cudaStream_t s_ = nullptr;
+};
 
 }  // namespace stencil

@@ -6,8 +6,9 @@
 // allocates its buffers stream-ordered, and drives it on one of several CUDA streams:
 //   SMOOTH: `sweeps` coloured Gauss-Seidel sweeps (the FP64 fixed-point kernels);
 //   SOLVE:  iterative refinement, one correction per step (residual and norms in FP64,
-//           inner coloured GS sweeps in FP32 / bf16 / FP64), with the norm read back
-//           asynchronously; the next correction is issued once the norm has arrived.
+//           inner coloured GS sweeps in FP32 / bf16 / FP64), or (solver MG) one FP64
+//           multigrid V-cycle per step; the norm is read back asynchronously and the
+//           next step is issued once it has arrived.
 // Work of different requests is on different streams and overlaps on the device; new
 // requests join as soon as memory and slots free up.  Each request uses only its own
 // buffers and deterministic kernels, so its result does not depend on what else runs.
@@ -72,6 +73,8 @@ struct Req {
   void *bounds = nullptr, *red = nullptr, *rlo = nullptr, *elo = nullptr, *wlo = nullptr;
   double *hnorms = nullptr;  // pinned, 2 doubles (a slot of the server's pool)
   int hslot = -1;
+  void *mgw = nullptr;  // multigrid: coarse-level arrays
+  MgCycle cyc;          // multigrid: the request's V-cycle
   cudaEvent_t ev = nullptr;
   bool step_in_flight = false;
   int iterations = 0;
@@ -122,6 +125,9 @@ size_t footprint_of(const stencil_server_opts_t &o, const stencil_request_t &r, 
   size_t b = 2 * span * 8 + 64 + 256;  // u, f, norms
   if (r.kind == STENCIL_REQ_SMOOTH) {
     b += 3 * span * 8 + gs_fx_bounds_bytes();
+  } else if (o.solver == STENCIL_SOLVER_MG) {
+    const int L = mg_levels(q, 3, MgCycle::kMaxLevels);
+    b += mg_work_bytes(q, 3, L) + mg_reduce_bytes(q, 3, L) + 3 * span * 8 + gs_fx_bounds_bytes();
   } else {
     const size_t e = elem_bytes(o.inner_dtype);
     b += ops_fx_reduce_bytes(q) + 2 * span * e;  // residual and correction in the inner type
@@ -136,11 +142,11 @@ cudaError_t dalloc(stencil_server *s, void **p, size_t bytes, cudaStream_t st) {
 
 void release_device(stencil_server *s, Req *q) {
   cudaStream_t st = s->streams[q->stream];
-  void *ptrs[] = {q->u, q->f, q->work, q->norms, q->bounds, q->red, q->rlo, q->elo, q->wlo};
+  void *ptrs[] = {q->u, q->f, q->work, q->norms, q->bounds, q->red, q->rlo, q->elo, q->wlo, q->mgw};
   for (void *p : ptrs)
     if (p) cudaFreeAsync(p, st);
   q->u = q->f = q->work = q->norms = nullptr;
-  q->bounds = q->red = q->rlo = q->elo = q->wlo = nullptr;
+  q->bounds = q->red = q->rlo = q->elo = q->wlo = q->mgw = nullptr;
   if (q->hslot >= 0) {
     s->hfree.push_back(q->hslot);
     q->hslot = -1;
@@ -156,7 +162,9 @@ void release_device(stencil_server *s, Req *q) {
 cudaError_t issue_residual(stencil_server *s, Req *q) {
   cudaStream_t st = s->streams[q->stream];
   const int kind = s->o.inner_dtype == STENCIL_F64 ? 0 : (s->o.inner_dtype == STENCIL_F32 ? 1 : 2);
-  cudaError_t e = launch_residual_fx3(q->q, q->u, q->f, (double *)q->rlo, q->norms, q->red, st, kind);
+  cudaError_t e = s->o.solver == STENCIL_SOLVER_MG
+                      ? launch_residual_fx3(q->q, q->u, q->f, nullptr, q->norms, q->red, st, 0)
+                      : launch_residual_fx3(q->q, q->u, q->f, (double *)q->rlo, q->norms, q->red, st, kind);
   if (!e) e = cudaMemcpyAsync(q->hnorms, q->norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (!e) e = cudaEventRecord(q->ev, st);
   q->step_in_flight = true;
@@ -164,6 +172,7 @@ cudaError_t issue_residual(stencil_server *s, Req *q) {
 }
 
 cudaError_t issue_correction(stencil_server *s, Req *q) {
+  if (s->o.solver == STENCIL_SOLVER_MG) return q->cyc.run(q->u, q->f);
   cudaStream_t st = s->streams[q->stream];
   const size_t span = (size_t)span_elems(q->q);
   const int dt = s->o.inner_dtype;
@@ -212,6 +221,17 @@ cudaError_t admit(stencil_server *s, Req *q) {
     if (!e && q->r.sweeps > 0) e = launch_gs_sweeps_fx3(q->q, q->u, q->f, q->r.sweeps, q->work, q->bounds, st);
     if (!e) e = cudaEventRecord(q->ev, st);
     q->step_in_flight = true;
+  } else if (s->o.solver == STENCIL_SOLVER_MG) {
+    const int L = mg_levels(q->q, 3, MgCycle::kMaxLevels);
+    const size_t rb = mg_reduce_bytes(q->q, 3, L);
+    e = dalloc(s, &q->red, rb, st);
+    if (!e) e = cudaMemsetAsync(q->red, 0, rb, st);
+    if (!e) e = dalloc(s, &q->mgw, mg_work_bytes(q->q, 3, L) + 256, st);
+    if (!e) e = dalloc(s, (void **)&q->work, 3 * span * 8, st);
+    if (!e) e = dalloc(s, &q->bounds, gs_fx_bounds_bytes(), st);
+    if (!e && !q->cyc.setup(q->q, 3, L, 2, 2, 20, q->mgw, q->work, q->bounds, q->norms, q->red, st))
+      e = cudaErrorInvalidValue;
+    if (!e) e = issue_residual(s, q);
   } else {
     const size_t eb = elem_bytes(s->o.inner_dtype);
     e = dalloc(s, &q->red, ops_fx_reduce_bytes(q->q), st);
@@ -238,11 +258,11 @@ void finish(stencil_server *s, Req *q, int status) {
   q->step_in_flight = false;
   // working buffers go back at once; u stays resident for fetch
   cudaStream_t st = s->streams[q->stream];
-  void *ptrs[] = {q->f, q->work, q->norms, q->bounds, q->red, q->rlo, q->elo, q->wlo};
+  void *ptrs[] = {q->f, q->work, q->norms, q->bounds, q->red, q->rlo, q->elo, q->wlo, q->mgw};
   for (void *p : ptrs)
     if (p) cudaFreeAsync(p, st);
   q->f = q->work = q->norms = nullptr;
-  q->bounds = q->red = q->rlo = q->elo = q->wlo = nullptr;
+  q->bounds = q->red = q->rlo = q->elo = q->wlo = q->mgw = nullptr;
   if (q->hslot >= 0) {
     s->hfree.push_back(q->hslot);
     q->hslot = -1;
@@ -357,6 +377,10 @@ int stencil_server_create(size_t hbm_budget_bytes, const stencil_server_opts_t *
   if (o.inner_sweeps <= 0) o.inner_sweeps = 8;
   if (o.inner_dtype != STENCIL_F64 && o.inner_dtype != STENCIL_BF16) o.inner_dtype = STENCIL_F32;
   if (o.max_outer <= 0) o.max_outer = 100000;
+  if (o.solver != STENCIL_SOLVER_REFINE && o.solver != STENCIL_SOLVER_MG) {
+    delete s;
+    return set_error(STENCIL_EINVAL, "server_create: unknown solver");
+  }
   s->o = o;
   cudaGetDevice(&s->device);
   s->t0 = std::chrono::steady_clock::now();

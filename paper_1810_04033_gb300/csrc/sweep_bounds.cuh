@@ -1,4 +1,4 @@
-// Per-sweep fixed-point scale shared by the multi-sweep Gauss-Seidel drivers (3D:
+// Per-sweep fixed-point scale shared by the multi-sweep Gauss-Seidel and Jacobi launchers (3D:
 // gs_fx.cu, 2D: gs2_fx.cu).  Intermediate sweeps keep the iterate in HBM as int64
 // fixed point; every value of sweep s is a multiple of 2^(R_s - 52) with |v| < 2^R_s,
 // where R_s comes from a bound tracked on the device (no host round trip):

@@ -45,6 +45,23 @@ def test_solve_request_matches_oracle_refinement():
     srv.close()
 
 
+@pytest.mark.parametrize("n", [16, 24, 15])
+def test_solve_request_multigrid_matches_oracle(n):
+    """SOLVE with the multigrid solver: same V-cycles as the oracle's (V(2,2), 20
+    coarsest sweeps), so the same cycle count and iterate; n = 15 coarsens to 8 (not nested)."""
+    f = synth.splitmix_field(n, 991 + n)
+    srv = st.Server(4 * GB, solver=st.SOLVER_MG)
+    t = srv.submit(st.REQ_SOLVE, n, rel_tol=1e-9, f_seed=991 + n)
+    res = srv.wait(t)
+    assert res["status"] == 0 and res["relres"] <= 1e-9
+    u = srv.fetch(t, n)
+    uo, hist, k, conv = oracle.mg_solve(np.zeros_like(f), f, 1.0 / n, 1e-9, 100000, pre=2, post=2,
+                                        coarse_sweeps=20)
+    assert conv and k == res["iterations"]
+    assert rel_err(u, uo) <= 1e-11
+    srv.close()
+
+
 def _mix(seed=3, count=24):
     g = synth.rng(seed)
     out = []
