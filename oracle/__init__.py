@@ -46,6 +46,11 @@ def lib():
             "oracle_mg_vcycle": (None, [ci, i64p, cd, dp, dp, ci, ci, ci, ci]),
             "oracle_mg_solve": (ci, [ci, i64p, cd, dp, dp, cd, ci, ci, ci, ci, ci, dp,
                                      ctypes.POINTER(ctypes.c_int)]),
+            "oracle_fd_weight": (cd, [ci, ci, ci, ci]),
+            "oracle_fd_apply": (None, [ci, i64p, cd, dp, dp]),
+            "oracle_fd_gs_redblack": (None, [ci, i64p, cd, dp, dp, ci]),
+            "oracle_fd_jacobi": (None, [ci, i64p, cd, dp, dp, dp, cd, ci]),
+            "oracle_fd_residual": (None, [ci, i64p, cd, dp, dp, dp, dp]),
             "oracle_f32_to_bf16": (ctypes.c_uint16, [ctypes.c_float]),
             "oracle_bf16_to_f32": (ctypes.c_float, [ctypes.c_uint16]),
         }
@@ -237,6 +242,48 @@ def mg_solve(u0, f, h, tol, max_cycles, levels=64, pre=2, post=2, coarse_sweeps=
                               _ptr(f, ctypes.c_double), tol, max_cycles, levels, pre, post,
                               coarse_sweeps, _ptr(relres, ctypes.c_double), ctypes.byref(conv))
     return u, relres[:k + 1], k, bool(conv.value)
+
+
+def fd_weight(dim, dx, dy, dz=0):
+    return lib().oracle_fd_weight(dim, dx, dy, dz)
+
+
+def fd_apply(u, h):
+    u = _f64(u)
+    dim, n = _grid(u.shape)
+    y = np.empty_like(u)
+    lib().oracle_fd_apply(dim, _ptr(n, ctypes.c_int64), h, _ptr(u, ctypes.c_double), _ptr(y, ctypes.c_double))
+    return y
+
+
+def fd_gs_redblack(u0, f, h, sweeps):
+    u = _f64(u0).copy()
+    f = _f64(f)
+    dim, n = _grid(u.shape)
+    lib().oracle_fd_gs_redblack(dim, _ptr(n, ctypes.c_int64), h, _ptr(u, ctypes.c_double),
+                                _ptr(f, ctypes.c_double), sweeps)
+    return u
+
+
+def fd_jacobi(u0, f, h, omega, sweeps):
+    u = _f64(u0).copy()
+    f = _f64(f)
+    w = np.empty_like(u)
+    dim, n = _grid(u.shape)
+    lib().oracle_fd_jacobi(dim, _ptr(n, ctypes.c_int64), h, _ptr(u, ctypes.c_double), _ptr(f, ctypes.c_double),
+                           _ptr(w, ctypes.c_double), omega, sweeps)
+    return u
+
+
+def fd_residual(u, f, h):
+    u = _f64(u)
+    f = _f64(f)
+    dim, n = _grid(u.shape)
+    r = np.empty_like(u)
+    nrm = np.zeros(2)
+    lib().oracle_fd_residual(dim, _ptr(n, ctypes.c_int64), h, _ptr(u, ctypes.c_double), _ptr(f, ctypes.c_double),
+                             _ptr(r, ctypes.c_double), _ptr(nrm, ctypes.c_double))
+    return r, nrm
 
 
 def patch_halo_fill(lat, np_sizes, offsets, u_all):

@@ -33,6 +33,10 @@
  *                             functions (nested and not); R is (n_c/n)^d P^T (adjoint
  *                             identity); the solve reaches the closed-form discrete
  *                             solution for even and odd n; V-cycle contraction.
+ *   oracle_fd_*               pinned: the 5-point stencil printed in Fig. 1 (golden
+ *                             file); dense Kronecker assembly; exactness on cubic
+ *                             polynomials; sine-mode symbol and closed-form solution;
+ *                             red-black GS = dense GS in Algorithm 1's colour order.
  *   oracle_patch_*            parity unpinned beyond: a single patch with zero
  *                             neighbours equals a plain Dirichlet GS; equal-size
  *                             neighbours copy the first interior layer (the halo rule
@@ -668,4 +672,104 @@ int oracle_mg_solve(int dim, const int64_t *n, double h, double *u, const double
   }
   free(r);
   return k;
+}
+
+/* --------------------------------------- 5/7-point finite differences, red-black */
+
+/* The compact 2d+1-point stencils of Section 2 (Fig. 1 middle prints the 2D 5-point
+ * one: centre 4, face neighbours -1): S u = 2d u - (sum of the 2d face neighbours),
+ * A = S / h^2 with the same Dirichlet convention as the Q1 functions.  Section 3 colours
+ * these with two colours (red-black); Algorithm 1 indexes the unknowns from 1 and its
+ * first pass visits the cells with x + y odd.  With the unknowns at our interior
+ * vertices 1..n-1 (x = i, y = j, z = k) the first pass is (i + j + k) odd, the second
+ * (i + j + k) even, lexicographic inside a pass. */
+
+double oracle_fd_weight(int dim, int dx, int dy, int dz) {
+  const int off = (dx != 0) + (dy != 0) + (dz != 0);
+  if (dim == 2 && dz != 0) return 0.0;
+  if (off == 0) return 2.0 * dim;
+  return off == 1 ? -1.0 : 0.0;
+}
+
+static double fd_neighbour_sum(int dim, const int64_t *n, const double *u, int64_t i,
+                               int64_t j, int64_t k) {
+  /* face neighbours in the order x-, x+, y-, y+, z-, z+ */
+  double s = u[vidx(n, i - 1, j, k)] + u[vidx(n, i + 1, j, k)];
+  s += u[vidx(n, i, j - 1, k)] + u[vidx(n, i, j + 1, k)];
+  if (dim == 3) s += u[vidx(n, i, j, k - 1)] + u[vidx(n, i, j, k + 1)];
+  return s;
+}
+
+void oracle_fd_apply(int dim, const int64_t *n, double h, const double *u, double *y) {
+  const int64_t nzc = nz_cells(dim, n);
+  const double h2 = h * h, c = 2.0 * dim;
+  for (int64_t k = 0; k <= nzc; ++k)
+    for (int64_t j = 0; j <= n[1]; ++j)
+      for (int64_t i = 0; i <= n[0]; ++i) {
+        const int64_t p = vidx(n, i, j, k);
+        y[p] = is_interior(dim, n, i, j, k)
+                   ? (c * u[p] - fd_neighbour_sum(dim, n, u, i, j, k)) / h2
+                   : 0.0;
+      }
+}
+
+void oracle_fd_gs_redblack(int dim, const int64_t *n, double h, double *u,
+                           const double *f, int sweeps) {
+  const int64_t nzc = nz_cells(dim, n);
+  const double h2 = h * h, c = 2.0 * dim;
+  for (int s = 0; s < sweeps; ++s)
+    for (int pass = 0; pass < 2; ++pass) {
+      const int64_t parity = pass == 0 ? 1 : 0; /* odd first */
+      for (int64_t k = 0; k <= nzc; ++k)
+        for (int64_t j = 0; j <= n[1]; ++j)
+          for (int64_t i = 0; i <= n[0]; ++i) {
+            if (!is_interior(dim, n, i, j, k) || ((i + j + k) & 1) != parity) continue;
+            const int64_t p = vidx(n, i, j, k);
+            u[p] = (h2 * f[p] + fd_neighbour_sum(dim, n, u, i, j, k)) / c;
+          }
+    }
+}
+
+void oracle_fd_jacobi(int dim, const int64_t *n, double h, double *u, const double *f,
+                      double *work, double omega, int sweeps) {
+  const int64_t nzc = nz_cells(dim, n), np = num_points(dim, n);
+  const double h2 = h * h, c = 2.0 * dim;
+  for (int s = 0; s < sweeps; ++s) {
+    for (int64_t k = 0; k <= nzc; ++k)
+      for (int64_t j = 0; j <= n[1]; ++j)
+        for (int64_t i = 0; i <= n[0]; ++i) {
+          const int64_t p = vidx(n, i, j, k);
+          if (!is_interior(dim, n, i, j, k)) {
+            work[p] = u[p];
+            continue;
+          }
+          /* u + omega D^-1 (f - A u), D = 2d / h^2 */
+          const double Au = (c * u[p] - fd_neighbour_sum(dim, n, u, i, j, k)) / h2;
+          work[p] = u[p] + omega * (h2 / c) * (f[p] - Au);
+        }
+    memcpy(u, work, (size_t)np * sizeof(double));
+  }
+}
+
+void oracle_fd_residual(int dim, const int64_t *n, double h, const double *u,
+                        const double *f, double *r, double *norms2) {
+  const int64_t nzc = nz_cells(dim, n), np = num_points(dim, n);
+  double *res = r ? r : (double *)malloc((size_t)np * sizeof(double));
+  oracle_fd_apply(dim, n, h, u, res);
+  double rr = 0.0, ff = 0.0;
+  for (int64_t k = 0; k <= nzc; ++k)
+    for (int64_t j = 0; j <= n[1]; ++j)
+      for (int64_t i = 0; i <= n[0]; ++i) {
+        const int64_t p = vidx(n, i, j, k);
+        if (!is_interior(dim, n, i, j, k)) {
+          res[p] = 0.0;
+          continue;
+        }
+        res[p] = f[p] - res[p];
+        rr += res[p] * res[p];
+        ff += f[p] * f[p];
+      }
+  norms2[0] = rr;
+  norms2[1] = ff;
+  if (!r) free(res);
 }

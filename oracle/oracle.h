@@ -124,6 +124,21 @@ int oracle_mg_solve(int dim, const int64_t *n, double h, double *u, const double
                     double tol, int max_cycles, int levels, int pre, int post,
                     int coarse_sweeps, double *relres, int *converged);
 
+/* 5-point (2D) / 7-point (3D) finite differences (Fig. 1 middle, Section 2) with the
+ * red-black colouring of Section 3: A u = (2d u - sum of face neighbours) / h^2.
+ * Red-black GS: first all interior vertices with (i+j+k) odd, then (i+j+k) even
+ * (Algorithm 1's order with its 1-based unknowns on our interior vertices).
+ * Jacobi: u <- u + omega h^2/(2d) (f - A u), boundary copied.  Residual as
+ * oracle_residual (sums in lexicographic order). */
+double oracle_fd_weight(int dim, int dx, int dy, int dz);
+void oracle_fd_apply(int dim, const int64_t *n, double h, const double *u, double *y);
+void oracle_fd_gs_redblack(int dim, const int64_t *n, double h, double *u,
+                           const double *f, int sweeps);
+void oracle_fd_jacobi(int dim, const int64_t *n, double h, double *u, const double *f,
+                      double *work, double omega, int sweeps);
+void oracle_fd_residual(int dim, const int64_t *n, double h, const double *u,
+                        const double *f, double *r, double *norms2);
+
 /* Round-to-nearest-even conversion helpers exposed for tests. */
 uint16_t oracle_f32_to_bf16(float x);
 float oracle_bf16_to_f32(uint16_t b);
