@@ -63,12 +63,26 @@ extern "C" {
 #define STENCIL_FORM_ELEMENTWISE 0 /* cell-wise element matrix, 2^d-colour scatter */
 #define STENCIL_FORM_STENCIL 1     /* assembled 3^d-point stencil, gathered */
 
+/* Operators (stencil_grid_t.op).
+ * STENCIL_OP_Q1: the Q1 (d-linear FE) Laplacian A = S / h^2, S the assembled 3^d-point
+ *   stencil (2D: the 9-point stencil of Fig. 1, right), coloured with 2^d colours.
+ * STENCIL_OP_FD: the 2d+1-point finite-difference Laplacian (2D: the 5-point stencil of
+ *   Fig. 1, middle; 3D: 7-point), S u = 2d u - (sum of the face neighbours), coloured
+ *   red-black (Section 3).  F64 only; supported by stencil_apply (stencil form),
+ *   stencil_smooth_coloured (red-black: first the interior vertices with i+j+k odd,
+ *   then even, the order of Algorithm 1), stencil_smooth_jacobi, stencil_jacobi_step
+ *   and stencil_residual; the other entry points return STENCIL_EINVAL. */
+#define STENCIL_OP_Q1 0
+#define STENCIL_OP_FD 1
+
 typedef struct stencil_grid {
   int32_t dim;   /* 2 or 3 */
   int32_t dtype; /* STENCIL_F64 | STENCIL_F32 | STENCIL_BF16 */
-  int64_t n[3];  /* cells along x, y, z; each >= 2 (n[2] ignored when dim == 2) */
+  int64_t n[3];  /* cells along x, y, z; each >= 1 (n[2] ignored when dim == 2) */
   int64_t pitch; /* elements between consecutive x-rows; 0 selects n[0] + 1 */
   double h;      /* mesh width (> 0) */
+  int32_t op;    /* STENCIL_OP_Q1 (0, the default of a zeroed descriptor) or STENCIL_OP_FD */
+  int32_t reserved; /* 0 */
 } stencil_grid_t;
 
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */

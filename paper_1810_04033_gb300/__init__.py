@@ -16,6 +16,7 @@ from . import build as _build
 
 F64, F32, BF16 = 0, 1, 2
 FORM_ELEMENTWISE, FORM_STENCIL = 0, 1
+OP_Q1, OP_FD = 0, 1
 
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "EADMIT", -4: "ETIMEDOUT", -5: "ECUDA",
           -6: "ENOTCONV", -7: "ENOTFOUND", -8: "EBUSY"}
@@ -34,7 +35,8 @@ class StencilError(RuntimeError):
 
 class Grid(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("dtype", ctypes.c_int32),
-                ("n", ctypes.c_int64 * 3), ("pitch", ctypes.c_int64), ("h", ctypes.c_double)]
+                ("n", ctypes.c_int64 * 3), ("pitch", ctypes.c_int64), ("h", ctypes.c_double),
+                ("op", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class PatchDesc(ctypes.Structure):
@@ -148,7 +150,7 @@ def _check(rc):
         raise StencilError(rc, lib().stencil_last_error().decode())
 
 
-def grid_for(t: torch.Tensor, h: float) -> Grid:
+def grid_for(t: torch.Tensor, h: float, op: int = 0) -> Grid:
     """Grid descriptor for a vertex tensor (validates layout, not device residency)."""
     if t.dim() not in (2, 3):
         raise ValueError("expected a 2D or 3D vertex tensor")
@@ -171,6 +173,7 @@ def grid_for(t: torch.Tensor, h: float) -> Grid:
         g.n[0], g.n[1], g.n[2] = nx, ny, 0
     g.pitch = pitch
     g.h = float(h)
+    g.op = int(op)
     return g
 
 
@@ -197,51 +200,51 @@ def stencil_version() -> int:
     return lib().stencil_version()
 
 
-def stencil_apply(u, y, h, form=FORM_STENCIL, stream=None):
-    """y = A u (boundary rows of y set to 0)."""
+def stencil_apply(u, y, h, form=FORM_STENCIL, stream=None, op=OP_Q1):
+    """y = A u (boundary rows of y set to 0); op OP_Q1 or OP_FD (stencil form only)."""
     _same_layout(u, y)
-    g = grid_for(u, h)
+    g = grid_for(u, h, op)
     _check(lib().stencil_apply(ctypes.byref(g), _ptr(u), _ptr(y), int(form), _stream(stream)))
     return y
 
 
-def stencil_smooth_coloured(u, f, h, sweeps, stream=None):
-    """`sweeps` coloured Gauss-Seidel sweeps on A u = f, in place on u."""
+def stencil_smooth_coloured(u, f, h, sweeps, stream=None, op=OP_Q1):
+    """`sweeps` coloured Gauss-Seidel sweeps on A u = f, in place on u (OP_FD: red-black)."""
     _same_layout(u, f)
-    g = grid_for(u, h)
+    g = grid_for(u, h, op)
     _check(lib().stencil_smooth_coloured(ctypes.byref(g), _ptr(u), _ptr(f), int(sweeps),
                                          _stream(stream)))
     return u
 
 
-def stencil_smooth_jacobi(u, f, work, h, sweeps, omega=2.0 / 3.0, stream=None):
+def stencil_smooth_jacobi(u, f, work, h, sweeps, omega=2.0 / 3.0, stream=None, op=OP_Q1):
     """`sweeps` damped Jacobi sweeps; result in u, work is scratch of u's layout."""
     _same_layout(u, f)
     _same_layout(u, work)
-    g = grid_for(u, h)
+    g = grid_for(u, h, op)
     _check(lib().stencil_smooth_jacobi(ctypes.byref(g), _ptr(u), _ptr(f), _ptr(work),
                                        int(sweeps), float(omega), _stream(stream)))
     return u
 
 
-def stencil_jacobi_step(u_in, f, u_out, h, omega=2.0 / 3.0, stream=None):
+def stencil_jacobi_step(u_in, f, u_out, h, omega=2.0 / 3.0, stream=None, op=OP_Q1):
     """One damped Jacobi sweep from u_in into u_out (boundary copied)."""
     _same_layout(u_in, f)
     _same_layout(u_in, u_out)
-    g = grid_for(u_in, h)
+    g = grid_for(u_in, h, op)
     _check(lib().stencil_jacobi_step(ctypes.byref(g), _ptr(u_in), _ptr(f), _ptr(u_out),
                                      float(omega), _stream(stream)))
     return u_out
 
 
-def stencil_residual(u, f, h, r=None, norms2=None, stream=None):
+def stencil_residual(u, f, h, r=None, norms2=None, stream=None, op=OP_Q1):
     """r = f - A u (if r given) and norms2 = [sum r^2, sum f^2] (device float64[2])."""
     _same_layout(u, f)
     if r is not None:
         _same_layout(u, r)
     if norms2 is None:
         norms2 = torch.empty(2, dtype=torch.float64, device=u.device)
-    g = grid_for(u, h)
+    g = grid_for(u, h, op)
     _check(lib().stencil_residual(ctypes.byref(g), _ptr(u), _ptr(f),
                                   _ptr(r) if r is not None else ctypes.c_void_p(0),
                                   _ptr(norms2), _stream(stream)))

@@ -143,10 +143,20 @@ static size_t elem_size(int dtype) {
   }
 }
 
+// Entry points that implement the Q1 operator only.
+static int require_q1(const stencil_grid_t *g, const char *what) {
+  if (g->op != STENCIL_OP_Q1)
+    return set_error(STENCIL_EINVAL, std::string(what) + ": the Q1 operator only (op = STENCIL_OP_Q1)");
+  return STENCIL_OK;
+}
+
 int check_grid(const stencil_grid_t *g) {
   if (!g) return set_error(STENCIL_EINVAL, "grid descriptor is NULL");
   if (g->dim != 2 && g->dim != 3) return set_error(STENCIL_EINVAL, "dim must be 2 or 3");
   if (!elem_size(g->dtype)) return set_error(STENCIL_EINVAL, "unknown dtype");
+  if (g->op != STENCIL_OP_Q1 && g->op != STENCIL_OP_FD) return set_error(STENCIL_EINVAL, "unknown operator");
+  if (g->op == STENCIL_OP_FD && g->dtype != STENCIL_F64)
+    return set_error(STENCIL_EINVAL, "the finite-difference operator supports F64 only");
   const int64_t lim = (int64_t)1 << 31;
   for (int a = 0; a < g->dim; ++a)
     if (g->n[a] < 1 || g->n[a] >= lim)
@@ -198,7 +208,11 @@ int stencil_apply(const stencil_grid_t *g, const void *u, void *y, int form, voi
     return set_error(STENCIL_EINVAL, "u and y overlap");
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
-  if (g->dim == 2)
+  if (g->op == STENCIL_OP_FD) {
+    if (form != STENCIL_FORM_STENCIL)
+      return set_error(STENCIL_EINVAL, "apply: the finite-difference operator has the stencil form only");
+    e = launch_fd_apply(q, g->dim, (const double *)u, (double *)y, s);
+  } else if (g->dim == 2)
     e = launch_apply_fx2(q, (const double *)u, (double *)y, form == STENCIL_FORM_ELEMENTWISE, s);
   else if (form == STENCIL_FORM_STENCIL)
     e = launch_apply_stencil_fx3(q, (const double *)u, (double *)y, s);
@@ -222,7 +236,9 @@ int stencil_smooth_coloured(const stencil_grid_t *g, void *u, const void *f, int
   if (sweeps == 0) return STENCIL_OK;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
-  if (g->dtype != STENCIL_F64) {
+  if (g->op == STENCIL_OP_FD) {
+    e = launch_fd_gs_redblack(q, g->dim, (double *)u, (const double *)f, sweeps, s);
+  } else if (g->dtype != STENCIL_F64) {
     void *work = device_scratch(SCRATCH_LP, (size_t)span_elems(q) * esz, s);
     if (!work) return set_error(STENCIL_ENOMEM, "smooth_coloured workspace allocation failed");
     e = g->dtype == STENCIL_F32
@@ -259,7 +275,7 @@ int stencil_smooth_jacobi(const stencil_grid_t *g, void *u, const void *f, void 
   if (overlap(u, f, bytes) || overlap(u, work, bytes) || overlap(f, work, bytes))
     return set_error(STENCIL_EINVAL, "u, f and work must not overlap");
   cudaStream_t s = (cudaStream_t)stream;
-  if (g->dim == 2 && sweeps >= 2 && omega > 0.0 && omega <= 1.0) {
+  if (g->op == STENCIL_OP_Q1 && g->dim == 2 && sweeps >= 2 && omega > 0.0 && omega <= 1.0) {
     void *scr = device_scratch(SCRATCH_PINGPONG, 2 * bytes, s);
     void *bnd = device_scratch(SCRATCH_BOUNDS, gs_fx_bounds_bytes(), s);
     if (!scr || !bnd) return set_error(STENCIL_ENOMEM, "jacobi workspace allocation failed");
@@ -270,8 +286,9 @@ int stencil_smooth_jacobi(const stencil_grid_t *g, void *u, const void *f, void 
   }
   double *a = (double *)u, *b = (double *)work;
   for (int it = 0; it < sweeps; ++it) {
-    cudaError_t e = g->dim == 3 ? launch_jacobi_fx3(q, a, (const double *)f, b, omega, s)
-                                : launch_jacobi_fx2(q, a, (const double *)f, b, omega, s);
+    cudaError_t e = g->op == STENCIL_OP_FD ? launch_fd_jacobi(q, g->dim, a, (const double *)f, b, omega, s)
+                    : g->dim == 3         ? launch_jacobi_fx3(q, a, (const double *)f, b, omega, s)
+                                          : launch_jacobi_fx2(q, a, (const double *)f, b, omega, s);
     if (e != cudaSuccess) return set_error(STENCIL_ECUDA, std::string("jacobi: ") + cudaGetErrorString(e));
     double *t = a;
     a = b;
@@ -298,7 +315,10 @@ int stencil_jacobi_step(const stencil_grid_t *g, const void *u_in, const void *f
   if (overlap(u_out, u_in, bytes) || overlap(u_out, f, bytes))
     return set_error(STENCIL_EINVAL, "u_out overlaps an input");
   cudaError_t e =
-      g->dim == 3 ? launch_jacobi_fx3(q, (const double *)u_in, (const double *)f, (double *)u_out, omega,
+      g->op == STENCIL_OP_FD
+          ? launch_fd_jacobi(q, g->dim, (const double *)u_in, (const double *)f, (double *)u_out, omega,
+                             (cudaStream_t)stream)
+      : g->dim == 3 ? launch_jacobi_fx3(q, (const double *)u_in, (const double *)f, (double *)u_out, omega,
                                       (cudaStream_t)stream)
                   : launch_jacobi_fx2(q, (const double *)u_in, (const double *)f, (double *)u_out, omega,
                                       (cudaStream_t)stream);
@@ -318,11 +338,16 @@ int stencil_residual(const stencil_grid_t *g, const void *u, const void *f, void
   const size_t bytes = (size_t)span_elems(q) * 8;
   if (r && (overlap(r, u, bytes) || overlap(r, f, bytes)))
     return set_error(STENCIL_EINVAL, "r overlaps u or f");
-  const size_t need = g->dim == 3 ? ops_fx_reduce_bytes(q) : ops2_reduce_bytes(q);
+  const size_t need = g->op == STENCIL_OP_FD ? fd_reduce_bytes(q)
+                      : g->dim == 3         ? ops_fx_reduce_bytes(q)
+                                            : ops2_reduce_bytes(q);
   void *scratch = device_scratch(SCRATCH_REDUCE, need, (cudaStream_t)stream);
   if (!scratch) return set_error(STENCIL_ENOMEM, "residual scratch allocation failed");
   cudaError_t e =
-      g->dim == 3 ? launch_residual_fx3(q, (const double *)u, (const double *)f, (double *)r, d_norms2,
+      g->op == STENCIL_OP_FD
+          ? launch_fd_residual(q, g->dim, (const double *)u, (const double *)f, (double *)r, d_norms2, scratch,
+                               (cudaStream_t)stream)
+      : g->dim == 3 ? launch_residual_fx3(q, (const double *)u, (const double *)f, (double *)r, d_norms2,
                                         scratch, (cudaStream_t)stream)
                   : launch_residual_fx2(q, (const double *)u, (const double *)f, (double *)r, d_norms2,
                                         scratch, (cudaStream_t)stream);
@@ -335,6 +360,7 @@ int stencil_solve(const stencil_grid_t *g, double *u, const double *f, const ste
   int rc = check_grid(g);
   if (rc) return rc;
   if (g->dtype != STENCIL_F64) return set_error(STENCIL_EINVAL, "solve: u and f must be F64");
+  if ((rc = require_q1(g, "solve"))) return rc;
   if ((rc = check_ptr(u, g, "u")) || (rc = check_ptr(f, g, "f"))) return rc;
   if (!opts) return set_error(STENCIL_EINVAL, "solve: opts is NULL");
   if (!(opts->rel_tol >= 0.0) || opts->max_outer < 0 || opts->inner_sweeps < 1)
@@ -438,6 +464,7 @@ static int mg_check_uf(const stencil_grid_t *g, const double *u, const double *f
   int rc = check_grid(g);
   if (rc) return rc;
   if (g->dtype != STENCIL_F64) return set_error(STENCIL_EINVAL, "mg: u and f must be F64");
+  if ((rc = require_q1(g, "mg"))) return rc;
   if ((rc = check_ptr(u, g, "u")) || (rc = check_ptr(f, g, "f"))) return rc;
   if (overlap(u, f, (size_t)span_elems(make_geo(*g)) * 8)) return set_error(STENCIL_EINVAL, "u and f overlap");
   return STENCIL_OK;
@@ -507,6 +534,7 @@ static int check_transfer(const stencil_grid_t *fine, const stencil_grid_t *coar
   if (fine->dtype != STENCIL_F64 || coarse->dtype != STENCIL_F64)
     return set_error(STENCIL_EINVAL, "mg transfer: F64 only");
   if (fine->dim != coarse->dim) return set_error(STENCIL_EINVAL, "mg transfer: dim mismatch");
+  if ((rc = require_q1(fine, "mg transfer")) || (rc = require_q1(coarse, "mg transfer"))) return rc;
   Geo qc;
   if (!mg_coarse(make_geo(*fine), fine->dim, qc))
     return set_error(STENCIL_EINVAL, "mg transfer: the fine grid has no coarse grid");

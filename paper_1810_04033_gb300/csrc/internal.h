@@ -132,6 +132,15 @@ cudaError_t launch_gs_sweeps_bf16_3d(const Geo &q, void *u, const void *f, int s
 // x += e on interior vertices, e of element type dtype (solve.cu).
 cudaError_t launch_add_correction(const Geo &q, int dim, double *x, const void *e, int dtype, cudaStream_t s);
 
+// 5/7-point finite differences with red-black GS (fd.cu); F64, 2D and 3D.
+size_t fd_reduce_bytes(const Geo &q);
+cudaError_t launch_fd_apply(const Geo &q, int dim, const double *u, double *y, cudaStream_t s);
+cudaError_t launch_fd_jacobi(const Geo &q, int dim, const double *u, const double *f, double *unew, double omega,
+                             cudaStream_t s);
+cudaError_t launch_fd_residual(const Geo &q, int dim, const double *u, const double *f, double *r, double *norms2,
+                               void *scratch, cudaStream_t s);
+cudaError_t launch_fd_gs_redblack(const Geo &q, int dim, double *u, const double *f, int sweeps, cudaStream_t s);
+
 // Geometric multigrid (mg.cu).  Coarse grids are dense (pitch n_c + 1): n/2 per axis
 // when all n are even, ceil(n/2) when all n are equal; none (false) below n = 4.
 bool mg_coarse(const Geo &qf, int dim, Geo &qc);

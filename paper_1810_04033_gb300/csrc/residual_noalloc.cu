@@ -173,6 +173,7 @@ extern "C" int stencil_residual_noalloc(const stencil_grid_t *g, const void *u, 
   int rc = check_grid(g);
   if (rc) return rc;
   if (g->dtype != STENCIL_F64) return set_error(STENCIL_EINVAL, "residual_noalloc supports F64 only");
+  if (g->op != STENCIL_OP_Q1) return set_error(STENCIL_EINVAL, "residual_noalloc: the Q1 operator only");
   if (!u || !f || !d_norms2) return set_error(STENCIL_EINVAL, "u, f and d_norms2 must not be NULL");
   if ((uintptr_t)u % 8 || (uintptr_t)f % 8 || (uintptr_t)d_norms2 % 8 || (r && (uintptr_t)r % 8))
     return set_error(STENCIL_EINVAL, "arrays must be 8-byte aligned");

@@ -43,6 +43,7 @@ def _grid(**kw):
     g.n[0], g.n[1], g.n[2] = n
     g.pitch = kw.get("pitch", 0)
     g.h = kw.get("h", 0.25)
+    g.op = kw.get("op", st.OP_Q1)
     return g
 
 
@@ -53,6 +54,8 @@ def _grid(**kw):
     (dict(pitch=3), "pitch"),
     (dict(h=0.0), "h must"),
     (dict(h=float("nan")), "h must"),
+    (dict(op=7), "operator"),
+    (dict(op=st.OP_FD, dtype=st.F32), "F64 only"),
 ])
 def test_bad_descriptors_are_rejected_without_gpu(kw, msg):
     L = st.lib()
@@ -61,6 +64,24 @@ def test_bad_descriptors_are_rejected_without_gpu(kw, msg):
     rc = L.stencil_apply(ctypes.byref(g), fake, ctypes.c_void_p(8192), 1, None)
     assert rc == -1
     assert msg in L.stencil_last_error().decode()
+
+
+def test_fd_operator_rejected_where_unsupported_without_gpu():
+    """Entry points that implement the Q1 operator only refuse op = FD before any
+    device work; the FD apply has no element-wise form."""
+    L = st.lib()
+    g = _grid(op=st.OP_FD)
+    fake, fake2 = ctypes.c_void_p(4096), ctypes.c_void_p(1 << 20)
+    assert L.stencil_apply(ctypes.byref(g), fake, fake2, st.FORM_ELEMENTWISE, None) == -1
+    assert "stencil form" in L.stencil_last_error().decode()
+    opts = st.SolveOpts(1e-8, 10, 8, st.F32)
+    assert L.stencil_solve(ctypes.byref(g), fake, fake2, ctypes.byref(opts), None, None) == -1
+    assert "Q1" in L.stencil_last_error().decode()
+    mo = st.MgOpts(1e-8, 10, 2, 2, 20, 0, 0)
+    assert L.stencil_mg_solve(ctypes.byref(g), fake, fake2, ctypes.byref(mo), None, None) == -1
+    assert "Q1" in L.stencil_last_error().decode()
+    assert L.stencil_residual_noalloc(ctypes.byref(g), fake, fake2, None, ctypes.c_void_p(1 << 21), None) == -1
+    assert "Q1" in L.stencil_last_error().decode()
 
 
 def test_null_and_misaligned_pointers_rejected():
