@@ -79,10 +79,12 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--n3", type=int, default=N3, help="3D cells per edge (0: no 3D grid)")
     ap.add_argument("--n2", type=int, default=N2, help="2D cells per edge (0: no 2D grid)")
-    ap.add_argument("--workload", default="grid", choices=["grid", "small", "patches", "refine", "serve"],
+    ap.add_argument("--workload", default="grid",
+                    choices=["grid", "small", "patches", "refine", "serve", "fd"],
                     help="grid (default): the 512^3 + 16384^2 op mix above; small: 32^3 apply + 10 GS "
                          "sweeps; patches: 4096 uneven patches x 20 sweeps; refine: refinement to 1e-10 "
-                         "at 256^3 (FP32 / bf16 inner) vs FP64 inner; serve: request server")
+                         "at 256^3 (FP32 / bf16 inner) vs FP64 inner; serve: request server; fd: the "
+                         "grid op mix with the 5/7-point finite-difference operator (red-black GS)")
     ap.add_argument("--requests", type=int, default=400, help="serve: requests per arrival rate")
     ap.add_argument("--rates", default="200,1000,5000", help="serve: arrival rates (req/s)")
     ap.add_argument("--solver", default="mg", choices=["mg", "refine"],
@@ -145,8 +147,9 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ GPU arm
 class GpuWorkload:
-    def __init__(self, torch, st, device, n3, n2):
+    def __init__(self, torch, st, device, n3, n2, op=0):
         self.torch, self.st, self.dev = torch, st, device
+        self.op = op  # st.OP_Q1 or st.OP_FD
         self.n = {"3": n3, "2": n2}
         self.grids = [g for g in ("3", "2") if self.n[g]]
         self.h = {"3": 1.0 / n3 if n3 else 0.0, "2": 1.0 / n2 if n2 else 0.0}
@@ -183,23 +186,24 @@ class GpuWorkload:
         st = self.st
         h = self.h[g]
         u, f, y = self.view("u" + g), self.view("f" + g), self.view("y" + g)
+        k = self.op
         if op == "apply_elementwise":
             for _ in range(N_APPLY):
                 st.stencil_apply(u, y, h, st.FORM_ELEMENTWISE, stream=stream)
         elif op == "apply_stencil":
             for _ in range(N_APPLY):
-                st.stencil_apply(u, y, h, st.FORM_STENCIL, stream=stream)
+                st.stencil_apply(u, y, h, st.FORM_STENCIL, stream=stream, op=k)
         elif op == "gs_sweep":
-            st.stencil_smooth_coloured(u, f, h, N_SWEEPS, stream=stream)
+            st.stencil_smooth_coloured(u, f, h, N_SWEEPS, stream=stream, op=k)
         elif op == "jacobi_sweep":
             st.stencil_smooth_jacobi(self.view("ja" + g), f, self.view("jb" + g), h, N_SWEEPS, OMEGA,
-                                     stream=stream)
+                                     stream=stream, op=k)
         elif op == "residual":
-            st.stencil_residual(u, f, h, norms2=self.d["n" + g], stream=stream)
+            st.stencil_residual(u, f, h, norms2=self.d["n" + g], stream=stream, op=k)
 
-    def step(self, stream, events=None):
+    def step(self, stream, events=None, ops=None):
         for g in self.grids:
-            for op in OPS:
+            for op in (ops or OPS):
                 if events is not None:
                     events[(op, g)][0].record(stream)
                 self.run_op(op, g, stream)
@@ -504,6 +508,51 @@ def run_patches(args):
             "patches": int(L.np_sizes.size), "vertices": L.total}
 
 
+def run_fd(args):
+    """The grid workload's op mix (stencil apply x50, one 50-sweep GS call, one 50-sweep
+    Jacobi call, 1 residual per grid) with the 5/7-point finite-difference operator;
+    GS is red-black.  Per-op CUDA events; fractions of the measured HBM bandwidth with
+    16 B (apply, residual) and 24 B (sweeps) per update for a single pass."""
+    import torch
+    import paper_1810_04033_gb300 as st
+    dev = torch.device("cuda", 0)
+    n3, n2 = args.n3, args.n2
+    wl = GpuWorkload(torch, st, dev, n3, n2, op=st.OP_FD)
+    ops = ["apply_stencil", "gs_sweep", "jacobi_sweep", "residual"]
+    stream = torch.cuda.Stream(device=dev)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, args.warmup)):
+            wl.step(stream, ops=ops)
+    stream.synchronize()
+    steps = max(1, min(args.steps, 5))
+    ev = [{(op, g): (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for op in ops for g in wl.grids} for _ in range(steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        t0.record(stream)
+        for k in range(steps):
+            wl.step(stream, ev[k], ops=ops)
+        t1.record(stream)
+    stream.synchronize()
+    ms = t0.elapsed_time(t1)
+    upd = sum(PASSES[op] * (interior(3, n3) + interior(2, n2)) for op in ops) * steps
+    per = {}
+    for g in wl.grids:
+        nn = wl.n[g]
+        for op in ops:
+            t = sum(e[(op, g)][0].elapsed_time(e[(op, g)][1]) for e in ev) / steps / PASSES[op]
+            b = BYTES_PER_UPDATE[op] * interior(int(g), nn)
+            per["%s_%sd" % (op, g)] = {"ms_per_pass": round(t, 4), "frac": round(b / (t * 1e-3) / 1e9 / peak, 3)}
+    return {"metric": "Mupdates/s (5/7-point FD op mix: 50 stencil applies, 50 red-black GS sweeps, "
+                      "50 Jacobi sweeps, 1 residual per grid)", "workload": "fd",
+            "value": round(upd / (ms * 1e-3) / 1e6, 1), "unit": "Mupdates/s", "steps": steps,
+            "ms_per_step": round(ms / steps, 3), "grid_3d": n3, "grid_2d": n2, "dtype": "f64",
+            "per_op": per}
+
+
 def run_refine(args):
     """256^3, f from u* = sin(2 pi x) sin(3 pi y) sin(pi z): refinement to a relative
     residual of 1e-10 with 8 inner GS sweeps in FP32 and in bf16 storage, against plain
@@ -612,7 +661,8 @@ def main():
     if args.workload != "grid" and args.impl == "gpu":
         import torch
         torch.cuda.set_device(0)
-        fn = {"small": run_small, "patches": run_patches, "refine": run_refine, "serve": run_serve}[args.workload]
+        fn = {"small": run_small, "patches": run_patches, "refine": run_refine, "serve": run_serve,
+              "fd": run_fd}[args.workload]
         if rank == 0:
             print(json.dumps(fn(args)))
         return

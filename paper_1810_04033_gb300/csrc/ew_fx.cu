@@ -169,14 +169,14 @@ __device__ void write_plane(const EwArgs &a, int64_t z, int x0, int y0, int R, c
   }
 }
 
-__global__ void __launch_bounds__(E_THREADS, 2) k_apply_elementwise_fx3(EwArgs a) {
+__global__ void __launch_bounds__(E_THREADS, 3) k_apply_elementwise_fx3(EwArgs a) {
   extern __shared__ long long smem[];
   __shared__ int red[E_THREADS / 32];
   const Geo &q = a.q;
   const int x0 = (int)blockIdx.x * ET_X, y0 = (int)blockIdx.y * ET_Y;
   const int64_t zs = (int64_t)blockIdx.z * a.cz;
   const int64_t ze = zs + a.cz < q.nz + 1 ? zs + a.cz : q.nz + 1;
-  long long *slot[4] = {smem, smem + E_PLANE, smem + 2 * E_PLANE, smem + 3 * E_PLANE};
+  auto slot = [&](int i) -> long long * { return smem + i * E_PLANE; };
   int ulo = 0, uhi = 1, alo = 2, ahi = 3;
   bool fix = true;
   int R = R_MIN;
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(E_THREADS, 2) k_apply_elementwise_fx3(EwArgs a
 #pragma unroll
     for (int k = 0; k < E_PER; ++k) {
       const int idx = threadIdx.x + k * E_THREADS;
-      if (idx < E_PLANE) slot[dst][idx] = fix ? fx::to_fixed(v[k], 1023 + R) : __double_as_longlong(v[k]);
+      if (idx < E_PLANE) slot(dst)[idx] = fix ? fx::to_fixed(v[k], 1023 + R) : __double_as_longlong(v[k]);
     }
   };
 
@@ -221,18 +221,18 @@ __global__ void __launch_bounds__(E_THREADS, 2) k_apply_elementwise_fx3(EwArgs a
     __syncthreads();
     if (k + 2 <= ze) prefetch_vplane(v, q, a.u, k + 2, x0, y0);
     if (fix)
-      scatter_layer<true>(q, k, x0, y0, slot[ulo], slot[uhi], slot[alo], slot[ahi]);
+      scatter_layer<true>(q, k, x0, y0, slot(ulo), slot(uhi), slot(alo), slot(ahi));
     else
-      scatter_layer<false>(q, k, x0, y0, slot[ulo], slot[uhi], slot[alo], slot[ahi]);
+      scatter_layer<false>(q, k, x0, y0, slot(ulo), slot(uhi), slot(alo), slot(ahi));
     // vertex plane k now holds all contributions
     if (k >= zs) {
       if (fix)
-        write_plane<true>(a, k, x0, y0, R, slot[alo]);
+        write_plane<true>(a, k, x0, y0, R, slot(alo));
       else
-        write_plane<false>(a, k, x0, y0, R, slot[alo]);
+        write_plane<false>(a, k, x0, y0, R, slot(alo));
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < E_PLANE; idx += E_THREADS) slot[alo][idx] = 0;
+    for (int idx = threadIdx.x; idx < E_PLANE; idx += E_THREADS) slot(alo)[idx] = 0;
     int t = ulo;
     ulo = uhi;
     uhi = t;
@@ -254,7 +254,7 @@ cudaError_t launch_apply_elementwise_fx3(const Geo &q, const double *u, double *
     attr_set = true;
   }
   const int64_t txy = ((q.nx + ET_X) / ET_X) * ((q.ny + ET_Y) / ET_Y);
-  const int cz = z_chunk(txy, q.nz + 1, E_CZ, 4, 2);
+  const int cz = z_chunk(txy, q.nz + 1, E_CZ, 4, 3);
   const dim3 g((unsigned)((q.nx + ET_X) / ET_X), (unsigned)((q.ny + ET_Y) / ET_Y), (unsigned)((q.nz + cz) / cz));
   if (g.y > 65535 || g.z > 65535) return cudaErrorInvalidConfiguration;
   EwArgs a;

@@ -225,7 +225,7 @@ __device__ void run_half(Ctx &c, int pz, int i0, int i1, const void *X, const vo
                          const void *F, long long *smem, long long &vmax) {
   const Geo &q = c.q;
   const int64_t P = q.plane;
-  long long *slot[3] = {smem, smem + GS_PLANE, smem + 2 * GS_PLANE};
+  auto slot = [&](int i) -> long long * { return smem + i * GS_PLANE; };
   int lo = 0, ce = 1, up = 2;
   long long pc[GS_NCE], pu[GS_NUP], fv[8];
   const char *Xc = (const char *)X, *Nc = (const char *)N, *Fc = (const char *)F;
@@ -234,7 +234,7 @@ __device__ void run_half(Ctx &c, int pz, int i0, int i1, const void *X, const vo
     const int64_t z = pz + 2 * (int64_t)i0;
     long long dummy[GS_NCE];
     prefetch<INNER>(c, nullptr, z >= 1 ? Nc + (z - 1) * P * 8 : nullptr, dummy, pu);
-    commit<FIXA, XF, NF>(c, dummy, pu, slot[ce], slot[lo], c.dn);
+    commit<FIXA, XF, NF>(c, dummy, pu, slot(ce), slot(lo), c.dn);
     const bool zin = z >= 1 && z <= q.nz - 1;
     prefetch<INNER>(c, zin ? Xc + z * P * 8 : nullptr, z + 1 <= q.nz ? Nc + (z + 1) * P * 8 : nullptr, pc, pu);
     prefetch_f<INNER>(c, zin ? Fc + z * P * 8 : nullptr, fv);
@@ -242,7 +242,7 @@ __device__ void run_half(Ctx &c, int pz, int i0, int i1, const void *X, const vo
   for (int i = i0; i < i1; ++i) {
     const int64_t z = pz + 2 * (int64_t)i;
     const bool zin = z >= 1 && z <= q.nz - 1;
-    commit<FIXA, XF, NF>(c, pc, pu, slot[ce], slot[up], c.dn);
+    commit<FIXA, XF, NF>(c, pc, pu, slot(ce), slot(up), c.dn);
     long long fcur[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) fcur[k] = fv[k];
@@ -256,9 +256,9 @@ __device__ void run_half(Ctx &c, int pz, int i0, int i1, const void *X, const vo
     const void *xp = Xc + z * P * 8;
     void *yp = Yc + z * P * 8;
     if (zin) {
-      phase<FIXA, XF, YF, INNER, 1>(c, slot[ce], slot[lo], slot[up], xp, yp, fcur, vmax);
+      phase<FIXA, XF, YF, INNER, 1>(c, slot(ce), slot(lo), slot(up), xp, yp, fcur, vmax);
       __syncthreads();
-      phase<FIXA, XF, YF, INNER, 2>(c, slot[ce], slot[lo], slot[up], xp, yp, fcur, vmax);
+      phase<FIXA, XF, YF, INNER, 2>(c, slot(ce), slot(lo), slot(up), xp, yp, fcur, vmax);
     } else if (c.write_bnd) {
       // Dirichlet plane: carry the tile through
       for (int idx = threadIdx.x; idx < GS_TX * GS_TY; idx += GS_THREADS) {

@@ -109,7 +109,7 @@ template <typename S>
 __global__ void __launch_bounds__(LP_THREADS) k_gs_lp_half(Geo q, int pz, const S *X, const S *N, S *Y, const S *f,
                                                            float g, int cz) {
   extern __shared__ float lps[];
-  float *slot[3] = {lps, lps + LP_PLANE, lps + 2 * LP_PLANE};
+  auto slot = [&](int i) -> float * { return lps + i * LP_PLANE; };
   const int x0 = (int)blockIdx.x * LP_TX, y0 = (int)blockIdx.y * LP_TY;
   const int64_t ncentre = (q.nz - pz) / 2 + 1;
   const int64_t i0 = (int64_t)blockIdx.z * cz;
@@ -120,18 +120,18 @@ __global__ void __launch_bounds__(LP_THREADS) k_gs_lp_half(Geo q, int pz, const 
     const int64_t z = pz + 2 * i;
     const bool zin = z >= 1 && z < q.nz;
     if (zin) {
-      if (!have_lower) stage<S>(slot[lo], N + (z - 1) * q.plane, q, x0, y0, false);
-      stage<S>(slot[ce], X + z * q.plane, q, x0, y0, true);
-      stage<S>(slot[up], N + (z + 1) * q.plane, q, x0, y0, false);
+      if (!have_lower) stage<S>(slot(lo), N + (z - 1) * q.plane, q, x0, y0, false);
+      stage<S>(slot(ce), X + z * q.plane, q, x0, y0, true);
+      stage<S>(slot(up), N + (z + 1) * q.plane, q, x0, y0, false);
     } else if (z + 1 <= q.nz) {
-      stage<S>(slot[up], N + (z + 1) * q.plane, q, x0, y0, false);
+      stage<S>(slot(up), N + (z + 1) * q.plane, q, x0, y0, false);
     }
     __syncthreads();
     if (zin) {
-      lp_phase<S, 1>(q, x0, y0, slot[ce], slot[lo], slot[up], X + z * q.plane, f + z * q.plane,
+      lp_phase<S, 1>(q, x0, y0, slot(ce), slot(lo), slot(up), X + z * q.plane, f + z * q.plane,
                      Y + z * q.plane, g);
       __syncthreads();
-      lp_phase<S, 2>(q, x0, y0, slot[ce], slot[lo], slot[up], X + z * q.plane, f + z * q.plane,
+      lp_phase<S, 2>(q, x0, y0, slot(ce), slot(lo), slot(up), X + z * q.plane, f + z * q.plane,
                      Y + z * q.plane, g);
     } else {
       for (int idx = threadIdx.x; idx < LP_TX * LP_TY; idx += LP_THREADS) {

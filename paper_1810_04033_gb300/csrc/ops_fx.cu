@@ -176,8 +176,13 @@ __device__ __forceinline__ void compute_plane(const OpArgs &a, int64_t z, int x0
   }
 }
 
+// CTAs per SM the register allocation targets: 3 (at most 85 registers) for the apply
+// and the residual; the Jacobi sweep keeps more values live and runs faster at 2.
 template <int OP>
-__global__ void __launch_bounds__(O_THREADS, 2) k_ops3(OpArgs a) {
+constexpr int ops3_min_blocks() { return OP == OP_JACOBI ? 2 : 3; }
+
+template <int OP>
+__global__ void __launch_bounds__(O_THREADS, ops3_min_blocks<OP>()) k_ops3(OpArgs a) {
   extern __shared__ long long smem[];
   __shared__ int red[O_THREADS / 32];
   __shared__ double sh2[2 * O_THREADS / 32];
@@ -186,7 +191,7 @@ __global__ void __launch_bounds__(O_THREADS, 2) k_ops3(OpArgs a) {
   const int64_t x0 = (int64_t)blockIdx.x * OT_X, y0 = (int64_t)blockIdx.y * OT_Y;
   const int64_t zs = (int64_t)blockIdx.z * a.cz;
   const int64_t ze = zs + a.cz < q.nz + 1 ? zs + a.cz : q.nz + 1;
-  long long *slot[3] = {smem, smem + OS_H * OS_W, smem + 2 * OS_H * OS_W};
+  auto slot = [&](int i) -> long long * { return smem + i * (OS_H * OS_W); };
   // interior tile: every staged vertex in the grid, every output an interior vertex
   const bool inner_tile = x0 >= 1 && x0 + OT_X <= q.nx && y0 >= 1 && y0 + OT_Y <= q.ny;
   int lo = 0, ce = 1, up = 2;
@@ -207,16 +212,16 @@ __global__ void __launch_bounds__(O_THREADS, 2) k_ops3(OpArgs a) {
         // FP64.  Rp < R_MIN with R == R_MIN means nothing larger has been seen.
         if (em == 2047 || Rp > R_MAX || R == R_MIN) {
           for (int idx = threadIdx.x; idx < OS_H * OS_W; idx += O_THREADS) {
-            slot[live0][idx] = __double_as_longlong(fx::to_double(slot[live0][idx], R - fx::FRAC));
-            slot[live1][idx] = __double_as_longlong(fx::to_double(slot[live1][idx], R - fx::FRAC));
+            slot(live0)[idx] = __double_as_longlong(fx::to_double(slot(live0)[idx], R - fx::FRAC));
+            slot(live1)[idx] = __double_as_longlong(fx::to_double(slot(live1)[idx], R - fx::FRAC));
           }
           fix = false;
         }
       } else if (Rn > R) {
         const int d = Rn - R;
         for (int idx = threadIdx.x; idx < OS_H * OS_W; idx += O_THREADS) {
-          slot[live0][idx] = d < 63 ? (slot[live0][idx] >> d) : (slot[live0][idx] >> 63);
-          slot[live1][idx] = d < 63 ? (slot[live1][idx] >> d) : (slot[live1][idx] >> 63);
+          slot(live0)[idx] = d < 63 ? (slot(live0)[idx] >> d) : (slot(live0)[idx] >> 63);
+          slot(live1)[idx] = d < 63 ? (slot(live1)[idx] >> d) : (slot(live1)[idx] >> 63);
         }
         R = Rn;
       }
@@ -226,7 +231,7 @@ __global__ void __launch_bounds__(O_THREADS, 2) k_ops3(OpArgs a) {
     for (int k = 0; k < O_PER; ++k) {
       const int idx = threadIdx.x + k * O_THREADS;
       if (idx < OS_H * OS_W)
-        slot[dst][idx] = fix ? fx::to_fixed(v[k], 1023 + R) : __double_as_longlong(v[k]);
+        slot(dst)[idx] = fix ? fx::to_fixed(v[k], 1023 + R) : __double_as_longlong(v[k]);
     }
   };
 
@@ -244,11 +249,11 @@ __global__ void __launch_bounds__(O_THREADS, 2) k_ops3(OpArgs a) {
     if (z + 2 <= ze) prefetch_plane(v, q, a.u, z + 2, x0, y0);
     if (fix) {
       if (inner_tile)
-        compute_plane<true, OP, true>(a, z, (int)x0, (int)y0, R, slot[lo], slot[ce], slot[up], rr, ff);
+        compute_plane<true, OP, true>(a, z, (int)x0, (int)y0, R, slot(lo), slot(ce), slot(up), rr, ff);
       else
-        compute_plane<true, OP, false>(a, z, (int)x0, (int)y0, R, slot[lo], slot[ce], slot[up], rr, ff);
+        compute_plane<true, OP, false>(a, z, (int)x0, (int)y0, R, slot(lo), slot(ce), slot(up), rr, ff);
     } else {
-      compute_plane<false, OP, false>(a, z, (int)x0, (int)y0, R, slot[lo], slot[ce], slot[up], rr, ff);
+      compute_plane<false, OP, false>(a, z, (int)x0, (int)y0, R, slot(lo), slot(ce), slot(up), rr, ff);
     }
     __syncthreads();
     const int t = lo;
@@ -317,7 +322,7 @@ __global__ void __launch_bounds__(O_THREADS, 2) k_ops3(OpArgs a) {
 
 int ops_cz(const Geo &q) {
   const int64_t txy = ((q.nx + OT_X) / OT_X) * ((q.ny + OT_Y) / OT_Y);
-  return z_chunk(txy, q.nz + 1, O_CZ, 4, 2);
+  return z_chunk(txy, q.nz + 1, O_CZ, 4, 3);
 }
 
 dim3 ops_grid(const Geo &q) {
