@@ -209,6 +209,36 @@ typedef struct stencil_solve_info {
 int stencil_solve(const stencil_grid_t *g, double *u, const double *f, const stencil_solve_opts_t *opts,
                   stencil_solve_info_t *info, void *stream);
 
+/* ------------------------------------------------------------ dependency-driven sweeps */
+/* The GPU form of the paper's Hyb-depend variant (Section 5, Algorithm 1): red-black
+ * sweeps of the finite-difference operator (op = STENCIL_OP_FD) as tasks with data
+ * dependencies instead of grid-wide barriers.  The grid is cut into blocks of `rows`
+ * x-rows (2D) or z-planes (3D); task (phase p = 2 sweep + colour, block b) updates one
+ * colour of block b in place once blocks b-1, b, b+1 have finished phase p-1.  Tasks
+ * are claimed by one persistent cooperative launch in phase-major order (the colouring
+ * as issue order).  The result equals stencil_smooth_coloured with op FD (the same
+ * updates in the same per-vertex order). */
+typedef struct stencil_depend_opts {
+  int32_t rows;        /* rows (2D) or planes (3D) per task; 0: 8 (2D), 2 (3D) */
+  int32_t ctas;        /* CTAs of the persistent launch; 0: every CTA that can be resident */
+  int64_t max_wait_ns; /* limit of one dependency wait in ns; 0: 1e9 (1 s) */
+  int32_t test_stall;  /* testing only: if > 0, block test_stall - 1 never reports its
+                          progress, so that a wait runs out; 0: off */
+  int32_t stalled_at;  /* out: the block a timed-out wait was waiting for */
+} stencil_depend_opts_t;
+
+/*
+ * `sweeps` red-black Gauss-Seidel sweeps on A u = f, dependency-driven.  u, f: device F64
+ * arrays of g's layout (g->op must be STENCIL_OP_FD).  Host-synchronous (reads the
+ * launch's error flag).  Uses a small library workspace (per stream, kept).
+ * Returns STENCIL_OK; STENCIL_ETIMEDOUT if a dependency wait exceeded max_wait_ns (u is
+ * then partly updated; opts->stalled_at names the block waited for; the CUDA context
+ * stays usable); STENCIL_EINVAL, STENCIL_ENOMEM, STENCIL_ECUDA (also if the device has
+ * no cooperative launch).
+ */
+int stencil_smooth_depend(const stencil_grid_t *g, double *u, const double *f, int sweeps,
+                          stencil_depend_opts_t *opts, void *stream);
+
 /* ------------------------------------------------------------ geometric multigrid */
 /* The paper's sweeps are the smoothers of matrix-free multigrid codes (Section 1).
  * Hierarchy: the coarse grid has n/2 cells per axis when every n[a] is even (every

@@ -25,6 +25,7 @@ _DTYPES = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
 
 
 SOLVER_REFINE, SOLVER_MG = 0, 1
+OK, EINVAL, ENOMEM, EADMIT, ETIMEDOUT, ECUDA, ENOTCONV, ENOTFOUND, EBUSY = 0, -1, -2, -3, -4, -5, -6, -7, -8
 
 
 class StencilError(RuntimeError):
@@ -80,6 +81,11 @@ class SolveInfo(ctypes.Structure):
                 ("relres", ctypes.c_double), ("relres_history", ctypes.POINTER(ctypes.c_double))]
 
 
+class DependOpts(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int32), ("ctas", ctypes.c_int32), ("max_wait_ns", ctypes.c_int64),
+                ("test_stall", ctypes.c_int32), ("stalled_at", ctypes.c_int32)]
+
+
 class MgOpts(ctypes.Structure):
     _fields_ = [("rel_tol", ctypes.c_double), ("max_cycles", ctypes.c_int32), ("pre", ctypes.c_int32),
                 ("post", ctypes.c_int32), ("coarse_sweeps", ctypes.c_int32), ("max_levels", ctypes.c_int32),
@@ -118,6 +124,7 @@ def lib():
             "stencil_jacobi_step": (ci, [gp, vp, vp, vp, cd, vp]),
             "stencil_residual_noalloc": (ci, [gp, vp, vp, vp, vp, vp]),
             "stencil_solve": (ci, [gp, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]),
+            "stencil_smooth_depend": (ci, [gp, vp, vp, ci, ctypes.POINTER(DependOpts), vp]),
             "stencil_mg_solve": (ci, [gp, vp, vp, ctypes.POINTER(MgOpts), ctypes.POINTER(MgInfo), vp]),
             "stencil_mg_vcycle": (ci, [gp, vp, vp, ctypes.POINTER(MgOpts), vp]),
             "stencil_mg_restrict": (ci, [gp, vp, gp, vp, vp]),
@@ -287,6 +294,19 @@ def stencil_solve(u, f, h, rel_tol=1e-10, max_outer=100000, inner_sweeps=8, inne
     if history:
         out["history"] = list(hist[:info.iterations + 1])
     return out
+
+
+def stencil_smooth_depend(u, f, h, sweeps, rows=0, ctas=0, max_wait_ns=0, test_stall=0, stream=None):
+    """Dependency-driven red-black sweeps (op FD) in place on u.  Returns
+    {"status": 0 or the timeout code, "stalled_at": block}; raises on other errors."""
+    _same_layout(u, f)
+    g = grid_for(u, h, OP_FD)
+    o = DependOpts(int(rows), int(ctas), int(max_wait_ns), int(test_stall), -1)
+    rc = lib().stencil_smooth_depend(ctypes.byref(g), _ptr(u), _ptr(f), int(sweeps), ctypes.byref(o),
+                                     _stream(stream))
+    if rc not in (0, ETIMEDOUT):
+        _check(rc)
+    return {"status": rc, "stalled_at": o.stalled_at}
 
 
 def _mg_opts(rel_tol, max_cycles, pre, post, coarse_sweeps, max_levels):

@@ -432,6 +432,40 @@ int stencil_solve(const stencil_grid_t *g, double *u, const double *f, const ste
   return STENCIL_OK;
 }
 
+// ------------------------------------------------------------ dependency-driven sweeps
+
+int stencil_smooth_depend(const stencil_grid_t *g, double *u, const double *f, int sweeps,
+                          stencil_depend_opts_t *opts, void *stream) {
+  int rc = check_grid(g);
+  if (rc) return rc;
+  if (g->op != STENCIL_OP_FD) return set_error(STENCIL_EINVAL, "smooth_depend: needs op = STENCIL_OP_FD");
+  if ((rc = check_ptr(u, g, "u")) || (rc = check_ptr(f, g, "f"))) return rc;
+  if (!opts) return set_error(STENCIL_EINVAL, "smooth_depend: opts is NULL");
+  if (sweeps < 0 || opts->rows < 0 || opts->ctas < 0 || opts->max_wait_ns < 0 || opts->test_stall < 0)
+    return set_error(STENCIL_EINVAL, "smooth_depend: negative argument");
+  const Geo q = make_geo(*g);
+  if (overlap(u, f, (size_t)span_elems(q) * 8)) return set_error(STENCIL_EINVAL, "u and f overlap");
+  opts->stalled_at = -1;
+  if (sweeps == 0) return STENCIL_OK;
+  const int rows = opts->rows > 0 ? opts->rows : (g->dim == 2 ? 8 : 2);
+  const int nb = depend_blocks(q, g->dim, rows);
+  cudaStream_t s = (cudaStream_t)stream;
+  void *state = device_scratch(SCRATCH_DEPEND, depend_state_bytes(nb), s);
+  int *hs = (int *)host_scratch(64, s);
+  if (!state || !hs) return set_error(STENCIL_ENOMEM, "smooth_depend: workspace allocation failed");
+  const long long wait = opts->max_wait_ns > 0 ? opts->max_wait_ns : 1000000000ll;
+  cudaError_t e = launch_depend_redblack(q, g->dim, u, f, sweeps, rows, opts->ctas, wait, opts->test_stall - 1,
+                                         state, hs, hs + 1, s);
+  if (!e) e = cudaStreamSynchronize(s);
+  if (e) return set_error(STENCIL_ECUDA, std::string("smooth_depend: ") + cudaGetErrorString(e));
+  if (hs[0]) {
+    opts->stalled_at = hs[1];
+    return set_error(STENCIL_ETIMEDOUT, "smooth_depend: a dependency wait exceeded max_wait_ns (block " +
+                                            std::to_string(hs[1]) + ")");
+  }
+  return STENCIL_OK;
+}
+
 // ------------------------------------------------------------ multigrid
 
 static int check_mg_opts(const stencil_mg_opts_t *o) {

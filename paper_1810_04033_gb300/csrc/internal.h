@@ -63,7 +63,8 @@ enum ScratchSlot {
   SCRATCH_SOLVE_E = 5, // refinement: correction
   SCRATCH_NORMS = 6,   // refinement: device norms
   SCRATCH_MG = 7,      // multigrid: coarse-level arrays
-  SCRATCH_SLOTS = 8
+  SCRATCH_DEPEND = 8,  // dependency-driven sweeps: task counter, flags, per-block progress
+  SCRATCH_SLOTS = 10
 };
 // Pinned host scratch of the (device, stream) set.
 void *host_scratch(size_t bytes, cudaStream_t stream);
@@ -140,6 +141,13 @@ cudaError_t launch_fd_jacobi(const Geo &q, int dim, const double *u, const doubl
 cudaError_t launch_fd_residual(const Geo &q, int dim, const double *u, const double *f, double *r, double *norms2,
                                void *scratch, cudaStream_t s);
 cudaError_t launch_fd_gs_redblack(const Geo &q, int dim, double *u, const double *f, int sweeps, cudaStream_t s);
+
+// Dependency-driven red-black sweeps (depend.cu), op FD, F64.
+size_t depend_state_bytes(int nblocks);
+int depend_blocks(const Geo &q, int dim, int rows);
+cudaError_t launch_depend_redblack(const Geo &q, int dim, double *u, const double *f, int sweeps, int rows,
+                                   int ctas, long long max_wait_ns, int stall_block, void *state, int *status_host,
+                                   int *stalled_host, cudaStream_t s);
 
 // Geometric multigrid (mg.cu).  Coarse grids are dense (pitch n_c + 1): n/2 per axis
 // when all n are even, ceil(n/2) when all n are equal; none (false) below n = 4.
