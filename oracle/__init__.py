@@ -51,6 +51,8 @@ def lib():
             "oracle_fd_gs_redblack": (None, [ci, i64p, cd, dp, dp, ci]),
             "oracle_fd_jacobi": (None, [ci, i64p, cd, dp, dp, dp, cd, ci]),
             "oracle_fd_residual": (None, [ci, i64p, cd, dp, dp, dp, dp]),
+            "oracle_cost_diagonal": (cd, [ci, i64p, ci, ci, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]),
+            "oracle_fd_gs_redblack_cost": (None, [ci, i64p, cd, dp, dp, ci, ci, ci]),
             "oracle_f32_to_bf16": (ctypes.c_uint16, [ctypes.c_float]),
             "oracle_bf16_to_f32": (ctypes.c_float, [ctypes.c_uint16]),
         }
@@ -284,6 +286,20 @@ def fd_residual(u, f, h):
     lib().oracle_fd_residual(dim, _ptr(n, ctypes.c_int64), h, _ptr(u, ctypes.c_double), _ptr(f, ctypes.c_double),
                              _ptr(r, ctypes.c_double), _ptr(nrm, ctypes.c_double))
     return r, nrm
+
+
+def cost_diagonal(shape, mode, kmax, i, j, k=0):
+    dim, n = _grid(shape)
+    return lib().oracle_cost_diagonal(dim, _ptr(n, ctypes.c_int64), mode, kmax, i, j, k)
+
+
+def fd_gs_redblack_cost(u0, f, h, sweeps, mode, kmax):
+    u = _f64(u0).copy()
+    f = _f64(f)
+    dim, n = _grid(u.shape)
+    lib().oracle_fd_gs_redblack_cost(dim, _ptr(n, ctypes.c_int64), h, _ptr(u, ctypes.c_double),
+                                     _ptr(f, ctypes.c_double), sweeps, mode, kmax)
+    return u
 
 
 def patch_halo_fill(lat, np_sizes, offsets, u_all):

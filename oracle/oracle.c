@@ -37,6 +37,11 @@
  *                             file); dense Kronecker assembly; exactness on cubic
  *                             polynomials; sine-mode symbol and closed-form solution;
  *                             red-black GS = dense GS in Algorithm 1's colour order.
+ *   oracle_*cost*             pinned: mode 0 equals the plain red-black sweep; the
+ *                             linear k pattern (0 on the first 1/kmax of the interior);
+ *                             the sweep equals a dense GS on the matrix with the
+ *                             perturbed diagonal; sigma_k against the closed form
+ *                             sin(k t/2) sin((k+1) t/2) / sin(t/2).
  *   oracle_patch_*            parity unpinned beyond: a single patch with zero
  *                             neighbours equals a plain Dirichlet GS; equal-size
  *                             neighbours copy the first interior layer (the halo rule
@@ -772,4 +777,58 @@ void oracle_fd_residual(int dim, const int64_t *n, double h, const double *u,
   norms2[0] = rr;
   norms2[1] = ff;
   if (!r) free(res);
+}
+
+/* ------------------------------------------- expensive stencil evaluations S(k) */
+
+/* Section 2 parameterises every stencil evaluation S(k) by a cost k, and Section 4
+ * realises k > 0 by adding k evaluations of sin to the prescribed entry: k = 100 on
+ * every vertex (homogeneous) or k running linearly from 0 to 99 over the mesh
+ * (heterogeneous: the first hundredth of the vertices uses the plain stencil, the next
+ * adds one sin evaluation, ...).  Our reading, for the red-black finite-difference sweep:
+ * the diagonal entry of vertex p becomes 2d + eps * sigma_k(p) / k with
+ *   sigma_k(p) = sum_{m=1..k} sin(m * theta_p),  theta_p = idx_p * 2^-20,  eps = 2^-20,
+ * idx_p the lexicographic index of p among the interior vertices (x fastest), and
+ * k(p) = kmax (uniform) or floor(kmax * idx_p / N) (linear; N interior vertices).  The
+ * perturbation is below 2^-20 relative: the operator stays the FD Laplacian to six
+ * digits while every update pays for its k sin evaluations. */
+
+static int64_t interior_index(int dim, const int64_t *n, int64_t i, int64_t j, int64_t k) {
+  const int64_t rowlen = n[0] - 1, plane = (n[0] - 1) * (n[1] - 1);
+  return (dim == 3 ? (k - 1) * plane : 0) + (j - 1) * rowlen + (i - 1);
+}
+
+double oracle_cost_diagonal(int dim, const int64_t *n, int mode, int kmax, int64_t i,
+                            int64_t j, int64_t k) {
+  const int64_t idx = interior_index(dim, n, i, j, k);
+  const int64_t N = (n[0] - 1) * (n[1] - 1) * (dim == 3 ? n[2] - 1 : 1);
+  int64_t kk = 0;
+  if (mode == 1) kk = kmax;
+  if (mode == 2) kk = (int64_t)kmax * idx / N;
+  double diag = 2.0 * dim;
+  if (kk > 0) {
+    const double theta = (double)idx * 0x1p-20;
+    double sigma = 0.0;
+    for (int64_t m = 1; m <= kk; ++m) sigma += sin((double)m * theta);
+    diag += 0x1p-20 * (sigma / (double)kk);
+  }
+  return diag;
+}
+
+void oracle_fd_gs_redblack_cost(int dim, const int64_t *n, double h, double *u,
+                                const double *f, int sweeps, int mode, int kmax) {
+  const int64_t nzc = nz_cells(dim, n);
+  const double h2 = h * h;
+  for (int s = 0; s < sweeps; ++s)
+    for (int pass = 0; pass < 2; ++pass) {
+      const int64_t parity = pass == 0 ? 1 : 0;
+      for (int64_t k = 0; k <= nzc; ++k)
+        for (int64_t j = 0; j <= n[1]; ++j)
+          for (int64_t i = 0; i <= n[0]; ++i) {
+            if (!is_interior(dim, n, i, j, k) || ((i + j + k) & 1) != parity) continue;
+            const int64_t p = vidx(n, i, j, k);
+            const double d = oracle_cost_diagonal(dim, n, mode, kmax, i, j, k);
+            u[p] = (h2 * f[p] + fd_neighbour_sum(dim, n, u, i, j, k)) / d;
+          }
+    }
 }

@@ -139,6 +139,16 @@ void oracle_fd_jacobi(int dim, const int64_t *n, double h, double *u, const doub
 void oracle_fd_residual(int dim, const int64_t *n, double h, const double *u,
                         const double *f, double *r, double *norms2);
 
+/* Expensive stencil evaluations S(k) (Section 2; Section 4: k sin evaluations added to
+ * the prescribed entry, k = kmax everywhere or running linearly over the mesh), for the
+ * red-black FD sweep.  mode: 0 none, 1 uniform k = kmax, 2 linear k = floor(kmax idx/N).
+ * oracle_cost_diagonal: the diagonal entry 2d + 2^-20 sigma_k / k of vertex (i,j,k)
+ * (definition in oracle.c).  oracle_fd_gs_redblack_cost: the sweep with it. */
+double oracle_cost_diagonal(int dim, const int64_t *n, int mode, int kmax, int64_t i,
+                            int64_t j, int64_t k);
+void oracle_fd_gs_redblack_cost(int dim, const int64_t *n, double h, double *u,
+                                const double *f, int sweeps, int mode, int kmax);
+
 /* Round-to-nearest-even conversion helpers exposed for tests. */
 uint16_t oracle_f32_to_bf16(float x);
 float oracle_bf16_to_f32(uint16_t b);

@@ -181,3 +181,71 @@ def test_residual_definition(dim, n):
     assert np.max(np.abs(r - rd)) <= 1e-12 * np.max(np.abs(yd))
     assert abs(nrm[0] - np.sum(rd[inner] ** 2)) <= 1e-10 * nrm[0]
     assert abs(nrm[1] - np.sum(f[inner] ** 2)) <= 1e-12 * nrm[1]
+
+
+# ------------------------------------------------------------ expensive stencils S(k)
+
+def test_cost_mode_none_is_the_plain_sweep():
+    dim, n = 2, (9, 7)
+    h = 1.0 / 9
+    u0 = synth.uniform_field(synth.grid_shape(dim, n), 51, zero_bc=False)
+    f = synth.uniform_field(u0.shape, 52)
+    assert np.array_equal(oracle.fd_gs_redblack_cost(u0, f, h, 2, 0, 100), oracle.fd_gs_redblack(u0, f, h, 2))
+
+
+@pytest.mark.parametrize("dim,n,i,j,k", [(2, (9, 7), 3, 4, 0), (3, (6, 5, 7), 2, 3, 4), (2, (300, 200), 250, 150, 0)])
+@pytest.mark.parametrize("kmax", [1, 7, 100])
+def test_cost_diagonal_closed_form(dim, n, i, j, k, kmax):
+    """sum_{m=1..k} sin(m t) = sin(k t / 2) sin((k + 1) t / 2) / sin(t / 2)."""
+    shape = synth.grid_shape(dim, n)
+    idx = (((k - 1) * (n[1] - 1) if dim == 3 else 0) + (j - 1)) * (n[0] - 1) + (i - 1)
+    t = idx * 2.0 ** -20
+    sigma = math.sin(kmax * t / 2) * math.sin((kmax + 1) * t / 2) / math.sin(t / 2)
+    want = 2 * dim + 2.0 ** -20 * sigma / kmax
+    got = oracle.cost_diagonal(shape, 1, kmax, i, j, k)
+    assert abs(got - want) <= 1e-15 * want
+
+
+def test_cost_linear_pattern():
+    """k runs linearly from 0 over the interior: the first 1/kmax of the vertices keep
+    the plain diagonal, the last ones use k = kmax - 1."""
+    dim, n, kmax = 2, (101, 41), 10
+    shape = synth.grid_shape(dim, n)
+    N = 100 * 40
+    for idx in (0, 1, N // kmax - 1):
+        j, i = 1 + idx // 100, 1 + idx % 100
+        assert oracle.cost_diagonal(shape, 2, kmax, i, j) == 4.0
+    idx = N - 1
+    j, i = 1 + idx // 100, 1 + idx % 100
+    t = idx * 2.0 ** -20
+    kk = kmax * idx // N
+    sigma = sum(math.sin(m * t) for m in range(1, kk + 1))
+    assert kk == kmax - 1
+    assert abs(oracle.cost_diagonal(shape, 2, kmax, i, j) - (4.0 + 2.0 ** -20 * sigma / kk)) <= 1e-15
+
+
+@pytest.mark.parametrize("dim,n,mode", [(2, (6, 5), 1), (2, (6, 6), 2), (3, (4, 3, 5), 1)])
+def test_cost_sweep_equals_dense_gs_with_perturbed_diagonal(dim, n, mode):
+    h = 1.0 / max(n)
+    shape = synth.grid_shape(dim, n)
+    u0 = synth.uniform_field(shape, 61 + sum(n), zero_bc=False)
+    f = synth.uniform_field(shape, 62 + sum(n))
+    kmax = 30
+    A = _dense_fd(dim, n, h)
+    inner = dr.interior_mask(shape)
+    idxs = np.argwhere(inner)
+    for ix in idxs:
+        kk, jj, ii = (ix if dim == 3 else (0, ix[0], ix[1]))
+        p = np.ravel_multi_index(tuple(ix), shape)
+        A[p, p] = oracle.cost_diagonal(shape, mode, kmax, ii, jj, kk) / (h * h)
+    par = np.indices(shape).sum(axis=0).ravel() % 2
+    u = u0.ravel().copy()
+    fr = f.ravel()
+    innr = inner.ravel()
+    for _ in range(2):
+        for parity in (1, 0):
+            for p in range(u.size):
+                if innr[p] and par[p] == parity:
+                    u[p] = (fr[p] - (A[p] @ u - A[p, p] * u[p])) / A[p, p]
+    got = oracle.fd_gs_redblack_cost(u0, f, h, 2, mode, kmax)
+    assert np.max(np.abs(got.ravel() - u)) <= 1e-12 * np.max(np.abs(u))
