@@ -212,19 +212,22 @@ int stencil_solve(const stencil_grid_t *g, double *u, const double *f, const ste
 /* ------------------------------------------------------------ dependency-driven sweeps */
 /* The GPU form of the paper's Hyb-depend variant (Section 5, Algorithm 1): red-black
  * sweeps of the finite-difference operator (op = STENCIL_OP_FD) as tasks with data
- * dependencies instead of grid-wide barriers.  The grid is cut into blocks of `rows`
- * x-rows (2D) or z-planes (3D); task (phase p = 2 sweep + colour, block b) updates one
- * colour of block b in place once blocks b-1, b, b+1 have finished phase p-1.  Tasks
+ * dependencies instead of grid-wide barriers.  The grid is cut into blocks (2D: `rows`
+ * x-rows; 3D: `rows` z-planes by `cols` y-rows); task (phase p = 2 sweep + colour,
+ * block b) updates one colour of block b in place once b and its face-neighbour blocks
+ * have finished phase p-1.  Tasks
  * are claimed by one persistent cooperative launch in phase-major order (the colouring
  * as issue order).  The result equals stencil_smooth_coloured with op FD (the same
  * updates in the same per-vertex order). */
 typedef struct stencil_depend_opts {
-  int32_t rows;        /* rows (2D) or planes (3D) per task; 0: 8 (2D), 2 (3D) */
+  int32_t rows;        /* x-rows (2D) or z-planes (3D) per task; 0: 8 (2D), 1 (3D) */
+  int32_t cols;        /* 3D: y-rows per task (blocks are numbered z-major); 0: 32 */
   int32_t ctas;        /* CTAs of the persistent launch; 0: every CTA that can be resident */
-  int64_t max_wait_ns; /* limit of one dependency wait in ns; 0: 1e9 (1 s) */
   int32_t test_stall;  /* testing only: if > 0, block test_stall - 1 never reports its
                           progress, so that a wait runs out; 0: off */
+  int64_t max_wait_ns; /* limit of one dependency wait in ns; 0: 1e9 (1 s) */
   int32_t stalled_at;  /* out: the block a timed-out wait was waiting for */
+  int32_t reserved;
 } stencil_depend_opts_t;
 
 /*
@@ -238,6 +241,32 @@ typedef struct stencil_depend_opts {
  */
 int stencil_smooth_depend(const stencil_grid_t *g, double *u, const double *f, int sweeps,
                           stencil_depend_opts_t *opts, void *stream);
+
+/* ------------------------------------------------------------ expensive stencils S(k) */
+/* Section 2 gives every stencil evaluation S(k) a cost parameter k; Section 4 realises
+ * k > 0 by adding k evaluations of sin to the prescribed entry, the same k on every
+ * vertex (homogeneous) or k running linearly over the mesh (heterogeneous).  Here, for
+ * the red-black finite-difference sweep, the diagonal entry of interior vertex p becomes
+ *   2d + 2^-20 sigma_k(p) / k,  sigma_k(p) = sum_{m=1..k} sin(m idx_p 2^-20),
+ * with idx_p the lexicographic index of p among the interior vertices, and
+ * k(p) = kmax (STENCIL_COST_UNIFORM) or floor(kmax idx_p / N) over the N interior
+ * vertices (STENCIL_COST_LINEAR: the first 1/kmax of the vertices use the plain stencil,
+ * the next one sin evaluation, ...).  The operator changes by less than 2^-20 relative;
+ * each update pays for its k FP64 sin evaluations. */
+#define STENCIL_COST_NONE 0
+#define STENCIL_COST_UNIFORM 1
+#define STENCIL_COST_LINEAR 2
+
+/*
+ * `sweeps` red-black sweeps of S(k) on A u = f (g->op must be STENCIL_OP_FD; F64), in
+ * place on u.  depend == NULL: one launch per colour pass (colouring with barriers);
+ * otherwise the dependency-driven sweep of stencil_smooth_depend with those options
+ * (host-synchronous, may return STENCIL_ETIMEDOUT).  mode STENCIL_COST_NONE gives the
+ * plain sweep with the update written as (h^2 f + neighbours) / 2d.
+ * Returns STENCIL_OK, STENCIL_EINVAL, STENCIL_ENOMEM, STENCIL_ETIMEDOUT, STENCIL_ECUDA.
+ */
+int stencil_smooth_expensive(const stencil_grid_t *g, double *u, const double *f, int sweeps, int cost_mode,
+                             int kmax, stencil_depend_opts_t *depend, void *stream);
 
 /* ------------------------------------------------------------ geometric multigrid */
 /* The paper's sweeps are the smoothers of matrix-free multigrid codes (Section 1).

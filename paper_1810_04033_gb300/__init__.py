@@ -82,8 +82,9 @@ class SolveInfo(ctypes.Structure):
 
 
 class DependOpts(ctypes.Structure):
-    _fields_ = [("rows", ctypes.c_int32), ("ctas", ctypes.c_int32), ("max_wait_ns", ctypes.c_int64),
-                ("test_stall", ctypes.c_int32), ("stalled_at", ctypes.c_int32)]
+    _fields_ = [("rows", ctypes.c_int32), ("cols", ctypes.c_int32), ("ctas", ctypes.c_int32),
+                ("test_stall", ctypes.c_int32), ("max_wait_ns", ctypes.c_int64), ("stalled_at", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class MgOpts(ctypes.Structure):
@@ -125,6 +126,7 @@ def lib():
             "stencil_residual_noalloc": (ci, [gp, vp, vp, vp, vp, vp]),
             "stencil_solve": (ci, [gp, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]),
             "stencil_smooth_depend": (ci, [gp, vp, vp, ci, ctypes.POINTER(DependOpts), vp]),
+            "stencil_smooth_expensive": (ci, [gp, vp, vp, ci, ci, ci, ctypes.POINTER(DependOpts), vp]),
             "stencil_mg_solve": (ci, [gp, vp, vp, ctypes.POINTER(MgOpts), ctypes.POINTER(MgInfo), vp]),
             "stencil_mg_vcycle": (ci, [gp, vp, vp, ctypes.POINTER(MgOpts), vp]),
             "stencil_mg_restrict": (ci, [gp, vp, gp, vp, vp]),
@@ -296,17 +298,37 @@ def stencil_solve(u, f, h, rel_tol=1e-10, max_outer=100000, inner_sweeps=8, inne
     return out
 
 
-def stencil_smooth_depend(u, f, h, sweeps, rows=0, ctas=0, max_wait_ns=0, test_stall=0, stream=None):
+def stencil_smooth_depend(u, f, h, sweeps, rows=0, ctas=0, max_wait_ns=0, test_stall=0, stream=None, cols=0):
     """Dependency-driven red-black sweeps (op FD) in place on u.  Returns
     {"status": 0 or the timeout code, "stalled_at": block}; raises on other errors."""
     _same_layout(u, f)
     g = grid_for(u, h, OP_FD)
-    o = DependOpts(int(rows), int(ctas), int(max_wait_ns), int(test_stall), -1)
+    o = DependOpts(int(rows), int(cols), int(ctas), int(test_stall), int(max_wait_ns), -1, 0)
     rc = lib().stencil_smooth_depend(ctypes.byref(g), _ptr(u), _ptr(f), int(sweeps), ctypes.byref(o),
                                      _stream(stream))
     if rc not in (0, ETIMEDOUT):
         _check(rc)
     return {"status": rc, "stalled_at": o.stalled_at}
+
+
+COST_NONE, COST_UNIFORM, COST_LINEAR = 0, 1, 2
+
+
+def stencil_smooth_expensive(u, f, h, sweeps, cost_mode, kmax, depend=None, stream=None):
+    """Red-black sweeps of the expensive stencil S(k) (op FD) in place on u.  depend:
+    None (colour passes with barriers) or a dict of stencil_smooth_depend options.
+    Returns the status (0 or the timeout code)."""
+    _same_layout(u, f)
+    g = grid_for(u, h, OP_FD)
+    o = None
+    if depend is not None:
+        o = DependOpts(int(depend.get("rows", 0)), int(depend.get("cols", 0)), int(depend.get("ctas", 0)),
+                       int(depend.get("test_stall", 0)), int(depend.get("max_wait_ns", 0)), -1, 0)
+    rc = lib().stencil_smooth_expensive(ctypes.byref(g), _ptr(u), _ptr(f), int(sweeps), int(cost_mode), int(kmax),
+                                        ctypes.byref(o) if o is not None else None, _stream(stream))
+    if rc not in (0, ETIMEDOUT):
+        _check(rc)
+    return rc
 
 
 def _mg_opts(rel_tol, max_cycles, pre, post, coarse_sweeps, max_levels):

@@ -434,28 +434,25 @@ int stencil_solve(const stencil_grid_t *g, double *u, const double *f, const ste
 
 // ------------------------------------------------------------ dependency-driven sweeps
 
-int stencil_smooth_depend(const stencil_grid_t *g, double *u, const double *f, int sweeps,
-                          stencil_depend_opts_t *opts, void *stream) {
-  int rc = check_grid(g);
-  if (rc) return rc;
-  if (g->op != STENCIL_OP_FD) return set_error(STENCIL_EINVAL, "smooth_depend: needs op = STENCIL_OP_FD");
-  if ((rc = check_ptr(u, g, "u")) || (rc = check_ptr(f, g, "f"))) return rc;
+static int smooth_depend_impl(const stencil_grid_t *g, double *u, const double *f, int sweeps,
+                              stencil_depend_opts_t *opts, int cost_mode, int kmax, void *stream) {
   if (!opts) return set_error(STENCIL_EINVAL, "smooth_depend: opts is NULL");
-  if (sweeps < 0 || opts->rows < 0 || opts->ctas < 0 || opts->max_wait_ns < 0 || opts->test_stall < 0)
+  if (sweeps < 0 || opts->rows < 0 || opts->cols < 0 || opts->ctas < 0 || opts->max_wait_ns < 0 ||
+      opts->test_stall < 0)
     return set_error(STENCIL_EINVAL, "smooth_depend: negative argument");
   const Geo q = make_geo(*g);
-  if (overlap(u, f, (size_t)span_elems(q) * 8)) return set_error(STENCIL_EINVAL, "u and f overlap");
   opts->stalled_at = -1;
   if (sweeps == 0) return STENCIL_OK;
-  const int rows = opts->rows > 0 ? opts->rows : (g->dim == 2 ? 8 : 2);
-  const int nb = depend_blocks(q, g->dim, rows);
+  const int rows = opts->rows > 0 ? opts->rows : (g->dim == 2 ? 8 : 1);
+  const int cols = opts->cols > 0 ? opts->cols : 32;
+  const int nb = depend_blocks(q, g->dim, rows, cols);
   cudaStream_t s = (cudaStream_t)stream;
   void *state = device_scratch(SCRATCH_DEPEND, depend_state_bytes(nb), s);
   int *hs = (int *)host_scratch(64, s);
   if (!state || !hs) return set_error(STENCIL_ENOMEM, "smooth_depend: workspace allocation failed");
   const long long wait = opts->max_wait_ns > 0 ? opts->max_wait_ns : 1000000000ll;
-  cudaError_t e = launch_depend_redblack(q, g->dim, u, f, sweeps, rows, opts->ctas, wait, opts->test_stall - 1,
-                                         state, hs, hs + 1, s);
+  cudaError_t e = launch_depend_redblack(q, g->dim, u, f, sweeps, rows, cols, opts->ctas, wait, opts->test_stall - 1,
+                                         state, hs, hs + 1, s, cost_mode, kmax);
   if (!e) e = cudaStreamSynchronize(s);
   if (e) return set_error(STENCIL_ECUDA, std::string("smooth_depend: ") + cudaGetErrorString(e));
   if (hs[0]) {
@@ -463,6 +460,37 @@ int stencil_smooth_depend(const stencil_grid_t *g, double *u, const double *f, i
     return set_error(STENCIL_ETIMEDOUT, "smooth_depend: a dependency wait exceeded max_wait_ns (block " +
                                             std::to_string(hs[1]) + ")");
   }
+  return STENCIL_OK;
+}
+
+static int check_fd_uf(const stencil_grid_t *g, const double *u, const double *f, const char *what) {
+  int rc = check_grid(g);
+  if (rc) return rc;
+  if (g->op != STENCIL_OP_FD) return set_error(STENCIL_EINVAL, std::string(what) + ": needs op = STENCIL_OP_FD");
+  if ((rc = check_ptr(u, g, "u")) || (rc = check_ptr(f, g, "f"))) return rc;
+  if (overlap(u, f, (size_t)span_elems(make_geo(*g)) * 8)) return set_error(STENCIL_EINVAL, "u and f overlap");
+  return STENCIL_OK;
+}
+
+int stencil_smooth_depend(const stencil_grid_t *g, double *u, const double *f, int sweeps,
+                          stencil_depend_opts_t *opts, void *stream) {
+  int rc = check_fd_uf(g, u, f, "smooth_depend");
+  if (rc) return rc;
+  return smooth_depend_impl(g, u, f, sweeps, opts, STENCIL_COST_NONE, 0, stream);
+}
+
+int stencil_smooth_expensive(const stencil_grid_t *g, double *u, const double *f, int sweeps, int cost_mode,
+                             int kmax, stencil_depend_opts_t *depend, void *stream) {
+  int rc = check_fd_uf(g, u, f, "smooth_expensive");
+  if (rc) return rc;
+  if (cost_mode != STENCIL_COST_NONE && cost_mode != STENCIL_COST_UNIFORM && cost_mode != STENCIL_COST_LINEAR)
+    return set_error(STENCIL_EINVAL, "smooth_expensive: unknown cost mode");
+  if (kmax < 0 || kmax > 100000 || sweeps < 0) return set_error(STENCIL_EINVAL, "smooth_expensive: need 0 <= kmax <= 100000, sweeps >= 0");
+  if (depend) return smooth_depend_impl(g, u, f, sweeps, depend, cost_mode, kmax, stream);
+  if (sweeps == 0) return STENCIL_OK;
+  cudaError_t e = launch_fd_gs_redblack_cost(make_geo(*g), g->dim, u, f, sweeps, cost_mode, kmax,
+                                             (cudaStream_t)stream);
+  if (e) return set_error(STENCIL_ECUDA, std::string("smooth_expensive: ") + cudaGetErrorString(e));
   return STENCIL_OK;
 }
 

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "cost.cuh"
 #include "internal.h"
 
 namespace stencil {
@@ -21,7 +22,7 @@ namespace {
 
 constexpr int FD_THREADS = 256;
 
-enum { FD_APPLY = 0, FD_JACOBI = 1, FD_RESIDUAL = 2, FD_GS = 3 };
+enum { FD_APPLY = 0, FD_JACOBI = 1, FD_RESIDUAL = 2, FD_GS = 3, FD_GS_COST = 4 };
 
 struct FdArgs {
   Geo q;
@@ -33,6 +34,9 @@ struct FdArgs {
   double c1;          // Jacobi: omega h^2 / (2d); GS: h^2 / (2d)
   double inv_c;       // GS: 1 / (2d)
   int parity;         // GS: colour of this pass, (i + j + k) & 1
+  int cost_mode;      // GS with S(k): COST_UNIFORM or COST_LINEAR (cost.cuh)
+  int kmax;
+  double h2;          // h^2
   double *partials;   // residual: 2 per CTA
   unsigned *counter;  // residual: CTAs finished
   double *norms2;     // residual: [sum r^2, sum f^2]
@@ -51,10 +55,15 @@ __global__ void __launch_bounds__(FD_THREADS) k_fd(FdArgs a) {
     const bool row_in = j > 0 && j < q.ny && (a.dim == 2 || (k > 0 && k < q.nz));
     const int64_t base = k * q.plane + j * q.pitch;
     const double *u = a.u + base;
-    for (int64_t i = threadIdx.x; i <= q.nx; i += FD_THREADS) {
+    constexpr bool GS = OP == FD_GS || OP == FD_GS_COST;
+    if (GS && !row_in) continue;
+    // GS: only the vertices of this pass's colour, every second one of the row
+    const int64_t i_first = GS ? 1 + ((a.parity + 1 + j + k) & 1) : 0;
+    const int64_t i_step = GS ? 2 : 1;
+    for (int64_t i = i_first + i_step * threadIdx.x; i <= q.nx; i += i_step * FD_THREADS) {
       const bool inner = row_in && i > 0 && i < q.nx;
-      if (OP == FD_GS) {
-        if (!inner || ((i + j + k) & 1) != a.parity) continue;
+      if (GS) {
+        if (!inner) continue;
       } else if (!inner) {
         if (OP == FD_APPLY) a.out[base + i] = 0.0;
         if (OP == FD_JACOBI) a.out[base + i] = u[i];
@@ -65,6 +74,11 @@ __global__ void __launch_bounds__(FD_THREADS) k_fd(FdArgs a) {
       if (a.dim == 3) s += u[i - q.plane] + u[i + q.plane];
       if (OP == FD_GS) {
         a.out[base + i] = fma(a.c1, a.f[base + i], s * a.inv_c);
+        continue;
+      }
+      if (OP == FD_GS_COST) {
+        const double d = cost_diagonal(q, a.dim, a.cost_mode, a.kmax, i, j, k);
+        a.out[base + i] = (a.h2 * a.f[base + i] + s) / d;
         continue;
       }
       const double Au = fma(c, u[i], -s) * a.inv_h2;
@@ -196,6 +210,25 @@ cudaError_t launch_fd_gs_redblack(const Geo &q, int dim, double *u, const double
     for (int pass = 0; pass < 2; ++pass) {
       a.parity = pass == 0 ? 1 : 0;
       k_fd<FD_GS><<<fd_blocks(q), FD_THREADS, 0, s>>>(a);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
+}
+
+cudaError_t launch_fd_gs_redblack_cost(const Geo &q, int dim, double *u, const double *f, int sweeps, int mode,
+                                       int kmax, cudaStream_t s) {
+  FdArgs a = fd_args(q, dim);
+  a.u = u;
+  a.f = f;
+  a.out = u;
+  a.h2 = q.h * q.h;
+  a.cost_mode = mode;
+  a.kmax = kmax;
+  for (int it = 0; it < sweeps; ++it)
+    for (int pass = 0; pass < 2; ++pass) {
+      a.parity = pass == 0 ? 1 : 0;
+      k_fd<FD_GS_COST><<<fd_blocks(q), FD_THREADS, 0, s>>>(a);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }

@@ -144,10 +144,13 @@ cudaError_t launch_fd_gs_redblack(const Geo &q, int dim, double *u, const double
 
 // Dependency-driven red-black sweeps (depend.cu), op FD, F64.
 size_t depend_state_bytes(int nblocks);
-int depend_blocks(const Geo &q, int dim, int rows);
-cudaError_t launch_depend_redblack(const Geo &q, int dim, double *u, const double *f, int sweeps, int rows,
+int depend_blocks(const Geo &q, int dim, int rows, int cols);
+cudaError_t launch_depend_redblack(const Geo &q, int dim, double *u, const double *f, int sweeps, int rows, int cols,
                                    int ctas, long long max_wait_ns, int stall_block, void *state, int *status_host,
-                                   int *stalled_host, cudaStream_t s);
+                                   int *stalled_host, cudaStream_t s, int cost_mode = 0, int kmax = 0);
+// Red-black sweeps with expensive stencil evaluations S(k) (fd.cu, cost.cuh).
+cudaError_t launch_fd_gs_redblack_cost(const Geo &q, int dim, double *u, const double *f, int sweeps, int mode,
+                                       int kmax, cudaStream_t s);
 
 // Geometric multigrid (mg.cu).  Coarse grids are dense (pitch n_c + 1): n/2 per axis
 // when all n are even, ceil(n/2) when all n are equal; none (false) below n = 4.

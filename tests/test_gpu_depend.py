@@ -14,16 +14,16 @@ from tests.parity_util import TOL_F64, rel_err, to_dev, to_host
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("dim,n,rows,ctas", [
-    (2, (64, 64), 0, 0), (2, (301, 97), 3, 5), (2, (30, 500), 1, 0), (2, (2, 2), 1, 1),
-    (3, (24, 24, 24), 0, 0), (3, (40, 17, 33), 1, 3), (3, (9, 9, 70), 4, 0)])
+@pytest.mark.parametrize("dim,n,rows,cols,ctas", [
+    (2, (64, 64), 0, 0, 0), (2, (301, 97), 3, 0, 5), (2, (30, 500), 1, 0, 0), (2, (2, 2), 1, 0, 1),
+    (3, (24, 24, 24), 0, 0, 0), (3, (40, 17, 33), 1, 4, 3), (3, (9, 9, 70), 4, 3, 0), (3, (33, 65, 20), 2, 7, 0)])
 @pytest.mark.parametrize("sweeps", [1, 4])
-def test_depend_matches_oracle_and_barrier_sweeps(dim, n, rows, ctas, sweeps):
+def test_depend_matches_oracle_and_barrier_sweeps(dim, n, rows, cols, ctas, sweeps):
     h = 1.0 / max(n)
     u0 = synth.uniform_field(synth.grid_shape(dim, n), 1200 + sum(n), zero_bc=False)
     f = synth.uniform_field(u0.shape, 1201 + sum(n))
     ud, fd = to_dev(u0, pad=3), to_dev(f, pad=3)
-    out = st.stencil_smooth_depend(ud, fd, h, sweeps, rows=rows, ctas=ctas)
+    out = st.stencil_smooth_depend(ud, fd, h, sweeps, rows=rows, cols=cols, ctas=ctas)
     assert out["status"] == 0
     bd = to_dev(u0, pad=3)
     st.stencil_smooth_coloured(bd, fd, h, sweeps, op=st.OP_FD)
@@ -58,7 +58,27 @@ def test_unmet_dependency_times_out_and_context_survives():
 def test_depend_refuses_q1():
     u = torch.zeros(synth.grid_shape(2, (8, 8)), dtype=torch.float64, device="cuda")
     g = st.grid_for(u, 0.125, st.OP_Q1)
-    o = st.DependOpts(0, 0, 0, 0, -1)
+    o = st.DependOpts(0, 0, 0, 0, 0, -1, 0)
     rc = st.lib().stencil_smooth_depend(__import__("ctypes").byref(g), st._ptr(u), st._ptr(u.clone()), 1,
                                         __import__("ctypes").byref(o), None)
     assert rc == st.EINVAL
+
+
+@pytest.mark.parametrize("dim,n", [(2, (61, 47)), (3, (13, 11, 17))])
+@pytest.mark.parametrize("mode,kmax", [(st.COST_UNIFORM, 100), (st.COST_LINEAR, 100), (st.COST_NONE, 5)])
+@pytest.mark.parametrize("depend", [None, {"rows": 3}, {"rows": 2, "cols": 4}])
+def test_expensive_stencil_matches_oracle(dim, n, mode, kmax, depend):
+    """S(k): k FP64 sin evaluations per update (uniform, or linear over the mesh); the
+    GPU sin differs from the host's by a few ulp, far below the 2^-20 scale of the
+    perturbation, so the result matches the oracle to FP64 tolerance."""
+    h = 1.0 / max(n)
+    u0 = synth.uniform_field(synth.grid_shape(dim, n), 1400 + sum(n), zero_bc=False)
+    f = synth.uniform_field(u0.shape, 1401 + sum(n))
+    ud = to_dev(u0, pad=2)
+    assert st.stencil_smooth_expensive(ud, to_dev(f, pad=2), h, 2, mode, kmax, depend=depend) == 0
+    torch.cuda.synchronize()
+    got = to_host(ud)
+    assert rel_err(got, oracle.fd_gs_redblack_cost(u0, f, h, 2, mode, kmax)) <= TOL_F64
+    if mode != st.COST_NONE:
+        # the perturbation is really applied: the plain sweep differs by far more than rounding
+        assert rel_err(got, oracle.fd_gs_redblack(u0, f, h, 2)) > 1e-9
