@@ -546,8 +546,37 @@ def run_fd(args):
             t = sum(e[(op, g)][0].elapsed_time(e[(op, g)][1]) for e in ev) / steps / PASSES[op]
             b = BYTES_PER_UPDATE[op] * interior(int(g), nn)
             per["%s_%sd" % (op, g)] = {"ms_per_pass": round(t, 4), "frac": round(b / (t * 1e-3) / 1e9 / peak, 3)}
+    # red-black sweeps: colour passes with barriers vs dependency-driven tasks, and the
+    # expensive stencils S(k) (k = 100 everywhere / k = 0..99 linear over the mesh)
+    def timed(fn, reps=2):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+    cmp = {}
+    for g in wl.grids:
+        nn, hh = wl.n[g], wl.h[g]
+        u, f = wl.view("u" + g), wl.view("f" + g)
+        tb = timed(lambda: st.stencil_smooth_coloured(u, f, hh, 10, op=st.OP_FD)) / 10
+        td = timed(lambda: st.stencil_smooth_depend(u, f, hh, 10)) / 10
+        cmp["redblack_%sd" % g] = {"barrier_ms_per_sweep": round(tb, 4), "depend_ms_per_sweep": round(td, 4)}
+        ns = 128 if g == "3" else 2048  # S(k): FP64 sin-bound, a smaller grid
+        hs = 1.0 / ns
+        us = torch.from_numpy(synth.uniform_field(synth.grid_shape(int(g), ns), 1)).to(dev)
+        fs = torch.from_numpy(synth.uniform_field(synth.grid_shape(int(g), ns), 2)).to(dev)
+        ups = interior(int(g), ns)
+        for mode, name in ((st.COST_UNIFORM, "k100"), (st.COST_LINEAR, "k0to99")):
+            tb = timed(lambda: st.stencil_smooth_expensive(us, fs, hs, 1, mode, 100))
+            td = timed(lambda: st.stencil_smooth_expensive(us, fs, hs, 1, mode, 100, depend={}))
+            cmp["expensive_%s_%sd_n%d" % (name, g, ns)] = {
+                "barrier_mupd_s": round(ups / tb / 1e3, 1), "depend_mupd_s": round(ups / td / 1e3, 1)}
     return {"metric": "Mupdates/s (5/7-point FD op mix: 50 stencil applies, 50 red-black GS sweeps, "
-                      "50 Jacobi sweeps, 1 residual per grid)", "workload": "fd",
+                      "50 Jacobi sweeps, 1 residual per grid)", "workload": "fd", "redblack_and_expensive": cmp,
             "value": round(upd / (ms * 1e-3) / 1e6, 1), "unit": "Mupdates/s", "steps": steps,
             "ms_per_step": round(ms / steps, 3), "grid_3d": n3, "grid_2d": n2, "dtype": "f64",
             "per_op": per}
