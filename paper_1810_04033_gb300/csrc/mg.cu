@@ -143,19 +143,18 @@ __global__ void __launch_bounds__(MG_THREADS) k_mg_prolong_add(Geo qf, Geo qc, D
         }
         const int m = (int)ox + (int)oy + (int)oz;
         acc = m == 0 ? sum : sum * (m == 1 ? 0.5 : (m == 2 ? 0.25 : 0.125));
-        out[i] += acc;
-        continue;
-      }
-      for (int64_t K = K0; K <= K1; ++K) {
-        const double wz = dim == 3 ? interp_w(k, d.f[2], K, d.c[2], d.inv_f[2]) : 1.0;
-        if (wz == 0.0) continue;
-        for (int64_t J = J0; J <= J1; ++J) {
-          const double wyz = interp_w(j, d.f[1], J, d.c[1], d.inv_f[1]) * wz;
-          if (wyz == 0.0) continue;
-          const double *pc = ec + K * qc.plane + J * qc.pitch;
-          for (int64_t I = I0; I <= I1; ++I) {
-            const double w = interp_w(i, d.f[0], I, d.c[0], d.inv_f[0]) * wyz;
-            if (w != 0.0) acc += w * pc[I];
+      } else {
+        for (int64_t K = K0; K <= K1; ++K) {
+          const double wz = dim == 3 ? interp_w(k, d.f[2], K, d.c[2], d.inv_f[2]) : 1.0;
+          if (wz == 0.0) continue;
+          for (int64_t J = J0; J <= J1; ++J) {
+            const double wyz = interp_w(j, d.f[1], J, d.c[1], d.inv_f[1]) * wz;
+            if (wyz == 0.0) continue;
+            const double *pc = ec + K * qc.plane + J * qc.pitch;
+            for (int64_t I = I0; I <= I1; ++I) {
+              const double w = interp_w(i, d.f[0], I, d.c[0], d.inv_f[0]) * wyz;
+              if (w != 0.0) acc += w * pc[I];
+            }
           }
         }
       }

@@ -196,8 +196,11 @@ def test_gs_extreme_magnitudes(scale):
     ref = oracle.gs_coloured(u0, f, h, 3)
     ud, fd = to_dev(u0), to_dev(f)
     st.stencil_smooth_coloured(ud, fd, h, 3)
+    jd = to_dev(u0)
+    st.stencil_smooth_jacobi(jd, fd, torch.empty_like(jd), h, 4, 0.8)
     torch.cuda.synchronize()
     assert rel_err(to_host(ud), ref) <= TOL_F64
+    assert rel_err(to_host(jd), oracle.jacobi(u0, f, h, 0.8, 4)) <= TOL_F64
 
 
 def test_gs_shrinking_iterate_keeps_relative_accuracy():
