@@ -54,22 +54,65 @@ __device__ __forceinline__ float quant<__nv_bfloat16>(float v) {
   return __bfloat162float(__float2bfloat16_rn(v));
 }
 
+constexpr int LP_NUP = LP_SH * LP_SW / LP_THREADS;                         // 9 values / thread
+constexpr int LP_NCE = (LP_SH / 2 * LP_SW + LP_THREADS - 1) / LP_THREADS;  // 5 (odd rows)
+
+// Raw loads of one centre plane's odd rows (pc) and one full neighbour plane (pu) of
+// the tile + 2-vertex halo into registers (zeros outside the grid or for a null plane).
 template <typename S>
-__device__ void stage(float *slot, const S *plane, const Geo &q, int x0, int y0, bool odd_only) {
-  const int nrows = odd_only ? LP_SH / 2 : LP_SH;
-  for (int idx = threadIdx.x; idx < nrows * LP_SW; idx += LP_THREADS) {
-    const int r = odd_only ? 2 * (idx >> 6) + 1 : (idx >> 6), col = idx & 63;
+__device__ __forceinline__ void lp_prefetch(const Geo &q, int x0, int y0, const S *cplane, const S *uplane,
+                                            float (&pc)[LP_NCE], float (&pu)[LP_NUP]) {
+#pragma unroll
+  for (int k = 0; k < LP_NCE; ++k) {
+    const int idx = threadIdx.x + k * LP_THREADS;
+    const int r = 2 * (idx >> 6) + 1, col = idx & 63;
     const int64_t x = x0 - 2 + col, j = y0 - 2 + r;
-    float v = 0.0f;
-    if (plane && col < LP_TX + 4 && r < LP_TY + 4 && x >= 0 && x <= q.nx && j >= 0 && j <= q.ny)
-      v = ld<S>(plane, j * q.pitch + x);
-    slot[r * LP_SW + col] = v;
+    const bool ok = cplane && idx < LP_SH / 2 * LP_SW && col < LP_TX + 4 && r < LP_TY + 4 && x >= 0 &&
+                    x <= q.nx && j >= 0 && j <= q.ny;
+    pc[k] = ok ? ld<S>(cplane, j * q.pitch + x) : 0.0f;
+  }
+#pragma unroll
+  for (int k = 0; k < LP_NUP; ++k) {
+    const int idx = threadIdx.x + k * LP_THREADS;
+    const int r = idx >> 6, col = idx & 63;
+    const int64_t x = x0 - 2 + col, j = y0 - 2 + r;
+    const bool ok = uplane && col < LP_TX + 4 && r < LP_TY + 4 && x >= 0 && x <= q.nx && j >= 0 && j <= q.ny;
+    pu[k] = ok ? ld<S>(uplane, j * q.pitch + x) : 0.0f;
+  }
+}
+
+__device__ __forceinline__ void lp_commit(const float (&pc)[LP_NCE], const float (&pu)[LP_NUP], float *ce,
+                                          float *up) {
+#pragma unroll
+  for (int k = 0; k < LP_NCE; ++k) {
+    const int idx = threadIdx.x + k * LP_THREADS;
+    if (ce && idx < LP_SH / 2 * LP_SW) ce[(2 * (idx >> 6) + 1) * LP_SW + (idx & 63)] = pc[k];
+  }
+#pragma unroll
+  for (int k = 0; k < LP_NUP; ++k) up[threadIdx.x + k * LP_THREADS] = pu[k];
+}
+
+// Right-hand sides of the two phases of one centre plane (4 rows each), 3/8 h^2 f.
+template <typename S>
+__device__ __forceinline__ void lp_prefetch_f(const Geo &q, int x0, int y0, const S *fplane, float g, float (&fv)[8]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int seg = warp & 1, grp = warp >> 1;
+#pragma unroll
+  for (int ph = 0; ph < 2; ++ph) {
+    const int col = (ph == 0 ? 0 : 1) + 30 * seg + lane;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int r = (ph == 0 ? 2 : 3) + 8 * grp + 2 * k;
+      const int64_t x = x0 - 2 + col, j = y0 - 2 + r;
+      const bool ok = fplane && lane >= 1 && lane <= 30 && x >= 1 && x < q.nx && j >= 1 && j < q.ny;
+      fv[4 * ph + k] = ok ? g * ld<S>(fplane, j * q.pitch + x) : 0.0f;
+    }
   }
 }
 
 template <typename S, int WHICH>
 __device__ void lp_phase(const Geo &q, int x0, int y0, float *ce, const float *lo, const float *up,
-                         const S *xplane, const S *fplane, S *yplane, float g) {
+                         const S *xplane, S *yplane, const float (&gf)[8]) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int seg = warp & 1, grp = warp >> 1;
   const int col = (WHICH == 1 ? 0 : 1) + 30 * seg + lane;
@@ -97,7 +140,7 @@ __device__ void lp_phase(const Geo &q, int x0, int y0, float *ce, const float *l
     const int64_t off = j * q.pitch + x;
     float v;
     if (x >= 1 && x < q.nx && j >= 1 && j < q.ny)
-      v = quant<S>(fmaf(Pm + Pp + 2.0f * Q, 0.03125f, g * ld<S>(fplane, off)));
+      v = quant<S>(fmaf(Pm + Pp + 2.0f * Q, 0.03125f, gf[(WHICH - 1) * 4 + k]));
     else
       v = ld<S>(xplane, off);  // Dirichlet value
     if (WHICH == 1) ce[r * LP_SW + col] = v;
@@ -115,24 +158,35 @@ __global__ void __launch_bounds__(LP_THREADS) k_gs_lp_half(Geo q, int pz, const 
   const int64_t i0 = (int64_t)blockIdx.z * cz;
   const int64_t i1 = i0 + cz < ncentre ? i0 + cz : ncentre;
   int lo = 0, ce = 1, up = 2;
-  bool have_lower = false;
+  float pc[LP_NCE], pu[LP_NUP], fv[8];
+  {
+    const int64_t z = pz + 2 * i0;
+    float dummy[LP_NCE];
+    lp_prefetch<S>(q, x0, y0, (const S *)nullptr, z >= 1 ? N + (z - 1) * q.plane : nullptr, dummy, pu);
+    lp_commit(dummy, pu, nullptr, slot(lo));
+    const bool zin = z >= 1 && z < q.nz;
+    lp_prefetch<S>(q, x0, y0, zin ? X + z * q.plane : nullptr, z + 1 <= q.nz ? N + (z + 1) * q.plane : nullptr, pc,
+                   pu);
+    lp_prefetch_f<S>(q, x0, y0, zin ? f + z * q.plane : nullptr, g, fv);
+  }
   for (int64_t i = i0; i < i1; ++i) {
     const int64_t z = pz + 2 * i;
     const bool zin = z >= 1 && z < q.nz;
-    if (zin) {
-      if (!have_lower) stage<S>(slot(lo), N + (z - 1) * q.plane, q, x0, y0, false);
-      stage<S>(slot(ce), X + z * q.plane, q, x0, y0, true);
-      stage<S>(slot(up), N + (z + 1) * q.plane, q, x0, y0, false);
-    } else if (z + 1 <= q.nz) {
-      stage<S>(slot(up), N + (z + 1) * q.plane, q, x0, y0, false);
-    }
+    lp_commit(pc, pu, slot(ce), slot(up));
+    float fcur[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) fcur[k] = fv[k];
     __syncthreads();
+    if (i + 1 < i1) {  // next centre plane z + 2 and its upper neighbour z + 3
+      const bool zn = z + 2 >= 1 && z + 2 < q.nz;
+      lp_prefetch<S>(q, x0, y0, zn ? X + (z + 2) * q.plane : nullptr, z + 3 <= q.nz ? N + (z + 3) * q.plane : nullptr,
+                     pc, pu);
+      lp_prefetch_f<S>(q, x0, y0, zn ? f + (z + 2) * q.plane : nullptr, g, fv);
+    }
     if (zin) {
-      lp_phase<S, 1>(q, x0, y0, slot(ce), slot(lo), slot(up), X + z * q.plane, f + z * q.plane,
-                     Y + z * q.plane, g);
+      lp_phase<S, 1>(q, x0, y0, slot(ce), slot(lo), slot(up), X + z * q.plane, Y + z * q.plane, fcur);
       __syncthreads();
-      lp_phase<S, 2>(q, x0, y0, slot(ce), slot(lo), slot(up), X + z * q.plane, f + z * q.plane,
-                     Y + z * q.plane, g);
+      lp_phase<S, 2>(q, x0, y0, slot(ce), slot(lo), slot(up), X + z * q.plane, Y + z * q.plane, fcur);
     } else {
       for (int idx = threadIdx.x; idx < LP_TX * LP_TY; idx += LP_THREADS) {
         const int64_t x = x0 + idx % LP_TX, j = y0 + idx / LP_TX;
@@ -141,10 +195,9 @@ __global__ void __launch_bounds__(LP_THREADS) k_gs_lp_half(Geo q, int pz, const 
       }
     }
     __syncthreads();
-    const int t = lo;
+    const int t = lo;  // the upper neighbour becomes the next centre plane's lower one
     lo = up;
     up = t;
-    have_lower = z + 1 <= q.nz;
   }
 }
 
