@@ -174,14 +174,15 @@ __device__ __forceinline__ int64_t ew3_layers(const EwArgs &a, Ew3Lane &L, int64
     if (k >= z0 && k <= q.nz && L.out_lane) {
       const bool zin = k >= 1 && k < q.nz;
       double *out = a.y + k * q.plane + L.x;
+      // scale 2^(R-52) / (12 h^2), exact power-of-two scaling of a.scale
+      const double sc = FIX ? a.scale * fx::pow2d(L.R - fx::FRAC) : a.scale;
 #pragma unroll
       for (int r = 0; r < S3_R; ++r) {
         const int64_t j = j0 + r;
         if (j > q.ny) break;
         const bool inner = zin && L.xin && j >= 1 && j < q.ny;
         double yv = 0.0;
-        if (inner)
-          yv = (FIX ? fx::to_double(L.acc[r], L.R - fx::FRAC) : __longlong_as_double(L.acc[r])) * a.scale;
+        if (inner) yv = (FIX ? __ll2double_rn(L.acc[r]) : __longlong_as_double(L.acc[r])) * sc;
         out[j * q.pitch] = yv;
       }
     }

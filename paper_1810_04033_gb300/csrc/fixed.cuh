@@ -8,7 +8,9 @@
 // common denominator they are integers.  Values are converted to int64 with FRAC
 // fraction bits relative to a power-of-two bound 2^R on their magnitudes; the
 // neighbour sums are then exact integer sums, and only the final scale-and-add runs on
-// the FP64 pipe.  Both conversions use integer instructions only.
+// the FP64 pipe.  to_fixed and to_double use integer instructions only; to_double_cvt
+// gives to_double's value through the FP64 pipe's conversion, for kernels whose integer
+// pipe is the bottleneck while the FP64 pipe has room.
 //
 // Accuracy: each input is truncated to a multiple of 2^(R-FRAC) (|error| < 2^(R-52)),
 // the integer sums are exact, and the conversion back rounds to nearest even; the
@@ -92,6 +94,15 @@ __host__ __device__ __forceinline__ double to_double(long long v, int e2) {
       ((unsigned long long)ebm1 << 52) + mant + ((unsigned long long)sg & 0x8000000000000000ull);
   return a ? bitsd(bits) : 0.0;
 }
+
+// 2^e as a double, -1022 <= e <= 1023.
+__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+
+// The same value as to_double(v, e2), computed with the FP64 pipe's int64 -> double
+// conversion (round to nearest even) and an exact power-of-two scaling: it moves the
+// ~20 integer instructions of to_double off the integer pipe, which bounds the
+// fixed-point kernels.  Requires -1022 <= e2 <= 1023 and a normal (or zero) result.
+__device__ __forceinline__ double to_double_cvt(long long v, int e2) { return __ll2double_rn(v) * pow2d(e2); }
 
 // |x| as ordered unsigned bits (monotone in |x| for finite and infinite x; NaN above).
 __host__ __device__ __forceinline__ unsigned long long abs_bits(double x) {

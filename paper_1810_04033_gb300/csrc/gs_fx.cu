@@ -210,7 +210,7 @@ __device__ __forceinline__ void phase(const Ctx &c, long long *ce, const long lo
       if (YF == FXP && FIXA) {
         ((long long *)yplane)[off] = rep;
       } else if (FIXA) {
-        ((double *)yplane)[off] = inner ? fx::to_double(rep, c.R - fx::FRAC) : __longlong_as_double(ld64(xplane, off));
+        ((double *)yplane)[off] = inner ? fx::to_double_cvt(rep, c.R - fx::FRAC) : __longlong_as_double(ld64(xplane, off));
       } else {
         ((long long *)yplane)[off] = rep;  // FP64 bits
       }

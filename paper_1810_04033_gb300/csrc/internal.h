@@ -70,20 +70,9 @@ enum ScratchSlot {
 void *host_scratch(size_t bytes, cudaStream_t stream);
 void *device_scratch(int slot, size_t bytes, cudaStream_t stream);
 
-// Kernel launchers (kernels_*.cu).  Return cudaGetLastError() of the launch.
-cudaError_t launch_apply_stencil_f64(const Geo &q, int dim, const double *u, double *y,
-                                     cudaStream_t s);
-cudaError_t launch_apply_elementwise_f64(const Geo &q, int dim, const double *u, double *y,
-                                         cudaStream_t s);
-cudaError_t launch_gs_sweeps_f64(const Geo &q, int dim, double *u, const double *f,
-                                 int sweeps, cudaStream_t s);
-cudaError_t launch_jacobi_sweep_f64(const Geo &q, int dim, const double *u, const double *f,
-                                    double *unew, double omega, cudaStream_t s);
 // Residual with norms.  Reduction scratch layout (all users): an unsigned counter in
 // the first 16 bytes (zero before the first call; kernels leave it zero), then the
 // per-CTA partial sums.
-constexpr int kReduceBlocks = 1216;  // 8 per SM on 152 SMs: fixed => fixed sum order
-size_t reduce_scratch_bytes();
 
 // Fixed-point FP64 paths (gs_fx.cu): 3D coloured GS, two launches per sweep.  work
 // holds 3 arrays of u's span (two int64 ping-pong buffers and 3/8 h^2 f in fixed point);
@@ -95,8 +84,6 @@ cudaError_t launch_gs_prepass(const Geo &q, int dim, const double *u, const doub
                               void *bounds, int sweeps, cudaStream_t s);
 cudaError_t launch_gs_sweeps_fx3(const Geo &q, double *u, const double *f, int sweeps,
                                  double *work, void *bounds, cudaStream_t s);
-cudaError_t launch_residual_f64(const Geo &q, int dim, const double *u, const double *f,
-                                double *r, double *norms2, void *scratch, cudaStream_t s);
 
 // Fixed-point out-of-place 3D operations (ops_fx.cu).  The residual needs
 // ops_fx_reduce_bytes(q) bytes of zero-initialised scratch (left zeroed).

@@ -177,8 +177,9 @@ __device__ __forceinline__ int64_t ew2_rows(const Op2Args &a, WarpScale &w, Stre
       }
       if (cj >= js && s.out_lane) {
         const bool inner = s.xin && cj >= 1 && cj < q.ny;
-        const double sv = FIX ? fx::to_double(alo, w.R - fx::FRAC) : __longlong_as_double(alo);
-        a.out[cj * q.pitch + s.x] = inner ? sv * a.c1 : 0.0;
+        // FIX: 2^(R-52) c1 times the converted sum (exact power-of-two scaling of c1)
+        const double sv = FIX ? __ll2double_rn(alo) : __longlong_as_double(alo);
+        a.out[cj * q.pitch + s.x] = inner ? sv * (FIX ? a.c1 * fx::pow2d(w.R - fx::FRAC) : a.c1) : 0.0;
       }
       alo = ahi;
       ahi = 0;
@@ -212,6 +213,8 @@ __device__ __forceinline__ int64_t op2_rows(const Op2Args &a, WarpScale &w, Stre
       if (OP != O2_APPLY && s.out_lane && inner) fv = fcol[j * q.pitch];
       const long long T = eight_u_minus_n<FIX>(s.um, s.uc, s.up);
       if (s.out_lane) {
+        // converted on the integer pipe here (measured faster than the FP64 pipe's
+        // conversion for these three operations; the element-wise apply uses the latter)
         const double Td = inner ? (FIX ? fx::to_double(T, w.R - fx::FRAC) : __longlong_as_double(T)) : 0.0;
         const int64_t go = j * q.pitch;
         if (OP == O2_APPLY) {
@@ -555,6 +558,10 @@ __global__ void __launch_bounds__(W2_THREADS) k_gs2_sweep(Geo q, const void *__r
   const int R = sweep_R(bnd, sweep % 4, g);
   const int Rx = sweep > 0 ? sweep_R(bnd, (sweep + 3) % 4, g) : R;
   const int dx = XF == SF_FXP ? R - Rx : 0, df = R - plan.Rf, rb = 1023 + R;
+  // shift amounts clamped once: inputs by dx (right, or left when the scale shrank),
+  // GF by df >= 0 (a shift by 63 leaves 0 or -1: below one unit of the last place)
+  const int dxr = dx > 0 ? (dx < 63 ? dx : 63) : 0, dxl = dx < 0 ? (-dx < 63 ? -dx : 63) : 0;
+  const int dfr = df < 63 ? df : 63;
   if (blockIdx.x == 0 && threadIdx.x == 0) bnd->umax[(sweep + 2) % 4] = 0ull;
   long long vmax = 0;
   if (js <= q.ny) {
@@ -567,7 +574,7 @@ __global__ void __launch_bounds__(W2_THREADS) k_gs2_sweep(Geo q, const void *__r
     auto rawx = [&](int64_t j) -> long long { return (xok && j >= 0 && j <= q.ny) ? Xl[j * q.pitch + x] : 0ll; };
     auto rawg = [&](int64_t j) -> long long { return (xin && j >= 1 && j < q.ny) ? GF[j * q.pitch + x] : 0ll; };
     auto cvx = [&](long long raw) -> long long {
-      return XF == SF_F64 ? fx::to_fixed(__longlong_as_double(raw), rb) : shr_any(raw, dx);
+      return XF == SF_F64 ? fx::to_fixed(__longlong_as_double(raw), rb) : (raw >> dxr) << dxl;
     };
     auto put = [&](int64_t j, long long v) {
       if (!out_lane) return;
@@ -576,7 +583,7 @@ __global__ void __launch_bounds__(W2_THREADS) k_gs2_sweep(Geo q, const void *__r
       if (YF == SF_FXP)
         ((long long *)Y)[j * q.pitch + x] = v;
       else
-        ((double *)Y)[j * q.pitch + x] = fx::to_double(v, R - fx::FRAC);
+        ((double *)Y)[j * q.pitch + x] = fx::to_double_cvt(v, R - fx::FRAC);
       const long long a = v < 0 ? -v : v;
       vmax = a > vmax ? a : vmax;
     };
@@ -598,7 +605,7 @@ __global__ void __launch_bounds__(W2_THREADS) k_gs2_sweep(Geo q, const void *__r
         const int64_t j = jb + 2 * t;
         if (j > je) break;
         const long long rc = cvx(qe[t]), rp = cvx(qo[t]);
-        const long long ge = shr_any(qge[t], df), go = shr_any(qgo[t], df);
+        const long long ge = qge[t] >> dfr, go = qgo[t] >> dfr;
         {
           const int64_t jn = j + 2 * PG;
           const bool ok = jn <= je;
@@ -675,6 +682,8 @@ __global__ void __launch_bounds__(W2_THREADS) k_jac2_sweep(Geo q, const void *__
   const int R = sweep_R(bnd, sweep % 4, g);
   const int Rx = sweep > 0 ? sweep_R(bnd, (sweep + 3) % 4, g) : R;
   const int dx = XF == SF_FXP ? R - Rx : 0, df = R - plan.Rf, rb = 1023 + R;
+  const int dxr = dx > 0 ? (dx < 63 ? dx : 63) : 0, dxl = dx < 0 ? (-dx < 63 ? -dx : 63) : 0;
+  const int dfr = df < 63 ? df : 63;
   if (blockIdx.x == 0 && threadIdx.x == 0) bnd->umax[(sweep + 2) % 4] = 0ull;
   const int64_t nseg = (q.nx + 30) / 30;
   const int64_t seg = gw % nseg, chunk = gw / nseg;
@@ -689,7 +698,7 @@ __global__ void __launch_bounds__(W2_THREADS) k_jac2_sweep(Geo q, const void *__
     auto rawx = [&](int64_t j) -> long long { return (xok && j >= 0 && j <= q.ny) ? Xl[j * q.pitch + x] : 0ll; };
     auto rawg = [&](int64_t j) -> long long { return (xin && j >= 1 && j < q.ny) ? GF[j * q.pitch + x] : 0ll; };
     auto cvx = [&](long long raw) -> long long {
-      return XF == SF_F64 ? fx::to_fixed(__longlong_as_double(raw), rb) : shr_any(raw, dx);
+      return XF == SF_F64 ? fx::to_fixed(__longlong_as_double(raw), rb) : (raw >> dxr) << dxl;
     };
     long long um = cvx(rawx(js - 1)), uc = cvx(rawx(js)), up = cvx(rawx(js + 1));
     constexpr int PQ = 3;
@@ -713,12 +722,12 @@ __global__ void __launch_bounds__(W2_THREADS) k_jac2_sweep(Geo q, const void *__
         if (out_lane) {
           const bool inner = xin && j >= 1 && j < q.ny;
           long long un = uc;  // Dirichlet value carried
-          if (inner) un = uc + omega_times(shr_any(gr, df) + ((Tm + Tp + V) >> 3) - uc, Wq);
+          if (inner) un = uc + omega_times((gr >> dfr) + ((Tm + Tp + V) >> 3) - uc, Wq);
           if (inner || write_bnd) {
             if (YF == SF_FXP)
               ((long long *)Y)[j * q.pitch + x] = un;
             else
-              ((double *)Y)[j * q.pitch + x] = fx::to_double(un, R - fx::FRAC);
+              ((double *)Y)[j * q.pitch + x] = fx::to_double_cvt(un, R - fx::FRAC);
             const long long aa = un < 0 ? -un : un;
             vmax = aa > vmax ? aa : vmax;
           }

@@ -146,15 +146,19 @@ __device__ __forceinline__ void compute_plane(const OpArgs &a, int64_t z, int x0
     const int off = j * pitch + x;
     const bool inner = zin && x_inner && (INNER || (j >= 1 && j < ny));
     double Td = 0.0;  // 32 u - (2E + C) = 12 (S u)
+    long long T = 0;
     if (inner) {
       const long long S = add<FIX>(add<FIX>(Pm, Pp), add<FIX>(Q, Q));
-      if (FIX)
-        Td = fx::to_double(32 * Cu - S, e2);
-      else
+      if (FIX) {
+        T = 32 * Cu - S;
+        // apply: converted on the FP64 pipe below; Jacobi / residual: on the integer pipe
+        if (OP != OP_APPLY) Td = fx::to_double(T, e2);
+      } else {
         Td = fma(32.0, __longlong_as_double(Cu), -__longlong_as_double(S));
+      }
     }
     if (OP == OP_APPLY) {
-      outp[off] = inner ? Td * a.c1 : 0.0;
+      outp[off] = inner ? (FIX ? __ll2double_rn(T) * (a.c1 * fx::pow2d(e2)) : Td * a.c1) : 0.0;
     } else if (OP == OP_JACOBI) {
       outp[off] = inner ? fma(a.c2, Td, fma(a.c1, fv[k], uv[k])) : uv[k];
     } else {
