@@ -69,6 +69,22 @@ def updates_per_step(n3, n2):
     return sum(PASSES.values()) * (interior(3, n3) + interior(2, n2))
 
 
+def max_over_ranks(torch, ms, world, device):
+    """The slowest rank's time: every rank runs its own replica of the workload, so
+    the job's time is the maximum (all_reduce MAX; the identity on one rank)."""
+    if world <= 1:
+        return ms
+    tt = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(units_per_rank, world, ms_max):
+    """Units of all ranks (weak scaling: each rank does the same work) per second, in
+    millions."""
+    return units_per_rank * world / (ms_max * 1e-3) / 1e6
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -294,13 +310,8 @@ def run_gpu(args, rank, world):
     barrier()
     per_op_ms = {key: sum(e[key][0].elapsed_time(e[key][1]) for e in ev) for key in ev[0]}
     ms = t0.elapsed_time(t1)
-    ms_max = ms
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(tt.item())
-    total_updates = updates_per_step(n3, n2) * args.steps * world
-    value = total_updates / (ms_max * 1e-3) / 1e6
+    ms_max = max_over_ranks(torch, ms, world, dev)
+    value = whole_job_rate(updates_per_step(n3, n2) * args.steps, world, ms_max)
 
     # dominant kernel: the (op, grid) with the largest share of the step; its achieved
     # bandwidth = algorithmic bytes of one pass / average duration of one pass
@@ -371,12 +382,8 @@ def run_e2e(torch, st, wl, stream, args, world):
             one(stream)
         t1.record(stream)
     stream.synchronize()
-    ms = t0.elapsed_time(t1)
-    if world > 1:
-        tt = torch.tensor([ms], device=wl.dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
-    val = updates_per_step(args.n3, args.n2) * steps * world / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(torch, t0.elapsed_time(t1), world, wl.dev)
+    val = whole_job_rate(updates_per_step(args.n3, args.n2) * steps, world, ms)
     return {"value": round(val, 1), "unit": "Mupdates/s", "h2d_bytes_per_step": bi,
             "d2h_bytes_per_step": bo, "steps": steps}
 
