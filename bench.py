@@ -170,11 +170,12 @@ class GpuWorkload:
         self.grids = [g for g in ("3", "2") if self.n[g]]
         self.h = {"3": 1.0 / n3 if n3 else 0.0, "2": 1.0 / n2 if n2 else 0.0}
         self.p2 = pitch2(n2) if n2 else 0
+        self.p3 = pitch2(n3) if n3 else 0  # rows on 64-byte boundaries (TMA plane loads)
         self.host = {}
         if n3:
             s3 = synth.grid_shape(3, n3)
-            self.host["u3"] = torch.from_numpy(synth.uniform_field(s3, 1)).pin_memory()
-            self.host["f3"] = torch.from_numpy(synth.sin_rhs(3, n3)).pin_memory()
+            self.host["u3"] = self._pad3(torch.from_numpy(synth.uniform_field(s3, 1))).pin_memory()
+            self.host["f3"] = self._pad3(torch.from_numpy(synth.sin_rhs(3, n3))).pin_memory()
         if n2:
             s2 = synth.grid_shape(2, n2)
             self.host["u2"] = self._pad2(torch.from_numpy(synth.uniform_field(s2, 1))).pin_memory()
@@ -194,9 +195,18 @@ class GpuWorkload:
         buf[:, :t.shape[1]] = t
         return buf
 
+    def _pad3(self, t):
+        buf = self.torch.zeros((t.shape[0], t.shape[1], self.p3), dtype=t.dtype)
+        buf[..., :t.shape[2]] = t
+        return buf
+
     def view(self, key):
         t = self.d[key]
-        return t[:, :self.n["2"] + 1] if key.endswith("2") else t
+        if key.endswith("2"):
+            return t[:, :self.n["2"] + 1]
+        if key.endswith("3"):
+            return t[..., :self.n["3"] + 1]
+        return t
 
     def run_op(self, op, g, stream):
         st = self.st
@@ -345,6 +355,7 @@ def run_gpu(args, rank, world):
            "config": {"workload": workload_name(n3, n2),
                       "grid_3d": [n3 + 1] * 3 if n3 else None,
                       "grid_2d": [n2 + 1, n2 + 1] if n2 else None, "pitch_2d": wl.p2 or None,
+                      "pitch_3d": wl.p3 or None,
                       "l2": "inputs larger than L2 (no flush)" if n3 >= 256 or n2 >= 8192
                             else "small case (profiling)",
                       "parallelism": "replicas" if world > 1 else "single GPU"},

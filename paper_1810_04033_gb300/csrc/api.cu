@@ -6,11 +6,13 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cudaTypedefs.h>
 #include <mutex>
 #include <string>
 #include <vector>
 
 #include "internal.h"
+#include "tma.cuh"
 
 namespace stencil {
 
@@ -38,6 +40,29 @@ int device_sm_count() {
     cached[dev] = n;
   }
   return cached[dev];
+}
+
+// ------------------------------------------------------------ TMA tensor maps
+bool tma_plane_map(const Geo &q, const void *base, int box_w, int box_h, CUtensorMap *map) {
+  if ((uintptr_t)base % 16 || q.pitch % 2) return false;  // strides and base need 16-byte alignment
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  std::call_once(once, [] {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr) ==
+            cudaSuccess &&
+        qr == cudaDriverEntryPointSuccess)
+      encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  });
+  if (!encode) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)q.nx + 1, (cuuint64_t)q.ny + 1, (cuuint64_t)q.nz + 1};
+  const cuuint64_t strides[2] = {(cuuint64_t)q.pitch * 8, (cuuint64_t)q.plane * 8};
+  const cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<void *>(base), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // ------------------------------------------------------------ per-stream scratch

@@ -21,6 +21,7 @@
 
 #include "fixed.cuh"
 #include "internal.h"
+#include "tma.cuh"
 
 namespace stencil {
 namespace {
@@ -180,6 +181,66 @@ __device__ __forceinline__ void compute_plane(const OpArgs &a, int64_t z, int x0
   }
 }
 
+// Residual norms: fixed-order CTA sum, one partial per CTA, the last CTA adds the
+// partials in order (deterministic for a given grid).
+__device__ __forceinline__ void ops3_reduce_norms(const OpArgs &a, double rr, double ff, double *sh2, bool *last_p) {
+  bool &last = *last_p;
+  // fixed-order CTA sum, one partial per CTA, the last CTA adds them in order
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    rr += __shfl_xor_sync(0xffffffffu, rr, o);
+    ff += __shfl_xor_sync(0xffffffffu, ff, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    sh2[2 * w] = rr;
+    sh2[2 * w + 1] = ff;
+  }
+  __syncthreads();
+  const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+  const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int k = 0; k < O_THREADS / 32; ++k) {
+      s0 += sh2[2 * k];
+      s1 += sh2[2 * k + 1];
+    }
+    a.partials[2 * bid] = s0;
+    a.partials[2 * bid + 1] = s1;
+    __threadfence();
+    last = atomicAdd(a.counter, 1u) == nblk - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s0 = 0.0, s1 = 0.0;
+  for (unsigned k = threadIdx.x; k < nblk; k += O_THREADS) {
+    s0 += __ldcg(a.partials + 2 * k);
+    s1 += __ldcg(a.partials + 2 * k + 1);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+  __syncthreads();
+  if (l == 0) {
+    sh2[2 * w] = s0;
+    sh2[2 * w + 1] = s1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t0 = 0.0, t1 = 0.0;
+    for (int k = 0; k < O_THREADS / 32; ++k) {
+      t0 += sh2[2 * k];
+      t1 += sh2[2 * k + 1];
+    }
+    a.norms2[0] = t0;
+    a.norms2[1] = t1;
+    *a.counter = 0u;
+  }
+}
+
 // CTAs per SM the register allocation targets: 3 (at most 85 registers) for the apply
 // and the residual; the Jacobi sweep keeps more values live and runs faster at 2.
 template <int OP>
@@ -266,62 +327,128 @@ __global__ void __launch_bounds__(O_THREADS, ops3_min_blocks<OP>()) k_ops3(OpArg
     up = t;
   }
 
-  if (OP == OP_RESIDUAL) {
-    // fixed-order CTA sum, one partial per CTA, the last CTA adds them in order
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      rr += __shfl_xor_sync(0xffffffffu, rr, o);
-      ff += __shfl_xor_sync(0xffffffffu, ff, o);
-    }
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) {
-      sh2[2 * w] = rr;
-      sh2[2 * w + 1] = ff;
-    }
-    __syncthreads();
-    const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
-    const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    if (threadIdx.x == 0) {
-      double s0 = 0.0, s1 = 0.0;
-      for (int k = 0; k < O_THREADS / 32; ++k) {
-        s0 += sh2[2 * k];
-        s1 += sh2[2 * k + 1];
-      }
-      a.partials[2 * bid] = s0;
-      a.partials[2 * bid + 1] = s1;
-      __threadfence();
-      last = atomicAdd(a.counter, 1u) == nblk - 1;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    double s0 = 0.0, s1 = 0.0;
-    for (unsigned k = threadIdx.x; k < nblk; k += O_THREADS) {
-      s0 += __ldcg(a.partials + 2 * k);
-      s1 += __ldcg(a.partials + 2 * k + 1);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-    }
-    __syncthreads();
-    if (l == 0) {
-      sh2[2 * w] = s0;
-      sh2[2 * w + 1] = s1;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t0 = 0.0, t1 = 0.0;
-      for (int k = 0; k < O_THREADS / 32; ++k) {
-        t0 += sh2[2 * k];
-        t1 += sh2[2 * k + 1];
-      }
-      a.norms2[0] = t0;
-      a.norms2[1] = t1;
-      *a.counter = 0u;
-    }
+  if (OP == OP_RESIDUAL) ops3_reduce_norms(a, rr, ff, sh2, &last);
+}
+
+// ------------------------------------------------------------ TMA-staged form
+// Same computation as k_ops3, with the planes brought into shared memory by TMA: four
+// plane slots (lo, ce, up and the plane two ahead, which is in flight while the
+// current plane computes), one mbarrier each.  The staged box starts at x0 - 2 (an even
+// x, as TMA requires); the compute reads it one column to the right, so its column c
+// is x0 - 1 + c as in k_ops3.  A plane arrives as FP64 bits and is converted in place
+// after the CTA agreed on the scale.  Wait limits: a TMA wait that runs out sets
+// g_ops3_tma_error and the CTA leaves.
+__device__ unsigned g_ops3_tma_error = 0;
+constexpr unsigned OT_WAIT_LIMIT = 1u << 22;
+constexpr unsigned OT_BOX_BYTES = OS_H * OS_W * 8;
+
+template <int OP>
+__global__ void __launch_bounds__(O_THREADS, ops3_min_blocks<OP>())
+    k_ops3t(OpArgs a, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ int red[O_THREADS / 32];
+  __shared__ double sh2[2 * O_THREADS / 32];
+  __shared__ __align__(8) uint64_t bars[4];
+  __shared__ bool last;
+  __shared__ int fail;
+  long long *smem = (long long *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  const Geo &q = a.q;
+  const int64_t x0 = (int64_t)blockIdx.x * OT_X, y0 = (int64_t)blockIdx.y * OT_Y;
+  const int64_t zs = (int64_t)blockIdx.z * a.cz;
+  const int64_t ze = zs + a.cz < q.nz + 1 ? zs + a.cz : q.nz + 1;
+  auto slot = [&](int i) -> long long * { return smem + i * (OS_H * OS_W); };
+  const bool inner_tile = x0 >= 1 && x0 + OT_X <= q.nx && y0 >= 1 && y0 + OT_Y <= q.ny;
+  int lo = 0, ce = 1, up = 2, nx = 3;
+  unsigned phase = 0;  // bit i: parity of the next completion on slot i
+  bool fix = true;
+  int R = R_MIN;
+  double rr = 0.0, ff = 0.0;
+  double v[O_PER];
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
+    fail = 0;
+    fence_mbar_init();
+    fence_proxy_async();
   }
+  __syncthreads();
+  auto issue = [&](int s, int64_t z) {
+    if (threadIdx.x == 0) {
+      fence_proxy_async();  // earlier generic accesses to this slot before the TMA writes it
+      tma_load_plane(slot(s), &tmap, (int)(x0 - 2), (int)(y0 - 1), (int)z, &bars[s], OT_BOX_BYTES);
+    }
+  };
+  // Wait for slot dst, agree on the scale (rescaling the live slots if it grows), then
+  // convert the slot in place.  Live slots are the already converted ones (-1: none);
+  // a slot with a load in flight is never touched.  Returns false if the wait ran out.
+  auto admit = [&](int dst, int live0, int live1) -> bool {
+    if (!mbar_wait(&bars[dst], (phase >> dst) & 1u, OT_WAIT_LIMIT)) atomicExch(&fail, 1);
+    phase ^= 1u << dst;
+#pragma unroll
+    for (int k = 0; k < O_PER; ++k) {
+      const int idx = threadIdx.x + k * O_THREADS;
+      v[k] = idx < OS_H * OS_W ? __longlong_as_double(slot(dst)[idx]) : 0.0;
+    }
+    const int em = cta_max_exponent(v, red);  // includes a barrier
+    if (fail) return false;
+    if (fix && em != 0) {
+      const int Rp = em - 1022 + 1;
+      const int Rn = Rp > R ? Rp : R;
+      if (em == 2047 || Rp > R_MAX || Rp < R_MIN) {
+        if (em == 2047 || Rp > R_MAX || R == R_MIN) {
+          for (int idx = threadIdx.x; idx < OS_H * OS_W; idx += O_THREADS) {
+            if (live0 >= 0) slot(live0)[idx] = __double_as_longlong(fx::to_double(slot(live0)[idx], R - fx::FRAC));
+            if (live1 >= 0) slot(live1)[idx] = __double_as_longlong(fx::to_double(slot(live1)[idx], R - fx::FRAC));
+          }
+          fix = false;
+        }
+      } else if (Rn > R) {
+        const int d = Rn - R;
+        for (int idx = threadIdx.x; idx < OS_H * OS_W; idx += O_THREADS) {
+          if (live0 >= 0) slot(live0)[idx] = d < 63 ? (slot(live0)[idx] >> d) : (slot(live0)[idx] >> 63);
+          if (live1 >= 0) slot(live1)[idx] = d < 63 ? (slot(live1)[idx] >> d) : (slot(live1)[idx] >> 63);
+        }
+        R = Rn;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < O_PER; ++k) {
+      const int idx = threadIdx.x + k * O_THREADS;
+      if (idx < OS_H * OS_W) slot(dst)[idx] = fix ? fx::to_fixed(v[k], 1023 + R) : __double_as_longlong(v[k]);
+    }
+    return true;
+  };
+
+  issue(lo, zs - 1);
+  issue(ce, zs);
+  issue(up, zs + 1);
+  bool ok = admit(lo, -1, -1) && admit(ce, lo, -1);
+  for (int64_t z = zs; z < ze && ok; ++z) {
+    ok = admit(up, lo, ce);
+    __syncthreads();
+    if (!ok) break;
+    if (z + 2 <= ze) issue(nx, z + 2);
+    // the staged box starts one column left of k_ops3's: read it shifted by one
+    if (fix) {
+      if (inner_tile)
+        compute_plane<true, OP, true>(a, z, (int)x0, (int)y0, R, slot(lo) + 1, slot(ce) + 1, slot(up) + 1, rr, ff);
+      else
+        compute_plane<true, OP, false>(a, z, (int)x0, (int)y0, R, slot(lo) + 1, slot(ce) + 1, slot(up) + 1, rr,
+                                       ff);
+    } else {
+      compute_plane<false, OP, false>(a, z, (int)x0, (int)y0, R, slot(lo) + 1, slot(ce) + 1, slot(up) + 1, rr, ff);
+    }
+    __syncthreads();
+    const int t = lo;
+    lo = ce;
+    ce = up;
+    up = nx;
+    nx = t;
+  }
+  // a wait ran out: the results are incomplete and the flag records it; the CTA still
+  // takes part in the norm reduction so that its counter stays consistent
+  if (!ok && threadIdx.x == 0) atomicExch(&g_ops3_tma_error, 1u);
+  if (OP == OP_RESIDUAL) ops3_reduce_norms(a, rr, ff, sh2, &last);
 }
 
 int ops_cz(const Geo &q) {
@@ -348,9 +475,22 @@ cudaError_t launch_op(const OpArgs &a, cudaStream_t s) {
   if (a.q.plane >= ((int64_t)1 << 31) - OS_W * OS_H) return cudaErrorInvalidValue;
   OpArgs b = a;
   b.cz = ops_cz(a.q);
-  k_ops3<OP><<<g, O_THREADS, O_SMEM, s>>>(b);
+  CUtensorMap map;
+  if (tma_plane_map(a.q, a.u, OS_W, OS_H, &map)) {
+    constexpr size_t smem_t = 4 * (size_t)OS_H * OS_W * sizeof(long long) + 128;
+    static bool attr_t = false;
+    if (!attr_t) {
+      cudaError_t e = cudaFuncSetAttribute(k_ops3t<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
+      if (e != cudaSuccess) return e;
+      attr_t = true;
+    }
+    k_ops3t<OP><<<g, O_THREADS, smem_t, s>>>(b, map);
+  } else {
+    k_ops3<OP><<<g, O_THREADS, O_SMEM, s>>>(b);
+  }
   return cudaGetLastError();
 }
+
 
 }  // namespace
 
