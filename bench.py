@@ -246,7 +246,7 @@ def traffic_from_profiles(kernel_key, units_per_launch):
         return None
     sha = hashlib.sha256()
     for fn in sorted(os.listdir(src)):
-        if fn.endswith((".cu", ".h")):
+        if fn.endswith((".cu", ".cuh", ".h")):
             sha.update(open(os.path.join(src, fn), "rb").read())
     cur = sha.hexdigest()[:16]
     for line in open(path):
