@@ -7,9 +7,12 @@
 // Values are int64 fixed point (fixed.cuh); N is formed from column sums
 //   V = u(j-1) + u(j+1),  T = V + u(j),  N(x) = T(x-1) + T(x+1) + V(x).
 //
-// Each warp owns a segment of 32 consecutive columns and streams down a chunk of rows,
-// keeping the rows it needs in registers and reaching x-neighbours by shuffles; no
-// shared memory and no block barriers.  For the single-pass operations the fixed-point
+// Each warp owns a window of 64 consecutive columns, two per lane (an even and an odd
+// x), and streams down a chunk of rows, keeping the rows it needs in registers and
+// reaching x-neighbours by shuffles; no shared memory and no block barriers (the
+// single-sweep FP64-adaptive Gauss-Seidel kernel keeps one column per lane).  Rows move
+// as 16-byte pairs where the arrays are 16-byte aligned with an even pitch.  For the
+// single-pass operations the fixed-point
 // reference R is per warp and only grows: every newly loaded row is reduced to its
 // largest exponent first, and when that exceeds R the rows held so far are shifted to
 // the new scale.  A warp that meets
@@ -31,6 +34,11 @@ constexpr int S2_ROWS = 256;  // rows per warp (multi-sweep GS and Jacobi)
 constexpr int R_MIN = -900, R_MAX = 1000;
 
 enum { O2_APPLY = 0, O2_JACOBI = 1, O2_RESIDUAL = 2, O2_ELEMENTWISE = 3 };
+
+// Per operation: convert the fixed-point result with the FP64 pipe (true) or with
+// integer instructions (false), whichever measured faster (the element-wise apply
+// always uses the FP64 pipe).
+constexpr bool OP2_CVT[4] = {true, true, false, true};
 
 struct Op2Args {
   Geo q;
@@ -78,111 +86,195 @@ __device__ __forceinline__ long long add(long long a, long long b) {
   return __double_as_longlong(__longlong_as_double(a) + __longlong_as_double(b));
 }
 
-// 8u - N at this lane's column (3 S u), from the rows above (m), at (c) and below (p).
-template <bool FIX>
-__device__ __forceinline__ long long eight_u_minus_n(long long m, long long c, long long p) {
-  const long long V = add<FIX>(m, p);
-  const long long T = add<FIX>(V, c);
-  const long long Tm = __shfl_up_sync(0xffffffffu, T, 1);
-  const long long Tp = __shfl_down_sync(0xffffffffu, T, 1);
-  const long long N = add<FIX>(add<FIX>(Tm, Tp), V);
-  if (FIX) return 8 * c - N;
-  return __double_as_longlong(fma(8.0, __longlong_as_double(c), -__longlong_as_double(N)));
+// ------------------------------------------------------------------ lane pairs
+// Each lane owns two adjacent columns, xa (even x) and xb = xa + 1, of its warp's
+// 64-column window; rows move as 16-byte pairs when the arrays allow it (V16: 16-byte
+// aligned bases, even pitch).  A neighbour across the pair boundary comes from the
+// adjacent lane by one 64-bit shuffle.
+struct Pair {
+  long long a, b;  // columns xa (even x) and xb (odd x)
+};
+
+// Columns of one lane and their validity.
+struct Cols {
+  int64_t xa;
+  bool oka, okb;  // inside the row (0 <= x <= nx)
+  bool ina, inb;  // interior column (1 <= x < nx)
+};
+
+__device__ __forceinline__ Cols make_cols(const Geo &q, int64_t xa) {
+  Cols c;
+  c.xa = xa;
+  c.oka = xa >= 0 && xa <= q.nx;
+  c.okb = xa + 1 >= 0 && xa + 1 <= q.nx;
+  c.ina = xa >= 1 && xa < q.nx;
+  c.inb = xa + 1 >= 1 && xa + 1 < q.nx;
+  return c;
 }
 
-constexpr int PF = 3;  // rows in flight per warp
+// Raw 64-bit pair of row pointer `row` (zeros outside the row).
+template <bool V16>
+__device__ __forceinline__ Pair ld_pair(const long long *__restrict__ row, const Cols &c) {
+  Pair p{0ll, 0ll};
+  if (V16 && c.oka && c.okb) {
+    const longlong2 v = *(const longlong2 *)(row + c.xa);
+    p.a = v.x;
+    p.b = v.y;
+  } else {
+    if (c.oka) p.a = row[c.xa];
+    if (c.okb) p.b = row[c.xa + 1];
+  }
+  return p;
+}
+
+template <bool V16>
+__device__ __forceinline__ void st_pair(long long *__restrict__ row, const Cols &c, bool wa, bool wb, long long a,
+                                        long long b) {
+  if (V16 && wa && wb) {
+    *(longlong2 *)(row + c.xa) = make_longlong2(a, b);
+  } else {
+    if (wa) row[c.xa] = a;
+    if (wb) row[c.xa + 1] = b;
+  }
+}
+
+__device__ __forceinline__ unsigned pair_exp(const Pair &r) {
+  return max(biased_exp(__longlong_as_double(r.a)), biased_exp(__longlong_as_double(r.b)));
+}
+
+template <bool FIX>
+__device__ __forceinline__ Pair pair_in(const Pair &raw, const WarpScale &w) {
+  if (!FIX) return raw;
+  return Pair{fx::to_fixed(__longlong_as_double(raw.a), 1023 + w.R), fx::to_fixed(__longlong_as_double(raw.b), 1023 + w.R)};
+}
+
+__device__ __forceinline__ Pair pair_shr(const Pair &p, int d) { return Pair{shr(p.a, d), shr(p.b, d)}; }
+
+__device__ __forceinline__ Pair pair_f64(const Pair &p, int R) { return Pair{to_f64_bits(p.a, R), to_f64_bits(p.b, R)}; }
+
+// 8u - N (3 S u) at both columns from the rows above (m), at (c) and below (p):
+//   V = m + p,  T = V + c,  N(x) = (T(x-1) + T(x+1)) + V(x).
+template <bool FIX>
+__device__ __forceinline__ Pair eight_u_minus_n(const Pair &m, const Pair &c, const Pair &p) {
+  const Pair V{add<FIX>(m.a, p.a), add<FIX>(m.b, p.b)};
+  const Pair T{add<FIX>(V.a, c.a), add<FIX>(V.b, c.b)};
+  const long long Tbl = __shfl_up_sync(0xffffffffu, T.b, 1);   // T(xa - 1)
+  const long long Tar = __shfl_down_sync(0xffffffffu, T.a, 1); // T(xb + 1)
+  const long long Na = add<FIX>(add<FIX>(Tbl, T.b), V.a), Nb = add<FIX>(add<FIX>(T.a, Tar), V.b);
+  if (FIX) return Pair{8 * c.a - Na, 8 * c.b - Nb};
+  return Pair{__double_as_longlong(fma(8.0, __longlong_as_double(c.a), -__longlong_as_double(Na))),
+              __double_as_longlong(fma(8.0, __longlong_as_double(c.b), -__longlong_as_double(Nb)))};
+}
+
+constexpr int PF = 2;      // rows in flight per warp
+constexpr int OPS2_OUT = 60;  // output columns per warp: lanes 1..30 (one halo column per side)
 
 // Per-warp streaming state of k_ops2.
 struct Stream2 {
-  int64_t x;
-  bool xok, xin, out_lane;
+  Cols c;
+  bool out_lane;
   int lane;
-  long long um, uc, up;  // converted rows j-1, j, j+1 (element-wise: ua = uc, acc = um/up)
-  double rc, rp;         // raw rows j, j+1
+  Pair um, uc, up;  // converted rows j-1, j, j+1 (element-wise: ua = uc, accumulators um/up)
+  Pair rc, rp;      // raw rows j, j+1 (FP64 bits)
   double rr, ff;
 };
 
-// Element-wise apply: cell rows cj in [cj0, je); returns the first row not done (a
-// switch to FP64 was requested) or je.
+// Element matrix 6 K_e of one cell times its vertex values v0 = (x, y), v1 = (x+1, y),
+// v2 = (x, y+1), v3 = (x+1, y+1): 4 v_w - (the two face-adjacent values) - 2 v_opposite.
 template <bool FIX>
+__device__ __forceinline__ void cell_contrib(long long v0, long long v1, long long v2, long long v3, long long &c0,
+                                             long long &c1, long long &c2, long long &c3) {
+  if (FIX) {
+    const long long s1 = v1 + v2, s2 = v0 + v3;
+    c0 = 4 * v0 - s1 - 2 * v3;
+    c1 = 4 * v1 - s2 - 2 * v2;
+    c2 = 4 * v2 - s2 - 2 * v1;
+    c3 = 4 * v3 - s1 - 2 * v0;
+  } else {
+    const double A0 = __longlong_as_double(v0), A1 = __longlong_as_double(v1), A2 = __longlong_as_double(v2),
+                 A3 = __longlong_as_double(v3);
+    c0 = __double_as_longlong(4.0 * A0 - (A1 + A2) - 2.0 * A3);
+    c1 = __double_as_longlong(4.0 * A1 - (A0 + A3) - 2.0 * A2);
+    c2 = __double_as_longlong(4.0 * A2 - (A0 + A3) - 2.0 * A1);
+    c3 = __double_as_longlong(4.0 * A3 - (A1 + A2) - 2.0 * A0);
+  }
+}
+
+// Element-wise apply: cell rows cj in [cj0, je); returns the first row not done (a
+// switch to FP64 was requested) or je.  The lane's cells are A (lower-left vertex xa:
+// all four vertices in this lane) and B (lower-left vertex xb: its right vertices are
+// the next lane's xa).  Each vertex column is owned by one lane, which adds the shares
+// of the cells on both of its sides (B of the lane to the left arrives by shuffle), so
+// the scatter has no write conflicts.  In fixed point the sums are exact, so the order
+// of the two x colours is immaterial; the FP64 path adds the even-x colour's share
+// first.
+template <bool FIX, bool V16>
 __device__ __forceinline__ int64_t ew2_rows(const Op2Args &a, WarpScale &w, Stream2 &s, int64_t cj0, int64_t js,
                                             int64_t je) {
   const Geo &q = a.q;
-  const double *ucol = a.u + (s.xok ? s.x : 0);
-  long long &ua = s.uc, &alo = s.um, &ahi = s.up;
-  double qb[PF];  // qb[t]: raw vertex row cj + 1 for the iteration cj = cb + t
+  const Cols &c = s.c;
+  const long long *ub_ = (const long long *)a.u;
+  Pair &ua = s.uc, &alo = s.um, &ahi = s.up;
+  // output scale c1 2^(R-52), re-formed only when R changes (an FP64 multiply per
+  // output would otherwise load the FP64 pipe, this kernel's bottleneck)
+  double sc = FIX ? a.c1 * fx::pow2d(w.R - fx::FRAC) : a.c1;
+  auto raw = [&](int64_t j) -> Pair {
+    return (j >= 0 && j <= q.ny) ? ld_pair<V16>(ub_ + j * q.pitch, c) : Pair{0ll, 0ll};
+  };
+  Pair qb[PF];  // qb[t]: raw vertex row cj + 1 for the iteration cj = cb + t
 #pragma unroll
-  for (int t = 0; t < PF; ++t)
-    qb[t] = (s.xok && cj0 + 1 + t <= q.ny && cj0 + 1 + t >= 0) ? ucol[(cj0 + 1 + t) * q.pitch] : 0.0;
+  for (int t = 0; t < PF; ++t) qb[t] = raw(cj0 + 1 + t);
   for (int64_t cb = cj0; cb < je; cb += PF) {
 #pragma unroll
     for (int t = 0; t < PF; ++t) {
       const int64_t cj = cb + t;
       if (cj >= je) return je;
-      const int slot = t;
-      const double rb = qb[slot];
-      const unsigned em = __reduce_max_sync(0xffffffffu, biased_exp(rb));
+      const Pair rb = qb[t];
+      const unsigned em = __reduce_max_sync(0xffffffffu, pair_exp(rb));
       if (FIX) {
         const int d = admit_row(w, em, 1);
         if (d < 0) {  // leave this row to the FP64 loop
-          ua = to_f64_bits(ua, w.R);
-          alo = to_f64_bits(alo, w.R);
-          ahi = to_f64_bits(ahi, w.R);
+          ua = pair_f64(ua, w.R);
+          alo = pair_f64(alo, w.R);
+          ahi = pair_f64(ahi, w.R);
           w.fix = false;
           return cj;
         }
         if (d > 0) {
-          ua = shr(ua, d);
-          alo = shr(alo, d);
-          ahi = shr(ahi, d);
+          ua = pair_shr(ua, d);
+          alo = pair_shr(alo, d);
+          ahi = pair_shr(ahi, d);
+          sc = a.c1 * fx::pow2d(w.R - fx::FRAC);
         }
       }
-      qb[slot] = (cj + 1 + PF <= je && s.xok && cj + 1 + PF <= q.ny) ? ucol[(cj + 1 + PF) * q.pitch] : 0.0;
-      const long long ub = FIX ? fx::to_fixed(rb, 1023 + w.R) : __double_as_longlong(rb);
-      // cell with lower-left vertex (x, cj): v0 = (x,cj), v1 = (x+1,cj), v2 = (x,cj+1),
-      // v3 = (x+1,cj+1); 6 (K u)_w = 4 u_w - (face-adjacent pair) - 2 u_opposite
-      const long long v1 = __shfl_down_sync(0xffffffffu, ua, 1);
-      const long long v3 = __shfl_down_sync(0xffffffffu, ub, 1);
-      const bool cell = s.lane <= 30 && s.x >= 0 && s.x < q.nx && cj >= 0 && cj < q.ny;
-      // Every lane forms its own cell's four contributions; each vertex column is owned
-      // by one lane, which adds the share of its own cell and (by shuffle) that of the
-      // cell on its left, so the scatter has no write conflicts.  In fixed point the
-      // sums are exact, so the order of the two x colours is immaterial; the FP64 path
-      // adds the even-x colour's share first.
-      long long c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-      if (cell) {
-        if (FIX) {
-          const long long s1 = v1 + ub, s2 = ua + v3;
-          c0 = 4 * ua - s1 - 2 * v3;
-          c1 = 4 * v1 - s2 - 2 * ub;
-          c2 = 4 * ub - s2 - 2 * v1;
-          c3 = 4 * v3 - s1 - 2 * ua;
-        } else {
-          const double A0 = __longlong_as_double(ua), A1 = __longlong_as_double(v1),
-                       A2 = __longlong_as_double(ub), A3 = __longlong_as_double(v3);
-          c0 = __double_as_longlong(4.0 * A0 - (A1 + A2) - 2.0 * A3);
-          c1 = __double_as_longlong(4.0 * A1 - (A0 + A3) - 2.0 * A2);
-          c2 = __double_as_longlong(4.0 * A2 - (A0 + A3) - 2.0 * A1);
-          c3 = __double_as_longlong(4.0 * A3 - (A1 + A2) - 2.0 * A0);
-        }
-      }
-      long long c1l = __shfl_up_sync(0xffffffffu, c1, 1), c3l = __shfl_up_sync(0xffffffffu, c3, 1);
-      if (s.lane == 0) c1l = c3l = 0;
-      if (FIX || (s.x & 1) == 0) {  // own cell has the even-x colour: it goes first
-        alo = add<FIX>(add<FIX>(alo, c0), c1l);
-        ahi = add<FIX>(add<FIX>(ahi, c2), c3l);
-      } else {
-        alo = add<FIX>(add<FIX>(alo, c1l), c0);
-        ahi = add<FIX>(add<FIX>(ahi, c3l), c2);
-      }
-      if (cj >= js && s.out_lane) {
-        const bool inner = s.xin && cj >= 1 && cj < q.ny;
-        // FIX: 2^(R-52) c1 times the converted sum (exact power-of-two scaling of c1)
-        const double sv = FIX ? __ll2double_rn(alo) : __longlong_as_double(alo);
-        a.out[cj * q.pitch + s.x] = inner ? sv * (FIX ? a.c1 * fx::pow2d(w.R - fx::FRAC) : a.c1) : 0.0;
+      qb[t] = cj + 1 + PF <= je ? raw(cj + 1 + PF) : Pair{0ll, 0ll};
+      const Pair ub = pair_in<FIX>(rb, w);
+      const long long uar = __shfl_down_sync(0xffffffffu, ua.a, 1);  // (xb + 1, cj)
+      const long long ubr = __shfl_down_sync(0xffffffffu, ub.a, 1);  // (xb + 1, cj + 1)
+      const bool crow = cj >= 0 && cj < q.ny;
+      const bool cellA = crow && c.xa >= 0 && c.xa < q.nx;
+      const bool cellB = crow && s.lane <= 30 && c.xa + 1 >= 0 && c.xa + 1 < q.nx;
+      long long a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+      if (cellA) cell_contrib<FIX>(ua.a, ua.b, ub.a, ub.b, a0, a1, a2, a3);
+      if (cellB) cell_contrib<FIX>(ua.b, uar, ub.b, ubr, b0, b1, b2, b3);
+      long long b1l = __shfl_up_sync(0xffffffffu, b1, 1), b3l = __shfl_up_sync(0xffffffffu, b3, 1);
+      if (s.lane == 0) b1l = b3l = 0;
+      // vertex xa: cell A (even x) then the left lane's cell B; vertex xb: A then B
+      alo.a = add<FIX>(add<FIX>(alo.a, a0), b1l);
+      ahi.a = add<FIX>(add<FIX>(ahi.a, a2), b3l);
+      alo.b = add<FIX>(add<FIX>(alo.b, a1), b0);
+      ahi.b = add<FIX>(add<FIX>(ahi.b, a3), b2);
+      if (cj >= js) {
+        const bool jin = cj >= 1 && cj < q.ny;
+        // FIX: the converted sum times c1 2^(R-52) (exact power-of-two scaling of c1)
+        const double va = FIX ? __ll2double_rn(alo.a) : __longlong_as_double(alo.a);
+        const double vb = FIX ? __ll2double_rn(alo.b) : __longlong_as_double(alo.b);
+        st_pair<V16>((long long *)a.out + cj * q.pitch, c, s.out_lane && c.oka, s.out_lane && c.okb,
+                     __double_as_longlong(jin && c.ina ? va * sc : 0.0),
+                     __double_as_longlong(jin && c.inb ? vb * sc : 0.0));
       }
       alo = ahi;
-      ahi = 0;
+      ahi = Pair{0ll, 0ll};
       ua = ub;
     }
   }
@@ -190,70 +282,93 @@ __device__ __forceinline__ int64_t ew2_rows(const Op2Args &a, WarpScale &w, Stre
 }
 
 // Assembled apply / Jacobi / residual: output rows j in [j0, je).
-template <bool FIX, int OP>
+template <bool FIX, int OP, bool V16>
 __device__ __forceinline__ int64_t op2_rows(const Op2Args &a, WarpScale &w, Stream2 &s, int64_t j0, int64_t js,
                                             int64_t je) {
   const Geo &q = a.q;
-  const double *ucol = a.u + (s.xok ? s.x : 0);
-  const double *fcol = a.f ? a.f + (s.xok ? s.x : 0) : nullptr;
-  double *ocol = a.out ? a.out + (s.xok ? s.x : 0) : nullptr;
-  double qb[PF];  // qb[t]: raw row j + 2 for the iteration j = jb + t
+  const Cols &c = s.c;
+  const long long *ub_ = (const long long *)a.u;
+  const long long *fb_ = (const long long *)a.f;
+  long long *ob_ = (long long *)a.out;
+  // CVT: T is converted by the FP64 pipe and multiplied by the factor of its term times
+  // 2^(R-52) (re-formed only when R changes); otherwise by fx::to_double on the integer
+  // pipe.  Both give the same bits.
+  constexpr bool CVT = OP2_CVT[OP];
+  const double cf = OP == O2_JACOBI ? a.c2 : a.c1;  // factor of the converted term
+  double sc = FIX && CVT ? cf * fx::pow2d(w.R - fx::FRAC) : cf;
+  auto raw = [&](int64_t j) -> Pair {
+    return (j >= 0 && j <= q.ny) ? ld_pair<V16>(ub_ + j * q.pitch, c) : Pair{0ll, 0ll};
+  };
+  Pair qb[PF];  // qb[t]: raw row j + 2 for the iteration j = jb + t
 #pragma unroll
-  for (int t = 0; t < PF; ++t) qb[t] = (s.xok && j0 + 2 + t <= q.ny) ? ucol[(j0 + 2 + t) * q.pitch] : 0.0;
+  for (int t = 0; t < PF; ++t) qb[t] = raw(j0 + 2 + t);
   for (int64_t jb = j0; jb < je; jb += PF) {
 #pragma unroll
     for (int t = 0; t < PF; ++t) {
       const int64_t j = jb + t;
       if (j >= je) return je;
-      const int slot = t;
-      const double rn = qb[slot];  // row j + 2
-      const unsigned em = __reduce_max_sync(0xffffffffu, biased_exp(rn));
-      const bool inner = s.xin && j >= 1 && j < q.ny;
-      double fv = 0.0;
-      if (OP != O2_APPLY && s.out_lane && inner) fv = fcol[j * q.pitch];
-      const long long T = eight_u_minus_n<FIX>(s.um, s.uc, s.up);
+      const Pair rn = qb[t];  // row j + 2
+      const unsigned em = __reduce_max_sync(0xffffffffu, pair_exp(rn));
+      const bool jin = j >= 1 && j < q.ny;
+      Pair fv{0ll, 0ll};  // FP64 bits
+      if (OP != O2_APPLY && s.out_lane && jin) fv = ld_pair<V16>(fb_ + j * q.pitch, c);
+      const Pair T = eight_u_minus_n<FIX>(s.um, s.uc, s.up);
       if (s.out_lane) {
-        // converted on the integer pipe here (measured faster than the FP64 pipe's
-        // conversion for these three operations; the element-wise apply uses the latter)
-        const double Td = inner ? (FIX ? fx::to_double(T, w.R - fx::FRAC) : __longlong_as_double(T)) : 0.0;
-        const int64_t go = j * q.pitch;
+        const bool ia = jin && c.ina, ib = jin && c.inb;
+        // Td * sc == T's value times the term's factor
+        auto conv = [&](long long v) -> double {
+          return !FIX ? __longlong_as_double(v) : CVT ? __ll2double_rn(v) : fx::to_double(v, w.R - fx::FRAC);
+        };
+        const double Ta = ia ? conv(T.a) : 0.0, Tb = ib ? conv(T.b) : 0.0;
+        const double fa = __longlong_as_double(fv.a), fb = __longlong_as_double(fv.b);
+        const double rca = __longlong_as_double(s.rc.a), rcb = __longlong_as_double(s.rc.b);
+        double oa, ob;
         if (OP == O2_APPLY) {
-          ocol[go] = inner ? Td * a.c1 : 0.0;
+          oa = ia ? Ta * sc : 0.0;
+          ob = ib ? Tb * sc : 0.0;
         } else if (OP == O2_JACOBI) {
-          ocol[go] = inner ? fma(a.c2, Td, fma(a.c1, fv, s.rc)) : s.rc;
+          oa = ia ? fma(sc, Ta, fma(a.c1, fa, rca)) : rca;
+          ob = ib ? fma(sc, Tb, fma(a.c1, fb, rcb)) : rcb;
         } else {
-          const double r = inner ? fma(a.c1, Td, fv) : 0.0;
-          if (ocol) ocol[go] = r;
-          if (inner) {
-            s.rr = fma(r, r, s.rr);
-            s.ff = fma(fv, fv, s.ff);
+          oa = ia ? fma(sc, Ta, fa) : 0.0;
+          ob = ib ? fma(sc, Tb, fb) : 0.0;
+          if (ia) {
+            s.rr = fma(oa, oa, s.rr);
+            s.ff = fma(fa, fa, s.ff);
+          }
+          if (ib) {
+            s.rr = fma(ob, ob, s.rr);
+            s.ff = fma(fb, fb, s.ff);
           }
         }
+        if (OP != O2_RESIDUAL || ob_)
+          st_pair<V16>(ob_ + j * q.pitch, c, c.oka, c.okb, __double_as_longlong(oa), __double_as_longlong(ob));
       }
       // admit row j + 2 (after row j is done)
       if (FIX) {
         const int d = admit_row(w, em, 1);
         if (d < 0) {
-          s.uc = to_f64_bits(s.uc, w.R);
-          s.up = to_f64_bits(s.up, w.R);
+          s.uc = pair_f64(s.uc, w.R);
+          s.up = pair_f64(s.up, w.R);
           w.fix = false;
           // row j is finished; rows j+1, j+2 continue in FP64 (rn still in the queue)
           s.um = s.uc;
           s.uc = s.up;
-          s.up = __double_as_longlong(rn);
+          s.up = rn;
           s.rc = s.rp;
           s.rp = rn;
           return j + 1;
         }
         if (d > 0) {
-          s.uc = shr(s.uc, d);
-          s.up = shr(s.up, d);
+          s.uc = pair_shr(s.uc, d);
+          s.up = pair_shr(s.up, d);
+          if (CVT) sc = cf * fx::pow2d(w.R - fx::FRAC);
         }
       }
-      qb[slot] = (j + 2 + PF <= je && s.xok && j + 2 + PF <= q.ny) ? ucol[(j + 2 + PF) * q.pitch] : 0.0;
+      qb[t] = j + 2 + PF <= je ? raw(j + 2 + PF) : Pair{0ll, 0ll};
       s.um = s.uc;
       s.uc = s.up;
-      s.up = FIX ? fx::to_fixed(rn, 1023 + w.R) : __double_as_longlong(rn);
+      s.up = pair_in<FIX>(rn, w);
       s.rc = s.rp;
       s.rp = rn;
     }
@@ -261,59 +376,64 @@ __device__ __forceinline__ int64_t op2_rows(const Op2Args &a, WarpScale &w, Stre
   return je;
 }
 
-// One warp's share of k_ops2: a segment of 30 output columns and a chunk of rows.
-template <int OP>
+// Work units of the single-pass 2D operations: 60-column segments x chunks of `rows`.
+__host__ __device__ __forceinline__ int64_t ops2_units(const Geo &q, int rows) {
+  return (int64_t)((q.nx + OPS2_OUT) / OPS2_OUT) * ((q.ny + rows) / rows);
+}
+
+// One warp's share of k_ops2: a segment of 60 output columns and a chunk of rows.
+template <int OP, bool V16>
 __device__ __forceinline__ void ops2_warp(const Op2Args &a, int lane, int64_t gw, Stream2 &s, int rows) {
   const Geo &q = a.q;
-  const int64_t nseg = (q.nx + 30) / 30;  // 30 outputs per segment
+  const int64_t nseg = (q.nx + OPS2_OUT) / OPS2_OUT;
   const int64_t seg = gw % nseg, chunk = gw / nseg;
   const int64_t js = chunk * rows;
   const int64_t je = js + rows < q.ny + 1 ? js + rows : q.ny + 1;
   s.lane = lane;
-  s.x = seg * 30 + lane - 1;  // lanes 1..30 produce outputs
-  s.xok = s.x >= 0 && s.x <= q.nx;
-  s.xin = s.x >= 1 && s.x < q.nx;
-  s.out_lane = lane >= 1 && lane <= 30 && s.xok;
+  s.c = make_cols(q, seg * OPS2_OUT - 2 + 2 * lane);  // lanes 1..30 produce outputs
+  s.out_lane = lane >= 1 && lane <= 30;
   s.rr = 0.0;
   s.ff = 0.0;
   WarpScale w;
   if (js <= q.ny) {
-    const double *ucol = a.u + (s.xok ? s.x : 0);
-    auto load = [&](int64_t j) -> double { return (s.xok && j >= 0 && j <= q.ny) ? ucol[j * q.pitch] : 0.0; };
+    const long long *ub_ = (const long long *)a.u;
+    auto load = [&](int64_t j) -> Pair {
+      return (j >= 0 && j <= q.ny) ? ld_pair<V16>(ub_ + j * q.pitch, s.c) : Pair{0ll, 0ll};
+    };
     if (OP == O2_ELEMENTWISE) {
-      const double ra = load(js - 1);
-      if (admit_row(w, __reduce_max_sync(0xffffffffu, biased_exp(ra)), 1) < 0) w.fix = false;
-      s.uc = w.fix ? fx::to_fixed(ra, 1023 + w.R) : __double_as_longlong(ra);
-      s.um = 0;
-      s.up = 0;
+      const Pair ra = load(js - 1);
+      if (admit_row(w, __reduce_max_sync(0xffffffffu, pair_exp(ra)), 1) < 0) w.fix = false;
+      s.uc = w.fix ? pair_in<true>(ra, w) : ra;
+      s.um = Pair{0ll, 0ll};
+      s.up = Pair{0ll, 0ll};
       int64_t cj = js - 1;
-      if (w.fix) cj = ew2_rows<true>(a, w, s, cj, js, je);
-      if (cj < je) ew2_rows<false>(a, w, s, cj, js, je);
+      if (w.fix) cj = ew2_rows<true, V16>(a, w, s, cj, js, je);
+      if (cj < je) ew2_rows<false, V16>(a, w, s, cj, js, je);
     } else {
       s.rc = load(js);
       s.rp = load(js + 1);
-      const double rm = load(js - 1);
-      unsigned em = __reduce_max_sync(0xffffffffu, biased_exp(rm));
-      em = max(em, __reduce_max_sync(0xffffffffu, biased_exp(s.rc)));
-      em = max(em, __reduce_max_sync(0xffffffffu, biased_exp(s.rp)));
+      const Pair rm = load(js - 1);
+      unsigned em = __reduce_max_sync(0xffffffffu, pair_exp(rm));
+      em = max(em, __reduce_max_sync(0xffffffffu, pair_exp(s.rc)));
+      em = max(em, __reduce_max_sync(0xffffffffu, pair_exp(s.rp)));
       if (admit_row(w, em, 1) < 0) w.fix = false;
-      s.um = w.fix ? fx::to_fixed(rm, 1023 + w.R) : __double_as_longlong(rm);
-      s.uc = w.fix ? fx::to_fixed(s.rc, 1023 + w.R) : __double_as_longlong(s.rc);
-      s.up = w.fix ? fx::to_fixed(s.rp, 1023 + w.R) : __double_as_longlong(s.rp);
+      s.um = w.fix ? pair_in<true>(rm, w) : rm;
+      s.uc = w.fix ? pair_in<true>(s.rc, w) : s.rc;
+      s.up = w.fix ? pair_in<true>(s.rp, w) : s.rp;
       int64_t j = js;
-      if (w.fix) j = op2_rows<true, OP>(a, w, s, j, js, je);
-      if (j < je) op2_rows<false, OP>(a, w, s, j, js, je);
+      if (w.fix) j = op2_rows<true, OP, V16>(a, w, s, j, js, je);
+      if (j < je) op2_rows<false, OP, V16>(a, w, s, j, js, je);
     }
   }
 }
 
-template <int OP>
+template <int OP, bool V16>
 __global__ void __launch_bounds__(W2_THREADS) k_ops2(Op2Args a) {
   __shared__ double sh[2 * W2_THREADS / 32];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   Stream2 s;
-  ops2_warp<OP>(a, lane, (int64_t)blockIdx.x * (W2_THREADS / 32) + wib, s, W2_ROWS);
+  ops2_warp<OP, V16>(a, lane, (int64_t)blockIdx.x * (W2_THREADS / 32) + wib, s, W2_ROWS);
   double rr = s.rr, ff = s.ff;
   if (OP == O2_RESIDUAL) {
 #pragma unroll
@@ -370,9 +490,7 @@ __global__ void __launch_bounds__(W2_THREADS) k_ops2(Op2Args a) {
 }
 
 unsigned ops2_blocks(const Geo &q) {
-  const int64_t nseg = (q.nx + 30) / 30;
-  const int64_t nchunk = (q.ny + W2_ROWS) / W2_ROWS;
-  return (unsigned)((nseg * nchunk + W2_THREADS / 32 - 1) / (W2_THREADS / 32));
+  return (unsigned)((ops2_units(q, W2_ROWS) + W2_THREADS / 32 - 1) / (W2_THREADS / 32));
 }
 
 // ------------------------------------------------------------------ Gauss-Seidel
@@ -525,123 +643,173 @@ __global__ void __launch_bounds__(W2_THREADS) k_gs2_fused(Geo q, const double *_
 // scale shared by the whole grid and tracked on the device (sweep_bounds.cuh), and
 // 3/8 h^2 f is precomputed once per call as fixed point (GF).  A sweep is then integer
 // arithmetic only: no conversion per element except on the first load from u and the
-// last store into u.  Same row wavefront as above.
+// last store into u.
+//
+// Each lane owns two adjacent columns, xa (even x) and xb = xa + 1 (odd x), so a colour
+// step that updates one x parity touches exactly one of the lane's columns and takes
+// one neighbour from an adjacent lane (one 64-bit shuffle); rows move as 16-byte
+// pairs when the arrays allow it (V16: 16-byte aligned base, even pitch).
 enum { SF_F64 = 0, SF_FXP = 1 };  // storage format: FP64, or int64 fixed point
 
-__device__ __forceinline__ void colour_pair_gs(long long &uc, long long V, long long gv, bool xin, int64_t x) {
-#pragma unroll
-  for (int px = 0; px < 2; ++px) {
-    const long long T = V + uc;
-    const long long Tm = __shfl_up_sync(0xffffffffu, T, 1);
-    const long long Tp = __shfl_down_sync(0xffffffffu, T, 1);
-    if (xin && (int)(x & 1) == px) uc = gv + ((Tm + Tp + V) >> 3);  // 3/8 h^2 f + N / 8
+// High word of |v| (ones' complement: |v| or |v| - 1), an upper bound of |v| / 2^32 - 1
+// in 3 integer instructions; the sweeps track max |u| through it.
+__device__ __forceinline__ unsigned mag_hi(long long v) {
+  const int hi = (int)(v >> 32);
+  return (unsigned)(hi ^ (hi >> 31));
+}
+
+// Store one row pair of the new iterate (fixed point, or FP64 for the call's last
+// sweep) and fold its magnitude into hmax.
+template <int YF, bool V16>
+__device__ __forceinline__ void put_pair(const Geo &q, void *Y, int64_t j, const Cols &c, bool out_lane,
+                                         bool write_bnd, int R, const Pair &v, unsigned &hmax) {
+  const bool jin = j >= 1 && j < q.ny;
+  const bool wa = out_lane && c.oka && ((c.ina && jin) || write_bnd);
+  const bool wb = out_lane && c.okb && ((c.inb && jin) || write_bnd);
+  const int64_t ro = j * q.pitch;
+  if (YF == SF_FXP) {
+    st_pair<V16>((long long *)Y + ro, c, wa, wb, v.a, v.b);
+  } else {
+    const double da = fx::to_double_cvt(v.a, R - fx::FRAC), db = fx::to_double_cvt(v.b, R - fx::FRAC);
+    st_pair<V16>((long long *)Y + ro, c, wa, wb, __double_as_longlong(da), __double_as_longlong(db));
+  }
+  const unsigned ha = wa ? mag_hi(v.a) : 0u, hb = wb ? mag_hi(v.b) : 0u;
+  hmax = max(hmax, max(ha, hb));
+}
+
+// Block max of the magnitude words -> FP64 bits -> the bound slot of the next sweep.
+__device__ __forceinline__ void publish_bound(SweepBounds *bnd, int slot, int R, unsigned hmax, unsigned *red) {
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  hmax = __reduce_max_sync(0xffffffffu, hmax);
+  if (lane == 0) red[wib] = hmax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned m = 0;
+    for (int w = 0; w < W2_THREADS / 32; ++w) m = red[w] > m ? red[w] : m;
+    // every |v| written is < (m + 1) 2^32
+    const long long ub = (long long)(((unsigned long long)m + 1ull) << 32);
+    atomicMax(&bnd->umax[slot], fx::abs_bits(fx::to_double(ub, R - fx::FRAC) * (1.0 + 0x1p-50)));
   }
 }
 
-template <int XF, int YF>
+// Converts raw input values of format XF to this sweep's scale.
+template <int XF>
+struct InScale {
+  int rb, dxr, dxl;
+  __device__ __forceinline__ long long operator()(long long raw) const {
+    return XF == SF_F64 ? fx::to_fixed(__longlong_as_double(raw), rb) : (raw >> dxr) << dxl;
+  }
+  __device__ __forceinline__ Pair operator()(const Pair &p) const { return Pair{(*this)(p.a), (*this)(p.b)}; }
+};
+
+// One colour pair of Gauss-Seidel on a row held as lane pairs: first the even-x
+// column (its x-neighbours: the odd column of the lane to the left and this lane's
+// odd column), then the odd-x column (this lane's new even column and the even column
+// of the lane to the right).  V: sum of the rows above and below; gv: 3/8 h^2 f.
+//   u_new = 3/8 h^2 f + N / 8,  N = T(x-1) + T(x+1) + V(x),  T = V + u.
+__device__ __forceinline__ void gs_pair(Pair &u, const Pair &V, const Pair &gv, const Cols &c) {
+  const long long Tb = V.b + u.b;
+  const long long Tbl = __shfl_up_sync(0xffffffffu, Tb, 1);
+  if (c.ina) u.a = gv.a + ((Tbl + Tb + V.a) >> 3);
+  const long long Ta = V.a + u.a;
+  const long long Tar = __shfl_down_sync(0xffffffffu, Ta, 1);
+  if (c.inb) u.b = gv.b + ((Ta + Tar + V.b) >> 3);
+}
+
+// Gauss-Seidel sweep, single pass over memory (row wavefront inside a warp): for even
+// row j colours 0 (x even) and 1 (x odd) from the old rows j-1, j+1; then odd row j-1,
+// colours 2 and 3, from the new rows j-2 and j.  Every value read is the one the
+// sequential colour order would read.  A warp covers 64 columns; each colour step
+// consumes one column of halo per side, so the 56 columns of lanes 2..29 are produced.
+// A chunk of rows [js, je] (js even) also recomputes its last even row je (which the
+// next chunk owns) so that its last odd row can be finished; chunks are independent.
+constexpr int GS2_OUT = 56;
+
+template <int XF, int YF, bool V16>
 __global__ void __launch_bounds__(W2_THREADS) k_gs2_sweep(Geo q, const void *__restrict__ X, void *__restrict__ Y,
                                                           const double *__restrict__ f,
                                                           const long long *__restrict__ GF, SweepBounds *bnd,
                                                           int sweep, int sweeps, double g, bool write_bnd) {
-  __shared__ long long red[W2_THREADS / 32];
+  __shared__ unsigned red[W2_THREADS / 32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * (W2_THREADS / 32) + wib;
-  const int64_t nseg = (q.nx + 24) / 24;
-  const int64_t seg = gw % nseg, chunk = gw / nseg;
-  const int64_t js = chunk * S2_ROWS;  // even
   const Plan plan = make_plan(bnd, g, sweeps);
   if (!plan.fix) {
-    // bound unusable for fixed point: every sweep of the call keeps FP64 buffers
-    if (js <= q.ny) gs2_fused_warp(q, (const double *)X, (double *)Y, f, g, seg, js, lane, S2_ROWS);
+    // bound unusable for fixed point: every sweep of the call keeps FP64 buffers and
+    // runs the per-warp adaptive kernel's work units (24-column segments), grid-stride
+    const int64_t nseg24 = (q.nx + 24) / 24, units = nseg24 * ((q.ny + S2_ROWS) / S2_ROWS);
+    for (int64_t w = gw; w < units; w += (int64_t)gridDim.x * (W2_THREADS / 32))
+      gs2_fused_warp(q, (const double *)X, (double *)Y, f, g, w % nseg24, (w / nseg24) * S2_ROWS, lane, S2_ROWS);
     return;
   }
   const int R = sweep_R(bnd, sweep % 4, g);
   const int Rx = sweep > 0 ? sweep_R(bnd, (sweep + 3) % 4, g) : R;
-  const int dx = XF == SF_FXP ? R - Rx : 0, df = R - plan.Rf, rb = 1023 + R;
+  const int dx = XF == SF_FXP ? R - Rx : 0, df = R - plan.Rf;
   // shift amounts clamped once: inputs by dx (right, or left when the scale shrank),
   // GF by df >= 0 (a shift by 63 leaves 0 or -1: below one unit of the last place)
-  const int dxr = dx > 0 ? (dx < 63 ? dx : 63) : 0, dxl = dx < 0 ? (-dx < 63 ? -dx : 63) : 0;
+  InScale<XF> cvx{1023 + R, dx > 0 ? (dx < 63 ? dx : 63) : 0, dx < 0 ? (-dx < 63 ? -dx : 63) : 0};
   const int dfr = df < 63 ? df : 63;
   if (blockIdx.x == 0 && threadIdx.x == 0) bnd->umax[(sweep + 2) % 4] = 0ull;
-  long long vmax = 0;
+  unsigned hmax = 0;
+  const int64_t nseg = (q.nx + GS2_OUT) / GS2_OUT;
+  const int64_t seg = gw % nseg, chunk = gw / nseg;
+  const int64_t js = chunk * S2_ROWS;  // even
   if (js <= q.ny) {
     int64_t je = js + S2_ROWS;
     if (je > q.ny) je = (q.ny & 1) ? q.ny + 1 : q.ny;
-    const int64_t x = seg * 24 + lane - 4;
-    const bool xok = x >= 0 && x <= q.nx, xin = x >= 1 && x < q.nx;
-    const bool out_lane = lane >= 4 && lane <= 27 && xok;
+    const Cols c = make_cols(q, seg * GS2_OUT - 4 + 2 * lane);
+    const bool out_lane = lane >= 2 && lane <= 29;
     const long long *Xl = (const long long *)X;
-    auto rawx = [&](int64_t j) -> long long { return (xok && j >= 0 && j <= q.ny) ? Xl[j * q.pitch + x] : 0ll; };
-    auto rawg = [&](int64_t j) -> long long { return (xin && j >= 1 && j < q.ny) ? GF[j * q.pitch + x] : 0ll; };
-    auto cvx = [&](long long raw) -> long long {
-      return XF == SF_F64 ? fx::to_fixed(__longlong_as_double(raw), rb) : (raw >> dxr) << dxl;
+    auto rawx = [&](int64_t j) -> Pair {
+      return (j >= 0 && j <= q.ny) ? ld_pair<V16>(Xl + j * q.pitch, c) : Pair{0ll, 0ll};
     };
-    auto put = [&](int64_t j, long long v) {
-      if (!out_lane) return;
-      const bool inner = xin && j >= 1 && j < q.ny;
-      if (!inner && !write_bnd) return;
-      if (YF == SF_FXP)
-        ((long long *)Y)[j * q.pitch + x] = v;
-      else
-        ((double *)Y)[j * q.pitch + x] = fx::to_double_cvt(v, R - fx::FRAC);
-      const long long a = v < 0 ? -v : v;
-      vmax = a > vmax ? a : vmax;
+    // GF is zero outside the interior, so any row inside the grid may be read
+    auto rawg = [&](int64_t j) -> Pair {
+      return (j >= 0 && j <= q.ny) ? ld_pair<V16>(GF + j * q.pitch, c) : Pair{0ll, 0ll};
     };
-    long long od_old = cvx(rawx(js - 1)), ev_new = 0;
-    constexpr int PG = 2;
-    long long qe[PG], qo[PG], qge[PG], qgo[PG];  // raw X rows j, j+1 and GF rows j, j-1
+    Pair od_old = cvx(rawx(js - 1)), ev_new{0ll, 0ll};
+    constexpr int PG = 1;
+    Pair qe[PG], qo[PG], qge[PG], qgo[PG];  // raw X rows j, j+1 and GF rows j, j-1
 #pragma unroll
     for (int t = 0; t < PG; ++t) {
       const int64_t j = js + 2 * t;
       const bool ok = j <= je;
-      qe[t] = ok ? rawx(j) : 0ll;
-      qo[t] = ok ? rawx(j + 1) : 0ll;
-      qge[t] = ok ? rawg(j) : 0ll;
-      qgo[t] = ok ? rawg(j - 1) : 0ll;
+      qe[t] = ok ? rawx(j) : Pair{0ll, 0ll};
+      qo[t] = ok ? rawx(j + 1) : Pair{0ll, 0ll};
+      qge[t] = ok ? rawg(j) : Pair{0ll, 0ll};
+      qgo[t] = ok ? rawg(j - 1) : Pair{0ll, 0ll};
     }
     for (int64_t jb = js; jb <= je; jb += 2 * PG) {
 #pragma unroll
       for (int t = 0; t < PG; ++t) {
         const int64_t j = jb + 2 * t;
         if (j > je) break;
-        const long long rc = cvx(qe[t]), rp = cvx(qo[t]);
-        const long long ge = qge[t] >> dfr, go = qgo[t] >> dfr;
+        const Pair rc = cvx(qe[t]), rp = cvx(qo[t]);
+        const Pair ge{qge[t].a >> dfr, qge[t].b >> dfr}, go{qgo[t].a >> dfr, qgo[t].b >> dfr};
         {
           const int64_t jn = j + 2 * PG;
           const bool ok = jn <= je;
-          qe[t] = ok ? rawx(jn) : 0ll;
-          qo[t] = ok ? rawx(jn + 1) : 0ll;
-          qge[t] = ok ? rawg(jn) : 0ll;
-          qgo[t] = ok ? rawg(jn - 1) : 0ll;
+          qe[t] = ok ? rawx(jn) : Pair{0ll, 0ll};
+          qo[t] = ok ? rawx(jn + 1) : Pair{0ll, 0ll};
+          qge[t] = ok ? rawg(jn) : Pair{0ll, 0ll};
+          qgo[t] = ok ? rawg(jn - 1) : Pair{0ll, 0ll};
         }
         // even row j: colours 0 and 1 from the old rows j-1 and j+1
-        long long ue = rc;
-        if (j >= 1 && j < q.ny) colour_pair_gs(ue, od_old + rp, ge, xin, x);
+        Pair ue = rc;
+        if (j >= 1 && j < q.ny) gs_pair(ue, Pair{od_old.a + rp.a, od_old.b + rp.b}, ge, c);
         // odd row j-1: colours 2 and 3 from the new rows j-2 and j
         if (j - 1 >= js + 1) {
-          long long uo = od_old;
-          if (j - 1 < q.ny) colour_pair_gs(uo, ev_new + ue, go, xin, x);
-          put(j - 1, uo);
+          Pair uo = od_old;
+          if (j - 1 < q.ny) gs_pair(uo, Pair{ev_new.a + ue.a, ev_new.b + ue.b}, go, c);
+          put_pair<YF, V16>(q, Y, j - 1, c, out_lane, write_bnd, R, uo, hmax);
         }
-        if (j < je || je == q.ny) put(j, ue);
+        if (j < je || je == q.ny) put_pair<YF, V16>(q, Y, j, c, out_lane, write_bnd, R, ue, hmax);
         ev_new = ue;
         od_old = rp;
       }
     }
   }
-  // block max of |new values| -> FP64 bits -> the next sweep's bound
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const long long w = __shfl_xor_sync(0xffffffffu, vmax, o);
-    vmax = w > vmax ? w : vmax;
-  }
-  if (lane == 0) red[wib] = vmax;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    long long m = 0;
-    for (int w = 0; w < W2_THREADS / 32; ++w) m = red[w] > m ? red[w] : m;
-    atomicMax(&bnd->umax[(sweep + 1) % 4], fx::abs_bits(fx::to_double(m, R - fx::FRAC) * (1.0 + 0x1p-50)));
-  }
+  publish_bound(bnd, (sweep + 1) % 4, R, hmax, red);
 }
 
 // Multi-sweep damped Jacobi in the same global-scale fixed point (0 < omega <= 1):
@@ -650,24 +818,34 @@ __global__ void __launch_bounds__(W2_THREADS) k_gs2_sweep(Geo q, const void *__r
 // rounded, exact to one unit of the last fixed-point place.  |u'| <= max|u| +
 // omega 3/8 h^2 max|f|, within the bound of sweep_bounds.cuh.  If the plan rules out
 // fixed point, every sweep of the call runs the FP64-capable single-sweep path on FP64
-// buffers.
-__device__ __forceinline__ long long omega_times(long long D, long long Wq) {
-  const long long hi = __mul64hi(D, Wq);
-  const unsigned long long lo = (unsigned long long)D * (unsigned long long)Wq;
-  return (long long)(((unsigned long long)hi << 2) | (lo >> 62));
-}
+// buffers.  Lane pairs as in the Gauss-Seidel sweep; one column of halo per side, so a
+// warp produces the 60 columns of lanes 1..30.
+// floor(D Wq / 2^62) for 0 < Wq < 2^62 as the high word of D * (4 Wq) (unsigned high
+// product, corrected for D < 0); Wq = 2^62 (omega = 1) is the identity.
+struct Omega {
+  unsigned long long w4;
+  bool one;
+  __device__ __forceinline__ long long operator()(long long D) const {
+    const unsigned long long hi = __umul64hi((unsigned long long)D, w4) - (D < 0 ? w4 : 0ull);
+    return one ? D : (long long)hi;
+  }
+};
 
-template <int XF, int YF>
+constexpr int JAC2_OUT = 60;
+
+template <int XF, int YF, bool V16>
 __global__ void __launch_bounds__(W2_THREADS) k_jac2_sweep(Geo q, const void *__restrict__ X, void *__restrict__ Y,
                                                            const double *__restrict__ f,
                                                            const long long *__restrict__ GF, SweepBounds *bnd,
                                                            int sweep, int sweeps, double g, double omega,
                                                            long long Wq, bool write_bnd) {
-  __shared__ long long red[W2_THREADS / 32];
+  __shared__ unsigned red[W2_THREADS / 32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * (W2_THREADS / 32) + wib;
   const Plan plan = make_plan(bnd, g, sweeps);
   if (!plan.fix) {
+    // FP64 buffers throughout: the single-sweep kernel's work units (30-column
+    // segments), grid-stride
     Op2Args a{};
     a.q = q;
     a.u = (const double *)X;
@@ -675,34 +853,38 @@ __global__ void __launch_bounds__(W2_THREADS) k_jac2_sweep(Geo q, const void *__
     a.out = (double *)Y;
     a.c1 = omega * g;
     a.c2 = -omega * 0.375 / 3.0;
-    Stream2 s;
-    ops2_warp<O2_JACOBI>(a, lane, gw, s, S2_ROWS);
+    const int64_t units = ops2_units(q, S2_ROWS);
+    for (int64_t w = gw; w < units; w += (int64_t)gridDim.x * (W2_THREADS / 32)) {
+      Stream2 s;
+      ops2_warp<O2_JACOBI, V16>(a, lane, w, s, S2_ROWS);
+    }
     return;
   }
   const int R = sweep_R(bnd, sweep % 4, g);
   const int Rx = sweep > 0 ? sweep_R(bnd, (sweep + 3) % 4, g) : R;
-  const int dx = XF == SF_FXP ? R - Rx : 0, df = R - plan.Rf, rb = 1023 + R;
-  const int dxr = dx > 0 ? (dx < 63 ? dx : 63) : 0, dxl = dx < 0 ? (-dx < 63 ? -dx : 63) : 0;
+  const int dx = XF == SF_FXP ? R - Rx : 0, df = R - plan.Rf;
+  InScale<XF> cvx{1023 + R, dx > 0 ? (dx < 63 ? dx : 63) : 0, dx < 0 ? (-dx < 63 ? -dx : 63) : 0};
   const int dfr = df < 63 ? df : 63;
   if (blockIdx.x == 0 && threadIdx.x == 0) bnd->umax[(sweep + 2) % 4] = 0ull;
-  const int64_t nseg = (q.nx + 30) / 30;
+  const Omega om{(unsigned long long)Wq << 2, Wq == (1ll << 62)};
+  const int64_t nseg = (q.nx + JAC2_OUT) / JAC2_OUT;
   const int64_t seg = gw % nseg, chunk = gw / nseg;
   const int64_t js = chunk * S2_ROWS;
-  long long vmax = 0;
+  unsigned hmax = 0;
   if (js <= q.ny) {
     const int64_t je = js + S2_ROWS < q.ny + 1 ? js + S2_ROWS : q.ny + 1;
-    const int64_t x = seg * 30 + lane - 1;
-    const bool xok = x >= 0 && x <= q.nx, xin = x >= 1 && x < q.nx;
-    const bool out_lane = lane >= 1 && lane <= 30 && xok;
+    const Cols c = make_cols(q, seg * JAC2_OUT - 2 + 2 * lane);
+    const bool out_lane = lane >= 1 && lane <= 30;
     const long long *Xl = (const long long *)X;
-    auto rawx = [&](int64_t j) -> long long { return (xok && j >= 0 && j <= q.ny) ? Xl[j * q.pitch + x] : 0ll; };
-    auto rawg = [&](int64_t j) -> long long { return (xin && j >= 1 && j < q.ny) ? GF[j * q.pitch + x] : 0ll; };
-    auto cvx = [&](long long raw) -> long long {
-      return XF == SF_F64 ? fx::to_fixed(__longlong_as_double(raw), rb) : (raw >> dxr) << dxl;
+    auto rawx = [&](int64_t j) -> Pair {
+      return (j >= 0 && j <= q.ny) ? ld_pair<V16>(Xl + j * q.pitch, c) : Pair{0ll, 0ll};
     };
-    long long um = cvx(rawx(js - 1)), uc = cvx(rawx(js)), up = cvx(rawx(js + 1));
-    constexpr int PQ = 3;
-    long long qx[PQ], qg[PQ];  // raw X row j + 2 and GF row j for the iteration j = jb + t
+    auto rawg = [&](int64_t j) -> Pair {
+      return (j >= 0 && j <= q.ny) ? ld_pair<V16>(GF + j * q.pitch, c) : Pair{0ll, 0ll};
+    };
+    Pair um = cvx(rawx(js - 1)), uc = cvx(rawx(js)), up = cvx(rawx(js + 1));
+    constexpr int PQ = 2;
+    Pair qx[PQ], qg[PQ];  // raw X row j + 2 and GF row j for the iteration j = jb + t
 #pragma unroll
     for (int t = 0; t < PQ; ++t) {
       qx[t] = rawx(js + 2 + t);
@@ -713,56 +895,53 @@ __global__ void __launch_bounds__(W2_THREADS) k_jac2_sweep(Geo q, const void *__
       for (int t = 0; t < PQ; ++t) {
         const int64_t j = jb + t;
         if (j >= je) break;
-        const long long rn = qx[t], gr = qg[t];
-        qx[t] = j + 2 + PQ <= je ? rawx(j + 2 + PQ) : 0ll;
-        qg[t] = j + PQ < je ? rawg(j + PQ) : 0ll;
-        const long long V = um + up, T = V + uc;
-        const long long Tm = __shfl_up_sync(0xffffffffu, T, 1);
-        const long long Tp = __shfl_down_sync(0xffffffffu, T, 1);
-        if (out_lane) {
-          const bool inner = xin && j >= 1 && j < q.ny;
-          long long un = uc;  // Dirichlet value carried
-          if (inner) un = uc + omega_times((gr >> dfr) + ((Tm + Tp + V) >> 3) - uc, Wq);
-          if (inner || write_bnd) {
-            if (YF == SF_FXP)
-              ((long long *)Y)[j * q.pitch + x] = un;
-            else
-              ((double *)Y)[j * q.pitch + x] = fx::to_double_cvt(un, R - fx::FRAC);
-            const long long aa = un < 0 ? -un : un;
-            vmax = aa > vmax ? aa : vmax;
-          }
+        const Pair rn = qx[t], gr = qg[t];
+        qx[t] = j + 2 + PQ <= je ? rawx(j + 2 + PQ) : Pair{0ll, 0ll};
+        qg[t] = j + PQ < je ? rawg(j + PQ) : Pair{0ll, 0ll};
+        const Pair V{um.a + up.a, um.b + up.b};
+        const Pair T{V.a + uc.a, V.b + uc.b};
+        const long long Tbl = __shfl_up_sync(0xffffffffu, T.b, 1);
+        const long long Tar = __shfl_down_sync(0xffffffffu, T.a, 1);
+        Pair un = uc;  // Dirichlet values carried
+        if (j >= 1 && j < q.ny) {
+          if (c.ina) un.a = uc.a + om((gr.a >> dfr) + ((Tbl + T.b + V.a) >> 3) - uc.a);
+          if (c.inb) un.b = uc.b + om((gr.b >> dfr) + ((T.a + Tar + V.b) >> 3) - uc.b);
         }
+        put_pair<YF, V16>(q, Y, j, c, out_lane, write_bnd, R, un, hmax);
         um = uc;
         uc = up;
         up = cvx(rn);
       }
     }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const long long w = __shfl_xor_sync(0xffffffffu, vmax, o);
-    vmax = w > vmax ? w : vmax;
-  }
-  if (lane == 0) red[wib] = vmax;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    long long m = 0;
-    for (int w = 0; w < W2_THREADS / 32; ++w) m = red[w] > m ? red[w] : m;
-    atomicMax(&bnd->umax[(sweep + 1) % 4], fx::abs_bits(fx::to_double(m, R - fx::FRAC) * (1.0 + 0x1p-50)));
-  }
+  publish_bound(bnd, (sweep + 1) % 4, R, hmax, red);
 }
 
 }  // namespace
+
+// Null counts as aligned (an absent array is never accessed).
+static bool aligned16(const void *p) { return ((uintptr_t)p % 16) == 0; }
 
 size_t ops2_reduce_bytes(const Geo &q) { return 16 + (size_t)ops2_blocks(q) * 2 * sizeof(double); }
 
 static cudaError_t launch_ops2(int op, const Op2Args &a, cudaStream_t s) {
   const unsigned nb = ops2_blocks(a.q);
-  switch (op) {
-    case O2_APPLY: k_ops2<O2_APPLY><<<nb, W2_THREADS, 0, s>>>(a); break;
-    case O2_JACOBI: k_ops2<O2_JACOBI><<<nb, W2_THREADS, 0, s>>>(a); break;
-    case O2_RESIDUAL: k_ops2<O2_RESIDUAL><<<nb, W2_THREADS, 0, s>>>(a); break;
-    default: k_ops2<O2_ELEMENTWISE><<<nb, W2_THREADS, 0, s>>>(a); break;
+  // 16-byte row pairs: even pitch and 16-byte aligned u, f and output
+  const bool v16 = a.q.pitch % 2 == 0 && aligned16(a.u) && aligned16(a.f) && aligned16(a.out);
+  if (v16) {
+    switch (op) {
+      case O2_APPLY: k_ops2<O2_APPLY, true><<<nb, W2_THREADS, 0, s>>>(a); break;
+      case O2_JACOBI: k_ops2<O2_JACOBI, true><<<nb, W2_THREADS, 0, s>>>(a); break;
+      case O2_RESIDUAL: k_ops2<O2_RESIDUAL, true><<<nb, W2_THREADS, 0, s>>>(a); break;
+      default: k_ops2<O2_ELEMENTWISE, true><<<nb, W2_THREADS, 0, s>>>(a); break;
+    }
+  } else {
+    switch (op) {
+      case O2_APPLY: k_ops2<O2_APPLY, false><<<nb, W2_THREADS, 0, s>>>(a); break;
+      case O2_JACOBI: k_ops2<O2_JACOBI, false><<<nb, W2_THREADS, 0, s>>>(a); break;
+      case O2_RESIDUAL: k_ops2<O2_RESIDUAL, false><<<nb, W2_THREADS, 0, s>>>(a); break;
+      default: k_ops2<O2_ELEMENTWISE, false><<<nb, W2_THREADS, 0, s>>>(a); break;
+    }
   }
   return cudaGetLastError();
 }
@@ -808,30 +987,45 @@ cudaError_t launch_residual_fx2(const Geo &q, const double *u, const double *f, 
 cudaError_t launch_gs_sweeps_fx2(const Geo &q, double *u, const double *f, int sweeps, double *work, void *bounds,
                                  cudaStream_t s) {
   const double g = 0.375 * q.h * q.h;
-  const int64_t nseg = (q.nx + 24) / 24;
   const int64_t nchunk = (q.ny + S2_ROWS) / S2_ROWS;
-  const unsigned nb = (unsigned)((nseg * nchunk + W2_THREADS / 32 - 1) / (W2_THREADS / 32));
   const int64_t span = span_elems(q);
   cudaError_t e;
   if (sweeps == 1) {
+    const int64_t nseg = (q.nx + 24) / 24;
+    const unsigned nb = (unsigned)((nseg * nchunk + W2_THREADS / 32 - 1) / (W2_THREADS / 32));
     k_gs2_fused<<<nb, W2_THREADS, 0, s>>>(q, u, work, f, g);
     e = cudaGetLastError();
     return e ? e : cudaMemcpyAsync(u, work, (size_t)span * sizeof(double), cudaMemcpyDeviceToDevice, s);
   }
+  const int64_t nseg = (q.nx + GS2_OUT) / GS2_OUT;
+  const unsigned nb = (unsigned)((nseg * nchunk + W2_THREADS / 32 - 1) / (W2_THREADS / 32));
   void *A = work, *B = work + span;
   long long *GF = (long long *)(work + 2 * span);
   SweepBounds *bnd = (SweepBounds *)bounds;
   e = launch_gs_prepass(q, 2, u, f, GF, bounds, sweeps, s);
+  // 16-byte row pairs need an even pitch and 16-byte aligned bases (u and work; the
+  // buffers inside work then follow, span being even)
+  const bool v16 = q.pitch % 2 == 0 && aligned16(u) && aligned16(work);
   const void *X = u;
   for (int it = 0; it < sweeps && !e; ++it) {
     const bool first = it == 0, last = it == sweeps - 1;
     void *Y = last ? (void *)u : (it % 2 == 0 ? A : B);
-    if (first)
-      k_gs2_sweep<SF_F64, SF_FXP><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, true);
-    else if (!last)
-      k_gs2_sweep<SF_FXP, SF_FXP><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, true);
-    else  // the caller's u: its Dirichlet values were never overwritten, leave them
-      k_gs2_sweep<SF_FXP, SF_F64><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, false);
+    // the caller's u (last sweep): its Dirichlet values were never overwritten, leave them
+    if (v16) {
+      if (first)
+        k_gs2_sweep<SF_F64, SF_FXP, true><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, true);
+      else if (!last)
+        k_gs2_sweep<SF_FXP, SF_FXP, true><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, true);
+      else
+        k_gs2_sweep<SF_FXP, SF_F64, true><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, false);
+    } else {
+      if (first)
+        k_gs2_sweep<SF_F64, SF_FXP, false><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, true);
+      else if (!last)
+        k_gs2_sweep<SF_FXP, SF_FXP, false><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, true);
+      else
+        k_gs2_sweep<SF_FXP, SF_F64, false><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, false);
+    }
     e = cudaGetLastError();
     X = Y;
   }
@@ -848,7 +1042,7 @@ namespace stencil {
 cudaError_t launch_jacobi_sweeps_fx2(const Geo &q, double *u, const double *f, int sweeps, double omega, double *A,
                                      double *scratch, void *bounds, cudaStream_t s) {
   const double g = 0.375 * q.h * q.h;
-  const int64_t nseg = (q.nx + 30) / 30;
+  const int64_t nseg = (q.nx + JAC2_OUT) / JAC2_OUT;
   const int64_t nchunk = (q.ny + S2_ROWS) / S2_ROWS;
   const unsigned nb = (unsigned)((nseg * nchunk + W2_THREADS / 32 - 1) / (W2_THREADS / 32));
   const int64_t span = span_elems(q);
@@ -861,16 +1055,34 @@ cudaError_t launch_jacobi_sweeps_fx2(const Geo &q, double *u, const double *f, i
     return e ? e : cudaMemcpyAsync(u, A, (size_t)span * sizeof(double), cudaMemcpyDeviceToDevice, s);
   }
   cudaError_t e = launch_gs_prepass(q, 2, u, f, GF, bounds, sweeps, s);
+  // 16-byte row pairs: even pitch and 16-byte aligned u, f (read by the FP64 path),
+  // A and scratch (the buffers inside scratch then follow, span being even)
+  const bool v16 = q.pitch % 2 == 0 && aligned16(u) && aligned16(f) && aligned16(A) && aligned16(scratch);
   const void *X = u;
   for (int it = 0; it < sweeps && !e; ++it) {
     const bool first = it == 0, last = it == sweeps - 1;
     void *Y = last ? (void *)u : (it % 2 == 0 ? (void *)A : B);
-    if (first)
-      k_jac2_sweep<SF_F64, SF_FXP><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, omega, Wq, true);
-    else if (!last)
-      k_jac2_sweep<SF_FXP, SF_FXP><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, omega, Wq, true);
-    else
-      k_jac2_sweep<SF_FXP, SF_F64><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, omega, Wq, false);
+    if (v16) {
+      if (first)
+        k_jac2_sweep<SF_F64, SF_FXP, true><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, omega, Wq,
+                                                                     true);
+      else if (!last)
+        k_jac2_sweep<SF_FXP, SF_FXP, true><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, omega, Wq,
+                                                                     true);
+      else
+        k_jac2_sweep<SF_FXP, SF_F64, true><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, omega, Wq,
+                                                                     false);
+    } else {
+      if (first)
+        k_jac2_sweep<SF_F64, SF_FXP, false><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, omega, Wq,
+                                                                      true);
+      else if (!last)
+        k_jac2_sweep<SF_FXP, SF_FXP, false><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, omega,
+                                                                      Wq, true);
+      else
+        k_jac2_sweep<SF_FXP, SF_F64, false><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, omega,
+                                                                      Wq, false);
+    }
     e = cudaGetLastError();
     X = Y;
   }

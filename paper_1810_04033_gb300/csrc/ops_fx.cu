@@ -36,6 +36,10 @@ constexpr int R_MIN = -900, R_MAX = 1000;
 
 enum { OP_APPLY = 0, OP_JACOBI = 1, OP_RESIDUAL = 2 };
 
+// Per operation: convert the fixed-point result with the FP64 pipe (true) or with
+// integer instructions (false), whichever measured faster.
+constexpr bool OPS3_CVT[3] = {true, false, false};
+
 struct OpArgs {
   Geo q;
   const double *u;
@@ -122,6 +126,11 @@ __device__ __forceinline__ void compute_plane(const OpArgs &a, int64_t z, int x0
     }
   }
   const int e2 = R - fx::FRAC;
+  // CVT: 12 S u is converted by the FP64 pipe and scaled by its term's factor times
+  // 2^e2; otherwise by fx::to_double on the integer pipe (the same bits either way)
+  constexpr bool CVT = OPS3_CVT[OP];
+  const double cf = OP == OP_JACOBI ? a.c2 : a.c1;
+  const double sc = FIX && CVT ? cf * fx::pow2d(e2) : cf;
   const long long *lc = lo + col, *uc = up + col, *cc = ce + col;
   long long Cm = cc[(r0 - 1) * OS_W], Cc = cc[r0 * OS_W];
   long long Wm = add<FIX>(lc[(r0 - 1) * OS_W], uc[(r0 - 1) * OS_W]);
@@ -146,24 +155,22 @@ __device__ __forceinline__ void compute_plane(const OpArgs &a, int64_t z, int x0
     if (!lane_out || (!INNER && j > ny)) continue;
     const int off = j * pitch + x;
     const bool inner = zin && x_inner && (INNER || (j >= 1 && j < ny));
-    double Td = 0.0;  // 32 u - (2E + C) = 12 (S u)
-    long long T = 0;
+    double Td = 0.0;  // 32 u - (2E + C) = 12 (S u); Td * sc is its term
     if (inner) {
       const long long S = add<FIX>(add<FIX>(Pm, Pp), add<FIX>(Q, Q));
       if (FIX) {
-        T = 32 * Cu - S;
-        // apply: converted on the FP64 pipe below; Jacobi / residual: on the integer pipe
-        if (OP != OP_APPLY) Td = fx::to_double(T, e2);
+        const long long T = 32 * Cu - S;
+        Td = CVT ? __ll2double_rn(T) : fx::to_double(T, e2);
       } else {
         Td = fma(32.0, __longlong_as_double(Cu), -__longlong_as_double(S));
       }
     }
     if (OP == OP_APPLY) {
-      outp[off] = inner ? (FIX ? __ll2double_rn(T) * (a.c1 * fx::pow2d(e2)) : Td * a.c1) : 0.0;
+      outp[off] = inner ? Td * sc : 0.0;
     } else if (OP == OP_JACOBI) {
-      outp[off] = inner ? fma(a.c2, Td, fma(a.c1, fv[k], uv[k])) : uv[k];
+      outp[off] = inner ? fma(sc, Td, fma(a.c1, fv[k], uv[k])) : uv[k];
     } else {
-      const double rv = inner ? fma(a.c1, Td, fv[k]) : 0.0;
+      const double rv = inner ? fma(sc, Td, fv[k]) : 0.0;
       if (a.out) {
         const int64_t e = z * q.plane + off;  // element index
         if (a.out_kind == 0)

@@ -359,3 +359,45 @@ def test_2d_extreme_and_growing_magnitudes(scale):
     torch.cuda.synchronize()
     assert rel_err(to_host(gd), oracle.gs_coloured(u, f, h, 4)) <= TOL_F64
     assert rel_err(to_host(jd), oracle.jacobi(u, f, h, 0.9, 4)) <= TOL_F64
+
+
+@pytest.mark.parametrize("n", [(130, 300), (57, 40)])
+def test_2d_sweeps_unaligned_base(n):
+    """Applies, Jacobi step, residual and multi-sweep GS and Jacobi on arrays whose base
+    is 8 but not 16-byte aligned (even pitch): the kernels must take their 8-byte
+    column path."""
+    h = 1.0 / max(n)
+    shape = synth.grid_shape(2, n)
+    u = synth.uniform_field(shape, 1800 + sum(n), zero_bc=False)
+    f = synth.uniform_field(shape, 1801 + sum(n))
+
+    def shifted(a):
+        pitch = shape[1] + 1 + (shape[1] + 1) % 2  # even, > nx + 1
+        buf = torch.full((shape[0], pitch), float("nan"), dtype=torch.float64, device="cuda")
+        v = buf[:, 1:1 + shape[1]]
+        v.copy_(torch.from_numpy(a).cuda())
+        assert v.data_ptr() % 16 == 8 and v.stride(0) % 2 == 0
+        return v
+
+    ud, fd = shifted(u), shifted(f)
+    for form, ref in ((st.FORM_ELEMENTWISE, oracle.apply_elementwise(u, h)),
+                      (st.FORM_STENCIL, oracle.apply_stencil(u, h))):
+        yd = shifted(np.full(shape, np.nan))
+        st.stencil_apply(ud, yd, h, form)
+        torch.cuda.synchronize()
+        assert apply_err(to_host(yd), ref, u, h) <= TOL_F64, form
+    od = shifted(np.full(shape, np.nan))
+    st.stencil_jacobi_step(ud, fd, od, h, 2.0 / 3.0)
+    rd = shifted(np.full(shape, np.nan))
+    st.stencil_residual(ud, fd, h, r=rd)
+    torch.cuda.synchronize()
+    assert rel_err(to_host(od), oracle.jacobi(u, f, h, 2.0 / 3.0, 1)) <= TOL_F64
+    assert apply_err(to_host(rd), oracle.residual(u, f, h)[0], u, h) <= TOL_F64
+    for sweeps in (2, 5):
+        gd, fd = shifted(u), shifted(f)
+        st.stencil_smooth_coloured(gd, fd, h, sweeps)
+        jd = shifted(u)
+        st.stencil_smooth_jacobi(jd, fd, shifted(np.zeros(shape)), h, sweeps, 2.0 / 3.0)
+        torch.cuda.synchronize()
+        assert rel_err(to_host(gd), oracle.gs_coloured(u, f, h, sweeps)) <= TOL_F64, sweeps
+        assert rel_err(to_host(jd), oracle.jacobi(u, f, h, 2.0 / 3.0, sweeps)) <= TOL_F64, sweeps
