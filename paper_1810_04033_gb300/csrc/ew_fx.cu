@@ -12,8 +12,8 @@
 //
 // The scatter runs in registers, one warp per column of cells (layout below): the z
 // colours are the cell layers processed in order, the y colours the cell rows processed
-// one after the other, and the x colours meet through shuffles, each vertex column
-// being owned by one lane.  After layer k, vertex plane k has received all 8
+// one after the other, and the x colours meet in registers and through shuffles, each
+// vertex column being owned by one lane.  After layer k, vertex plane k has received all 8
 // contributions and is written out.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -50,207 +50,353 @@ __device__ __forceinline__ long long times4(long long a) {
   return __double_as_longlong(4.0 * __longlong_as_double(a));
 }
 
-// ------------------------------------------------------------ register-streaming form
-// A warp owns 32 consecutive cell columns (lanes 1..30 own the output vertex columns),
-// R vertex rows y and a chunk of planes, and streams the cell layers k in z order with
-// everything in registers: the vertex values of planes k and k+1 for rows j0-1..j0+R,
-// the sums of plane k (contributions of layers k-1 and k) and the partial sums of plane
-// k+1 (layer k).  Per layer it forms the R+1 cell rows' 8 contributions per cell; the
-// right-hand vertices' shares reach the next lane by a shuffle (the x colours meet in
-// registers), the y colours are the cell rows processed one after the other, the z
-// colours the layers in order; after layer k, plane k has all 8 shares and is written.
-// The fixed-point reference is per warp and only grows (as in the 2D kernels); a warp
-// that meets a value outside the fixed-point range switches to FP64 at a layer start.
-constexpr int S3_R = 4;          // output vertex rows per warp
-constexpr int S3_CZ = 32;        // output planes per warp (at most)
-constexpr int S3_THREADS = 128;
-constexpr int S3_RMIN = -900, S3_RMAX = 1000;
+// ------------------------------------------------------------ plane-staged form
+// A warp owns a window of 64 vertex columns, two per lane (xa even, xb = xa + 1; lanes
+// 1..30 own the 60 output columns), E3_R vertex rows y and a chunk of planes, and
+// streams the cell layers k in z order.  Rows j0-1 .. j0+E3_R of each plane are copied
+// into the warp's own shared-memory slots with cp.async (zero-filled outside the grid)
+// two planes ahead of use, and converted to fixed point in place; the sums of plane k
+// (contributions of layers k-1 and k) and the partial sums of plane k+1 (layer k) stay
+// in registers.  A lane has two cells per cell row: A (from xa to xb) and B (from xb to
+// the next lane's xa, read from the staged plane).  B's shares for the next lane's xa
+// column are summed per vertex row and handed over by one shuffle per row once the
+// layer is done (the x colours meet there); the y colours are the cell rows processed
+// one after the other, the z colours the layers in order; after layer k, plane k has all
+// 8 shares and is written.  The fixed-point reference is per warp and only grows (as in
+// the 2D kernels); a warp that meets a value outside the fixed-point range switches to
+// FP64 at a layer start.
+constexpr int E3_R = 4;                         // output vertex rows per warp
+constexpr int E3_ROWS = E3_R + 2;               // staged rows per plane
+constexpr int E3_W = 64;                        // staged columns
+constexpr int E3_BUF = E3_ROWS * E3_W;          // elements per staged plane
+constexpr int E3_CZ = 32;                       // output planes per warp (at most)
+constexpr int E3_THREADS = 128;
+constexpr int E3_OUT = 60;                      // output columns per warp
+constexpr size_t E3_SMEM = (size_t)(E3_THREADS / 32) * 3 * E3_BUF * sizeof(long long);
+constexpr int E3_RMIN = -900, E3_RMAX = 1000;
+
+struct P2 {
+  long long a, b;  // columns xa, xb
+};
 
 struct Ew3Lane {
-  int64_t x;
-  bool xok, xin, cell_lane, out_lane;
+  int64_t xa;
+  bool oka, okb, ina, inb, cellA, cellB, out_lane;
   int lane;
-  long long bk[S3_R + 2];  // plane k, rows j0-1 .. j0+R
-  long long acc[S3_R];     // plane k rows j0 .. j0+R-1
+  long long *buf;     // the warp's 3 plane slots
+  P2 acc[E3_R];       // plane k rows j0 .. j0+R-1
+  long long accR[E3_R];  // shares of plane k for the next lane's xa column
   int R;
-  bool fix;
 };
 
 __device__ __forceinline__ unsigned bexp(double v) { return (unsigned)(fx::dbits(v) >> 52) & 0x7ffu; }
 
 __device__ __forceinline__ long long shr_pos(long long v, int d) { return d >= 63 ? (v >> 63) : (v >> d); }
 
-// Layers k0 .. z1-1 of the warp's column; returns the first layer not done (the warp
-// switched to FP64) or z1.
-template <bool FIX>
-__device__ __forceinline__ int64_t ew3_layers(const EwArgs &a, Ew3Lane &L, int64_t j0, int64_t z0, int64_t z1,
-                                              int64_t k0) {
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Slot of plane z (planes z0-1, z0, z0+1, ... rotate through 3 slots).
+__device__ __forceinline__ long long *e3_slot(const Ew3Lane &L, int64_t z, int64_t z0) {
+  return L.buf + ((z - z0 + 1) % 3) * E3_BUF;
+}
+
+// Start the copy of plane z's staged rows (this lane's two columns) into its slot;
+// zeros outside the grid.  One commit group per plane (empty when z is not needed).
+template <bool V16>
+__device__ __forceinline__ void e3_issue(const EwArgs &a, const Ew3Lane &L, int64_t z, int64_t z0, int64_t j0,
+                                         bool need) {
   const Geo &q = a.q;
-  const double *ucol = a.u + (L.xok ? L.x : 0);
-  auto load_plane = [&](double (&v)[S3_R + 2], int64_t z) {
+  if (need) {
+    long long *slot = e3_slot(L, z, z0) + 2 * L.lane;
+    const long long *base = (const long long *)a.u;
 #pragma unroll
-    for (int c = 0; c < S3_R + 2; ++c) {
+    for (int c = 0; c < E3_ROWS; ++c) {
       const int64_t j = j0 - 1 + c;
-      v[c] = (L.xok && z >= 0 && z <= q.nz && j >= 0 && j <= q.ny) ? ucol[z * q.plane + j * q.pitch] : 0.0;
+      const bool row = z >= 0 && z <= q.nz && j >= 0 && j <= q.ny;
+      const long long *src = row && L.oka ? base + z * q.plane + j * q.pitch + L.xa : base;
+      const uint32_t dst = smem_addr(slot + c * E3_W);
+      if (V16) {
+        const int bytes = row && L.oka ? (L.okb ? 16 : 8) : 0;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+      } else {
+        const int ba = row && L.oka ? 8 : 0, bb = row && L.okb ? 8 : 0;
+        const long long *srcb = row && L.okb ? base + z * q.plane + j * q.pitch + L.xa + 1 : base;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(ba) : "memory");
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst + 8), "l"(srcb), "r"(bb) : "memory");
+      }
     }
-  };
-  double qn[S3_R + 2];
-  load_plane(qn, k0 + 1);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// 12 K_e u_e of one cell (bottom face b0..b3, top face t0..t3; index bit 0 = x, bit 1 =
+// y): cb_w for the bottom vertices, ct_w for the top ones.
+template <bool FIX>
+__device__ __forceinline__ void cell12(long long b0, long long b1, long long b2, long long b3, long long t0,
+                                       long long t1, long long t2, long long t3, long long (&cb)[4],
+                                       long long (&ct)[4]) {
+  const long long Sb = add<FIX>(add<FIX>(b0, b1), add<FIX>(b2, b3));
+  const long long St = add<FIX>(add<FIX>(t0, t1), add<FIX>(t2, t3));
+  cb[0] = add<FIX>(sub<FIX>(times4<FIX>(b0), b3), sub<FIX>(t0, St));
+  cb[1] = add<FIX>(sub<FIX>(times4<FIX>(b1), b2), sub<FIX>(t1, St));
+  cb[2] = add<FIX>(sub<FIX>(times4<FIX>(b2), b1), sub<FIX>(t2, St));
+  cb[3] = add<FIX>(sub<FIX>(times4<FIX>(b3), b0), sub<FIX>(t3, St));
+  ct[0] = add<FIX>(sub<FIX>(times4<FIX>(t0), t3), sub<FIX>(b0, Sb));
+  ct[1] = add<FIX>(sub<FIX>(times4<FIX>(t1), t2), sub<FIX>(b1, Sb));
+  ct[2] = add<FIX>(sub<FIX>(times4<FIX>(t2), t1), sub<FIX>(b2, Sb));
+  ct[3] = add<FIX>(sub<FIX>(times4<FIX>(t3), t0), sub<FIX>(b3, Sb));
+}
+
+// This lane's staged pair of row c and the next lane's xa value of that row.
+struct Row3 {
+  long long a, b, r;
+};
+
+__device__ __forceinline__ Row3 e3_row(const long long *plane, int c, int lane) {
+  const longlong2 v = *(const longlong2 *)(plane + c * E3_W + 2 * lane);
+  const int rc = lane < 31 ? 2 * lane + 2 : 2 * lane;  // lane 31 has no cell B
+  return Row3{v.x, v.y, plane[c * E3_W + rc]};
+}
+
+// Layers k0 .. z1-1 of the warp's column; returns the first layer not done (the warp
+// switched to FP64) or z1.  resume: plane k0+1 is already waited for and k0+2 issued.
+template <bool FIX, bool V16>
+__device__ __forceinline__ int64_t ew3_layers(const EwArgs &a, Ew3Lane &L, int64_t j0, int64_t z0, int64_t z1,
+                                              int64_t k0, bool resume) {
+  const Geo &q = a.q;
+  const long long zero = FIX ? 0ll : __double_as_longlong(0.0);
+  long long *own = nullptr;
   for (int64_t k = k0; k < z1; ++k) {
-    double tr[S3_R + 2];
-#pragma unroll
-    for (int c = 0; c < S3_R + 2; ++c) tr[c] = qn[c];
+    if (!(resume && k == k0)) {
+      e3_issue<V16>(a, L, k + 2, z0, j0, k + 2 <= z1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+      __syncwarp();
+    }
+    long long *bot = e3_slot(L, k, z0), *top = e3_slot(L, k + 1, z0);
+    own = top + 2 * L.lane;
     if (FIX) {
       unsigned em = 0;
 #pragma unroll
-      for (int c = 0; c < S3_R + 2; ++c) em = max(em, bexp(tr[c]));
+      for (int c = 0; c < E3_ROWS; ++c) {
+        const longlong2 v = *(const longlong2 *)(own + c * E3_W);
+        em = max(em, max(bexp(__longlong_as_double(v.x)), bexp(__longlong_as_double(v.y))));
+      }
       em = __reduce_max_sync(0xffffffffu, em);
       if (em != 0) {
         const int Rp = (int)em - 1022 + 1;
-        if (em == 2047 || Rp > S3_RMAX || (Rp < S3_RMIN && L.R == S3_RMIN)) {
+        long long *ob = bot + 2 * L.lane;
+        if (em == 2047 || Rp > E3_RMAX || (Rp < E3_RMIN && L.R == E3_RMIN)) {
+          auto cv = [&](long long v) { return __double_as_longlong(fx::to_double(v, L.R - fx::FRAC)); };
 #pragma unroll
-          for (int c = 0; c < S3_R + 2; ++c) L.bk[c] = __double_as_longlong(fx::to_double(L.bk[c], L.R - fx::FRAC));
+          for (int c = 0; c < E3_ROWS; ++c) {
+            ob[c * E3_W] = cv(ob[c * E3_W]);
+            ob[c * E3_W + 1] = cv(ob[c * E3_W + 1]);
+          }
 #pragma unroll
-          for (int r = 0; r < S3_R; ++r) L.acc[r] = __double_as_longlong(fx::to_double(L.acc[r], L.R - fx::FRAC));
-          L.fix = false;
-          return k;  // redo this layer in FP64 (it reloads plane k+1)
+          for (int r = 0; r < E3_R; ++r) {
+            L.acc[r] = P2{cv(L.acc[r].a), cv(L.acc[r].b)};
+            L.accR[r] = cv(L.accR[r]);
+          }
+          __syncwarp();
+          return k;  // redo this layer in FP64
         }
         if (Rp > L.R) {
           const int d = Rp - L.R;
 #pragma unroll
-          for (int c = 0; c < S3_R + 2; ++c) L.bk[c] = shr_pos(L.bk[c], d);
+          for (int c = 0; c < E3_ROWS; ++c) {
+            ob[c * E3_W] = shr_pos(ob[c * E3_W], d);
+            ob[c * E3_W + 1] = shr_pos(ob[c * E3_W + 1], d);
+          }
 #pragma unroll
-          for (int r = 0; r < S3_R; ++r) L.acc[r] = shr_pos(L.acc[r], d);
+          for (int r = 0; r < E3_R; ++r) {
+            L.acc[r] = P2{shr_pos(L.acc[r].a, d), shr_pos(L.acc[r].b, d)};
+            L.accR[r] = shr_pos(L.accR[r], d);
+          }
           L.R = Rp;
         }
       }
-    }
-    if (k + 1 < z1) load_plane(qn, k + 2);
-    long long tk[S3_R + 2];
 #pragma unroll
-    for (int c = 0; c < S3_R + 2; ++c) tk[c] = FIX ? fx::to_fixed(tr[c], 1023 + L.R) : __double_as_longlong(tr[c]);
-    long long part[S3_R];
-#pragma unroll
-    for (int r = 0; r < S3_R; ++r) part[r] = FIX ? 0ll : __double_as_longlong(0.0);
-    if (k >= 0 && k < q.nz) {
-#pragma unroll
-      for (int c = 0; c <= S3_R; ++c) {
-        const int64_t cj = j0 - 1 + c;
-        const long long b0 = L.bk[c], b2 = L.bk[c + 1], t0 = tk[c], t2 = tk[c + 1];
-        const long long b1 = __shfl_down_sync(0xffffffffu, b0, 1);
-        const long long b3 = __shfl_down_sync(0xffffffffu, b2, 1);
-        const long long t1 = __shfl_down_sync(0xffffffffu, t0, 1);
-        const long long t3 = __shfl_down_sync(0xffffffffu, t2, 1);
-        const bool cell = L.cell_lane && cj >= 0 && cj < q.ny;
-        long long cb0 = 0, cb1 = 0, cb2 = 0, cb3 = 0, ct0 = 0, ct1 = 0, ct2 = 0, ct3 = 0;
-        if (cell) {
-          const long long Sb = add<FIX>(add<FIX>(b0, b1), add<FIX>(b2, b3));
-          const long long St = add<FIX>(add<FIX>(t0, t1), add<FIX>(t2, t3));
-          cb0 = add<FIX>(sub<FIX>(times4<FIX>(b0), b3), sub<FIX>(t0, St));
-          cb1 = add<FIX>(sub<FIX>(times4<FIX>(b1), b2), sub<FIX>(t1, St));
-          cb2 = add<FIX>(sub<FIX>(times4<FIX>(b2), b1), sub<FIX>(t2, St));
-          cb3 = add<FIX>(sub<FIX>(times4<FIX>(b3), b0), sub<FIX>(t3, St));
-          ct0 = add<FIX>(sub<FIX>(times4<FIX>(t0), t3), sub<FIX>(b0, Sb));
-          ct1 = add<FIX>(sub<FIX>(times4<FIX>(t1), t2), sub<FIX>(b1, Sb));
-          ct2 = add<FIX>(sub<FIX>(times4<FIX>(t2), t1), sub<FIX>(b2, Sb));
-          ct3 = add<FIX>(sub<FIX>(times4<FIX>(t3), t0), sub<FIX>(b3, Sb));
-        } else if (!FIX) {
-          cb0 = cb1 = cb2 = cb3 = ct0 = ct1 = ct2 = ct3 = __double_as_longlong(0.0);
-        }
-        // the left neighbour's right-hand shares land on this lane's column
-        long long lb1 = __shfl_up_sync(0xffffffffu, cb1, 1), lb3 = __shfl_up_sync(0xffffffffu, cb3, 1);
-        long long lt1 = __shfl_up_sync(0xffffffffu, ct1, 1), lt3 = __shfl_up_sync(0xffffffffu, ct3, 1);
-        if (L.lane == 0) lb1 = lb3 = lt1 = lt3 = FIX ? 0ll : __double_as_longlong(0.0);
-        if (c >= 1) {  // vertex row cj (index c-1)
-          L.acc[c - 1] = add<FIX>(L.acc[c - 1], add<FIX>(cb0, lb1));
-          part[c - 1] = add<FIX>(part[c - 1], add<FIX>(ct0, lt1));
-        }
-        if (c < S3_R) {  // vertex row cj + 1 (index c)
-          L.acc[c] = add<FIX>(L.acc[c], add<FIX>(cb2, lb3));
-          part[c] = add<FIX>(part[c], add<FIX>(ct2, lt3));
-        }
+      for (int c = 0; c < E3_ROWS; ++c) {
+        longlong2 *p = (longlong2 *)(own + c * E3_W);
+        const longlong2 v = *p;
+        *p = make_longlong2(fx::to_fixed(__longlong_as_double(v.x), 1023 + L.R),
+                            fx::to_fixed(__longlong_as_double(v.y), 1023 + L.R));
       }
+      __syncwarp();
+    }
+    P2 part[E3_R];
+    long long partR[E3_R];
+#pragma unroll
+    for (int r = 0; r < E3_R; ++r) {
+      part[r] = P2{zero, zero};
+      partR[r] = zero;
+    }
+    if (k >= 0 && k < q.nz) {
+      Row3 b0 = e3_row(bot, 0, L.lane), t0 = e3_row(top, 0, L.lane);
+#pragma unroll
+      for (int c = 0; c <= E3_R; ++c) {
+        const Row3 b1 = e3_row(bot, c + 1, L.lane), t1 = e3_row(top, c + 1, L.lane);
+        const int64_t cj = j0 - 1 + c;
+        if (cj >= 0 && cj < q.ny) {  // warp-uniform
+          long long cb[4], ct[4];
+          if (L.cellA) {  // vertices xa, xb of rows cj, cj+1
+            cell12<FIX>(b0.a, b0.b, b1.a, b1.b, t0.a, t0.b, t1.a, t1.b, cb, ct);
+            if (c >= 1) {
+              L.acc[c - 1].a = add<FIX>(L.acc[c - 1].a, cb[0]);
+              L.acc[c - 1].b = add<FIX>(L.acc[c - 1].b, cb[1]);
+              part[c - 1].a = add<FIX>(part[c - 1].a, ct[0]);
+              part[c - 1].b = add<FIX>(part[c - 1].b, ct[1]);
+            }
+            if (c < E3_R) {
+              L.acc[c].a = add<FIX>(L.acc[c].a, cb[2]);
+              L.acc[c].b = add<FIX>(L.acc[c].b, cb[3]);
+              part[c].a = add<FIX>(part[c].a, ct[2]);
+              part[c].b = add<FIX>(part[c].b, ct[3]);
+            }
+          }
+          if (L.cellB) {  // vertices xb and the next lane's xa
+            cell12<FIX>(b0.b, b0.r, b1.b, b1.r, t0.b, t0.r, t1.b, t1.r, cb, ct);
+            if (c >= 1) {
+              L.acc[c - 1].b = add<FIX>(L.acc[c - 1].b, cb[0]);
+              L.accR[c - 1] = add<FIX>(L.accR[c - 1], cb[1]);
+              part[c - 1].b = add<FIX>(part[c - 1].b, ct[0]);
+              partR[c - 1] = add<FIX>(partR[c - 1], ct[1]);
+            }
+            if (c < E3_R) {
+              L.acc[c].b = add<FIX>(L.acc[c].b, cb[2]);
+              L.accR[c] = add<FIX>(L.accR[c], cb[3]);
+              part[c].b = add<FIX>(part[c].b, ct[2]);
+              partR[c] = add<FIX>(partR[c], ct[3]);
+            }
+          }
+        }
+        b0 = b1;
+        t0 = t1;
+      }
+    }
+    // plane k complete: the left lane's B shares land on this lane's xa column
+#pragma unroll
+    for (int r = 0; r < E3_R; ++r) {
+      long long l = __shfl_up_sync(0xffffffffu, L.accR[r], 1);
+      if (L.lane == 0) l = zero;
+      L.acc[r].a = add<FIX>(L.acc[r].a, l);
     }
     if (k >= z0 && k <= q.nz && L.out_lane) {
       const bool zin = k >= 1 && k < q.nz;
-      double *out = a.y + k * q.plane + L.x;
+      long long *out = (long long *)a.y + k * q.plane;
       // scale 2^(R-52) / (12 h^2), exact power-of-two scaling of a.scale
       const double sc = FIX ? a.scale * fx::pow2d(L.R - fx::FRAC) : a.scale;
 #pragma unroll
-      for (int r = 0; r < S3_R; ++r) {
+      for (int r = 0; r < E3_R; ++r) {
         const int64_t j = j0 + r;
         if (j > q.ny) break;
-        const bool inner = zin && L.xin && j >= 1 && j < q.ny;
-        double yv = 0.0;
-        if (inner) yv = (FIX ? __ll2double_rn(L.acc[r]) : __longlong_as_double(L.acc[r])) * sc;
-        out[j * q.pitch] = yv;
+        const bool jin = zin && j >= 1 && j < q.ny;
+        const double va = FIX ? __ll2double_rn(L.acc[r].a) : __longlong_as_double(L.acc[r].a);
+        const double vb = FIX ? __ll2double_rn(L.acc[r].b) : __longlong_as_double(L.acc[r].b);
+        const long long ya = __double_as_longlong(jin && L.ina ? va * sc : 0.0);
+        const long long yb = __double_as_longlong(jin && L.inb ? vb * sc : 0.0);
+        long long *row = out + j * q.pitch;
+        if (V16 && L.oka && L.okb) {
+          *(longlong2 *)(row + L.xa) = make_longlong2(ya, yb);
+        } else {
+          if (L.oka) row[L.xa] = ya;
+          if (L.okb) row[L.xa + 1] = yb;
+        }
       }
     }
 #pragma unroll
-    for (int r = 0; r < S3_R; ++r) L.acc[r] = part[r];
-#pragma unroll
-    for (int c = 0; c < S3_R + 2; ++c) L.bk[c] = tk[c];
+    for (int r = 0; r < E3_R; ++r) {
+      L.acc[r] = part[r];
+      L.accR[r] = partR[r];
+    }
+    __syncwarp();  // every lane is done with plane k's slot before it is refilled
   }
   return z1;
 }
 
-__global__ void __launch_bounds__(S3_THREADS) k_apply_elementwise_s3(EwArgs a) {
+template <bool V16>
+__global__ void __launch_bounds__(E3_THREADS) k_apply_elementwise_s3(EwArgs a) {
+  extern __shared__ long long e3_smem[];
   const Geo &q = a.q;
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = (int64_t)blockIdx.x * (S3_THREADS / 32) + (threadIdx.x >> 5);
-  const int64_t nseg = (q.nx + 30) / 30, njc = (q.ny + S3_R) / S3_R;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * (E3_THREADS / 32) + wib;
+  const int64_t nseg = (q.nx + E3_OUT) / E3_OUT, njc = (q.ny + E3_R) / E3_R;
   const int64_t seg = gw % nseg, rest = gw / nseg;
   const int64_t jc = rest % njc, zc = rest / njc;
   const int64_t z0 = zc * a.cz;
   if (z0 > q.nz) return;
   const int64_t z1 = z0 + a.cz < q.nz + 1 ? z0 + a.cz : q.nz + 1;
-  const int64_t j0 = jc * S3_R;
+  const int64_t j0 = jc * E3_R;
   Ew3Lane L;
   L.lane = lane;
-  L.x = seg * 30 + lane - 1;
-  L.xok = L.x >= 0 && L.x <= q.nx;
-  L.xin = L.x >= 1 && L.x < q.nx;
-  L.cell_lane = lane <= 30 && L.x >= 0 && L.x < q.nx;
-  L.out_lane = lane >= 1 && lane <= 30 && L.xok;
-  L.R = S3_RMIN;
-  L.fix = true;
-  // plane z0-1 (the first layer's bottom face) and no contributions yet
+  L.buf = e3_smem + (size_t)wib * 3 * E3_BUF;
+  L.xa = seg * E3_OUT - 2 + 2 * lane;
+  L.oka = L.xa >= 0 && L.xa <= q.nx;
+  L.okb = L.xa + 1 >= 0 && L.xa + 1 <= q.nx;
+  L.ina = L.xa >= 1 && L.xa < q.nx;
+  L.inb = L.xa + 1 >= 1 && L.xa + 1 < q.nx;
+  L.cellA = L.xa >= 0 && L.xa < q.nx;
+  L.cellB = lane <= 30 && L.xa + 1 >= 0 && L.xa + 1 < q.nx;
+  L.out_lane = lane >= 1 && lane <= 30;
+  L.R = E3_RMIN;
+  // plane z0-1 (the first layer's bottom face) and no contributions yet; plane z0 in
+  // flight behind it
+  e3_issue<V16>(a, L, z0 - 1, z0, j0, true);
+  e3_issue<V16>(a, L, z0, z0, j0, true);
+  asm volatile("cp.async.wait_group 1;" ::: "memory");
+  __syncwarp();
+  bool fix = true;
   {
-    const double *ucol = a.u + (L.xok ? L.x : 0);
-    double v[S3_R + 2];
+    long long *own = e3_slot(L, z0 - 1, z0) + 2 * lane;
     unsigned em = 0;
 #pragma unroll
-    for (int c = 0; c < S3_R + 2; ++c) {
-      const int64_t j = j0 - 1 + c, z = z0 - 1;
-      v[c] = (L.xok && z >= 0 && j >= 0 && j <= q.ny) ? ucol[z * q.plane + j * q.pitch] : 0.0;
-      em = max(em, bexp(v[c]));
+    for (int c = 0; c < E3_ROWS; ++c) {
+      const longlong2 v = *(const longlong2 *)(own + c * E3_W);
+      em = max(em, max(bexp(__longlong_as_double(v.x)), bexp(__longlong_as_double(v.y))));
     }
     em = __reduce_max_sync(0xffffffffu, em);
     if (em != 0) {
       const int Rp = (int)em - 1022 + 1;
-      if (em == 2047 || Rp > S3_RMAX || Rp < S3_RMIN)
-        L.fix = false;
+      if (em == 2047 || Rp > E3_RMAX || Rp < E3_RMIN)
+        fix = false;
       else
         L.R = Rp;
     }
+    if (fix) {
 #pragma unroll
-    for (int c = 0; c < S3_R + 2; ++c) L.bk[c] = L.fix ? fx::to_fixed(v[c], 1023 + L.R) : __double_as_longlong(v[c]);
+      for (int c = 0; c < E3_ROWS; ++c) {
+        longlong2 *p = (longlong2 *)(own + c * E3_W);
+        const longlong2 v = *p;
+        *p = make_longlong2(fx::to_fixed(__longlong_as_double(v.x), 1023 + L.R),
+                            fx::to_fixed(__longlong_as_double(v.y), 1023 + L.R));
+      }
+    }
+    __syncwarp();
+    const long long zero = fix ? 0ll : __double_as_longlong(0.0);
 #pragma unroll
-    for (int r = 0; r < S3_R; ++r) L.acc[r] = L.fix ? 0ll : __double_as_longlong(0.0);
+    for (int r = 0; r < E3_R; ++r) {
+      L.acc[r] = P2{zero, zero};
+      L.accR[r] = zero;
+    }
   }
   int64_t k = z0 - 1;
-  if (L.fix) k = ew3_layers<true>(a, L, j0, z0, z1, k);
-  if (k < z1) ew3_layers<false>(a, L, j0, z0, z1, k);
+  bool resume = false;
+  if (fix) {
+    k = ew3_layers<true, V16>(a, L, j0, z0, z1, k, false);
+    resume = true;  // a switch happens after plane k+1 was waited for
+  }
+  if (k < z1) ew3_layers<false, V16>(a, L, j0, z0, z1, k, resume);
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 }  // namespace
 
 cudaError_t launch_apply_elementwise_fx3(const Geo &q, const double *u, double *y, cudaStream_t s) {
-  const int64_t nseg = (q.nx + 30) / 30, njc = (q.ny + S3_R) / S3_R;
-  const int cz = z_chunk(nseg * njc, q.nz + 1, S3_CZ, 4, 64);
+  const int64_t nseg = (q.nx + E3_OUT) / E3_OUT, njc = (q.ny + E3_R) / E3_R;
+  const int cz = z_chunk(nseg * njc, q.nz + 1, E3_CZ, 4, 64);
   const int64_t nzc = (q.nz + cz) / cz;
   const int64_t warps = nseg * njc * nzc;
-  const int64_t blocks = (warps + S3_THREADS / 32 - 1) / (S3_THREADS / 32);
+  const int64_t blocks = (warps + E3_THREADS / 32 - 1) / (E3_THREADS / 32);
   if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
   EwArgs a;
   a.q = q;
@@ -258,7 +404,23 @@ cudaError_t launch_apply_elementwise_fx3(const Geo &q, const double *u, double *
   a.y = y;
   a.scale = 1.0 / (12.0 * q.h * q.h);
   a.cz = cz;
-  k_apply_elementwise_s3<<<(unsigned)blocks, S3_THREADS, 0, s>>>(a);
+  // 16-byte pairs: even pitch (so every plane and row start is even too) and 16-byte
+  // aligned arrays
+  const bool v16 = q.pitch % 2 == 0 && ((uintptr_t)u % 16) == 0 && ((uintptr_t)y % 16) == 0;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_apply_elementwise_s3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)E3_SMEM);
+    if (!e)
+      e = cudaFuncSetAttribute(k_apply_elementwise_s3<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)E3_SMEM);
+    if (e) return e;
+    attr = true;
+  }
+  if (v16)
+    k_apply_elementwise_s3<true><<<(unsigned)blocks, E3_THREADS, E3_SMEM, s>>>(a);
+  else
+    k_apply_elementwise_s3<false><<<(unsigned)blocks, E3_THREADS, E3_SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
