@@ -40,6 +40,10 @@ enum { OP_APPLY = 0, OP_JACOBI = 1, OP_RESIDUAL = 2 };
 // integer instructions (false), whichever measured faster.
 constexpr bool OPS3_CVT[3] = {true, false, false};
 
+// Per operation: the TMA-staged kernel computes on column pairs (compute_plane2, true)
+// or one column per lane (compute_plane), whichever measured faster.
+constexpr bool OPS3_PAIRS[3] = {true, false, false};
+
 struct OpArgs {
   Geo q;
   const double *u;
@@ -52,6 +56,7 @@ struct OpArgs {
   double *norms2;    // residual: [sum r^2, sum f^2]
   int out_kind;      // residual: 0 = r in FP64, 1 = FP32, 2 = bf16 (FP64 -> FP32 -> bf16)
   int cz;            // output planes per CTA
+  bool v16;          // f and out (FP64) 16-byte aligned with an even pitch: pair accesses
 };
 
 __device__ __forceinline__ void prefetch_plane(double (&v)[O_PER], const Geo &q, const double *src,
@@ -184,6 +189,151 @@ __device__ __forceinline__ void compute_plane(const OpArgs &a, int64_t z, int x0
         rr = fma(rv, rv, rr);
         ff = fma(fv[k], fv[k], ff);
       }
+    }
+  }
+}
+
+// Lane-pair form of compute_plane for the TMA-staged kernel, whose staged column c is
+// x0 - 2 + c: lane l owns the columns 2l and 2l + 1 (xa even, xb = xa + 1) and lanes
+// 1..30 produce outputs, so every shared-memory access moves a 16-byte pair and one
+// shuffle per direction serves two outputs.  Warp w walks the 4 rows 1 + 4w ..
+// 4 + 4w.  With P as in compute_plane,
+//   2E + C at xa = (P(xa - 1) + P(xb)) + 2 Q(xa),  at xb = (P(xa) + P(xb + 1)) + 2 Q(xb),
+// P(xa - 1) being the left lane's P(xb) and P(xb + 1) the right lane's P(xa).
+struct LL2 {
+  long long a, b;
+};
+
+template <bool FIX>
+__device__ __forceinline__ LL2 add2(const LL2 &x, const LL2 &y) {
+  return LL2{add<FIX>(x.a, y.a), add<FIX>(x.b, y.b)};
+}
+
+__device__ __forceinline__ LL2 lds2(const long long *p) {
+  const longlong2 v = *(const longlong2 *)p;
+  return LL2{v.x, v.y};
+}
+
+// A pair of FP64 values of row pointer p at columns xa, xb (zeros where not wanted).
+__device__ __forceinline__ void ldg2(const double *p, int xa, bool wa, bool wb, bool v16, double &va, double &vb) {
+  if (v16 && wa && wb) {
+    const double2 v = *(const double2 *)(p + xa);
+    va = v.x;
+    vb = v.y;
+  } else {
+    va = wa ? p[xa] : 0.0;
+    vb = wb ? p[xa + 1] : 0.0;
+  }
+}
+
+template <bool FIX, int OP, bool INNER>
+__device__ __forceinline__ void compute_plane2(const OpArgs &a, int64_t z, int x0, int y0, int R,
+                                               const long long *lo, const long long *ce, const long long *up,
+                                               double &rr, double &ff) {
+  const Geo &q = a.q;
+  const int nx = (int)q.nx, ny = (int)q.ny, pitch = (int)q.pitch;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int col = 2 * lane, r0 = 1 + 4 * warp;
+  const int xa = x0 - 2 + col;  // >= x0 >= 0 on output lanes
+  const bool zin = z >= 1 && z < q.nz;
+  const bool lane_out = lane >= 1 && lane <= 30;
+  const bool oka = INNER || xa <= nx, okb = INNER || xa + 1 <= nx;
+  const bool ina = INNER || (xa >= 1 && xa < nx), inb = INNER || (xa + 1 >= 1 && xa + 1 < nx);
+  const double *fp = a.f ? a.f + z * q.plane : nullptr;
+  const double *up_src = a.u + z * q.plane;
+  double fa[4], fb[4], ua[4], ub[4];
+  if (OP != OP_APPLY) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int j = y0 - 1 + r0 + k;
+      const bool ok = lane_out && (INNER || j <= ny);
+      const bool jin = ok && zin && (INNER || (j >= 1 && j < ny));
+      ldg2(fp + j * pitch, xa, jin && ina, jin && inb, a.v16, fa[k], fb[k]);
+      if (OP == OP_JACOBI)
+        ldg2(up_src + j * pitch, xa, ok && oka, ok && okb, a.v16, ua[k], ub[k]);
+    }
+  }
+  const int e2 = R - fx::FRAC;
+  constexpr bool CVT = OPS3_CVT[OP];
+  const double cf = OP == OP_JACOBI ? a.c2 : a.c1;
+  const double sc = FIX && CVT ? cf * fx::pow2d(e2) : cf;
+  auto conv = [&](long long T) -> double { return CVT ? __ll2double_rn(T) : fx::to_double(T, e2); };
+  const long long *lc = lo + col, *uc = up + col, *cc = ce + col;
+  LL2 Cm = lds2(cc + (r0 - 1) * OS_W), Cc = lds2(cc + r0 * OS_W);
+  LL2 Wm = add2<FIX>(lds2(lc + (r0 - 1) * OS_W), lds2(uc + (r0 - 1) * OS_W));
+  LL2 Wc = add2<FIX>(lds2(lc + r0 * OS_W), lds2(uc + r0 * OS_W));
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int r = r0 + k;
+    const LL2 Cp = lds2(cc + (r + 1) * OS_W);
+    const LL2 Wp = add2<FIX>(lds2(lc + (r + 1) * OS_W), lds2(uc + (r + 1) * OS_W));
+    const LL2 V = add2<FIX>(Cm, Cp);
+    const LL2 Q = add2<FIX>(Wm, Wp);
+    const LL2 VW = add2<FIX>(V, Wc);
+    const LL2 P = add2<FIX>(add2<FIX>(VW, VW), Q);
+    const long long Pl = __shfl_up_sync(0xffffffffu, P.b, 1);
+    const long long Pr = __shfl_down_sync(0xffffffffu, P.a, 1);
+    const LL2 Cu = Cc;
+    Cm = Cc;
+    Cc = Cp;
+    Wm = Wc;
+    Wc = Wp;
+    const int j = y0 - 1 + r;
+    if (!lane_out || (!INNER && j > ny)) continue;
+    const bool jin = zin && (INNER || (j >= 1 && j < ny));
+    const bool ia = jin && ina, ib = jin && inb;
+    // 12 S u = 32 u - (2E + C); Td * sc is its term
+    double Ta = 0.0, Tb = 0.0;
+    if (ia || ib) {
+      const long long Sa = add<FIX>(add<FIX>(Pl, P.b), add<FIX>(Q.a, Q.a));
+      const long long Sb = add<FIX>(add<FIX>(P.a, Pr), add<FIX>(Q.b, Q.b));
+      if (FIX) {
+        Ta = conv(32 * Cu.a - Sa);
+        Tb = conv(32 * Cu.b - Sb);
+      } else {
+        Ta = fma(32.0, __longlong_as_double(Cu.a), -__longlong_as_double(Sa));
+        Tb = fma(32.0, __longlong_as_double(Cu.b), -__longlong_as_double(Sb));
+      }
+    }
+    const int off = j * pitch + xa;
+    double oa, ob;
+    if (OP == OP_APPLY) {
+      oa = ia ? Ta * sc : 0.0;
+      ob = ib ? Tb * sc : 0.0;
+    } else if (OP == OP_JACOBI) {
+      oa = ia ? fma(sc, Ta, fma(a.c1, fa[k], ua[k])) : ua[k];
+      ob = ib ? fma(sc, Tb, fma(a.c1, fb[k], ub[k])) : ub[k];
+    } else {
+      oa = ia ? fma(sc, Ta, fa[k]) : 0.0;
+      ob = ib ? fma(sc, Tb, fb[k]) : 0.0;
+      if (ia) {
+        rr = fma(oa, oa, rr);
+        ff = fma(fa[k], fa[k], ff);
+      }
+      if (ib) {
+        rr = fma(ob, ob, rr);
+        ff = fma(fb[k], fb[k], ff);
+      }
+    }
+    if (OP == OP_RESIDUAL && (!a.out || a.out_kind != 0)) {
+      if (a.out) {
+        const int64_t e = z * q.plane + off;  // element index
+        if (a.out_kind == 1) {
+          if (oka) ((float *)a.out)[e] = (float)oa;
+          if (okb) ((float *)a.out)[e + 1] = (float)ob;
+        } else {
+          if (oka) ((__nv_bfloat16 *)a.out)[e] = __float2bfloat16_rn((float)oa);
+          if (okb) ((__nv_bfloat16 *)a.out)[e + 1] = __float2bfloat16_rn((float)ob);
+        }
+      }
+      continue;
+    }
+    double *op = a.out + z * q.plane + off;
+    if (a.v16 && oka && okb) {
+      *(double2 *)op = make_double2(oa, ob);
+    } else {
+      if (oka) op[0] = oa;
+      if (okb) op[1] = ob;
     }
   }
 }
@@ -341,8 +491,9 @@ __global__ void __launch_bounds__(O_THREADS, ops3_min_blocks<OP>()) k_ops3(OpArg
 // Same computation as k_ops3, with the planes brought into shared memory by TMA: four
 // plane slots (lo, ce, up and the plane two ahead, which is in flight while the
 // current plane computes), one mbarrier each.  The staged box starts at x0 - 2 (an even
-// x, as TMA requires); the compute reads it one column to the right, so its column c
-// is x0 - 1 + c as in k_ops3.  A plane arrives as FP64 bits and is converted in place
+// x, as TMA requires), so staged column c is x0 - 2 + c; the lanes work on column
+// pairs (compute_plane2) or, reading the box one column to the right, on single columns
+// as in k_ops3 (compute_plane).  A plane arrives as FP64 bits and is converted in place
 // after the CTA agreed on the scale.  Wait limits: a TMA wait that runs out sets
 // g_ops3_tma_error and the CTA leaves.
 __device__ unsigned g_ops3_tma_error = 0;
@@ -435,15 +586,30 @@ __global__ void __launch_bounds__(O_THREADS, ops3_min_blocks<OP>())
     __syncthreads();
     if (!ok) break;
     if (z + 2 <= ze) issue(nx, z + 2);
-    // the staged box starts one column left of k_ops3's: read it shifted by one
-    if (fix) {
-      if (inner_tile)
-        compute_plane<true, OP, true>(a, z, (int)x0, (int)y0, R, slot(lo) + 1, slot(ce) + 1, slot(up) + 1, rr, ff);
-      else
-        compute_plane<true, OP, false>(a, z, (int)x0, (int)y0, R, slot(lo) + 1, slot(ce) + 1, slot(up) + 1, rr,
-                                       ff);
+    constexpr bool PAIRS = OPS3_PAIRS[OP];
+    if (PAIRS) {
+      if (fix) {
+        if (inner_tile)
+          compute_plane2<true, OP, true>(a, z, (int)x0, (int)y0, R, slot(lo), slot(ce), slot(up), rr, ff);
+        else
+          compute_plane2<true, OP, false>(a, z, (int)x0, (int)y0, R, slot(lo), slot(ce), slot(up), rr, ff);
+      } else {
+        compute_plane2<false, OP, false>(a, z, (int)x0, (int)y0, R, slot(lo), slot(ce), slot(up), rr, ff);
+      }
     } else {
-      compute_plane<false, OP, false>(a, z, (int)x0, (int)y0, R, slot(lo) + 1, slot(ce) + 1, slot(up) + 1, rr, ff);
+      // one column per lane: the staged box starts one column left of k_ops3's, so
+      // read it shifted by one
+      if (fix) {
+        if (inner_tile)
+          compute_plane<true, OP, true>(a, z, (int)x0, (int)y0, R, slot(lo) + 1, slot(ce) + 1, slot(up) + 1, rr,
+                                        ff);
+        else
+          compute_plane<true, OP, false>(a, z, (int)x0, (int)y0, R, slot(lo) + 1, slot(ce) + 1, slot(up) + 1, rr,
+                                         ff);
+      } else {
+        compute_plane<false, OP, false>(a, z, (int)x0, (int)y0, R, slot(lo) + 1, slot(ce) + 1, slot(up) + 1, rr,
+                                        ff);
+      }
     }
     __syncthreads();
     const int t = lo;
@@ -482,6 +648,8 @@ cudaError_t launch_op(const OpArgs &a, cudaStream_t s) {
   if (a.q.plane >= ((int64_t)1 << 31) - OS_W * OS_H) return cudaErrorInvalidValue;
   OpArgs b = a;
   b.cz = ops_cz(a.q);
+  b.v16 = a.q.pitch % 2 == 0 && ((uintptr_t)a.f % 16) == 0 &&
+          (a.out_kind != 0 || ((uintptr_t)a.out % 16) == 0);
   CUtensorMap map;
   if (tma_plane_map(a.q, a.u, OS_W, OS_H, &map)) {
     constexpr size_t smem_t = 4 * (size_t)OS_H * OS_W * sizeof(long long) + 128;

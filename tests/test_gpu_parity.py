@@ -401,3 +401,38 @@ def test_2d_sweeps_unaligned_base(n):
         torch.cuda.synchronize()
         assert rel_err(to_host(gd), oracle.gs_coloured(u, f, h, sweeps)) <= TOL_F64, sweeps
         assert rel_err(to_host(jd), oracle.jacobi(u, f, h, 2.0 / 3.0, sweeps)) <= TOL_F64, sweeps
+
+
+@pytest.mark.parametrize("n", [(70, 40, 9), (33, 9, 7)])
+def test_3d_ops_misaligned_f_and_out(n):
+    """3D apply, Jacobi step and residual with u 16-byte aligned (even pitch: the staged
+    TMA path) but f and the outputs 8 bytes off: pair accesses must fall back."""
+    h = 1.0 / max(n)
+    shape = synth.grid_shape(3, n)
+    u = synth.uniform_field(shape, 1900 + sum(n), zero_bc=False)
+    f = synth.uniform_field(shape, 1901 + sum(n))
+    pitch = shape[2] + 1 + (shape[2] + 1) % 2  # even, room for a one-element offset
+
+    def view(a, off):
+        buf = torch.full(shape[:2] + (pitch,), float("nan"), dtype=torch.float64, device="cuda")
+        v = buf[:, :, off:off + shape[2]]
+        v.copy_(torch.from_numpy(a).cuda())
+        return v
+
+    ud = view(u, 0)
+    fd = view(f, 1)
+    assert ud.data_ptr() % 16 == 0 and fd.data_ptr() % 16 == 8
+    yd = view(np.full(shape, np.nan), 1)
+    st.stencil_apply(ud, yd, h, st.FORM_STENCIL)
+    od = view(np.full(shape, np.nan), 1)
+    st.stencil_jacobi_step(ud, fd, od, h, 2.0 / 3.0)
+    rd = view(np.full(shape, np.nan), 1)
+    nrm = st.stencil_residual(ud, fd, h, r=rd)
+    torch.cuda.synchronize()
+    assert apply_err(to_host(yd), oracle.apply_stencil(u, h), u, h) <= TOL_F64
+    assert rel_err(to_host(od), oracle.jacobi(u, f, h, 2.0 / 3.0, 1)) <= TOL_F64
+    rref, nref = oracle.residual(u, f, h)
+    assert apply_err(to_host(rd), rref, u, h) <= TOL_F64
+    got = nrm.cpu().numpy()
+    assert abs(got[1] - nref[1]) <= 1e-12 * nref[1]
+    assert abs(got[0] - nref[0]) <= 1e-11 * nref[0]
