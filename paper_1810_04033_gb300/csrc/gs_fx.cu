@@ -35,6 +35,7 @@
 #include "fixed.cuh"
 #include "internal.h"
 #include "sweep_bounds.cuh"
+#include "tma.cuh"
 
 namespace stencil {
 namespace {
@@ -346,6 +347,323 @@ __global__ void __launch_bounds__(GS_THREADS, 2)
   }
 }
 
+// ------------------------------------------------------------ TMA-staged form
+// The same half sweep with the planes brought into shared memory by TMA
+// (cp.async.bulk.tensor, one mbarrier per slot, bounded waits): five plane slots hold
+// the neighbour planes z-1 and z+1 (from N), the centre plane z (from X) and, in
+// flight, the next centre plane's two new planes, issued one centre plane ahead.  A
+// staged box is 64 x 34 vertices from (x0 - 2, y0 - 2), x0 even, so staged column c is
+// x0 - 2 + c and row r is y0 - 2 + r; lane l works on the column pair 2l, 2l + 1.
+// Phase 1 (even rows, the tile grown by one vertex) writes its results into the staged
+// centre plane, whose other values are the old ones (Dirichlet vertices stay as they
+// are); phase 2 (odd rows, the tile) reads them.  Staged int64 planes already at this
+// sweep's scale are used as they arrive; FP64 planes (first sweep) or a scale change
+// are converted in place.  Used when X, N and Y are 16-byte aligned with an even pitch
+// and the result is fixed point or the Dirichlet values are not written (an exact FP64
+// copy of them stays with k_gs_half_sweep).  A wait that runs out sets
+// g_gs_tma_error and the CTA leaves (its part of the sweep is then missing).
+constexpr int GT_W = 64, GT_H = 34;          // staged box
+constexpr int GT_TX = 60, GT_TY = 30;        // output tile
+constexpr int GT_THREADS = 256;
+constexpr int GT_SLOT = GT_W * GT_H;         // elements per slot (17408 bytes)
+constexpr int GT_NSLOT = 5;
+constexpr size_t GT_SMEM = (size_t)GT_NSLOT * GT_SLOT * sizeof(long long) + 128;
+constexpr unsigned GT_WAIT = 1u << 22;
+__device__ unsigned g_gs_tma_error = 0;
+
+struct LP {
+  long long a, b;
+};
+
+template <bool FIXA>
+__device__ __forceinline__ LP addp(const LP &x, const LP &y) {
+  return LP{add<FIXA>(x.a, y.a), add<FIXA>(x.b, y.b)};
+}
+
+__device__ __forceinline__ LP ldsp(const long long *p) {
+  const longlong2 v = *(const longlong2 *)p;
+  return LP{v.x, v.y};
+}
+
+// Right-hand side pair (GF in fixed arithmetic, f otherwise) of row j at columns xa,
+// xa + 1 for an interior row; zeros where the columns leave the grid.
+__device__ __forceinline__ LP ld_rhs(const Ctx &c, const void *fplane, int j, int xa) {
+  LP p{0ll, 0ll};
+  if (!fplane || j < 1 || j >= c.ny) return p;
+  const long long *row = (const long long *)fplane + (int64_t)j * c.pitch;
+  if (xa >= 0 && xa + 1 <= c.nx) {
+    const longlong2 v = *(const longlong2 *)(row + xa);
+    p.a = v.x;
+    p.b = v.y;
+  } else if (xa >= 0 && xa <= c.nx) {
+    p.a = row[xa];
+  }
+  return p;
+}
+
+// One phase on the staged centre plane for the pair rows r0 and r0 + 2 of this warp.
+// WHICH = 1: even rows 2 + 4w, 4 + 4w on staged columns 1..62 (results also written
+// back into the centre plane); WHICH = 2: odd rows 3 + 4w, 5 + 4w (up to 31) on
+// columns 2..61.  Y receives the core (columns 2..61, rows 2..31) inside the grid.
+template <bool FIXA, int YF, bool INNER, int WHICH>
+__device__ __forceinline__ void phase_t(const Ctx &c, long long *ce, const long long *lo, const long long *up,
+                                        void *yplane, const LP (&fv)[2], long long &vmax) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int col = 2 * lane;
+  const int r0 = (WHICH == 1 ? 2 : 3) + 4 * warp;
+  const int xa = c.x0 - 2 + col;
+  // columns this phase computes: WHICH 1: 1..62, WHICH 2: 2..61
+  const bool va = WHICH == 1 ? lane >= 1 : (lane >= 1 && lane <= 30);
+  const bool vb = WHICH == 1 ? lane <= 30 : (lane >= 1 && lane <= 30);
+  const bool core = lane >= 1 && lane <= 30;
+  const bool xa_in = INNER || (xa >= 1 && xa < c.nx), xb_in = INNER || (xa + 1 >= 1 && xa + 1 < c.nx);
+  const bool xa_ok = INNER || (xa >= 0 && xa <= c.nx), xb_ok = INNER || (xa + 1 >= 0 && xa + 1 <= c.nx);
+  const long long *lc = lo + col, *uc = up + col;
+  long long *cc = ce + col;
+  LP Dm = addp<FIXA>(ldsp(lc + (r0 - 1) * GT_W), ldsp(uc + (r0 - 1) * GT_W));
+  LP Cm = ldsp(cc + (r0 - 1) * GT_W);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int r = r0 + 2 * k;
+    if (WHICH == 2 && r > 31) break;  // warp-uniform
+    const LP Dp = addp<FIXA>(ldsp(lc + (r + 1) * GT_W), ldsp(uc + (r + 1) * GT_W));
+    const LP Cp = ldsp(cc + (r + 1) * GT_W);
+    const LP W = addp<FIXA>(ldsp(lc + r * GT_W), ldsp(uc + r * GT_W));
+    const LP V = addp<FIXA>(Cm, Cp);
+    const LP Q = addp<FIXA>(Dm, Dp);
+    const LP VW = addp<FIXA>(V, W);
+    const LP P = addp<FIXA>(addp<FIXA>(VW, VW), Q);
+    const long long Pl = __shfl_up_sync(0xffffffffu, P.b, 1);
+    const long long Pr = __shfl_down_sync(0xffffffffu, P.a, 1);
+    Dm = Dp;
+    Cm = Cp;
+    const int j = c.y0 - 2 + r;
+    const bool jin = INNER || (j >= 1 && j < c.ny);
+    const bool ja = va && xa_in && jin, jb = vb && xb_in && jin;  // updated vertices
+    const LP old = ldsp(cc + r * GT_W);
+    LP nw = old;
+    const long long Sa = add<FIXA>(add<FIXA>(Pl, P.b), add<FIXA>(Q.a, Q.a));  // 2E + C
+    const long long Sb = add<FIXA>(add<FIXA>(P.a, Pr), add<FIXA>(Q.b, Q.b));
+    if (FIXA) {
+      if (ja) nw.a = shr(fv[k].a, c.df) + (Sa >> 5);
+      if (jb) nw.b = shr(fv[k].b, c.df) + (Sb >> 5);
+    } else {
+      if (ja) nw.a = __double_as_longlong(fma(__longlong_as_double(Sa), 0.03125, c.g * __longlong_as_double(fv[k].a)));
+      if (jb) nw.b = __double_as_longlong(fma(__longlong_as_double(Sb), 0.03125, c.g * __longlong_as_double(fv[k].b)));
+    }
+    if (WHICH == 1) *(longlong2 *)(cc + r * GT_W) = make_longlong2(nw.a, nw.b);
+    // Y: core rows 2..31 inside the grid; Dirichlet copies only if write_bnd
+    const bool jok = INNER || (j >= 0 && j <= c.ny);
+    const bool rcore = r >= 2 && r <= 31;
+    const bool wa = core && rcore && jok && xa_ok && (ja || c.write_bnd);
+    const bool wb = core && rcore && jok && xb_ok && (jb || c.write_bnd);
+    if (wa || wb) {
+      long long ya = nw.a, yb = nw.b;
+      if (FIXA && YF == F64) {  // last sweep: only updated vertices are written
+        ya = __double_as_longlong(fx::to_double_cvt(nw.a, c.R - fx::FRAC));
+        yb = __double_as_longlong(fx::to_double_cvt(nw.b, c.R - fx::FRAC));
+      }
+      long long *yrow = (long long *)yplane + (int64_t)j * c.pitch;
+      if (wa && wb) {
+        *(longlong2 *)(yrow + xa) = make_longlong2(ya, yb);
+      } else if (wa) {
+        yrow[xa] = ya;
+      } else {
+        yrow[xa + 1] = yb;
+      }
+      auto mag = [&](long long v) -> long long {
+        return FIXA ? (v < 0 ? -v : v) : (long long)fx::abs_bits(__longlong_as_double(v));
+      };
+      if (wa) vmax = max(vmax, mag(nw.a));
+      if (wb) vmax = max(vmax, mag(nw.b));
+    }
+  }
+}
+
+template <bool FIXA, int XF, int NF, int YF, bool INNER>
+__device__ void run_half_t(Ctx &c, int pz, int i0, int i1, const void *F, void *Y, long long *sm, uint64_t *bars,
+                           int *fail, const CUtensorMap *mapX, const CUtensorMap *mapN, long long &vmax) {
+  const Geo &q = c.q;
+  auto slot = [&](int i) -> long long * { return sm + i * GT_SLOT; };
+  unsigned ph = 0;    // bit s: parity of the next completion on slot s
+  unsigned pend = 0;  // bit s: a load into slot s not yet waited for
+  int sl_lo = 0, sl_up = 1, sl_ce = 2, sl_nup = 3, sl_nce = 4;
+  auto issue = [&](int s, const CUtensorMap *m, int64_t z) {
+    pend |= 1u << s;
+    if (threadIdx.x == 0) {
+      fence_proxy_async();  // earlier generic accesses to the slot before the TMA writes it
+      tma_load_plane(slot(s), m, c.x0 - 2, c.y0 - 2, (int)z, &bars[s], GT_SLOT * 8);
+    }
+  };
+  auto wait = [&](int s) {
+    if (!mbar_wait(&bars[s], (ph >> s) & 1u, GT_WAIT)) {
+      atomicExch(fail, 1);  // the load stays pending
+      return;
+    }
+    ph ^= 1u << s;
+    pend &= ~(1u << s);
+  };
+  // after a failed wait: wait once more (bounded) for every load still in flight so that
+  // none lands in shared memory after the CTA has left
+  auto drain = [&]() {
+    for (int s = 0; s < GT_NSLOT; ++s)
+      if (pend & (1u << s)) mbar_wait(&bars[s], (ph >> s) & 1u, GT_WAIT);
+  };
+  // bring a staged slot to this sweep's representation (format fmt, extra shift d)
+  auto convert = [&](int s, int fmt, int d) {
+    if (!FIXA || (fmt == FXP && d == 0)) return;
+    long long *p = slot(s);
+    for (int idx = threadIdx.x; idx < GT_SLOT; idx += GT_THREADS)
+      p[idx] = fmt == F64 ? fx::to_fixed(__longlong_as_double(p[idx]), 1023 + c.R) : shr(p[idx], d);
+  };
+  const char *Fc = (const char *)F;
+  char *Yc = (char *)Y;
+  const int64_t P = q.plane;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int xa = c.x0 - 2 + 2 * lane;
+  // right-hand sides of this warp's rows: phase 1 rows 2+4w, 4+4w; phase 2 rows 3+4w, 5+4w
+  auto load_f = [&](int64_t z, LP (&f1)[2], LP (&f2)[2]) {
+    const bool zin = z >= 1 && z <= q.nz - 1;
+    const void *fp = zin ? Fc + z * P * 8 : nullptr;
+    for (int k = 0; k < 2; ++k) {
+      f1[k] = ld_rhs(c, fp, c.y0 - 2 + 2 + 4 * warp + 2 * k, xa);
+      f2[k] = ld_rhs(c, fp, c.y0 - 2 + 3 + 4 * warp + 2 * k, xa);
+    }
+  };
+  {
+    const int64_t z = pz + 2 * (int64_t)i0;
+    issue(sl_lo, mapN, z - 1);
+    issue(sl_up, mapN, z + 1);
+    issue(sl_ce, mapX, z);
+    if (i0 + 1 < i1) {
+      issue(sl_nce, mapX, z + 2);
+      issue(sl_nup, mapN, z + 3);
+    }
+    wait(sl_lo);
+    __syncthreads();
+    if (*fail) {
+      drain();
+      return;
+    }
+    convert(sl_lo, NF, c.dn);
+  }
+  LP f1[2], f2[2];
+  load_f(pz + 2 * (int64_t)i0, f1, f2);
+  for (int i = i0; i < i1; ++i) {
+    const int64_t z = pz + 2 * (int64_t)i;
+    const bool zin = z >= 1 && z <= q.nz - 1;
+    wait(sl_ce);
+    wait(sl_up);
+    __syncthreads();
+    if (*fail) {  // a TMA wait ran out
+      drain();
+      return;
+    }
+    convert(sl_up, NF, c.dn);
+    convert(sl_ce, XF, c.dx);
+    __syncthreads();
+    const LP g1[2] = {f1[0], f1[1]}, g2[2] = {f2[0], f2[1]};
+    if (i + 1 < i1) load_f(z + 2, f1, f2);
+    void *yp = Yc + z * P * 8;
+    if (zin) {
+      phase_t<FIXA, YF, INNER, 1>(c, slot(sl_ce), slot(sl_lo), slot(sl_up), yp, g1, vmax);
+      __syncthreads();
+      phase_t<FIXA, YF, INNER, 2>(c, slot(sl_ce), slot(sl_lo), slot(sl_up), yp, g2, vmax);
+    } else if (c.write_bnd) {
+      // Dirichlet plane (fixed-point output): carry the core through
+      const long long *cs = slot(sl_ce);
+      for (int idx = threadIdx.x; idx < GT_TX * GT_TY; idx += GT_THREADS) {
+        const int x = c.x0 + idx % GT_TX, j = c.y0 + idx / GT_TX;
+        if (x > c.nx || j > c.ny) continue;
+        const long long v = cs[(j - c.y0 + 2) * GT_W + (x - c.x0 + 2)];
+        ((long long *)yp)[(int64_t)j * c.pitch + x] = v;
+        const long long m = FIXA ? (v < 0 ? -v : v) : (long long)fx::abs_bits(__longlong_as_double(v));
+        vmax = max(vmax, m);
+      }
+    }
+    __syncthreads();  // every access to the freed slots is done
+    // rotate: N(z+1) becomes the lower neighbour, the in-flight planes the current ones
+    const int t_lo = sl_lo, t_ce = sl_ce;
+    sl_lo = sl_up;
+    sl_up = sl_nup;
+    sl_ce = sl_nce;
+    sl_nup = t_lo;
+    sl_nce = t_ce;
+    if (i + 2 < i1) {
+      issue(sl_nce, mapX, z + 4);
+      issue(sl_nup, mapN, z + 5);
+    }
+  }
+}
+
+template <int XF, int NF, int YF>
+__global__ void __launch_bounds__(GT_THREADS, 2)
+    k_gs_half_t(Geo q, int pz, const void *X, const void *N, void *Y, const double *f, const long long *GF,
+                SweepBounds *bnd, int sweep, int sweeps, double g, int cz, bool write_bnd,
+                const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapN) {
+  extern __shared__ unsigned char gt_raw[];
+  __shared__ __align__(8) uint64_t bars[GT_NSLOT];
+  __shared__ long long red[GT_THREADS / 32];
+  __shared__ int fail;
+  long long *sm = (long long *)(((uintptr_t)gt_raw + 127) & ~(uintptr_t)127);
+  Ctx c;
+  c.q = q;
+  c.x0 = (int)blockIdx.x * GT_TX;
+  c.y0 = (int)blockIdx.y * GT_TY;
+  c.g = g;
+  c.nx = (int)q.nx;
+  c.ny = (int)q.ny;
+  c.pitch = (int)q.pitch;
+  c.write_bnd = write_bnd;
+  const Plan plan = make_plan(bnd, g, sweeps);
+  const int rd = sweep % 4, wr = (sweep + 1) % 4, cl = (sweep + 2) % 4;
+  c.R = sweep_R(bnd, rd, g);
+  const int Rx = sweep > 0 ? sweep_R(bnd, (sweep + 3) % 4, g) : c.R;
+  c.dx = XF == FXP ? c.R - Rx : 0;
+  c.dn = NF == FXP ? (pz == 0 ? c.dx : 0) : 0;
+  c.df = c.R - plan.Rf;
+  if (pz == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) bnd->umax[cl] = 0ull;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < GT_NSLOT; ++i) mbar_init(&bars[i], 1);
+    fail = 0;
+    fence_mbar_init();
+    fence_proxy_async();
+  }
+  __syncthreads();
+  const int ncentre = q.nz >= pz ? (int)((q.nz - pz) / 2 + 1) : 0;
+  const int i0 = (int)blockIdx.z * cz;
+  const int i1 = i0 + cz < ncentre ? i0 + cz : ncentre;
+  // every computed vertex (staged columns 1..62, rows 1..32) interior
+  const bool inner = c.x0 - 1 >= 1 && c.x0 + 60 <= c.nx - 1 && c.y0 - 1 >= 1 && c.y0 + 30 <= c.ny - 1;
+  long long vmax = 0;
+  if (i0 < i1) {
+    if (plan.fix) {
+      if (inner)
+        run_half_t<true, XF, NF, YF, true>(c, pz, i0, i1, GF, Y, sm, bars, &fail, &mapX, &mapN, vmax);
+      else
+        run_half_t<true, XF, NF, YF, false>(c, pz, i0, i1, GF, Y, sm, bars, &fail, &mapX, &mapN, vmax);
+    } else {
+      run_half_t<false, F64, F64, F64, false>(c, pz, i0, i1, f, Y, sm, bars, &fail, &mapX, &mapN, vmax);
+    }
+  }
+  __syncthreads();
+  if (fail && threadIdx.x == 0) atomicExch(&g_gs_tma_error, 1u);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long w = __shfl_xor_sync(0xffffffffu, vmax, o);
+    vmax = w > vmax ? w : vmax;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = vmax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long m = 0;
+    for (int w = 0; w < GT_THREADS / 32; ++w) m = red[w] > m ? red[w] : m;
+    const unsigned long long mb =
+        plan.fix ? fx::abs_bits(fx::to_double(m, c.R - fx::FRAC) * (1.0 + 0x1p-50)) : (unsigned long long)m;
+    atomicMax(&bnd->umax[wr], mb);
+  }
+}
+
 // 3/8 h^2 f in fixed point (scale Rf of the plan) on interior vertices, 0 elsewhere.
 __global__ void __launch_bounds__(256) k_prep_gf(Geo q, int dim, const double *__restrict__ f,
                                                  long long *__restrict__ GF, const SweepBounds *bnd, double g,
@@ -438,6 +756,45 @@ static cudaError_t launch_half(const Geo &q, int pz, const void *X, const void *
   return cudaGetLastError();
 }
 
+// TMA-staged half sweep; false (nothing launched) when the arrays do not allow it.
+template <int XF, int NF, int YF>
+static bool launch_half_t(const Geo &q, int pz, const void *X, const void *N, void *Y, const double *f,
+                          const long long *GF, SweepBounds *bnd, int sweep, int sweeps, double g, bool write_bnd,
+                          cudaStream_t s, cudaError_t *err) {
+  if (((uintptr_t)Y | (uintptr_t)f | (uintptr_t)GF) % 16) return false;
+  CUtensorMap mx, mn;
+  if (!tma_plane_map(q, X, GT_W, GT_H, &mx) || !tma_plane_map(q, N, GT_W, GT_H, &mn)) return false;
+  static bool attr_set = false;
+  if (!attr_set) {
+    *err = cudaFuncSetAttribute(k_gs_half_t<XF, NF, YF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GT_SMEM);
+    if (*err != cudaSuccess) return true;
+    attr_set = true;
+  }
+  const unsigned tx = (unsigned)((q.nx + 1 + GT_TX - 1) / GT_TX);
+  const unsigned ty = (unsigned)((q.ny + 1 + GT_TY - 1) / GT_TY);
+  const int64_t ncentre = (q.nz - pz) / 2 + 1;
+  const int cz = z_chunk((int64_t)tx * ty, ncentre, GS_CZ, 2, 2);
+  const unsigned tz = (unsigned)((ncentre + cz - 1) / cz);
+  if (ty > 65535 || tz > 65535) {
+    *err = cudaErrorInvalidConfiguration;
+    return true;
+  }
+  k_gs_half_t<XF, NF, YF><<<dim3(tx, ty, tz), GT_THREADS, GT_SMEM, s>>>(q, pz, X, N, Y, f, GF, bnd, sweep, sweeps,
+                                                                      g, cz, write_bnd, mx, mn);
+  *err = cudaGetLastError();
+  return true;
+}
+
+// The TMA-staged kernel where it applies, k_gs_half_sweep otherwise.
+template <int XF, int NF, int YF>
+static cudaError_t launch_half_any(const Geo &q, int pz, const void *X, const void *N, void *Y, const double *f,
+                                   const long long *GF, SweepBounds *bnd, int sweep, int sweeps, double g,
+                                   bool write_bnd, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (launch_half_t<XF, NF, YF>(q, pz, X, N, Y, f, GF, bnd, sweep, sweeps, g, write_bnd, s, &e)) return e;
+  return launch_half<XF, NF, YF>(q, pz, X, N, Y, f, GF, bnd, sweep, sweeps, g, write_bnd, s);
+}
+
 // work: 3 arrays of u's span (8 bytes per element): two ping-pong buffers and GF.
 cudaError_t launch_gs_sweeps_fx3(const Geo &q, double *u, const double *f, int sweeps, double *work,
                                  void *bounds, cudaStream_t s) {
@@ -461,15 +818,15 @@ cudaError_t launch_gs_sweeps_fx3(const Geo &q, double *u, const double *f, int s
     const bool first = it == 0, last = it == sweeps - 1;
     void *Y = last ? (void *)u : (it % 2 == 0 ? A : B);
     if (first) {
-      e = launch_half<F64, F64, FXP>(q, 0, X, X, Y, f, GF, bnd, it, sweeps, g, true, s);
-      if (!e) e = launch_half<F64, FXP, FXP>(q, 1, X, Y, Y, f, GF, bnd, it, sweeps, g, true, s);
+      e = launch_half_any<F64, F64, FXP>(q, 0, X, X, Y, f, GF, bnd, it, sweeps, g, true, s);
+      if (!e) e = launch_half_any<F64, FXP, FXP>(q, 1, X, Y, Y, f, GF, bnd, it, sweeps, g, true, s);
     } else if (!last) {
-      e = launch_half<FXP, FXP, FXP>(q, 0, X, X, Y, f, GF, bnd, it, sweeps, g, true, s);
-      if (!e) e = launch_half<FXP, FXP, FXP>(q, 1, X, Y, Y, f, GF, bnd, it, sweeps, g, true, s);
+      e = launch_half_any<FXP, FXP, FXP>(q, 0, X, X, Y, f, GF, bnd, it, sweeps, g, true, s);
+      if (!e) e = launch_half_any<FXP, FXP, FXP>(q, 1, X, Y, Y, f, GF, bnd, it, sweeps, g, true, s);
     } else {
       // the caller's u: its Dirichlet values were never overwritten, leave them
-      e = launch_half<FXP, FXP, F64>(q, 0, X, X, Y, f, GF, bnd, it, sweeps, g, false, s);
-      if (!e) e = launch_half<FXP, F64, F64>(q, 1, X, Y, Y, f, GF, bnd, it, sweeps, g, false, s);
+      e = launch_half_any<FXP, FXP, F64>(q, 0, X, X, Y, f, GF, bnd, it, sweeps, g, false, s);
+      if (!e) e = launch_half_any<FXP, F64, F64>(q, 1, X, Y, Y, f, GF, bnd, it, sweeps, g, false, s);
     }
     X = Y;
   }

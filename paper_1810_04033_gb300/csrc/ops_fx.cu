@@ -518,6 +518,7 @@ __global__ void __launch_bounds__(O_THREADS, ops3_min_blocks<OP>())
   const bool inner_tile = x0 >= 1 && x0 + OT_X <= q.nx && y0 >= 1 && y0 + OT_Y <= q.ny;
   int lo = 0, ce = 1, up = 2, nx = 3;
   unsigned phase = 0;  // bit i: parity of the next completion on slot i
+  unsigned pend = 0;   // bit i: a load into slot i not yet waited for
   bool fix = true;
   int R = R_MIN;
   double rr = 0.0, ff = 0.0;
@@ -530,6 +531,7 @@ __global__ void __launch_bounds__(O_THREADS, ops3_min_blocks<OP>())
   }
   __syncthreads();
   auto issue = [&](int s, int64_t z) {
+    pend |= 1u << s;
     if (threadIdx.x == 0) {
       fence_proxy_async();  // earlier generic accesses to this slot before the TMA writes it
       tma_load_plane(slot(s), &tmap, (int)(x0 - 2), (int)(y0 - 1), (int)z, &bars[s], OT_BOX_BYTES);
@@ -539,8 +541,12 @@ __global__ void __launch_bounds__(O_THREADS, ops3_min_blocks<OP>())
   // convert the slot in place.  Live slots are the already converted ones (-1: none);
   // a slot with a load in flight is never touched.  Returns false if the wait ran out.
   auto admit = [&](int dst, int live0, int live1) -> bool {
-    if (!mbar_wait(&bars[dst], (phase >> dst) & 1u, OT_WAIT_LIMIT)) atomicExch(&fail, 1);
-    phase ^= 1u << dst;
+    if (mbar_wait(&bars[dst], (phase >> dst) & 1u, OT_WAIT_LIMIT)) {
+      phase ^= 1u << dst;
+      pend &= ~(1u << dst);
+    } else {
+      atomicExch(&fail, 1);  // the load stays pending
+    }
 #pragma unroll
     for (int k = 0; k < O_PER; ++k) {
       const int idx = threadIdx.x + k * O_THREADS;
@@ -618,9 +624,15 @@ __global__ void __launch_bounds__(O_THREADS, ops3_min_blocks<OP>())
     up = nx;
     nx = t;
   }
-  // a wait ran out: the results are incomplete and the flag records it; the CTA still
-  // takes part in the norm reduction so that its counter stays consistent
-  if (!ok && threadIdx.x == 0) atomicExch(&g_ops3_tma_error, 1u);
+  // a wait ran out: the results are incomplete and the flag records it; every load
+  // still in flight is waited for once more (bounded) so that none lands after the CTA
+  // has left, and the CTA still takes part in the norm reduction so that its counter
+  // stays consistent
+  if (!ok) {
+    for (int s = 0; s < 4; ++s)
+      if (pend & (1u << s)) mbar_wait(&bars[s], (phase >> s) & 1u, OT_WAIT_LIMIT);
+    if (threadIdx.x == 0) atomicExch(&g_ops3_tma_error, 1u);
+  }
   if (OP == OP_RESIDUAL) ops3_reduce_norms(a, rr, ff, sh2, &last);
 }
 
