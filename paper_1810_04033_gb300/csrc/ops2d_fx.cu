@@ -166,7 +166,8 @@ __device__ __forceinline__ Pair eight_u_minus_n(const Pair &m, const Pair &c, co
               __double_as_longlong(fma(8.0, __longlong_as_double(c.b), -__longlong_as_double(Nb)))};
 }
 
-constexpr int PF = 2;      // rows in flight per warp
+constexpr int PF = 2;      // rows in flight per warp (assembled operations)
+constexpr int PF_EW = 1;   // rows in flight per warp (element-wise apply; measured faster)
 constexpr int OPS2_OUT = 60;  // output columns per warp: lanes 1..30 (one halo column per side)
 
 // Per-warp streaming state of k_ops2.
@@ -221,12 +222,12 @@ __device__ __forceinline__ int64_t ew2_rows(const Op2Args &a, WarpScale &w, Stre
   auto raw = [&](int64_t j) -> Pair {
     return (j >= 0 && j <= q.ny) ? ld_pair<V16>(ub_ + j * q.pitch, c) : Pair{0ll, 0ll};
   };
-  Pair qb[PF];  // qb[t]: raw vertex row cj + 1 for the iteration cj = cb + t
+  Pair qb[PF_EW];  // qb[t]: raw vertex row cj + 1 for the iteration cj = cb + t
 #pragma unroll
-  for (int t = 0; t < PF; ++t) qb[t] = raw(cj0 + 1 + t);
-  for (int64_t cb = cj0; cb < je; cb += PF) {
+  for (int t = 0; t < PF_EW; ++t) qb[t] = raw(cj0 + 1 + t);
+  for (int64_t cb = cj0; cb < je; cb += PF_EW) {
 #pragma unroll
-    for (int t = 0; t < PF; ++t) {
+    for (int t = 0; t < PF_EW; ++t) {
       const int64_t cj = cb + t;
       if (cj >= je) return je;
       const Pair rb = qb[t];
@@ -247,7 +248,7 @@ __device__ __forceinline__ int64_t ew2_rows(const Op2Args &a, WarpScale &w, Stre
           sc = a.c1 * fx::pow2d(w.R - fx::FRAC);
         }
       }
-      qb[t] = cj + 1 + PF <= je ? raw(cj + 1 + PF) : Pair{0ll, 0ll};
+      qb[t] = cj + 1 + PF_EW <= je ? raw(cj + 1 + PF_EW) : Pair{0ll, 0ll};
       const Pair ub = pair_in<FIX>(rb, w);
       const long long uar = __shfl_down_sync(0xffffffffu, ua.a, 1);  // (xb + 1, cj)
       const long long ubr = __shfl_down_sync(0xffffffffu, ub.a, 1);  // (xb + 1, cj + 1)

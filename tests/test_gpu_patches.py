@@ -32,7 +32,8 @@ def _run(lat, edges, seed, sweeps, u_random=True, tune=False):
 
 @pytest.mark.parametrize("lat,edges,sweeps", [((2, 2, 2), (4, 6, 8), 1), ((3, 2, 2), (4, 8, 12), 3),
                                               ((2, 3, 2), (8, 12, 16, 24, 32), 2), ((1, 1, 1), (2,), 2),
-                                              ((4, 4, 4), (8, 12, 16, 24, 32), 2)])
+                                              ((4, 4, 4), (8, 12, 16, 24, 32), 2),
+                                              ((2, 1, 1), (61, 64), 2), ((1, 2, 1), (3, 63), 1)])
 def test_patch_batch_matches_oracle(lat, edges, sweeps):
     got, ref, _ = _run(lat, edges, 11, sweeps)
     assert rel_err(got, ref) <= TOL_F64
