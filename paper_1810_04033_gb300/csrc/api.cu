@@ -300,12 +300,15 @@ int stencil_smooth_jacobi(const stencil_grid_t *g, void *u, const void *f, void 
   if (overlap(u, f, bytes) || overlap(u, work, bytes) || overlap(f, work, bytes))
     return set_error(STENCIL_EINVAL, "u, f and work must not overlap");
   cudaStream_t s = (cudaStream_t)stream;
-  if (g->op == STENCIL_OP_Q1 && g->dim == 2 && sweeps >= 2 && omega > 0.0 && omega <= 1.0) {
+  if (g->op == STENCIL_OP_Q1 && sweeps >= 2 && omega > 0.0 && omega <= 1.0) {
     void *scr = device_scratch(SCRATCH_PINGPONG, 2 * bytes, s);
     void *bnd = device_scratch(SCRATCH_BOUNDS, gs_fx_bounds_bytes(), s);
     if (!scr || !bnd) return set_error(STENCIL_ENOMEM, "jacobi workspace allocation failed");
-    cudaError_t e = launch_jacobi_sweeps_fx2(q, (double *)u, (const double *)f, sweeps, omega, (double *)work,
-                                             (double *)scr, bnd, s);
+    cudaError_t e =
+        g->dim == 2 ? launch_jacobi_sweeps_fx2(q, (double *)u, (const double *)f, sweeps, omega, (double *)work,
+                                               (double *)scr, bnd, s)
+                    : launch_jacobi_sweeps_fx3(q, (double *)u, (const double *)f, sweeps, omega, (double *)work,
+                                               (double *)scr, bnd, s);
     if (e != cudaSuccess) return set_error(STENCIL_ECUDA, std::string("jacobi: ") + cudaGetErrorString(e));
     return STENCIL_OK;
   }

@@ -106,6 +106,8 @@ cudaError_t launch_gs_sweeps_fx2(const Geo &q, double *u, const double *f, int s
 // A: one u-sized buffer; scratch: two; bounds: gs_fx_bounds_bytes().  Result in u.
 cudaError_t launch_jacobi_sweeps_fx2(const Geo &q, double *u, const double *f, int sweeps, double omega, double *A,
                                      double *scratch, void *bounds, cudaStream_t s);
+cudaError_t launch_jacobi_sweeps_fx3(const Geo &q, double *u, const double *f, int sweeps, double omega, double *A,
+                                     double *scratch, void *bounds, cudaStream_t s);
 // out_kind: r stored as 0 = FP64, 1 = FP32, 2 = bf16 (r is an element pointer of that
 // type passed as double*; the layout is u's).
 cudaError_t launch_residual_fx3(const Geo &q, const double *u, const double *f, double *r,

@@ -821,16 +821,7 @@ __global__ void __launch_bounds__(W2_THREADS) k_gs2_sweep(Geo q, const void *__r
 // fixed point, every sweep of the call runs the FP64-capable single-sweep path on FP64
 // buffers.  Lane pairs as in the Gauss-Seidel sweep; one column of halo per side, so a
 // warp produces the 60 columns of lanes 1..30.
-// floor(D Wq / 2^62) for 0 < Wq < 2^62 as the high word of D * (4 Wq) (unsigned high
-// product, corrected for D < 0); Wq = 2^62 (omega = 1) is the identity.
-struct Omega {
-  unsigned long long w4;
-  bool one;
-  __device__ __forceinline__ long long operator()(long long D) const {
-    const unsigned long long hi = __umul64hi((unsigned long long)D, w4) - (D < 0 ? w4 : 0ull);
-    return one ? D : (long long)hi;
-  }
-};
+
 
 constexpr int JAC2_OUT = 60;
 
@@ -867,7 +858,7 @@ __global__ void __launch_bounds__(W2_THREADS) k_jac2_sweep(Geo q, const void *__
   InScale<XF> cvx{1023 + R, dx > 0 ? (dx < 63 ? dx : 63) : 0, dx < 0 ? (-dx < 63 ? -dx : 63) : 0};
   const int dfr = df < 63 ? df : 63;
   if (blockIdx.x == 0 && threadIdx.x == 0) bnd->umax[(sweep + 2) % 4] = 0ull;
-  const Omega om{(unsigned long long)Wq << 2, Wq == (1ll << 62)};
+  const Omega om(Wq);
   const int64_t nseg = (q.nx + JAC2_OUT) / JAC2_OUT;
   const int64_t seg = gw % nseg, chunk = gw / nseg;
   const int64_t js = chunk * S2_ROWS;

@@ -1,5 +1,5 @@
 // Per-sweep fixed-point scale shared by the multi-sweep Gauss-Seidel and Jacobi launchers (3D:
-// gs_fx.cu, 2D: gs2_fx.cu).  Intermediate sweeps keep the iterate in HBM as int64
+// gs_fx.cu and jac3_fx.cu, 2D: ops2d_fx.cu).  Intermediate sweeps keep the iterate in HBM as int64
 // fixed point; every value of sweep s is a multiple of 2^(R_s - 52) with |v| < 2^R_s,
 // where R_s comes from a bound tracked on the device (no host round trip):
 //   B_s = max |u| written by sweep s - 1  +  4 * (3/8) h^2 max |f|,
@@ -46,6 +46,20 @@ __device__ __forceinline__ int sweep_R(const SweepBounds *bnd, int slot, double 
   const int R = fx::bound_exponent(B) + 1;  // one spare bit: rounding can never reach 2^R
   return R < -900 ? -900 : R;
 }
+
+// Damping factor of the multi-sweep Jacobi kernels as an integer product: floor(D Wq /
+// 2^62) with Wq = omega 2^62 rounded; for 0 < Wq < 2^62 it is the high word of
+// D * (4 Wq) (unsigned high product, corrected for D < 0); Wq = 2^62 (omega = 1) is the
+// identity.
+struct Omega {
+  unsigned long long w4;
+  bool one;
+  __device__ __forceinline__ Omega(long long Wq) : w4((unsigned long long)Wq << 2), one(Wq == (1ll << 62)) {}
+  __device__ __forceinline__ long long operator()(long long D) const {
+    const unsigned long long hi = __umul64hi((unsigned long long)D, w4) - (D < 0 ? w4 : 0ull);
+    return one ? D : (long long)hi;
+  }
+};
 
 // Arithmetic right shift by d (left shift for d < 0).
 __device__ __forceinline__ long long shr_any(long long v, int d) {

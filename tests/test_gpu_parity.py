@@ -185,19 +185,21 @@ def test_gs_multi_tile_and_chunk(n):
 
 
 @pytest.mark.parametrize("scale", [1e305, 1e-280, 1e-5, 1e12])
-def test_gs_extreme_magnitudes(scale):
+@pytest.mark.parametrize("pad", [0, 1])
+def test_gs_extreme_magnitudes(scale, pad):
     """Magnitudes outside the fixed-point range take the kernel's FP64 branch; the
-    others exercise the tracked bound at unusual scales."""
+    others exercise the tracked bound at unusual scales (odd pitch: register-staged
+    kernels; even pitch: TMA-staged)."""
     n = (12, 9, 14)
     h = 1.0 / 14
     shape = synth.grid_shape(3, n)
     u0 = synth.uniform_field(shape, 77, zero_bc=False) * scale
     f = synth.uniform_field(shape, 78) * scale
     ref = oracle.gs_coloured(u0, f, h, 3)
-    ud, fd = to_dev(u0), to_dev(f)
+    ud, fd = to_dev(u0, pad), to_dev(f, pad)
     st.stencil_smooth_coloured(ud, fd, h, 3)
-    jd = to_dev(u0)
-    st.stencil_smooth_jacobi(jd, fd, torch.empty_like(jd), h, 4, 0.8)
+    jd = to_dev(u0, pad)
+    st.stencil_smooth_jacobi(jd, fd, to_dev(np.zeros(shape), pad), h, 4, 0.8)
     torch.cuda.synchronize()
     assert rel_err(to_host(ud), ref) <= TOL_F64
     assert rel_err(to_host(jd), oracle.jacobi(u0, f, h, 0.8, 4)) <= TOL_F64
