@@ -130,21 +130,65 @@ __device__ __forceinline__ long long add(long long a, long long b) {
   return __double_as_longlong(__longlong_as_double(a) + __longlong_as_double(b));
 }
 
+// Software pipeline of one patch sweep: the raw values of the next step's two planes
+// are loaded into registers (up to P_PF per thread, the rest when they are stored)
+// while the current step computes, and the right-hand sides of a step's four phases
+// (up to P_FPF items per thread and phase) are loaded when the step starts.
+constexpr int P_PF = 10;
+constexpr int P_FPF = 2;
+
 template <bool FIX>
-__device__ void patch_stage(long long *slot, const double *src, int W, int rb) {
-  for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) slot[idx] = enc<FIX>(src[idx], rb);
+__device__ __forceinline__ void stage_issue(double (&pf)[P_PF], const double *u, int W, int z0, int n) {
+  const int P = W * W;
+#pragma unroll
+  for (int k = 0; k < P_PF; ++k) {
+    const int idx = threadIdx.x + k * (int)blockDim.x;  // over planes z0, z0 + 1
+    const int z = z0 + idx / P;
+    pf[k] = idx < 2 * P && z <= n ? u[(int64_t)z0 * P + idx] : 0.0;
+  }
+}
+
+// store planes z0, z0 + 1 (those <= n) into their slots: prefetched values first
+template <bool FIX, typename SlotFn>
+__device__ __forceinline__ void stage_commit(const double (&pf)[P_PF], const double *u, int W, int z0, int n,
+                                             int rb, SlotFn slot) {
+  const int P = W * W;
+#pragma unroll
+  for (int k = 0; k < P_PF; ++k) {
+    const int idx = threadIdx.x + k * (int)blockDim.x;
+    const int z = z0 + idx / P;
+    if (idx < 2 * P && z <= n) slot(z)[idx % P] = enc<FIX>(pf[k], rb);
+  }
+  for (int idx = threadIdx.x + P_PF * (int)blockDim.x; idx < 2 * P; idx += blockDim.x) {
+    const int z = z0 + idx / P;
+    if (z <= n) slot(z)[idx % P] = enc<FIX>(u[(int64_t)z0 * P + idx], rb);
+  }
+}
+
+// right-hand sides of this thread's first P_FPF items of a phase (rows of parity pr)
+__device__ __forceinline__ void phase_f(double (&fv)[P_FPF], const double *fplane, int n, int pr) {
+  const int W = n + 1;
+  const int j0 = pr ? 1 : 2;
+  const int nrows = n - 1 >= j0 ? (n - 1 - j0) / 2 + 1 : 0;
+  const int items = nrows * (n - 1);
+#pragma unroll
+  for (int k = 0; k < P_FPF; ++k) {
+    const int it = threadIdx.x + k * (int)blockDim.x;
+    fv[k] = fplane && it < items ? fplane[(j0 + 2 * (it / (n - 1))) * W + 1 + it % (n - 1)] : 0.0;
+  }
 }
 
 // rows of parity pr of plane z (interior), from planes z-1, z, z+1 in shared memory
 template <bool FIX>
 __device__ void patch_phase(long long *ce, const long long *lo, const long long *up, int n, int pr,
-                            const double *fplane, double *uplane, double g, int rb, int e2,
-                            unsigned long long &vmax) {
+                            const double *fplane, const double (&fv)[P_FPF], double *uplane, double g, int rb,
+                            int e2, unsigned long long &vmax) {
   const int W = n + 1;
   const int j0 = pr ? 1 : 2;  // first interior row of parity pr
   const int nrows = n - 1 >= j0 ? (n - 1 - j0) / 2 + 1 : 0;
   const int items = nrows * (n - 1);
-  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+  int k = 0;
+  for (int it = threadIdx.x; it < items; it += blockDim.x, ++k) {
     const int j = j0 + 2 * (it / (n - 1)), i = 1 + it % (n - 1);
     const int c = j * W + i;
     // E: edges (x,y in plane; x,z; y,z), C: corners; face weights are 0
@@ -155,12 +199,16 @@ __device__ void patch_phase(long long *ce, const long long *lo, const long long 
                                  add<FIX>(add<FIX>(up[c - W - 1], up[c - W + 1]), add<FIX>(up[c + W - 1], up[c + W + 1])));
     const long long E = add<FIX>(add<FIX>(Exy, Exz), Eyz);
     const long long S = add<FIX>(add<FIX>(E, E), C);  // 2E + C
-    const double fv = fplane[c];
+    double f0 = 0.0;
+#pragma unroll
+    for (int q = 0; q < P_FPF; ++q)
+      if (k == q) f0 = fv[q];
+    const double fval = k < P_FPF ? f0 : fplane[c];
     double un;
     if (FIX)
-      un = fma(g, fv, fx::to_double(S, e2));
+      un = fma(g, fval, fx::to_double(S, e2));
     else
-      un = fma(__longlong_as_double(S), 0.03125, g * fv);
+      un = fma(__longlong_as_double(S), 0.03125, g * fval);
     ce[c] = enc<FIX>(un, rb);
     uplane[c] = un;
     vmax = umax64(vmax, fx::abs_bits(un));
@@ -172,32 +220,40 @@ __device__ void patch_sweep(int n, double *u, const double *f, double g, int R, 
                             unsigned long long &vmax) {
   const int W = n + 1, P = W * W;
   const int rb = 1023 + R, e2 = R - fx::FRAC - 5;
-  long long *slot[4] = {smem, smem + P, smem + 2 * P, smem + 3 * P};
+  auto slot = [&](int z) -> long long * { return smem + (z & 3) * P; };
+  double pf[P_PF];
+  stage_issue<FIX>(pf, u, W, 0, n);
   for (int t = 0; 2 * t - 1 <= n; ++t) {
     const int za = 2 * t, zc = 2 * t - 1;
-    if (za <= n) patch_stage<FIX>(slot[za & 3], u + (int64_t)za * P, W, rb);
-    if (za + 1 <= n) patch_stage<FIX>(slot[(za + 1) & 3], u + (int64_t)(za + 1) * P, W, rb);
+    if (za <= n) stage_commit<FIX>(pf, u, W, za, n, rb, slot);
+    if (za + 2 <= n) stage_issue<FIX>(pf, u, W, za + 2, n);
+    const bool da = za >= 1 && za <= n - 1, dc = zc >= 1 && zc <= n - 1;
+    double fa0[P_FPF], fa1[P_FPF], fc0[P_FPF], fc1[P_FPF];
+    phase_f(fa0, da ? f + (int64_t)za * P : nullptr, n, 0);
+    phase_f(fa1, da ? f + (int64_t)za * P : nullptr, n, 1);
+    phase_f(fc0, dc ? f + (int64_t)zc * P : nullptr, n, 0);
+    phase_f(fc1, dc ? f + (int64_t)zc * P : nullptr, n, 1);
     __syncthreads();
-    if (za >= 1 && za <= n - 1) {
-      patch_phase<FIX>(slot[za & 3], slot[(za - 1) & 3], slot[(za + 1) & 3], n, 0, f + (int64_t)za * P,
-                       u + (int64_t)za * P, g, rb, e2, vmax);
+    if (da) {
+      patch_phase<FIX>(slot(za), slot(za - 1), slot(za + 1), n, 0, f + (int64_t)za * P, fa0, u + (int64_t)za * P,
+                       g, rb, e2, vmax);
       __syncthreads();
-      patch_phase<FIX>(slot[za & 3], slot[(za - 1) & 3], slot[(za + 1) & 3], n, 1, f + (int64_t)za * P,
-                       u + (int64_t)za * P, g, rb, e2, vmax);
+      patch_phase<FIX>(slot(za), slot(za - 1), slot(za + 1), n, 1, f + (int64_t)za * P, fa1, u + (int64_t)za * P,
+                       g, rb, e2, vmax);
       __syncthreads();
     }
-    if (zc >= 1 && zc <= n - 1) {
-      patch_phase<FIX>(slot[zc & 3], slot[(zc - 1) & 3], slot[(zc + 1) & 3], n, 0, f + (int64_t)zc * P,
-                       u + (int64_t)zc * P, g, rb, e2, vmax);
+    if (dc) {
+      patch_phase<FIX>(slot(zc), slot(zc - 1), slot(zc + 1), n, 0, f + (int64_t)zc * P, fc0, u + (int64_t)zc * P,
+                       g, rb, e2, vmax);
       __syncthreads();
-      patch_phase<FIX>(slot[zc & 3], slot[(zc - 1) & 3], slot[(zc + 1) & 3], n, 1, f + (int64_t)zc * P,
-                       u + (int64_t)zc * P, g, rb, e2, vmax);
+      patch_phase<FIX>(slot(zc), slot(zc - 1), slot(zc + 1), n, 1, f + (int64_t)zc * P, fc1, u + (int64_t)zc * P,
+                       g, rb, e2, vmax);
     }
     __syncthreads();
   }
 }
 
-__global__ void k_patch_gs(const PatchDev *pd, const int *order, int npatch, double *u, const double *f,
+__global__ void __launch_bounds__(512) k_patch_gs(const PatchDev *pd, const int *order, int npatch, double *u, const double *f,
                            unsigned long long *umax, const unsigned long long *hmax,
                            const unsigned long long *fmx, unsigned *counter) {
   extern __shared__ long long psm[];
@@ -366,12 +422,14 @@ int stencil_patch_batch_autotune(stencil_batch_t *b, const double *u_all, const 
   cudaEventCreate(&e1);
   const int th[] = {128, 256, 512};
   const int cps[] = {2, 4, 8};
+  int smem_sm = 0;  // shared memory per SM; each resident CTA also reserves 1 KB
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, b->device);
   float best = 1e30f;
   int bt = b->threads, bc = b->ctas_per_sm;
   int rc = STENCIL_OK;
   for (int t : th) {
     for (int c : cps) {
-      if (patch_smem(b->maxn) * c > 200 * 1024) continue;  // does not fit on an SM
+      if ((patch_smem(b->maxn) + 1024) * c > (size_t)smem_sm) continue;  // does not fit on an SM
       cudaMemcpyAsync(tmp, u_all, (size_t)b->span * sizeof(double), cudaMemcpyDeviceToDevice, s);
       rc = batch_sweeps(b, tmp, f_all, 1, s, t, c);  // warm
       if (rc) break;
