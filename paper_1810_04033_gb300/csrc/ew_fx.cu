@@ -74,6 +74,7 @@ constexpr int E3_THREADS = 128;
 constexpr int E3_OUT = 60;                      // output columns per warp
 constexpr size_t E3_SMEM = (size_t)(E3_THREADS / 32) * 3 * E3_BUF * sizeof(long long);
 constexpr int E3_RMIN = -900, E3_RMAX = 1000;
+constexpr bool E3_SPLIT = false;  // output conversion split between the pipes (measured slower here)
 
 struct P2 {
   long long a, b;  // columns xa, xb
@@ -291,10 +292,14 @@ __device__ __forceinline__ int64_t ew3_layers(const EwArgs &a, Ew3Lane &L, int64
         const int64_t j = j0 + r;
         if (j > q.ny) break;
         const bool jin = zin && j >= 1 && j < q.ny;
+        // the odd column converts with integer instructions (E3_SPLIT), moving a quarter
+        // of the conversions' FP64-pipe work to the integer pipes; the same bits
         const double va = FIX ? __ll2double_rn(L.acc[r].a) : __longlong_as_double(L.acc[r].a);
-        const double vb = FIX ? __ll2double_rn(L.acc[r].b) : __longlong_as_double(L.acc[r].b);
+        const double vb = !FIX ? __longlong_as_double(L.acc[r].b)
+                          : E3_SPLIT ? fx::to_double(L.acc[r].b, L.R - fx::FRAC) : __ll2double_rn(L.acc[r].b);
+        const double sb = FIX && E3_SPLIT ? a.scale : sc;
         const long long ya = __double_as_longlong(jin && L.ina ? va * sc : 0.0);
-        const long long yb = __double_as_longlong(jin && L.inb ? vb * sc : 0.0);
+        const long long yb = __double_as_longlong(jin && L.inb ? vb * sb : 0.0);
         long long *row = out + j * q.pitch;
         if (V16 && L.oka && L.okb) {
           *(longlong2 *)(row + L.xa) = make_longlong2(ya, yb);

@@ -40,6 +40,11 @@ enum { O2_APPLY = 0, O2_JACOBI = 1, O2_RESIDUAL = 2, O2_ELEMENTWISE = 3 };
 // always uses the FP64 pipe).
 constexpr bool OP2_CVT[4] = {true, true, false, true};
 
+// With OP2_CVT: the odd-x column of each lane pair converts with integer instructions
+// instead (true), which moves a quarter of the FP64-pipe work of the conversions onto
+// the integer pipes; both give the same bits.
+constexpr bool OP2_SPLIT[4] = {true, false, false, false};
+
 struct Op2Args {
   Geo q;
   const double *u, *f;
@@ -268,11 +273,14 @@ __device__ __forceinline__ int64_t ew2_rows(const Op2Args &a, WarpScale &w, Stre
       if (cj >= js) {
         const bool jin = cj >= 1 && cj < q.ny;
         // FIX: the converted sum times c1 2^(R-52) (exact power-of-two scaling of c1)
+        constexpr bool SPLIT = OP2_SPLIT[O2_ELEMENTWISE];
         const double va = FIX ? __ll2double_rn(alo.a) : __longlong_as_double(alo.a);
-        const double vb = FIX ? __ll2double_rn(alo.b) : __longlong_as_double(alo.b);
+        const double vb = !FIX ? __longlong_as_double(alo.b)
+                          : SPLIT ? fx::to_double(alo.b, w.R - fx::FRAC) : __ll2double_rn(alo.b);
+        const double sb = FIX && SPLIT ? a.c1 : sc;
         st_pair<V16>((long long *)a.out + cj * q.pitch, c, s.out_lane && c.oka, s.out_lane && c.okb,
                      __double_as_longlong(jin && c.ina ? va * sc : 0.0),
-                     __double_as_longlong(jin && c.inb ? vb * sc : 0.0));
+                     __double_as_longlong(jin && c.inb ? vb * sb : 0.0));
       }
       alo = ahi;
       ahi = Pair{0ll, 0ll};
@@ -294,9 +302,11 @@ __device__ __forceinline__ int64_t op2_rows(const Op2Args &a, WarpScale &w, Stre
   // CVT: T is converted by the FP64 pipe and multiplied by the factor of its term times
   // 2^(R-52) (re-formed only when R changes); otherwise by fx::to_double on the integer
   // pipe.  Both give the same bits.
-  constexpr bool CVT = OP2_CVT[OP];
+  constexpr bool CVT = OP2_CVT[OP], CVTB = CVT && !OP2_SPLIT[OP];
   const double cf = OP == O2_JACOBI ? a.c2 : a.c1;  // factor of the converted term
   double sc = FIX && CVT ? cf * fx::pow2d(w.R - fx::FRAC) : cf;
+  const double scb_int = cf;  // the odd column's factor when it converts on the integer pipe
+  auto scb = [&]() -> double { return FIX && !CVTB ? scb_int : sc; };
   auto raw = [&](int64_t j) -> Pair {
     return (j >= 0 && j <= q.ny) ? ld_pair<V16>(ub_ + j * q.pitch, c) : Pair{0ll, 0ll};
   };
@@ -317,22 +327,23 @@ __device__ __forceinline__ int64_t op2_rows(const Op2Args &a, WarpScale &w, Stre
       if (s.out_lane) {
         const bool ia = jin && c.ina, ib = jin && c.inb;
         // Td * sc == T's value times the term's factor
-        auto conv = [&](long long v) -> double {
-          return !FIX ? __longlong_as_double(v) : CVT ? __ll2double_rn(v) : fx::to_double(v, w.R - fx::FRAC);
+        auto conv = [&](long long v, bool cvt) -> double {
+          return !FIX ? __longlong_as_double(v) : cvt ? __ll2double_rn(v) : fx::to_double(v, w.R - fx::FRAC);
         };
-        const double Ta = ia ? conv(T.a) : 0.0, Tb = ib ? conv(T.b) : 0.0;
+        const double Ta = ia ? conv(T.a, CVT) : 0.0, Tb = ib ? conv(T.b, CVTB) : 0.0;
+        const double sb = scb();
         const double fa = __longlong_as_double(fv.a), fb = __longlong_as_double(fv.b);
         const double rca = __longlong_as_double(s.rc.a), rcb = __longlong_as_double(s.rc.b);
         double oa, ob;
         if (OP == O2_APPLY) {
           oa = ia ? Ta * sc : 0.0;
-          ob = ib ? Tb * sc : 0.0;
+          ob = ib ? Tb * sb : 0.0;
         } else if (OP == O2_JACOBI) {
           oa = ia ? fma(sc, Ta, fma(a.c1, fa, rca)) : rca;
-          ob = ib ? fma(sc, Tb, fma(a.c1, fb, rcb)) : rcb;
+          ob = ib ? fma(sb, Tb, fma(a.c1, fb, rcb)) : rcb;
         } else {
           oa = ia ? fma(sc, Ta, fa) : 0.0;
-          ob = ib ? fma(sc, Tb, fb) : 0.0;
+          ob = ib ? fma(sb, Tb, fb) : 0.0;
           if (ia) {
             s.rr = fma(oa, oa, s.rr);
             s.ff = fma(fa, fa, s.ff);

@@ -44,6 +44,10 @@ constexpr bool OPS3_CVT[3] = {true, false, false};
 // or one column per lane (compute_plane), whichever measured faster.
 constexpr bool OPS3_PAIRS[3] = {true, false, false};
 
+// On column pairs with OPS3_CVT: the odd-x column converts with integer instructions
+// (true), a quarter of the conversions' FP64-pipe work moved to the integer pipes.
+constexpr bool OPS3_SPLIT[3] = {true, false, false};
+
 struct OpArgs {
   Geo q;
   const double *u;
@@ -254,10 +258,11 @@ __device__ __forceinline__ void compute_plane2(const OpArgs &a, int64_t z, int x
     }
   }
   const int e2 = R - fx::FRAC;
-  constexpr bool CVT = OPS3_CVT[OP];
+  constexpr bool CVT = OPS3_CVT[OP], CVTB = CVT && !OPS3_SPLIT[OP];
   const double cf = OP == OP_JACOBI ? a.c2 : a.c1;
   const double sc = FIX && CVT ? cf * fx::pow2d(e2) : cf;
-  auto conv = [&](long long T) -> double { return CVT ? __ll2double_rn(T) : fx::to_double(T, e2); };
+  const double scb = FIX && CVTB ? sc : (FIX ? cf : sc);  // the odd column's factor
+  auto conv = [&](long long T, bool cvt) -> double { return cvt ? __ll2double_rn(T) : fx::to_double(T, e2); };
   const long long *lc = lo + col, *uc = up + col, *cc = ce + col;
   LL2 Cm = lds2(cc + (r0 - 1) * OS_W), Cc = lds2(cc + r0 * OS_W);
   LL2 Wm = add2<FIX>(lds2(lc + (r0 - 1) * OS_W), lds2(uc + (r0 - 1) * OS_W));
@@ -288,8 +293,8 @@ __device__ __forceinline__ void compute_plane2(const OpArgs &a, int64_t z, int x
       const long long Sa = add<FIX>(add<FIX>(Pl, P.b), add<FIX>(Q.a, Q.a));
       const long long Sb = add<FIX>(add<FIX>(P.a, Pr), add<FIX>(Q.b, Q.b));
       if (FIX) {
-        Ta = conv(32 * Cu.a - Sa);
-        Tb = conv(32 * Cu.b - Sb);
+        Ta = conv(32 * Cu.a - Sa, CVT);
+        Tb = conv(32 * Cu.b - Sb, CVTB);
       } else {
         Ta = fma(32.0, __longlong_as_double(Cu.a), -__longlong_as_double(Sa));
         Tb = fma(32.0, __longlong_as_double(Cu.b), -__longlong_as_double(Sb));
@@ -299,13 +304,13 @@ __device__ __forceinline__ void compute_plane2(const OpArgs &a, int64_t z, int x
     double oa, ob;
     if (OP == OP_APPLY) {
       oa = ia ? Ta * sc : 0.0;
-      ob = ib ? Tb * sc : 0.0;
+      ob = ib ? Tb * scb : 0.0;
     } else if (OP == OP_JACOBI) {
       oa = ia ? fma(sc, Ta, fma(a.c1, fa[k], ua[k])) : ua[k];
-      ob = ib ? fma(sc, Tb, fma(a.c1, fb[k], ub[k])) : ub[k];
+      ob = ib ? fma(scb, Tb, fma(a.c1, fb[k], ub[k])) : ub[k];
     } else {
       oa = ia ? fma(sc, Ta, fa[k]) : 0.0;
-      ob = ib ? fma(sc, Tb, fb[k]) : 0.0;
+      ob = ib ? fma(scb, Tb, fb[k]) : 0.0;
       if (ia) {
         rr = fma(oa, oa, rr);
         ff = fma(fa[k], fa[k], ff);
