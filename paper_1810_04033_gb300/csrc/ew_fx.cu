@@ -74,6 +74,10 @@ constexpr int E3_THREADS = 128;
 constexpr int E3_OUT = 60;                      // output columns per warp
 constexpr size_t E3_SMEM = (size_t)(E3_THREADS / 32) * 3 * E3_BUF * sizeof(long long);
 constexpr int E3_RMIN = -900, E3_RMAX = 1000;
+// Every lane evaluates both of its cells, also where a cell lies outside the grid (its
+// shares then land only on boundary vertices, whose output is 0, or on columns that
+// are not written): no divergent branch per cell.
+constexpr bool E3_ALLCELLS = true;
 constexpr bool E3_SPLIT = false;  // output conversion split between the pipes (measured slower here)
 
 struct P2 {
@@ -240,7 +244,7 @@ __device__ __forceinline__ int64_t ew3_layers(const EwArgs &a, Ew3Lane &L, int64
         const int64_t cj = j0 - 1 + c;
         if (cj >= 0 && cj < q.ny) {  // warp-uniform
           long long cb[4], ct[4];
-          if (L.cellA) {  // vertices xa, xb of rows cj, cj+1
+          if (E3_ALLCELLS || L.cellA) {  // vertices xa, xb of rows cj, cj+1
             cell12<FIX>(b0.a, b0.b, b1.a, b1.b, t0.a, t0.b, t1.a, t1.b, cb, ct);
             if (c >= 1) {
               L.acc[c - 1].a = add<FIX>(L.acc[c - 1].a, cb[0]);
@@ -255,7 +259,7 @@ __device__ __forceinline__ int64_t ew3_layers(const EwArgs &a, Ew3Lane &L, int64
               part[c].b = add<FIX>(part[c].b, ct[3]);
             }
           }
-          if (L.cellB) {  // vertices xb and the next lane's xa
+          if (E3_ALLCELLS || L.cellB) {  // vertices xb and the next lane's xa
             cell12<FIX>(b0.b, b0.r, b1.b, b1.r, t0.b, t0.r, t1.b, t1.r, cb, ct);
             if (c >= 1) {
               L.acc[c - 1].b = add<FIX>(L.acc[c - 1].b, cb[0]);

@@ -173,6 +173,10 @@ __device__ __forceinline__ Pair eight_u_minus_n(const Pair &m, const Pair &c, co
 
 constexpr int PF = 2;      // rows in flight per warp (assembled operations)
 constexpr int PF_EW = 1;   // rows in flight per warp (element-wise apply; measured faster)
+// Element-wise apply: every lane evaluates both of its cells in a cell row inside the
+// grid, also a cell beyond the last column (its shares land only on boundary vertices,
+// whose output is 0, or on columns that are not written): no divergent branch per cell.
+constexpr bool EW2_ALLCELLS = true;
 constexpr int OPS2_OUT = 60;  // output columns per warp: lanes 1..30 (one halo column per side)
 
 // Per-warp streaming state of k_ops2.
@@ -261,8 +265,8 @@ __device__ __forceinline__ int64_t ew2_rows(const Op2Args &a, WarpScale &w, Stre
       const bool cellA = crow && c.xa >= 0 && c.xa < q.nx;
       const bool cellB = crow && s.lane <= 30 && c.xa + 1 >= 0 && c.xa + 1 < q.nx;
       long long a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
-      if (cellA) cell_contrib<FIX>(ua.a, ua.b, ub.a, ub.b, a0, a1, a2, a3);
-      if (cellB) cell_contrib<FIX>(ua.b, uar, ub.b, ubr, b0, b1, b2, b3);
+      if (EW2_ALLCELLS ? crow : cellA) cell_contrib<FIX>(ua.a, ua.b, ub.a, ub.b, a0, a1, a2, a3);
+      if (EW2_ALLCELLS ? crow : cellB) cell_contrib<FIX>(ua.b, uar, ub.b, ubr, b0, b1, b2, b3);
       long long b1l = __shfl_up_sync(0xffffffffu, b1, 1), b3l = __shfl_up_sync(0xffffffffu, b3, 1);
       if (s.lane == 0) b1l = b3l = 0;
       // vertex xa: cell A (even x) then the left lane's cell B; vertex xb: A then B
