@@ -45,6 +45,10 @@ constexpr bool OP2_CVT[4] = {true, true, false, true};
 // the integer pipes; both give the same bits.
 constexpr bool OP2_SPLIT[4] = {true, false, false, false};
 
+// Per assembled operation: compute on the halo lanes too instead of branching around
+// them (true), whichever measured faster.
+constexpr bool OP2_NOBRANCH[4] = {false, false, true, false};
+
 struct Op2Args {
   Geo q;
   const double *u, *f;
@@ -328,13 +332,16 @@ __device__ __forceinline__ int64_t op2_rows(const Op2Args &a, WarpScale &w, Stre
       Pair fv{0ll, 0ll};  // FP64 bits
       if (OP != O2_APPLY && s.out_lane && jin) fv = ld_pair<V16>(fb_ + j * q.pitch, c);
       const Pair T = eight_u_minus_n<FIX>(s.um, s.uc, s.up);
-      if (s.out_lane) {
-        const bool ia = jin && c.ina, ib = jin && c.inb;
+      constexpr bool NB = OP2_NOBRANCH[OP];
+      if (NB || s.out_lane) {
+        // OP2_NOBRANCH: every lane computes (no branch around the halo lanes); only
+        // output lanes store
+        const bool ia = jin && c.ina && s.out_lane, ib = jin && c.inb && s.out_lane;
         // Td * sc == T's value times the term's factor
         auto conv = [&](long long v, bool cvt) -> double {
           return !FIX ? __longlong_as_double(v) : cvt ? __ll2double_rn(v) : fx::to_double(v, w.R - fx::FRAC);
         };
-        const double Ta = ia ? conv(T.a, CVT) : 0.0, Tb = ib ? conv(T.b, CVTB) : 0.0;
+        const double Ta = conv(T.a, CVT), Tb = conv(T.b, CVTB);
         const double sb = scb();
         const double fa = __longlong_as_double(fv.a), fb = __longlong_as_double(fv.b);
         const double rca = __longlong_as_double(s.rc.a), rcb = __longlong_as_double(s.rc.b);
@@ -358,7 +365,8 @@ __device__ __forceinline__ int64_t op2_rows(const Op2Args &a, WarpScale &w, Stre
           }
         }
         if (OP != O2_RESIDUAL || ob_)
-          st_pair<V16>(ob_ + j * q.pitch, c, c.oka, c.okb, __double_as_longlong(oa), __double_as_longlong(ob));
+          st_pair<V16>(ob_ + j * q.pitch, c, s.out_lane && c.oka, s.out_lane && c.okb, __double_as_longlong(oa),
+                       __double_as_longlong(ob));
       }
       // admit row j + 2 (after row j is done)
       if (FIX) {

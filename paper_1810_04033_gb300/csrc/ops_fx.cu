@@ -284,12 +284,13 @@ __device__ __forceinline__ void compute_plane2(const OpArgs &a, int64_t z, int x
     Wm = Wc;
     Wc = Wp;
     const int j = y0 - 1 + r;
-    if (!lane_out || (!INNER && j > ny)) continue;
+    if (!INNER && j > ny) continue;  // warp-uniform
     const bool jin = zin && (INNER || (j >= 1 && j < ny));
-    const bool ia = jin && ina, ib = jin && inb;
+    // every lane computes (no branch around the halo lanes); only output lanes store
+    const bool ia = jin && ina && lane_out, ib = jin && inb && lane_out;
     // 12 S u = 32 u - (2E + C); Td * sc is its term
     double Ta = 0.0, Tb = 0.0;
-    if (ia || ib) {
+    {
       const long long Sa = add<FIX>(add<FIX>(Pl, P.b), add<FIX>(Q.a, Q.a));
       const long long Sb = add<FIX>(add<FIX>(P.a, Pr), add<FIX>(Q.b, Q.b));
       if (FIX) {
@@ -324,21 +325,21 @@ __device__ __forceinline__ void compute_plane2(const OpArgs &a, int64_t z, int x
       if (a.out) {
         const int64_t e = z * q.plane + off;  // element index
         if (a.out_kind == 1) {
-          if (oka) ((float *)a.out)[e] = (float)oa;
-          if (okb) ((float *)a.out)[e + 1] = (float)ob;
+          if (lane_out && oka) ((float *)a.out)[e] = (float)oa;
+          if (lane_out && okb) ((float *)a.out)[e + 1] = (float)ob;
         } else {
-          if (oka) ((__nv_bfloat16 *)a.out)[e] = __float2bfloat16_rn((float)oa);
-          if (okb) ((__nv_bfloat16 *)a.out)[e + 1] = __float2bfloat16_rn((float)ob);
+          if (lane_out && oka) ((__nv_bfloat16 *)a.out)[e] = __float2bfloat16_rn((float)oa);
+          if (lane_out && okb) ((__nv_bfloat16 *)a.out)[e + 1] = __float2bfloat16_rn((float)ob);
         }
       }
       continue;
     }
     double *op = a.out + z * q.plane + off;
-    if (a.v16 && oka && okb) {
+    if (a.v16 && lane_out && oka && okb) {
       *(double2 *)op = make_double2(oa, ob);
     } else {
-      if (oka) op[0] = oa;
-      if (okb) op[1] = ob;
+      if (lane_out && oka) op[0] = oa;
+      if (lane_out && okb) op[1] = ob;
     }
   }
 }
