@@ -438,3 +438,24 @@ def test_3d_ops_misaligned_f_and_out(n):
     got = nrm.cpu().numpy()
     assert abs(got[1] - nref[1]) <= 1e-12 * nref[1]
     assert abs(got[0] - nref[0]) <= 1e-11 * nref[0]
+
+
+@pytest.mark.parametrize("pad", [0, 1])
+@pytest.mark.parametrize("sweeps", [2, 5])
+def test_gs_3d_many_tiles_and_chunks(pad, sweeps):
+    """Multi-sweep 3D GS over several (x, y) tiles with ragged tails and several plane
+    chunks (odd and even pitch: the single-pass and the two-launch kernels), nonzero
+    Dirichlet data."""
+    n = (130, 61, 45)
+    h = 1.0 / 130
+    shape = synth.grid_shape(3, n)
+    u0 = synth.uniform_field(shape, 2100 + sweeps, zero_bc=False)
+    f = synth.uniform_field(shape, 2101)
+    ref = oracle.gs_coloured(u0, f, h, sweeps)
+    ud, fd = to_dev(u0, pad), to_dev(f, pad)
+    st.stencil_smooth_coloured(ud, fd, h, sweeps)
+    torch.cuda.synchronize()
+    got = to_host(ud)
+    assert rel_err(got, ref) <= TOL_F64
+    b = ~_interior(shape)
+    assert np.array_equal(got[b], u0[b])
