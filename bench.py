@@ -649,10 +649,20 @@ def run_refine(args):
     mm = [(2 + math.cos(m * math.pi * h)) / 3 for m in modes]
     lam = a[0] * mm[1] * mm[2] + mm[0] * a[1] * mm[2] + mm[0] * mm[1] * a[2]
     uh = h * h * f / lam
-    fd = torch.from_numpy(f).cuda()
+    # rows padded to a 64-byte multiple (pitch 264), as in the grid workload: every
+    # precision then runs its TMA-staged kernels
+    pitch = pitch2(n)
+
+    def padded(a):
+        buf = torch.zeros(a.shape[:-1] + (pitch,), dtype=torch.float64, device="cuda")
+        v = buf[..., :a.shape[-1]]
+        v.copy_(torch.from_numpy(a).cuda())
+        return v
+
+    fd = padded(f)
     out = {}
     for name, prec in (("fp64", st.F64), ("fp32", st.F32), ("bf16", st.BF16)):
-        ud = torch.zeros_like(fd)
+        ud = padded(np.zeros_like(f))
         torch.cuda.synchronize()
         t = time.perf_counter()
         res = st.stencil_solve(ud, fd, h, rel_tol=1e-10, max_outer=20000, inner_sweeps=8, inner_dtype=prec,
@@ -663,7 +673,7 @@ def run_refine(args):
         out[name] = {"seconds": round(sec, 3), "corrections": res["iterations"], "sweeps": 8 * res["iterations"],
                      "relres": res["relres"], "converged": res["converged"], "rel_err_vs_closed_form": err}
     # the multigrid solver (FP64 V(2,2) cycles) on the same problem, for comparison
-    ud = torch.zeros_like(fd)
+    ud = padded(np.zeros_like(f))
     st.stencil_mg_solve(ud, fd, h, rel_tol=1e-10, max_cycles=50, history=False)  # workspace warm-up
     ud.zero_()
     torch.cuda.synchronize()
@@ -679,7 +689,7 @@ def run_refine(args):
             "mg_speedup_over_fp64_refinement": round(out["fp64"]["seconds"] / out["mg"]["seconds"], 1),
             "unit": "x (FP64 time / FP32-inner time)", "bf16_speedup": round(out["fp64"]["seconds"] /
                                                                              out["bf16"]["seconds"], 3),
-            "runs": out}
+            "pitch": pitch, "runs": out}
 
 
 def run_serve(args):

@@ -44,7 +44,13 @@ int device_sm_count() {
 
 // ------------------------------------------------------------ TMA tensor maps
 bool tma_plane_map(const Geo &q, const void *base, int box_w, int box_h, CUtensorMap *map) {
-  if ((uintptr_t)base % 16 || q.pitch % 2) return false;  // strides and base need 16-byte alignment
+  return tma_plane_map_elem(q, base, 8, box_w, box_h, map);
+}
+
+bool tma_plane_map_elem(const Geo &q, const void *base, int elem_bytes, int box_w, int box_h, CUtensorMap *map) {
+  // strides and base need 16-byte alignment
+  if ((uintptr_t)base % 16 || (q.pitch * elem_bytes) % 16) return false;
+  if (elem_bytes != 8 && elem_bytes != 4) return false;
   static std::once_flag once;
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   std::call_once(once, [] {
@@ -57,10 +63,11 @@ bool tma_plane_map(const Geo &q, const void *base, int box_w, int box_h, CUtenso
   });
   if (!encode) return false;
   const cuuint64_t dims[3] = {(cuuint64_t)q.nx + 1, (cuuint64_t)q.ny + 1, (cuuint64_t)q.nz + 1};
-  const cuuint64_t strides[2] = {(cuuint64_t)q.pitch * 8, (cuuint64_t)q.plane * 8};
+  const cuuint64_t strides[2] = {(cuuint64_t)q.pitch * elem_bytes, (cuuint64_t)q.plane * elem_bytes};
   const cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
   const cuuint32_t es[3] = {1, 1, 1};
-  return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<void *>(base), dims, strides, box, es,
+  const CUtensorMapDataType dt = elem_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  return encode(map, dt, 3, const_cast<void *>(base), dims, strides, box, es,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }

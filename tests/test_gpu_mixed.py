@@ -110,3 +110,42 @@ def test_solve_reports_not_converged_and_keeps_iterate():
     assert not res["converged"] and res["iterations"] == 3
     assert len(res["history"]) == 4 and res["history"][-1] < res["history"][0]
     assert float(ud.abs().max()) > 0
+
+
+@pytest.mark.parametrize("n", [(33, 9, 7), (64, 40, 20), (130, 61, 45)])
+def test_fp32_gs_padded_matches_fp32_oracle(n):
+    """FP32 sweeps on arrays whose pitch is a multiple of 4 floats (the TMA-staged
+    kernel): several tiles with ragged tails, nonzero Dirichlet data."""
+    h = 1.0 / max(n)
+    shape = synth.grid_shape(3, n)
+    u0 = synth.uniform_field(shape, 2200 + sum(n), zero_bc=False).astype(np.float32)
+    f = synth.uniform_field(shape, 2201 + sum(n)).astype(np.float32)
+    pad = (-shape[2]) % 4 or 4
+    for sweeps in (1, 4):
+        ref = oracle.gs_coloured_f32(u0, f, h, sweeps).astype(np.float64)
+        ud = to_dev(u0, pad, torch.float32)
+        fd = to_dev(f, pad, torch.float32)
+        assert ud.stride(1) % 4 == 0
+        st.stencil_smooth_coloured(ud, fd, h, sweeps)
+        torch.cuda.synchronize()
+        got = ud.double().cpu().numpy()
+        assert rel_err(got, ref) <= TOL_F32, sweeps
+        b = np.ones(shape, dtype=bool)
+        b[1:-1, 1:-1, 1:-1] = False
+        assert np.array_equal(got[b], u0.astype(np.float64)[b])
+
+
+def test_refinement_iterates_match_oracle_padded_fp32():
+    """FP32-inner refinement on a pitch that is a multiple of 4 (TMA-staged inner
+    sweeps): iterate k against the oracle's iterate k."""
+    n = 24
+    h = 1.0 / n
+    f = synth.sin_rhs(3, n, (2, 3, 1))
+    _, _, k, _, hist = oracle.ir_solve(np.zeros_like(f), f, h, 0.0, 3, 8, 1, keep_history=True)
+    for it in range(1, 4):
+        ud = to_dev(np.zeros_like(f), 3)
+        fd = to_dev(f, 3)
+        assert ud.stride(1) % 4 == 0
+        res = st.stencil_solve(ud, fd, h, rel_tol=0.0, max_outer=it, inner_sweeps=8, inner_dtype=st.F32)
+        assert res["iterations"] == it
+        assert rel_err(to_host(ud), hist[it - 1]) <= 1e-5, it
