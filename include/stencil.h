@@ -25,7 +25,9 @@
  * Memory.  All array arguments are DEVICE pointers owned by the caller unless a call
  *   says otherwise; the library never frees them.  Element type follows
  *   stencil_grid_t.dtype.  Pointers must be aligned to their element size; 16-byte
- *   alignment of the base and an even pitch (F64) give the fastest paths.
+ *   aligned bases with rows on 16-byte boundaries (an even pitch for F64, a multiple
+ *   of 4 for F32) give the fastest paths (plane staging by TMA, 16-byte accesses);
+ *   other layouts give the same results on slower kernels.
  * Streams.  `stream` is a cudaStream_t passed as void*; NULL selects the legacy
  *   default stream.  Calls check their arguments synchronously and report launch
  *   failures synchronously; faults inside kernels surface at the next synchronising

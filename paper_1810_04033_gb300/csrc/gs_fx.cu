@@ -14,6 +14,11 @@
 // Every value a phase reads is exactly the value the sequential colour order would
 // read, so the result equals the in-place sweep (up to rounding of the sums).
 //
+// Two kernels implement the half sweep: k_gs_half_t (further below) stages the planes by
+// TMA and works on column pairs; it is used whenever the arrays allow it (16-byte
+// aligned, even pitch).  k_gs_half_sweep, described next, stages through registers and
+// takes the remaining cases (and the single-sweep FP64 -> FP64 call).
+//
 // Tiling: a CTA owns an (x, y) tile of 58 x 30 vertices and a chunk of centre planes.
 // For each centre plane it stages the plane's odd rows and the two neighbour planes
 // (tile + 2-vertex halo) in shared memory as int64 fixed point; phase 1 (A or C) is

@@ -6,7 +6,8 @@
 // planes, reading the new even planes from Y.  In 3D, colours 2m and 2m+1 are
 // uncoupled (Q1 face weight 0), so each phase updates whole x-rows; the result equals
 // the sequential colour order.  Arithmetic is FP32 (u_new = 3/8 h^2 f + (2E + C)/32);
-// bf16 values are widened on load and rounded to nearest even on every store.
+// bf16 values are widened on load and rounded to nearest even on every store.  FP32
+// arrays that TMA can stage take k_gs_lp_t (below), the rest k_gs_lp_half.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>

@@ -8,7 +8,8 @@
 //   diagonal (r+-1, z+-1) values, P = 2(V + W) + Q, and 2E + C = P(c-1) + P(c+1) + 2Q(c).
 // A CTA owns a 60 x 32 (x, y) tile and a chunk of 32 planes; it streams z with three
 // staged planes (tile + 1-vertex halo) in shared memory and prefetches the next plane
-// into registers while it computes the current one.
+// into registers while it computes the current one (k_ops3), or has TMA bring the
+// planes two ahead into four slots (k_ops3t, used when the array allows it).
 //
 // Fixed-point scale without a pre-pass: the CTA keeps a reference exponent R that only
 // grows.  Each newly staged plane's largest exponent is reduced over the CTA first; if
