@@ -49,15 +49,24 @@ BYTES_PER_UPDATE = {"apply_elementwise": 16, "apply_stencil": 16, "gs_sweep": 24
                     "jacobi_sweep": 24, "residual": 16}
 
 
+def bytes_per_update(op, g, fd=False):
+    """Compulsory bytes per update and sweep: the Q1 2D Jacobi call runs two sweeps per
+    pass over memory (read u and 3/8 h^2 f, write u once per pair), 12 B per sweep."""
+    if op == "jacobi_sweep" and g == "2" and not fd:
+        return 12
+    return BYTES_PER_UPDATE[op]
+
+
 def pitch2(n2):
     return ((n2 + 1 + 7) // 8) * 8  # rows start on 64-byte boundaries
 
 
 def launches_per_step(n3, n2):
-    """Kernel launches of the library per step (3D: GS two launches per sweep plus two
-    per-call pre-passes; 2D: one fused launch per sweep)."""
-    d3 = 2 * N_APPLY + (2 * N_SWEEPS + 2) + N_SWEEPS + 1
-    d2 = 2 * N_APPLY + N_SWEEPS + N_SWEEPS + 1
+    """Kernel launches of the library per step (every multi-sweep call has two pre-pass
+    launches; 3D: GS two launches per sweep, Jacobi one; 2D: GS one launch per sweep,
+    Jacobi one launch per two sweeps)."""
+    d3 = 2 * N_APPLY + (2 * N_SWEEPS + 2) + (N_SWEEPS + 2) + 1
+    d2 = 2 * N_APPLY + (N_SWEEPS + 2) + (N_SWEEPS // 2 + 2) + 1
     return (d3 if n3 else 0) + (d2 if n2 else 0)
 
 
@@ -330,10 +339,10 @@ def run_gpu(args, rank, world):
     nn = n3 if top_g == "3" else n2
     units = interior(int(top_g), nn)
     ms_pass = per_op_ms[top_key] / args.steps / PASSES[top_op]
-    achieved = BYTES_PER_UPDATE[top_op] * units / (ms_pass * 1e-3) / 1e9
+    achieved = bytes_per_update(top_op, top_g) * units / (ms_pass * 1e-3) / 1e9
     per_pass = {g: {op: round(per_op_ms[(op, g)] / args.steps / PASSES[op], 4) for op in OPS}
                 for g in wl.grids}
-    gbs = {g: {op: round(BYTES_PER_UPDATE[op] * interior(int(g), wl.n[g]) /
+    gbs = {g: {op: round(bytes_per_update(op, g) * interior(int(g), wl.n[g]) /
                          (per_op_ms[(op, g)] / args.steps / PASSES[op] * 1e-3) / 1e9, 1) for op in OPS}
            for g in wl.grids}
     roofline = {"bound": "hbm", "kernel": "%s (%sD, %d cells per edge)" % (top_op, top_g, nn),
@@ -596,7 +605,7 @@ def run_fd(args):
         nn = wl.n[g]
         for op in ops:
             t = sum(e[(op, g)][0].elapsed_time(e[(op, g)][1]) for e in ev) / steps / PASSES[op]
-            b = BYTES_PER_UPDATE[op] * interior(int(g), nn)
+            b = bytes_per_update(op, g, fd=True) * interior(int(g), nn)
             per["%s_%sd" % (op, g)] = {"ms_per_pass": round(t, 4), "frac": round(b / (t * 1e-3) / 1e9 / peak, 3)}
     # red-black sweeps: colour passes with barriers vs dependency-driven tasks, and the
     # expensive stencils S(k) (k = 100 everywhere / k = 0..99 linear over the mesh)

@@ -932,6 +932,126 @@ __global__ void __launch_bounds__(W2_THREADS) k_jac2_sweep(Geo q, const void *__
   publish_bound(bnd, (sweep + 1) % 4, R, hmax, red);
 }
 
+
+// Two damped Jacobi sweeps in one pass (temporal blocking): a warp streaming down its
+// rows computes sweep 1 at row j and sweep 2 at row j - 1 from sweep 1's rows j - 2 ..
+// j, held in registers; only sweep 2 is stored.  Sweep 1 is computed on the staged
+// columns 1..62 and sweep 2 on 2..61 (the 60 output columns of lanes 1..30); a chunk
+// of rows [js, je) computes sweep 1 on rows js - 1 .. je.  Every sweep-2 value is the
+// one two separate sweeps would produce: both use the same fixed-point scale (the
+// tracked bound covers the growth of two damped sweeps, at most 2 omega 3/8 h^2 max|f|),
+// and in FP64 mode (bound unusable) the same formula as the single-sweep kernel.
+template <bool FIX>
+__device__ __forceinline__ Pair jac_row(const Pair &m, const Pair &c, const Pair &p, const Pair &rhs, bool jin,
+                                        const Cols &cl, int dfr, const Omega &om, double c1, double c2) {
+  const Pair V{add<FIX>(m.a, p.a), add<FIX>(m.b, p.b)};
+  const Pair T{add<FIX>(V.a, c.a), add<FIX>(V.b, c.b)};
+  const long long Tbl = __shfl_up_sync(0xffffffffu, T.b, 1);
+  const long long Tar = __shfl_down_sync(0xffffffffu, T.a, 1);
+  Pair un = c;  // Dirichlet values carried
+  if (jin) {
+    if (FIX) {
+      if (cl.ina) un.a = c.a + om((rhs.a >> dfr) + ((Tbl + T.b + V.a) >> 3) - c.a);
+      if (cl.inb) un.b = c.b + om((rhs.b >> dfr) + ((T.a + Tar + V.b) >> 3) - c.b);
+    } else {
+      auto upd = [&](long long u, long long N, long long f) {
+        const double Td = fma(8.0, __longlong_as_double(u), -__longlong_as_double(N));
+        return __double_as_longlong(fma(c2, Td, fma(c1, __longlong_as_double(f), __longlong_as_double(u))));
+      };
+      if (cl.ina) un.a = upd(c.a, add<false>(add<false>(Tbl, T.b), V.a), rhs.a);
+      if (cl.inb) un.b = upd(c.b, add<false>(add<false>(T.a, Tar), V.b), rhs.b);
+    }
+  }
+  return un;
+}
+
+template <bool FIX, int XF, int YF, bool V16>
+__device__ __forceinline__ void jac2x2_rows(const Geo &q, const void *X, void *Y, const long long *rhs_arr,
+                                            const Cols &c, int64_t js, int64_t je, int lane, const InScale<XF> &cvx,
+                                            int dfr, const Omega &om, double c1, double c2, int R, bool write_bnd,
+                                            unsigned &hmax) {
+  const bool out_lane = lane >= 1 && lane <= 30;
+  const long long *Xl = (const long long *)X;
+  auto rawx = [&](int64_t j) -> Pair {
+    return (j >= 0 && j <= q.ny) ? ld_pair<V16>(Xl + j * q.pitch, c) : Pair{0ll, 0ll};
+  };
+  auto rawg = [&](int64_t j) -> Pair {
+    return (j >= 1 && j < q.ny) ? ld_pair<V16>(rhs_arr + j * q.pitch, c) : Pair{0ll, 0ll};
+  };
+  auto in = [&](const Pair &p) -> Pair { return FIX ? cvx(p) : p; };
+  Pair xm = in(rawx(js - 2)), xc = in(rawx(js - 1)), xp = in(rawx(js));
+  Pair s1m{0ll, 0ll}, s1c{0ll, 0ll};  // sweep-1 rows j1 - 2, j1 - 1
+  Pair gprev{0ll, 0ll};               // rhs row j1 - 1
+  constexpr int PQ = 2;
+  Pair qx[PQ], qg[PQ];  // raw X row j1 + 2 and rhs row j1 for the iteration j1 = jb + t
+#pragma unroll
+  for (int t = 0; t < PQ; ++t) {
+    qx[t] = rawx(js + 1 + t);
+    qg[t] = rawg(js - 1 + t);
+  }
+  for (int64_t jb = js - 1; jb <= je; jb += PQ) {
+#pragma unroll
+    for (int t = 0; t < PQ; ++t) {
+      const int64_t j1 = jb + t;
+      if (j1 > je) break;  // warp-uniform
+      const Pair rn = qx[t], g1 = qg[t];
+      qx[t] = j1 + PQ <= je ? rawx(j1 + 2 + PQ) : Pair{0ll, 0ll};
+      qg[t] = j1 + PQ <= je ? rawg(j1 + PQ) : Pair{0ll, 0ll};
+      // sweep 1 at row j1 from X rows j1 - 1, j1, j1 + 1
+      const Pair s1n = jac_row<FIX>(xm, xc, xp, g1, j1 >= 1 && j1 < q.ny, c, dfr, om, c1, c2);
+      // sweep 2 at row j1 - 1 from sweep-1 rows j1 - 2, j1 - 1, j1
+      const int64_t j2 = j1 - 1;
+      if (j2 >= js && j2 < je) {
+        const Pair s2 = jac_row<FIX>(s1m, s1c, s1n, gprev, j2 >= 1 && j2 < q.ny, c, dfr, om, c1, c2);
+        // FP64 mode: the buffers hold FP64 bits, stored as they are
+        put_pair<FIX ? YF : SF_FXP, V16>(q, Y, j2, c, out_lane, write_bnd, R, s2, hmax);
+      }
+      s1m = s1c;
+      s1c = s1n;
+      gprev = g1;
+      xm = xc;
+      xc = xp;
+      xp = in(rn);
+    }
+  }
+}
+
+template <int XF, int YF, bool V16>
+__global__ void __launch_bounds__(W2_THREADS) k_jac2_sweep2(Geo q, const void *__restrict__ X, void *__restrict__ Y,
+                                                            const double *__restrict__ f,
+                                                            const long long *__restrict__ GF, SweepBounds *bnd,
+                                                            int sweep, int sweeps, double g, double omega,
+                                                            long long Wq, bool write_bnd) {
+  __shared__ unsigned red[W2_THREADS / 32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * (W2_THREADS / 32) + wib;
+  const Plan plan = make_plan(bnd, g, sweeps);
+  const int R = sweep_R(bnd, sweep % 4, g);
+  const int Rx = sweep > 0 ? sweep_R(bnd, (sweep + 3) % 4, g) : R;
+  const int dx = XF == SF_FXP ? R - Rx : 0, df = R - plan.Rf;
+  InScale<XF> cvx{1023 + R, dx > 0 ? (dx < 63 ? dx : 63) : 0, dx < 0 ? (-dx < 63 ? -dx : 63) : 0};
+  const int dfr = df < 63 ? df : 63;
+  if (blockIdx.x == 0 && threadIdx.x == 0) bnd->umax[(sweep + 2) % 4] = 0ull;
+  const Omega om(Wq);
+  const double c1 = omega * g, c2 = -omega * 0.375 / 3.0;
+  const int64_t nseg = (q.nx + JAC2_OUT) / JAC2_OUT;
+  const int64_t seg = gw % nseg, chunk = gw / nseg;
+  const int64_t js = chunk * S2_ROWS;
+  unsigned hmax = 0;
+  if (js <= q.ny) {
+    const int64_t je = js + S2_ROWS < q.ny + 1 ? js + S2_ROWS : q.ny + 1;
+    const Cols c = make_cols(q, seg * JAC2_OUT - 2 + 2 * lane);
+    if (plan.fix)
+      jac2x2_rows<true, XF, YF, V16>(q, X, Y, GF, c, js, je, lane, cvx, dfr, om, c1, c2, R, write_bnd, hmax);
+    else  // FP64 buffers throughout the call
+      jac2x2_rows<false, SF_F64, SF_F64, V16>(q, X, Y, (const long long *)f, c, js, je, lane, InScale<SF_F64>{},
+                                               0, om, c1, c2, R, write_bnd, hmax);
+  }
+  if (plan.fix) {
+    publish_bound(bnd, (sweep + 1) % 4, R, hmax, red);
+  }
+}
+
 }  // namespace
 
 // Null counts as aligned (an absent array is never accessed).
@@ -1073,33 +1193,43 @@ cudaError_t launch_jacobi_sweeps_fx2(const Geo &q, double *u, const double *f, i
   // 16-byte row pairs: even pitch and 16-byte aligned u, f (read by the FP64 path),
   // A and scratch (the buffers inside scratch then follow, span being even)
   const bool v16 = q.pitch % 2 == 0 && aligned16(u) && aligned16(f) && aligned16(A) && aligned16(scratch);
+  // two sweeps per launch (temporal blocking), a single-sweep launch for an odd rest
   const void *X = u;
-  for (int it = 0; it < sweeps && !e; ++it) {
-    const bool first = it == 0, last = it == sweeps - 1;
+  int done = 0;
+  for (int it = 0; done < sweeps && !e; ++it) {
+    // a fused launch reads X and writes Y, so it is never both the first (X = u) and the
+    // last (Y = u) launch: two sweeps in all go as two single-sweep launches
+    const bool two = sweeps - done >= 2 && sweeps != 2;
+    const bool first = done == 0, last = done + (two ? 2 : 1) == sweeps;
     void *Y = last ? (void *)u : (it % 2 == 0 ? (void *)A : B);
-    if (v16) {
-      if (first)
-        k_jac2_sweep<SF_F64, SF_FXP, true><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, omega, Wq,
-                                                                     true);
-      else if (!last)
-        k_jac2_sweep<SF_FXP, SF_FXP, true><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, omega, Wq,
-                                                                     true);
+    const bool wb = !last;  // the caller's u keeps its Dirichlet values
+#define JAC2_LAUNCH(KER, XF_, YF_, V)                                                                   \
+  KER<XF_, YF_, V><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, omega, Wq, wb)
+#define JAC2_PICK(KER, V)                                   \
+  do {                                                      \
+    if (first)                                              \
+      JAC2_LAUNCH(KER, SF_F64, SF_FXP, V);                  \
+    else if (!last)                                         \
+      JAC2_LAUNCH(KER, SF_FXP, SF_FXP, V);                  \
+    else                                                    \
+      JAC2_LAUNCH(KER, SF_FXP, SF_F64, V);                  \
+  } while (0)
+    if (two) {
+      if (v16)
+        JAC2_PICK(k_jac2_sweep2, true);
       else
-        k_jac2_sweep<SF_FXP, SF_F64, true><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, omega, Wq,
-                                                                     false);
+        JAC2_PICK(k_jac2_sweep2, false);
     } else {
-      if (first)
-        k_jac2_sweep<SF_F64, SF_FXP, false><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, omega, Wq,
-                                                                      true);
-      else if (!last)
-        k_jac2_sweep<SF_FXP, SF_FXP, false><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, omega,
-                                                                      Wq, true);
+      if (v16)
+        JAC2_PICK(k_jac2_sweep, true);
       else
-        k_jac2_sweep<SF_FXP, SF_F64, false><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, omega,
-                                                                      Wq, false);
+        JAC2_PICK(k_jac2_sweep, false);
     }
+#undef JAC2_PICK
+#undef JAC2_LAUNCH
     e = cudaGetLastError();
     X = Y;
+    done += two ? 2 : 1;
   }
   return e;
 }
