@@ -982,7 +982,7 @@ __device__ __forceinline__ void jac2x2_rows(const Geo &q, const void *X, void *Y
   Pair xm = in(rawx(js - 2)), xc = in(rawx(js - 1)), xp = in(rawx(js));
   Pair s1m{0ll, 0ll}, s1c{0ll, 0ll};  // sweep-1 rows j1 - 2, j1 - 1
   Pair gprev{0ll, 0ll};               // rhs row j1 - 1
-  constexpr int PQ = 2;
+  constexpr int PQ = 1;
   Pair qx[PQ], qg[PQ];  // raw X row j1 + 2 and rhs row j1 for the iteration j1 = jb + t
 #pragma unroll
   for (int t = 0; t < PQ; ++t) {
