@@ -50,7 +50,7 @@ bool tma_plane_map(const Geo &q, const void *base, int box_w, int box_h, CUtenso
 bool tma_plane_map_elem(const Geo &q, const void *base, int elem_bytes, int box_w, int box_h, CUtensorMap *map) {
   // strides and base need 16-byte alignment
   if ((uintptr_t)base % 16 || (q.pitch * elem_bytes) % 16) return false;
-  if (elem_bytes != 8 && elem_bytes != 4) return false;
+  if (elem_bytes != 8 && elem_bytes != 4 && elem_bytes != 2) return false;
   static std::once_flag once;
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   std::call_once(once, [] {
@@ -66,7 +66,9 @@ bool tma_plane_map_elem(const Geo &q, const void *base, int elem_bytes, int box_
   const cuuint64_t strides[2] = {(cuuint64_t)q.pitch * elem_bytes, (cuuint64_t)q.plane * elem_bytes};
   const cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
   const cuuint32_t es[3] = {1, 1, 1};
-  const CUtensorMapDataType dt = elem_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const CUtensorMapDataType dt = elem_bytes == 8   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                 : elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                   : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   return encode(map, dt, 3, const_cast<void *>(base), dims, strides, box, es,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;

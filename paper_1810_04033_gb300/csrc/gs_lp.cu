@@ -203,54 +203,80 @@ __global__ void __launch_bounds__(LP_THREADS) k_gs_lp_half(Geo q, int pz, const 
   }
 }
 
-// ------------------------------------------------------------ TMA-staged form (FP32)
+// ------------------------------------------------------------ TMA-staged form
 // The same half sweep with the planes brought into shared memory by TMA: five plane
 // slots (neighbour planes z-1 and z+1 from N, centre plane z from X, and the next
 // centre plane's two new planes in flight, issued one centre plane ahead), one mbarrier
-// each, bounded waits.  The staged box is 64 x 34 floats from (x0 - 4, y0 - 2) (x0 a
-// multiple of 56: the box starts on a 16-byte boundary), so staged column c is x0 - 4 +
-// c; lane l works on the column pair 2l, 2l + 1.  Phase 1 (even rows, the tile grown by
-// one vertex) writes its results into the staged centre plane, whose other values are
-// the old ones (Dirichlet vertices stay as they are); phase 2 (odd rows) reads them.
-// Used for FP32 storage when X, N, Y and f are 16-byte aligned and the pitch is a
-// multiple of 4.  A wait that runs out sets g_lp_tma_error and the CTA leaves.
+// each, bounded waits.  The staged box is 64 x 34 values of the storage type from
+// (x0 - HL, y0 - 2), HL chosen so that the box starts on a 16-byte boundary (FP32: tile
+// 56 wide, HL = 4; bf16: tile 48 wide, HL = 8), so staged column c is x0 - HL + c; lane
+// l works on the column pair 2l, 2l + 1.  Phase 1 (even rows, the tile grown by one
+// vertex) writes its results into the staged centre plane, whose other values are the
+// old ones (Dirichlet vertices stay as they are); phase 2 (odd rows) reads them.
+// Arithmetic as in k_gs_lp_half (FP32; bf16 widened on load, every store rounded to
+// nearest even).  Used when X, N, Y and f are 16-byte aligned and the row pitch is a
+// multiple of 16 bytes.  A wait that runs out sets g_lp_tma_error and the CTA leaves.
 constexpr int LT_W = 64, LT_H = 34;   // staged box
-constexpr int LT_TX = 56, LT_TY = 30; // output tile
-constexpr int LT_SLOT = LT_W * LT_H;  // floats per slot (8704 bytes)
+constexpr int LT_TY = 30;             // output tile rows
+constexpr int LT_SLOT = LT_W * LT_H;  // values per slot
 constexpr int LT_NSLOT = 5;
-constexpr size_t LT_SMEM = (size_t)LT_NSLOT * LT_SLOT * sizeof(float) + 128;
 constexpr unsigned LT_WAIT = 1u << 22;
 __device__ unsigned g_lp_tma_error = 0;
+
+template <typename S>
+struct LtTile;
+template <>
+struct LtTile<float> {
+  static constexpr int TX = 56, HL = 4;
+};
+template <>
+struct LtTile<__nv_bfloat16> {
+  static constexpr int TX = 48, HL = 8;
+};
+
+template <typename S>
+constexpr size_t lt_smem() {
+  return (size_t)LT_NSLOT * LT_SLOT * sizeof(S) + 128;
+}
 
 struct F2 {
   float a, b;
 };
 
-__device__ __forceinline__ F2 ldf2(const float *p) {
+__device__ __forceinline__ F2 ld2(const float *p) {
   const float2 v = *(const float2 *)p;
   return F2{v.x, v.y};
 }
+__device__ __forceinline__ F2 ld2(const __nv_bfloat16 *p) {
+  const __nv_bfloat162 v = *(const __nv_bfloat162 *)p;
+  return F2{__low2float(v), __high2float(v)};
+}
+__device__ __forceinline__ void st2(float *p, float a, float b) { *(float2 *)p = make_float2(a, b); }
+__device__ __forceinline__ void st2(__nv_bfloat16 *p, float a, float b) {
+  *(__nv_bfloat162 *)p = __floats2bfloat162_rn(a, b);
+}
 
-// One phase: WHICH 1 = even rows 2 + 4w, 4 + 4w on staged columns 3..60 (written back
-// into ce); WHICH 2 = odd rows 3 + 4w, 5 + 4w (up to 31) on columns 4..59.  Y receives
-// columns 4..59, rows 2..31 inside the grid.
-template <int WHICH>
-__device__ __forceinline__ void lpt_phase(const Geo &q, int x0, int y0, float *ce, const float *lo, const float *up,
-                                          const float *fplane, float *yplane, float g) {
+// One phase: WHICH 1 = even rows 2 + 4w, 4 + 4w on staged columns HL-1 .. HL+TX
+// (written back into ce); WHICH 2 = odd rows 3 + 4w, 5 + 4w (up to 31) on the tile's
+// columns HL .. HL+TX-1.  Y receives the tile (rows 2..31) inside the grid.
+template <typename S, int WHICH>
+__device__ __forceinline__ void lpt_phase(const Geo &q, int x0, int y0, S *ce, const S *lo, const S *up,
+                                          const S *fplane, S *yplane, float g) {
+  constexpr int TX = LtTile<S>::TX, HL = LtTile<S>::HL;
+  constexpr int c0 = WHICH == 1 ? HL - 1 : HL, c1 = WHICH == 1 ? HL + TX : HL + TX - 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int col = 2 * lane;
   const int r0 = (WHICH == 1 ? 2 : 3) + 4 * warp;
-  const int64_t xa = x0 - 4 + col;
-  const bool va = WHICH == 1 ? (lane >= 2 && lane <= 30) : (lane >= 2 && lane <= 29);
-  const bool vb = WHICH == 1 ? (lane >= 1 && lane <= 29) : (lane >= 2 && lane <= 29);
-  const bool core = lane >= 2 && lane <= 29;
+  const int64_t xa = x0 - HL + col;
+  const bool va = col >= c0 && col <= c1, vb = col + 1 >= c0 && col + 1 <= c1;
+  const bool core = col >= HL && col + 1 <= HL + TX - 1;
   const bool xa_in = xa >= 1 && xa < q.nx, xb_in = xa + 1 >= 1 && xa + 1 < q.nx;
   const bool xa_ok = xa >= 0 && xa <= q.nx, xb_ok = xa + 1 >= 0 && xa + 1 <= q.nx;
-  const float *lc = lo + col, *uc = up + col;
-  float *cc = ce + col;
-  F2 Dm = ldf2(lc + (r0 - 1) * LT_W), Dum = ldf2(uc + (r0 - 1) * LT_W);
+  const S *lc = lo + col, *uc = up + col;
+  S *cc = ce + col;
+  F2 Dm = ld2(lc + (r0 - 1) * LT_W), Dum = ld2(uc + (r0 - 1) * LT_W);
   Dm = F2{Dm.a + Dum.a, Dm.b + Dum.b};
-  F2 Cm = ldf2(cc + (r0 - 1) * LT_W);
+  F2 Cm = ld2(cc + (r0 - 1) * LT_W);
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     const int r = r0 + 2 * k;
@@ -261,16 +287,16 @@ __device__ __forceinline__ void lpt_phase(const Geo &q, int x0, int y0, float *c
     // right-hand side 3/8 h^2 f (FP32) of the updated vertices
     F2 gf{0.f, 0.f};
     if (ja && jb && fplane) {
-      const F2 fv = ldf2(fplane + j * q.pitch + xa);
+      const F2 fv = ld2(fplane + j * q.pitch + xa);
       gf = F2{g * fv.a, g * fv.b};
     } else if (fplane) {
-      if (ja) gf.a = g * fplane[j * q.pitch + xa];
-      if (jb) gf.b = g * fplane[j * q.pitch + xa + 1];
+      if (ja) gf.a = g * ld<S>(fplane, j * q.pitch + xa);
+      if (jb) gf.b = g * ld<S>(fplane, j * q.pitch + xa + 1);
     }
-    const F2 l1 = ldf2(lc + (r + 1) * LT_W), u1 = ldf2(uc + (r + 1) * LT_W);
+    const F2 l1 = ld2(lc + (r + 1) * LT_W), u1 = ld2(uc + (r + 1) * LT_W);
     const F2 Dp{l1.a + u1.a, l1.b + u1.b};
-    const F2 Cp = ldf2(cc + (r + 1) * LT_W);
-    const F2 l0 = ldf2(lc + r * LT_W), u0 = ldf2(uc + r * LT_W);
+    const F2 Cp = ld2(cc + (r + 1) * LT_W);
+    const F2 l0 = ld2(lc + r * LT_W), u0 = ld2(uc + r * LT_W);
     const F2 W{l0.a + u0.a, l0.b + u0.b};
     const F2 V{Cm.a + Cp.a, Cm.b + Cp.b}, Q{Dm.a + Dp.a, Dm.b + Dp.b};
     const F2 P{2.0f * (V.a + W.a) + Q.a, 2.0f * (V.b + W.b) + Q.b};
@@ -278,33 +304,35 @@ __device__ __forceinline__ void lpt_phase(const Geo &q, int x0, int y0, float *c
     const float Pr = __shfl_down_sync(0xffffffffu, P.a, 1);
     Dm = Dp;
     Cm = Cp;
-    const F2 old = ldf2(cc + r * LT_W);
+    const F2 old = ld2(cc + r * LT_W);
     F2 nw = old;
-    if (ja) nw.a = fmaf(Pl + P.b + 2.0f * Q.a, 0.03125f, gf.a);
-    if (jb) nw.b = fmaf(P.a + Pr + 2.0f * Q.b, 0.03125f, gf.b);
-    if (WHICH == 1) *(float2 *)(cc + r * LT_W) = make_float2(nw.a, nw.b);
+    if (ja) nw.a = quant<S>(fmaf(Pl + P.b + 2.0f * Q.a, 0.03125f, gf.a));
+    if (jb) nw.b = quant<S>(fmaf(P.a + Pr + 2.0f * Q.b, 0.03125f, gf.b));
+    if (WHICH == 1) st2(cc + r * LT_W, nw.a, nw.b);
     const bool jok = j >= 0 && j <= q.ny;
     const bool rcore = r >= 2 && r <= 31;
     const bool wa = core && rcore && jok && xa_ok, wb = core && rcore && jok && xb_ok;
-    float *yrow = yplane + j * q.pitch;
+    S *yrow = yplane + j * q.pitch;
     if (wa && wb) {
-      *(float2 *)(yrow + xa) = make_float2(nw.a, nw.b);
+      st2(yrow + xa, nw.a, nw.b);
     } else {
-      if (wa) yrow[xa] = nw.a;
-      if (wb) yrow[xa + 1] = nw.b;
+      if (wa) st<S>(yrow, xa, nw.a);
+      if (wb) st<S>(yrow, xa + 1, nw.b);
     }
   }
 }
 
-__global__ void __launch_bounds__(LP_THREADS) k_gs_lp_t(Geo q, int pz, float *Y, const float *f, float g, int cz,
+template <typename S>
+__global__ void __launch_bounds__(LP_THREADS) k_gs_lp_t(Geo q, int pz, S *Y, const S *f, float g, int cz,
                                                         const __grid_constant__ CUtensorMap mapX,
                                                         const __grid_constant__ CUtensorMap mapN) {
+  constexpr int TX = LtTile<S>::TX, HL = LtTile<S>::HL;
   extern __shared__ unsigned char lt_raw[];
   __shared__ __align__(8) uint64_t bars[LT_NSLOT];
   __shared__ int fail;
-  float *sm = (float *)(((uintptr_t)lt_raw + 127) & ~(uintptr_t)127);
-  auto slot = [&](int i) -> float * { return sm + i * LT_SLOT; };
-  const int x0 = (int)blockIdx.x * LT_TX, y0 = (int)blockIdx.y * LT_TY;
+  S *sm = (S *)(((uintptr_t)lt_raw + 127) & ~(uintptr_t)127);
+  auto slot = [&](int i) -> S * { return sm + i * LT_SLOT; };
+  const int x0 = (int)blockIdx.x * TX, y0 = (int)blockIdx.y * LT_TY;
   const int64_t ncentre = (q.nz - pz) / 2 + 1;
   const int64_t i0 = (int64_t)blockIdx.z * cz;
   const int64_t i1 = i0 + cz < ncentre ? i0 + cz : ncentre;
@@ -321,7 +349,7 @@ __global__ void __launch_bounds__(LP_THREADS) k_gs_lp_t(Geo q, int pz, float *Y,
     pend |= 1u << s;
     if (threadIdx.x == 0) {
       fence_proxy_async();  // earlier generic accesses to the slot before the TMA writes it
-      tma_load_plane(slot(s), m, x0 - 4, y0 - 2, (int)z, &bars[s], LT_SLOT * 4);
+      tma_load_plane(slot(s), m, x0 - HL, y0 - 2, (int)z, &bars[s], LT_SLOT * sizeof(S));
     }
   };
   auto wait = [&](int s) {
@@ -353,19 +381,19 @@ __global__ void __launch_bounds__(LP_THREADS) k_gs_lp_t(Geo q, int pz, float *Y,
       ok = false;
       break;
     }
-    float *yp = Y + z * q.plane;
+    S *yp = Y + z * q.plane;
     if (z >= 1 && z < q.nz) {
-      const float *fp = f + z * q.plane;
-      lpt_phase<1>(q, x0, y0, slot(sl_ce), slot(sl_lo), slot(sl_up), fp, yp, g);
+      const S *fp = f + z * q.plane;
+      lpt_phase<S, 1>(q, x0, y0, slot(sl_ce), slot(sl_lo), slot(sl_up), fp, yp, g);
       __syncthreads();
-      lpt_phase<2>(q, x0, y0, slot(sl_ce), slot(sl_lo), slot(sl_up), fp, yp, g);
+      lpt_phase<S, 2>(q, x0, y0, slot(sl_ce), slot(sl_lo), slot(sl_up), fp, yp, g);
     } else {
       // Dirichlet plane: carry the tile through
-      const float *cs = slot(sl_ce);
-      for (int idx = threadIdx.x; idx < LT_TX * LT_TY; idx += LP_THREADS) {
-        const int64_t x = x0 + idx % LT_TX, j = y0 + idx / LT_TX;
+      const S *cs = slot(sl_ce);
+      for (int idx = threadIdx.x; idx < TX * LT_TY; idx += LP_THREADS) {
+        const int64_t x = x0 + idx % TX, j = y0 + idx / TX;
         if (x > q.nx || j > q.ny) continue;
-        yp[j * q.pitch + x] = cs[(j - y0 + 2) * LT_W + (x - x0 + 4)];
+        yp[j * q.pitch + x] = cs[(j - y0 + 2) * LT_W + (x - x0 + HL)];
       }
     }
     __syncthreads();  // every access to the freed slots is done
@@ -402,19 +430,21 @@ static cudaError_t gs_lp_sweeps(const Geo &q, S *u, const S *f, int sweeps, S *w
   const unsigned tx = (unsigned)((q.nx + LP_TX) / LP_TX), ty = (unsigned)((q.ny + LP_TY) / LP_TY);
   if (ty > 65535) return cudaErrorInvalidConfiguration;
   S *X = u, *Y = work;
-  // FP32 storage: the TMA-staged kernel where the arrays allow it
+  // the TMA-staged kernel where the arrays allow it
   CUtensorMap mu, mw;
-  const bool tma = sizeof(S) == 4 && ((uintptr_t)f % 16) == 0 && tma_plane_map_elem(q, u, 4, LT_W, LT_H, &mu) &&
-                   tma_plane_map_elem(q, work, 4, LT_W, LT_H, &mw);
+  const bool tma = ((uintptr_t)f % 16) == 0 && tma_plane_map_elem(q, u, (int)sizeof(S), LT_W, LT_H, &mu) &&
+                   tma_plane_map_elem(q, work, (int)sizeof(S), LT_W, LT_H, &mw);
   if (tma) {
     static bool attr_t = false;
     if (!attr_t) {
-      cudaError_t e = cudaFuncSetAttribute(k_gs_lp_t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LT_SMEM);
+      cudaError_t e =
+          cudaFuncSetAttribute(k_gs_lp_t<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lt_smem<S>());
       if (e != cudaSuccess) return e;
       attr_t = true;
     }
   }
-  const unsigned ttx = (unsigned)((q.nx + LT_TX) / LT_TX), tty = (unsigned)((q.ny + LT_TY) / LT_TY);
+  constexpr int TTX = LtTile<S>::TX;
+  const unsigned ttx = (unsigned)((q.nx + TTX) / TTX), tty = (unsigned)((q.ny + LT_TY) / LT_TY);
   if (tty > 65535) return cudaErrorInvalidConfiguration;
   for (int it = 0; it < sweeps; ++it) {
     for (int pz = 0; pz < 2; ++pz) {
@@ -423,8 +453,8 @@ static cudaError_t gs_lp_sweeps(const Geo &q, S *u, const S *f, int sweeps, S *w
         const int cz = z_chunk((int64_t)ttx * tty, ncentre, LP_CZ, 2, 4);
         const unsigned tz = (unsigned)((ncentre + cz - 1) / cz);
         const CUtensorMap &mx = X == u ? mu : mw, &my = Y == u ? mu : mw;
-        k_gs_lp_t<<<dim3(ttx, tty, tz), LP_THREADS, LT_SMEM, s>>>(q, pz, (float *)Y, (const float *)f, g, cz, mx,
-                                                                  pz == 0 ? mx : my);
+        k_gs_lp_t<S><<<dim3(ttx, tty, tz), LP_THREADS, lt_smem<S>(), s>>>(q, pz, Y, f, g, cz, mx,
+                                                                          pz == 0 ? mx : my);
       } else {
         const int cz = z_chunk((int64_t)tx * ty, ncentre, LP_CZ, 2, 8);
         const unsigned tz = (unsigned)((ncentre + cz - 1) / cz);

@@ -64,7 +64,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsign
 // does not meet TMA's alignment rules or the driver has no encoder.
 bool tma_plane_map(const Geo &q, const void *base, int box_w, int box_h, CUtensorMap *map);
 
-// The same for elements of elem_bytes bytes (8: FP64 or int64, 4: FP32); the row pitch
+// The same for elements of elem_bytes bytes (8: FP64 or int64, 4: FP32, 2: bf16); the row pitch
 // in bytes must be a multiple of 16 and the box must start at an x whose byte offset
 // is a multiple of 16.
 bool tma_plane_map_elem(const Geo &q, const void *base, int elem_bytes, int box_w, int box_h, CUtensorMap *map);
