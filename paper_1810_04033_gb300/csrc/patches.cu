@@ -93,21 +93,25 @@ __global__ void k_patch_halo(const PatchDev *pd, const int *nbr, int npatch, dou
     const int n = pd[p].n, W = n + 1;
     const int64_t off = pd[p].off;
     unsigned long long mh = 0;
-    // shell vertices: rows (j, k) on the boundary are full rows, others only i = 0, n
-    for (int row = threadIdx.x >> 5; row < W * W; row += blockDim.x >> 5) {
-      const int j = row % W, k = row / W;
-      const bool full = j == 0 || j == n || k == 0 || k == n;
-      for (int i = full ? (threadIdx.x & 31) : (threadIdx.x & 31) * n; i <= n;
-           i += full ? 32 : 2 * n + 1) {
-        const int dx = i == 0 ? -1 : (i == n ? 1 : 0);
-        const int dy = j == 0 ? -1 : (j == n ? 1 : 0);
-        const int dz = k == 0 ? -1 : (k == n ? 1 : 0);
-        const int q = nbr[27 * p + (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)];
+    // the shell vertices by outward direction (dx, dy, dz): per axis index 0 (d = -1),
+    // n (d = +1) or 1 .. n-1 (d = 0), a rectangle per direction; one neighbour lookup
+    // per direction, the block's threads over its vertices (x fastest)
+    for (int dir = 0; dir < 27; ++dir) {
+      if (dir == 13) continue;  // (0, 0, 0): the interior
+      const int dx = dir % 3 - 1, dy = (dir / 3) % 3 - 1, dz = dir / 9 - 1;
+      const int q = nbr[27 * p + dir];
+      const int m = q >= 0 ? pd[q].n : 0, M = m + 1;
+      const int64_t qoff = q >= 0 ? pd[q].off : 0;
+      const int lx = dx ? 1 : n - 1, ly = dy ? 1 : n - 1, lz = dz ? 1 : n - 1;
+      const int bx = dx < 0 ? 0 : (dx > 0 ? n : 1), by = dy < 0 ? 0 : (dy > 0 ? n : 1),
+                bz = dz < 0 ? 0 : (dz > 0 ? n : 1);
+      const int count = lx * ly * lz;
+      for (int t = threadIdx.x; t < count; t += blockDim.x) {
+        const int i = bx + t % lx, j = by + (t / lx) % ly, k = bz + t / (lx * ly);
         double v = 0.0;
         if (q >= 0) {
-          const int m = pd[q].n, M = m + 1;
           const int iq = halo_index(i, dx, n, m), jq = halo_index(j, dy, n, m), kq = halo_index(k, dz, n, m);
-          v = u[pd[q].off + ((int64_t)kq * M + jq) * M + iq];
+          v = u[qoff + ((int64_t)kq * M + jq) * M + iq];
         }
         u[off + ((int64_t)k * W + j) * W + i] = v;
         mh = umax64(mh, fx::abs_bits(v));
