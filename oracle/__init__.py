@@ -36,6 +36,7 @@ def lib():
             "oracle_gs_coloured_bf16": (None, [ci, i64p, cd, u16p, u16p, ci]),
             "oracle_jacobi": (None, [ci, i64p, cd, dp, dp, dp, cd, ci, ci]),
             "oracle_residual": (None, [ci, i64p, cd, dp, dp, dp, dp, ci]),
+            "oracle_residual_ld": (None, [ci, i64p, cd, dp, dp, dp]),
             "oracle_ir_solve": (ci, [ci, i64p, cd, dp, dp, cd, ci, ci, ci, dp, dp,
                                      ctypes.POINTER(ctypes.c_int)]),
             "oracle_patch_halo_fill": (None, [i32p, i32p, i64p, dp]),
@@ -162,6 +163,17 @@ def residual(u, f, h, nthreads=1):
                           _ptr(f, ctypes.c_double), _ptr(r, ctypes.c_double),
                           _ptr(nrm, ctypes.c_double), nthreads)
     return r, nrm
+
+
+def residual_norms_ld(u, f, h):
+    """[sum r^2, sum f^2] computed in long double (returned as doubles)."""
+    u = _f64(u)
+    f = _f64(f)
+    nrm = np.zeros(2)
+    dim, n = _grid(u.shape)
+    lib().oracle_residual_ld(dim, _ptr(n, ctypes.c_int64), h, _ptr(u, ctypes.c_double),
+                             _ptr(f, ctypes.c_double), _ptr(nrm, ctypes.c_double))
+    return nrm
 
 
 def ir_solve(x0, f, h, tol, max_outer, inner_sweeps, inner_prec, keep_history=False):

@@ -25,7 +25,10 @@
  *                             casts; sweep vs FP32 sweep within bf16 rounding.
  *   oracle_jacobi             pinned: closed-form eigenmode damping factor; dense
  *                             brute force.
- *   oracle_residual           pinned: dense brute force; zero at the discrete solution.
+ *   oracle_residual           pinned: dense brute force; zero at the discrete solution;
+ *                             exact rational arithmetic on tiny grids, within a
+ *                             forward error bound.
+ *   oracle_residual_ld        pinned: exact rational arithmetic on tiny grids.
  *   oracle_ir_solve           pinned: converges to the closed-form discrete solution of
  *                             the manufactured problem; FP64 inner equals plain GS.
  *   oracle_mg_*               pinned: Galerkin identity R A_h P = A_2h on random
@@ -363,6 +366,45 @@ void oracle_residual(int dim, const int64_t *n, double h, const double *u,
   norms2[0] = rr;
   norms2[1] = ff;
   if (!r) free(res);
+}
+
+/* The same norms in long double throughout (stencil weights as long double quotients,
+ * products, the division by h^2 and both sums), from the same FP64 inputs: a near-exact
+ * value against which the rounding of oracle_residual itself can be bounded (the FP64
+ * norms must lie within a standard forward error bound of these).  One thread,
+ * lexicographic order; norms2_ld receives the two sums rounded to double. */
+static long double stencil_weight_ld(int dim, int dx, int dy, int dz) {
+  const int m = (dx != 0) + (dy != 0) + (dim == 3 ? (dz != 0) : 0);
+  if (m == 0) return 8.0L / 3.0L;
+  if (dim == 2) return -1.0L / 3.0L;
+  if (m == 1) return 0.0L;
+  if (m == 2) return -1.0L / 6.0L;
+  return -1.0L / 12.0L;
+}
+
+void oracle_residual_ld(int dim, const int64_t *n, double h, const double *u,
+                        const double *f, double *norms2_ld) {
+  const int64_t nzc = nz_cells(dim, n);
+  const long double h2 = (long double)h * (long double)h;
+  const int zlo = dim == 3 ? -1 : 0, zhi = dim == 3 ? 1 : 0;
+  long double rr = 0.0L, ff = 0.0L;
+  for (int64_t k = 0; k <= nzc; ++k)
+    for (int64_t j = 0; j <= n[1]; ++j)
+      for (int64_t i = 0; i <= n[0]; ++i) {
+        if (!is_interior(dim, n, i, j, k)) continue;
+        long double s = 0.0L;
+        for (int dz = zlo; dz <= zhi; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx)
+              s += stencil_weight_ld(dim, dx, dy, dz) *
+                   (long double)u[vidx(n, i + dx, j + dy, k + dz)];
+        const long double fi = (long double)f[vidx(n, i, j, k)];
+        const long double r = fi - s / h2;
+        rr += r * r;
+        ff += fi * fi;
+      }
+  norms2_ld[0] = (double)rr;
+  norms2_ld[1] = (double)ff;
 }
 
 /* ------------------------------------------------------ iterative refinement */

@@ -78,6 +78,12 @@ void oracle_jacobi(int dim, const int64_t *n, double h, double *u,
 void oracle_residual(int dim, const int64_t *n, double h, const double *u,
                      const double *f, double *r, double *norms2, int nthreads);
 
+/* The two norms of oracle_residual computed in long double throughout from the same
+ * FP64 inputs (rounded to double on return): a near-exact value that bounds the FP64
+ * oracle's own rounding. */
+void oracle_residual_ld(int dim, const int64_t *n, double h, const double *u,
+                        const double *f, double *norms2_ld);
+
 /* Mixed-precision iterative refinement (see oracle.c for the steps).
  * inner_prec: 0 = FP64, 1 = FP32, 2 = bf16 storage / FP32 arithmetic.
  * x (in/out) holds the FP64 iterate incl. its Dirichlet boundary.

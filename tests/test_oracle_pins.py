@@ -349,6 +349,72 @@ def test_residual_equals_dense_and_vanishes_at_discrete_solution():
     assert math.sqrt(nrm2[0] / nrm2[1]) < 1e-14
 
 
+def _exact_weight(dim, m):
+    """Assembled Q1 stencil weight as an exact rational (m = coordinates that differ)."""
+    if m == 0:
+        return Fraction(8, 3)
+    if dim == 2:
+        return Fraction(-1, 3)
+    return [None, Fraction(0), Fraction(-1, 6), Fraction(-1, 12)][m]
+
+
+@pytest.mark.parametrize("dim,n", [(2, 7), (3, 5)])
+def test_residual_norms_against_exact_rational_arithmetic(dim, n):
+    """The norms of r = f - S u / h^2 over the interior, evaluated exactly in rational
+    arithmetic on the FP64 inputs.  The long double oracle must agree to far below
+    FP64 rounding; the FP64 oracle within a forward error bound: each r_i carries at
+    most (K + 8) eps (|f_i| + sum |w||u| / h^2) (K stencil products, the rounded
+    weights, h^2 and the division), and the sum of N squares a further (N + 2) eps."""
+    h = 1.0 / n
+    shape = synth.grid_shape(dim, n)
+    u = synth.uniform_field(shape, 91 + dim)
+    f = synth.uniform_field(shape, 93 + dim)
+    hq = Fraction(h)
+    offs = [(dz, dy, dx) for dz in ((-1, 0, 1) if dim == 3 else (0,)) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+    u3 = u.reshape((1,) + u.shape) if dim == 2 else u
+    f3 = f.reshape((1,) + f.shape) if dim == 2 else f
+    ks = range(1, n) if dim == 3 else range(0, 1)
+    rr = ff = Fraction(0)
+    bound_terms = []
+    for k in ks:
+        for j in range(1, n):
+            for i in range(1, n):
+                s = Fraction(0)
+                mag = 0.0
+                for dz, dy, dx in offs:
+                    w = _exact_weight(dim, abs(dx) + abs(dy) + abs(dz))
+                    uv = float(u3[k + dz, j + dy, i + dx])
+                    s += w * Fraction(uv)
+                    mag += abs(float(w)) * abs(uv)
+                fi = Fraction(float(f3[k, j, i]))
+                r = fi - s / (hq * hq)
+                rr += r * r
+                ff += fi * fi
+                bound_terms.append((abs(float(r)), abs(float(fi)) + mag / (h * h)))
+    eps = np.finfo(np.float64).eps
+    K, N = len(offs), len(bound_terms)
+    err_rr = sum(2 * ar * (K + 8) * eps * m + ((K + 8) * eps * m) ** 2 for ar, m in bound_terms)
+    err_rr += (N + 2) * eps * float(rr) * 1.01
+
+    ld = oracle.residual_norms_ld(u, f, h)
+    assert abs(ld[0] - float(rr)) <= 1e-15 * float(rr)
+    assert abs(ld[1] - float(ff)) <= 1e-15 * float(ff)
+    _, nrm = oracle.residual(u, f, h)
+    assert abs(nrm[0] - float(rr)) <= err_rr
+    assert abs(nrm[1] - float(ff)) <= (N + 2) * eps * float(ff)
+    assert err_rr < 1e-11 * float(rr)  # the bound is not vacuous
+    # a dropped term is far outside the bound: the residual without the last neighbour
+    rr_bad = Fraction(0)
+    for k in ks:
+        for j in range(1, n):
+            for i in range(1, n):
+                s = sum(_exact_weight(dim, abs(dx) + abs(dy) + abs(dz)) * Fraction(float(u3[k + dz, j + dy, i + dx]))
+                        for dz, dy, dx in offs[:-1])
+                r = Fraction(float(f3[k, j, i])) - s / (hq * hq)
+                rr_bad += r * r
+    assert abs(float(rr_bad) - float(rr)) > 1e3 * err_rr
+
+
 # ------------------------------------------------------------ iterative refinement
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
