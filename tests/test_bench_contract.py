@@ -1,9 +1,12 @@
-"""The benchmark's reference arm on CPU: one JSON line with the contract's keys, the
-oracle timed on the host cores, no host-device copies."""
+"""The benchmark's host logic on CPU: the reference arm's JSON line (the oracle timed
+on the host cores, no host-device copies), alone and under two ranks; the unit counts
+the rates divide by; the rule that drops DRAM-traffic figures taken on other sources."""
 import json
 import os
 import subprocess
 import sys
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -25,3 +28,63 @@ def test_reference_arm_prints_one_contract_line():
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
     assert "workload" in d["config"]
+
+
+def _bench():
+    sys.path.insert(0, ROOT)
+    import bench
+    return bench
+
+
+def test_unit_counts():
+    """Updates, bytes and rates the benchmark divides by, checked by hand."""
+    b = _bench()
+    passes = 50 + 50 + 50 + 50 + 1
+    assert b.updates_per_step(512, 16384) == passes * (511 ** 3 + 16383 ** 2)
+    assert b.updates_per_step(0, 64) == passes * 63 ** 2
+    assert b.interior(3, 0) == 0
+    assert b.bytes_per_update("jacobi_sweep", "2") == 12      # two sweeps per pass over memory
+    assert b.bytes_per_update("jacobi_sweep", "3") == 24
+    assert b.bytes_per_update("jacobi_sweep", "2", fd=True) == 24
+    assert b.bytes_per_update("gs_sweep", "2") == 24
+    p = b.pitch2(16384)
+    assert p >= 16385 and p % 8 == 0 and p - 16385 < 8       # 64-byte rows, minimal padding
+    # V(2,2) on 8^3: levels 8, 4 (2 is the coarsest: 20 sweeps on its single interior vertex)
+    assert b.mg_cycle_updates(8) == 4 * 7 ** 3 + 4 * 3 ** 3 + 20 * 1
+    # weak scaling: every rank does the same units; the slowest rank's time counts
+    assert b.whole_job_rate(1e6, 4, 1000.0) == pytest.approx(4.0)
+    # launches per step: 3D 2x50 applies, GS 2 launches per sweep + 2 pre-passes, Jacobi
+    # 1 per sweep + 2, residual 1; 2D the same except GS 1 per sweep, Jacobi 1 per 2 sweeps
+    assert b.launches_per_step(512, 16384) == (100 + 102 + 52 + 1) + (100 + 52 + 27 + 1)
+
+
+def test_traffic_is_dropped_when_the_kernel_sources_change(tmp_path, monkeypatch):
+    """A committed DRAM-traffic line counts only for the sources it was captured on."""
+    import shutil
+    b = _bench()
+    got = b.traffic_from_profiles("gs_sweep_3d", 1000.0)
+    assert got is None or got > 0
+    root = tmp_path / "repo"
+    shutil.copytree(os.path.join(ROOT, "profiles"), root / "profiles")
+    shutil.copytree(os.path.join(ROOT, "paper_1810_04033_gb300", "csrc"),
+                    root / "paper_1810_04033_gb300" / "csrc")
+    monkeypatch.setattr(b, "ROOT", str(root))
+    assert b.traffic_from_profiles("gs_sweep_3d", 1000.0) == got
+    src = root / "paper_1810_04033_gb300" / "csrc" / "gs_fx.cu"
+    src.write_text(src.read_text() + "\n// edited\n")
+    assert b.traffic_from_profiles("gs_sweep_3d", 1000.0) is None
+    assert b.traffic_from_profiles("no_such_kernel", 1000.0) is None
+
+
+def test_reference_arm_under_two_ranks_prints_once():
+    """Launched like the multi-GPU runs (torchrun, 2 ranks): rank 0 alone times the oracle
+    and prints; the other rank exits 0 without work."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", "29531", "bench.py", "--impl", "reference",
+           "--gpus", "2", "--n3", "16", "--n2", "64", "--steps", "1", "--warmup", "0"]
+    out = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
