@@ -45,10 +45,14 @@
  *                             the sweep equals a dense GS on the matrix with the
  *                             perturbed diagonal; sigma_k against the closed form
  *                             sin(k t/2) sin((k+1) t/2) / sin(t/2).
- *   oracle_patch_*            parity unpinned beyond: a single patch with zero
- *                             neighbours equals a plain Dirichlet GS; equal-size
- *                             neighbours copy the first interior layer (the halo rule
- *                             is a reading, the paper is silent on it).
+ *   oracle_patch_*            equal sizes pinned: the iteration converges to the dense
+ *                             solution of the global system on the collapsed grid of
+ *                             the patches' interiors (faces, edges and corners of the
+ *                             halo alike); a single patch with zero neighbours equals a
+ *                             plain Dirichlet GS; equal-size neighbours copy the first
+ *                             interior layer.  Uneven sizes: parity unpinned beyond the
+ *                             nearest-index and tie checks (the halo rule is a reading,
+ *                             the paper is silent on it).
  */
 #include "oracle.h"
 

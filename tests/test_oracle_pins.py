@@ -486,3 +486,63 @@ def test_uneven_neighbour_nearest_index_ties_to_lower():
         assert a[4, j, 8] == b[6, jq, 1]  # k = 4 -> 6 exactly
     # tangential indices clamp into [1, n_q - 1]
     assert a[4, 0, 8] == 0.0  # j = 0 is on the -y outer boundary -> 0
+
+
+def _collapsed_global(lat, L, n):
+    """Dense solution of the global system on the collapsed grid of equal patches, and
+    the map from patch interiors into it."""
+    h = 1.0 / n
+    N = tuple(L[a] * (n - 1) + 1 for a in range(3))  # cells per axis
+    shape = (N[2] + 1, N[1] + 1, N[0] + 1)
+    F = np.zeros(shape)
+
+    def block(p):
+        px, py, pz = p % L[0], (p // L[0]) % L[1], p // (L[0] * L[1])
+        return (slice(pz * (n - 1) + 1, pz * (n - 1) + n), slice(py * (n - 1) + 1, py * (n - 1) + n),
+                slice(px * (n - 1) + 1, px * (n - 1) + n))
+
+    npatch = L[0] * L[1] * L[2]
+    for p in range(npatch):
+        F[block(p)] = lat.view(lat.f, p)[1:n, 1:n, 1:n]
+    A = dr.global_matrix(3, N, h)
+    inner = dr.interior_mask(shape).ravel()
+    U = np.zeros(F.size)
+    U[inner] = np.linalg.solve(A[np.ix_(inner, inner)], F.ravel()[inner])
+    return U.reshape(shape), block, npatch
+
+
+@pytest.mark.parametrize("L,n", [((2, 2, 2), 4), ((3, 2, 1), 5)])
+def test_equal_patches_converge_to_the_collapsed_global_solution(L, n):
+    """Equal patches of n cells.  Vertex n of a patch and vertex 0 of its +x neighbour sit
+    at the same point, yet both are halo: each is filled from the other patch's first
+    interior layer.  So the interior vertices of all patches form one grid of L(n-1)
+    unknowns per axis, and across an interface (face, edge or corner) a stencil's
+    neighbour is the adjacent unknown of that grid, with h = 1/n in every stencil.  The
+    patch iteration (halo fill, then a coloured GS sweep per patch) is a block splitting
+    of that global system, so it must converge to the system's solution, computed here
+    by a dense solve of the Kronecker-assembled matrix."""
+    lat = synth.PatchLattice(lat=L, seed=5, edges=(n,))
+    U, block, npatch = _collapsed_global(lat, L, n)
+    out = oracle.patch_smooth(lat.lat, lat.np_sizes, lat.offsets, lat.u, lat.f, 300)
+    scale = np.max(np.abs(U))
+    err = max(np.max(np.abs(lat.view(out, p)[1:n, 1:n, 1:n] - U[block(p)])) for p in range(npatch))
+    assert err <= 1e-12 * scale
+    # the other reading, with the interface vertex an unknown shared by both patches
+    # (a global grid of L n cells), is a different system and is far from the result
+    N2 = tuple(L[a] * n for a in range(3))
+    shape2 = (N2[2] + 1, N2[1] + 1, N2[0] + 1)
+    F2 = np.zeros(shape2)
+    for p in range(npatch):
+        px, py, pz = p % L[0], (p // L[0]) % L[1], p // (L[0] * L[1])
+        F2[pz * n + 1:pz * n + n, py * n + 1:py * n + n, px * n + 1:px * n + n] = lat.view(lat.f, p)[1:n, 1:n, 1:n]
+    A2 = dr.global_matrix(3, N2, 1.0 / n)
+    in2 = dr.interior_mask(shape2).ravel()
+    U2 = np.zeros(F2.size)
+    U2[in2] = np.linalg.solve(A2[np.ix_(in2, in2)], F2.ravel()[in2])
+    U2 = U2.reshape(shape2)
+    err2 = 0.0
+    for p in range(npatch):
+        px, py, pz = p % L[0], (p // L[0]) % L[1], p // (L[0] * L[1])
+        g = U2[pz * n + 1:pz * n + n, py * n + 1:py * n + n, px * n + 1:px * n + n]
+        err2 = max(err2, np.max(np.abs(lat.view(out, p)[1:n, 1:n, 1:n] - g)))
+    assert err2 > 1e-3 * scale
