@@ -205,6 +205,23 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _device_buffer(t, what, device, min_numel=0, contiguous=True):
+    """Checks a float64 buffer the library reads or writes by raw pointer: a CUDA tensor
+    (on `device` unless None), contiguous when the library takes it as a flat array, and
+    at least `min_numel` elements long, so that a wrong argument raises here instead of
+    letting a kernel touch memory outside it."""
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+        raise ValueError("%s must be a CUDA tensor" % what)
+    if device is not None and t.device != device:
+        raise ValueError("%s must be on %s" % (what, device))
+    if t.dtype != torch.float64:
+        raise ValueError("%s must be float64" % what)
+    if contiguous and not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
+    if t.numel() < min_numel:
+        raise ValueError("%s needs at least %d elements" % (what, min_numel))
+
+
 def stencil_version() -> int:
     return lib().stencil_version()
 
@@ -253,6 +270,7 @@ def stencil_residual(u, f, h, r=None, norms2=None, stream=None, op=OP_Q1):
         _same_layout(u, r)
     if norms2 is None:
         norms2 = torch.empty(2, dtype=torch.float64, device=u.device)
+    _device_buffer(norms2, "norms2", u.device, 2)
     g = grid_for(u, h, op)
     _check(lib().stencil_residual(ctypes.byref(g), _ptr(u), _ptr(f),
                                   _ptr(r) if r is not None else ctypes.c_void_p(0),
@@ -266,6 +284,7 @@ def stencil_residual_noalloc(u, f, h, norms2, r=None, stream=None):
     _same_layout(u, f)
     if r is not None:
         _same_layout(u, r)
+    _device_buffer(norms2, "norms2", u.device, 2)
     g = grid_for(u, h)
     _check(lib().stencil_residual_noalloc(ctypes.byref(g), _ptr(u), _ptr(f),
                                           _ptr(r) if r is not None else ctypes.c_void_p(0),
@@ -372,6 +391,8 @@ def stencil_mg_vcycle(u, f, h, pre=2, post=2, coarse_sweeps=20, max_levels=0, st
 
 def stencil_mg_restrict(rf, rc, h, stream=None):
     """rc = R rf (full weighting); rc is a vertex array of the coarse grid."""
+    _device_buffer(rf, "rf", None, contiguous=False)
+    _device_buffer(rc, "rc", rf.device, contiguous=False)
     gf, gc = grid_for(rf, h), grid_for(rc, 2.0 * h)
     _check(lib().stencil_mg_restrict(ctypes.byref(gf), _ptr(rf), ctypes.byref(gc), _ptr(rc), _stream(stream)))
     return rc
@@ -379,9 +400,22 @@ def stencil_mg_restrict(rf, rc, h, stream=None):
 
 def stencil_mg_prolong_add(ec, uf, h, stream=None):
     """uf += P ec on the fine interior; h is the fine mesh width."""
+    _device_buffer(uf, "uf", None, contiguous=False)
+    _device_buffer(ec, "ec", uf.device, contiguous=False)
     gf, gc = grid_for(uf, h), grid_for(ec, 2.0 * h)
     _check(lib().stencil_mg_prolong_add(ctypes.byref(gf), _ptr(uf), ctypes.byref(gc), _ptr(ec), _stream(stream)))
     return uf
+
+
+def packed_numel(sizes, offsets) -> int:
+    """Elements a packed patch array must hold: the end of the patch that ends last
+    (patch p spans offsets[p] .. offsets[p] + (sizes[p]+1)^3)."""
+    import numpy as np
+    sizes = np.asarray(sizes, dtype=np.int64)
+    offsets = np.asarray(offsets, dtype=np.int64)
+    if sizes.size == 0:
+        return 0
+    return int((offsets + (sizes + 1) ** 3).max())
 
 
 class PatchBatch:
@@ -404,12 +438,19 @@ class PatchBatch:
         _check(lib().stencil_patch_batch_create(descs, n, nb.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                                 ctypes.byref(self._h)))
         self.npatch = n
+        self.numel = packed_numel(sizes, offsets)
+
+    def _arrays(self, u_all, f_all):
+        _device_buffer(u_all, "u_all", None, self.numel)
+        _device_buffer(f_all, "f_all", u_all.device, self.numel)
 
     def smooth(self, u_all, f_all, sweeps, stream=None):
+        self._arrays(u_all, f_all)
         _check(lib().stencil_patch_batch_smooth(self._h, _ptr(u_all), _ptr(f_all), int(sweeps), _stream(stream)))
         return u_all
 
     def autotune(self, u_all, f_all, stream=None):
+        self._arrays(u_all, f_all)
         _check(lib().stencil_patch_batch_autotune(self._h, _ptr(u_all), _ptr(f_all), _stream(stream)))
         return self.config()
 
@@ -440,25 +481,32 @@ class Server:
                        int(solver))
         self._h = ctypes.c_void_p()
         _check(lib().stencil_server_create(int(hbm_budget_bytes), ctypes.byref(o), ctypes.byref(self._h)))
-        self._keep = {}
+        self._n = {}  # ticket -> cells per edge, for the size of fetched results
 
     def submit(self, kind, n, sweeps=20, rel_tol=1e-8, f=None, f_seed=0, u0=None):
-        """f / u0: host float64 arrays of (n+1)^3 or None (f: drawn from f_seed)."""
+        """f / u0: host float64 arrays of (n+1)^3 or None (f: drawn from f_seed).  The
+        library copies them during the call (it reads exactly (n+1)^3 values each)."""
         import numpy as np
         r = Request()
         r.kind, r.n, r.sweeps, r.reserved, r.rel_tol = int(kind), int(n), int(sweeps), 0, float(rel_tol)
-        keep = []
+        span = (int(n) + 1) ** 3 if int(n) > 0 else 0
+        keep = []  # alive until the call returns
         if f is not None:
             fa = np.ascontiguousarray(f, dtype=np.float64)
+            if fa.size != span:
+                raise ValueError("f must hold (n+1)^3 = %d values, got %d" % (span, fa.size))
             keep.append(fa)
             r.f = fa.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         r.f_seed = int(f_seed) & 0xFFFFFFFFFFFFFFFF
         if u0 is not None:
             ua = np.ascontiguousarray(u0, dtype=np.float64)
+            if ua.size != span:
+                raise ValueError("u0 must hold (n+1)^3 = %d values, got %d" % (span, ua.size))
             keep.append(ua)
             r.u0 = ua.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         t = ctypes.c_uint64()
         _check(lib().stencil_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        self._n[t.value] = int(n)
         return t.value
 
     @staticmethod
@@ -479,14 +527,22 @@ class Server:
         _check(lib().stencil_server_wait(self._h, ticket, int(timeout_us), ctypes.byref(r)))
         return self._res(r)
 
-    def fetch(self, ticket, n):
+    def fetch(self, ticket, n=None):
+        """The request's solution as a host array of (n+1)^3 values; n is the request's
+        own edge (an `n` given here must match it)."""
         import numpy as np
-        out = np.empty((n + 1,) * 3, dtype=np.float64)
+        if ticket not in self._n:
+            raise StencilError(ENOTFOUND, "server_fetch: unknown ticket")
+        m = self._n[ticket]
+        if n is not None and int(n) != m:
+            raise ValueError("ticket %d has n = %d, not %d" % (ticket, m, int(n)))
+        out = np.empty((m + 1,) * 3, dtype=np.float64)
         _check(lib().stencil_server_fetch(self._h, ticket, out.ctypes.data_as(ctypes.c_void_p)))
         return out
 
     def release(self, ticket):
         _check(lib().stencil_server_release(self._h, ticket))
+        self._n.pop(ticket, None)
 
     def stats(self):
         st = ServerStats()
