@@ -246,18 +246,43 @@ class GpuWorkload:
                     events[(op, g)][1].record(stream)
 
 
+# Kernel sources behind each (op, grid) of the grid workload, beside the shared ones
+# (api.cu, which routes the calls, and every header).  The multi-sweep smoothers also
+# run the pre-pass kernels of gs_fx.cu; the 3D Jacobi call can fall back to ops_fx.cu.
+TRAFFIC_SOURCES = {
+    "apply_elementwise_3d": ["ew_fx.cu"],
+    "apply_stencil_3d": ["ops_fx.cu"],
+    "residual_3d": ["ops_fx.cu"],
+    "gs_sweep_3d": ["gs_fx.cu"],
+    "jacobi_sweep_3d": ["jac3_fx.cu", "gs_fx.cu", "ops_fx.cu"],
+    "apply_elementwise_2d": ["ops2d_fx.cu"],
+    "apply_stencil_2d": ["ops2d_fx.cu"],
+    "residual_2d": ["ops2d_fx.cu"],
+    "gs_sweep_2d": ["ops2d_fx.cu", "gs_fx.cu"],
+    "jacobi_sweep_2d": ["ops2d_fx.cu", "gs_fx.cu"],
+}
+
+
+def traffic_source_sha(kernel_key, root=None):
+    """First 16 hex digits of sha256 over the sources of one (op, grid): its kernel
+    files, api.cu and every header of the library, in sorted order."""
+    src = os.path.join(root or ROOT, "paper_1810_04033_gb300", "csrc")
+    files = set(TRAFFIC_SOURCES[kernel_key]) | {"api.cu"}
+    files |= {fn for fn in os.listdir(src) if fn.endswith((".cuh", ".h"))}
+    sha = hashlib.sha256()
+    for fn in sorted(files):
+        sha.update(fn.encode() + b"\0")
+        sha.update(open(os.path.join(src, fn), "rb").read())
+    return sha.hexdigest()[:16]
+
+
 def traffic_from_profiles(kernel_key, units_per_launch):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel source (null otherwise)."""
+    current sources of that kernel (null otherwise)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
-    src = os.path.join(ROOT, "paper_1810_04033_gb300", "csrc")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or kernel_key not in TRAFFIC_SOURCES:
         return None
-    sha = hashlib.sha256()
-    for fn in sorted(os.listdir(src)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            sha.update(open(os.path.join(src, fn), "rb").read())
-    cur = sha.hexdigest()[:16]
+    cur = traffic_source_sha(kernel_key)
     for line in open(path):
         m = re.match(r"\s*kernel=(\S+)\s+src_sha=(\S+)\s+dram_bytes_per_update=([\d.eE+-]+)", line)
         if m and m.group(1) == kernel_key and m.group(2) == cur:

@@ -59,20 +59,38 @@ def test_unit_counts():
 
 
 def test_traffic_is_dropped_when_the_kernel_sources_change(tmp_path, monkeypatch):
-    """A committed DRAM-traffic line counts only for the sources it was captured on."""
+    """A committed DRAM-traffic line counts only for the sources of its own kernel: an
+    edit to another kernel's file keeps it, an edit to its kernel file, to api.cu or to
+    a header drops it."""
     import shutil
     b = _bench()
-    got = b.traffic_from_profiles("gs_sweep_3d", 1000.0)
-    assert got is None or got > 0
+    csrc = os.path.join(ROOT, "paper_1810_04033_gb300", "csrc")
+    for key, files in b.TRAFFIC_SOURCES.items():
+        for fn in files:
+            assert os.path.exists(os.path.join(csrc, fn)), (key, fn)
+    keys = list(b.TRAFFIC_SOURCES)
+    got = {k: b.traffic_from_profiles(k, 1000.0) for k in keys}
+    assert all(v is None or v > 0 for v in got.values())
     root = tmp_path / "repo"
     shutil.copytree(os.path.join(ROOT, "profiles"), root / "profiles")
-    shutil.copytree(os.path.join(ROOT, "paper_1810_04033_gb300", "csrc"),
-                    root / "paper_1810_04033_gb300" / "csrc")
+    shutil.copytree(csrc, root / "paper_1810_04033_gb300" / "csrc")
     monkeypatch.setattr(b, "ROOT", str(root))
-    assert b.traffic_from_profiles("gs_sweep_3d", 1000.0) == got
-    src = root / "paper_1810_04033_gb300" / "csrc" / "gs_fx.cu"
-    src.write_text(src.read_text() + "\n// edited\n")
-    assert b.traffic_from_profiles("gs_sweep_3d", 1000.0) is None
+    assert {k: b.traffic_from_profiles(k, 1000.0) for k in keys} == got
+
+    def edit(fn):
+        src = root / "paper_1810_04033_gb300" / "csrc" / fn
+        src.write_text(src.read_text() + "\n// edited\n")
+
+    edit("patches.cu")  # no grid-workload kernel lives there
+    assert {k: b.traffic_from_profiles(k, 1000.0) for k in keys} == got
+    edit("gs_fx.cu")    # the 3D GS kernels and the smoothers' pre-passes
+    after = {k: b.traffic_from_profiles(k, 1000.0) for k in keys}
+    for k in ("gs_sweep_3d", "jacobi_sweep_3d", "gs_sweep_2d", "jacobi_sweep_2d"):
+        assert after[k] is None
+    for k in ("apply_elementwise_2d", "apply_stencil_2d", "residual_2d", "apply_elementwise_3d"):
+        assert after[k] == got[k]
+    edit("fixed.cuh")   # shared by every kernel
+    assert all(b.traffic_from_profiles(k, 1000.0) is None for k in keys)
     assert b.traffic_from_profiles("no_such_kernel", 1000.0) is None
 
 
