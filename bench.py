@@ -594,11 +594,27 @@ def run_patches(args):
             "patches": int(L.np_sizes.size), "vertices": L.total}
 
 
+# FP64 instructions per interior update of the finite-difference kernels (FMA = one):
+# the neighbour sum (3D: 5 adds, 2D: 3), then apply: FMA + scale; GS: scale + FMA;
+# Jacobi: apply + subtract + FMA; residual: apply + subtract + two FMA for the norms.
+FD_FP64_OPS = {"apply_stencil": {"3": 7, "2": 5}, "gs_sweep": {"3": 7, "2": 5},
+               "jacobi_sweep": {"3": 9, "2": 7}, "residual": {"3": 10, "2": 8}}
+FP64_PER_CLK_SM = 2.0    # FP64 add/FMA/multiply instructions per clock per SM (measured)
+SM_CLOCK_MAX_HZ = 2.07e9
+
+
+def fd_fp64_frac(op, g, updates, ms, sms):
+    """Fraction of the FP64 pipe's instruction rate (FP64_PER_CLK_SM x SMs x maximum SM
+    clock) that `updates` interior updates of op on grid g in `ms` milliseconds use."""
+    return FD_FP64_OPS[op][g] * updates / (ms * 1e-3) / (FP64_PER_CLK_SM * sms * SM_CLOCK_MAX_HZ)
+
+
 def run_fd(args):
     """The grid workload's op mix (stencil apply x50, one 50-sweep GS call, one 50-sweep
     Jacobi call, 1 residual per grid) with the 5/7-point finite-difference operator;
     GS is red-black.  Per-op CUDA events; fractions of the measured HBM bandwidth with
-    16 B (apply, residual) and 24 B (sweeps) per update for a single pass."""
+    16 B (apply, residual) and 24 B (sweeps) per update for a single pass, and of the
+    FP64 pipe's instruction rate (these kernels compute in FP64)."""
     import torch
     import paper_1810_04033_gb300 as st
     dev = torch.device("cuda", 0)
@@ -609,6 +625,7 @@ def run_fd(args):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     with torch.cuda.stream(stream):
         for _ in range(max(1, args.warmup)):
             wl.step(stream, ops=ops)
@@ -631,7 +648,8 @@ def run_fd(args):
         for op in ops:
             t = sum(e[(op, g)][0].elapsed_time(e[(op, g)][1]) for e in ev) / steps / PASSES[op]
             b = bytes_per_update(op, g, fd=True) * interior(int(g), nn)
-            per["%s_%sd" % (op, g)] = {"ms_per_pass": round(t, 4), "frac": round(b / (t * 1e-3) / 1e9 / peak, 3)}
+            per["%s_%sd" % (op, g)] = {"ms_per_pass": round(t, 4), "frac": round(b / (t * 1e-3) / 1e9 / peak, 3),
+                                       "fp64_frac": round(fd_fp64_frac(op, g, interior(int(g), nn), t, sms), 3)}
     # red-black sweeps: colour passes with barriers vs dependency-driven tasks, and the
     # expensive stencils S(k) (k = 100 everywhere / k = 0..99 linear over the mesh)
     def timed(fn, reps=2):

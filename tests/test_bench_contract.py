@@ -56,6 +56,10 @@ def test_unit_counts():
     # launches per step: 3D 2x50 applies, GS 2 launches per sweep + 2 pre-passes, Jacobi
     # 1 per sweep + 2, residual 1; 2D the same except GS 1 per sweep, Jacobi 1 per 2 sweeps
     assert b.launches_per_step(512, 16384) == (100 + 102 + 52 + 1) + (100 + 52 + 27 + 1)
+    # FP64-pipe fraction of the finite-difference kernels: 7 FP64 instructions per 3D
+    # apply update, 1e6 updates in 1 ms on 152 SMs at 2 per clock and 2.07 GHz
+    assert b.fd_fp64_frac("apply_stencil", "3", 1e6, 1.0, 152) == pytest.approx(7e9 / (2 * 152 * 2.07e9))
+    assert b.FD_FP64_OPS["residual"]["2"] == 8 and b.FD_FP64_OPS["jacobi_sweep"]["3"] == 9
 
 
 def test_traffic_is_dropped_when_the_kernel_sources_change(tmp_path, monkeypatch):
