@@ -39,6 +39,7 @@ import synth  # noqa: E402
 N3 = 512
 N2 = 16384
 OMEGA = 2.0 / 3.0
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal (the roofline's peak is the measured copy rate)
 N_APPLY = 50      # per form
 N_SWEEPS = 50     # GS and Jacobi sweeps per call
 OPS = ("apply_elementwise", "apply_stencil", "gs_sweep", "jacobi_sweep", "residual")
@@ -373,6 +374,7 @@ def run_gpu(args, rank, world):
     roofline = {"bound": "hbm", "kernel": "%s (%sD, %d cells per edge)" % (top_op, top_g, nn),
                 "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved / hbm_peak, 4), "peak_source": peak_src,
+                "nominal_peak": HBM_NOMINAL_GBS, "frac_of_nominal": round(achieved / HBM_NOMINAL_GBS, 4),
                 "traffic": traffic_from_profiles("%s_%sd" % (top_op, top_g), units),
                 "share_of_step": round(per_op_ms[top_key] / ms, 3),
                 "ms_per_pass": per_pass, "algorithmic_gbs": gbs}
