@@ -568,6 +568,16 @@ def run_small(args):
             "note": "launch-bound size (30K interior vertices); one CUDA graph replay per step"}
 
 
+def patches_oracle_sample(nthreads, lat=(8, 8, 8), sweeps=20):
+    """The oracle's patch iteration (halo fill, then a coloured GS sweep per patch) on a
+    bounded lattice of the same edge distribution.  Returns (updates, seconds)."""
+    import oracle
+    L = synth.PatchLattice(lat=lat, seed=2)
+    t = time.perf_counter()
+    oracle.patch_smooth(L.lat, L.np_sizes, L.offsets, L.u, L.f, sweeps, nthreads)
+    return sweeps * L.interior_updates_per_sweep, time.perf_counter() - t
+
+
 def run_patches(args):
     """4096 patches in a 16^3 lattice, edges from {8,12,16,24,32} (seed 2), f ~ U[-1,1],
     u0 = 0, 20 coloured GS sweeps with a halo fill before each; launch shape autotuned."""
@@ -593,7 +603,15 @@ def run_patches(args):
             "value": round(upd / ms / 1e3, 1), "unit": "Mupdates/s", "ms_per_step": round(ms, 3),
             "algorithmic_gbs": round(24 * upd / ms / 1e6, 1), "hbm_frac": round(24 * upd / ms / 1e6 / 6683.2, 4),
             "autotuned_launch": {"threads": tuned[0], "ctas_per_sm": tuned[1]}, "dtype": "f64",
-            "patches": int(L.np_sizes.size), "vertices": L.total}
+            "patches": int(L.np_sizes.size), "vertices": L.total, "cpu_baseline": patches_cpu_baseline()}
+
+
+def patches_cpu_baseline():
+    nthreads = os.cpu_count() or 1
+    upd, sec = patches_oracle_sample(nthreads)
+    return {"value": round(upd / sec / 1e6, 2), "unit": "Mupdates/s", "cores": nthreads, "kind": "oracle",
+            "sample": "512 patches (8^3 lattice, same edge distribution), 20 sweeps with halo fill, "
+                      "%.1f s, OpenMP colour passes inside each patch" % sec}
 
 
 # FP64 instructions per interior update of the finite-difference kernels (FMA = one):

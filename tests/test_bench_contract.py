@@ -110,3 +110,13 @@ def test_reference_arm_under_two_ranks_prints_once():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+def test_patches_oracle_sample_counts_interior_updates():
+    """The patch workload's CPU baseline: updates = sweeps x sum over patches of (n-1)^3."""
+    import numpy as np
+    b = _bench()
+    import synth
+    upd, sec = b.patches_oracle_sample(1, lat=(2, 2, 1), sweeps=3)
+    L = synth.PatchLattice(lat=(2, 2, 1), seed=2)
+    assert upd == 3 * int(np.sum((L.np_sizes.astype(np.int64) - 1) ** 3)) and sec > 0
