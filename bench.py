@@ -51,9 +51,10 @@ BYTES_PER_UPDATE = {"apply_elementwise": 16, "apply_stencil": 16, "gs_sweep": 24
 
 
 def bytes_per_update(op, g, fd=False):
-    """Compulsory bytes per update and sweep: the Q1 2D Jacobi call runs two sweeps per
-    pass over memory (read u and 3/8 h^2 f, write u once per pair), 12 B per sweep."""
-    if op == "jacobi_sweep" and g == "2" and not fd:
+    """Compulsory bytes per update and sweep: the Q1 2D Jacobi and Gauss-Seidel calls run
+    two sweeps per pass over memory (read u and 3/8 h^2 f, write u once per pair), 12 B
+    per sweep."""
+    if op in ("jacobi_sweep", "gs_sweep") and g == "2" and not fd:
         return 12
     return BYTES_PER_UPDATE[op]
 
@@ -64,10 +65,10 @@ def pitch2(n2):
 
 def launches_per_step(n3, n2):
     """Kernel launches of the library per step (every multi-sweep call has two pre-pass
-    launches; 3D: GS two launches per sweep, Jacobi one; 2D: GS one launch per sweep,
-    Jacobi one launch per two sweeps)."""
+    launches; 3D: GS two launches per sweep, Jacobi one; 2D: GS and Jacobi one launch per
+    two sweeps)."""
     d3 = 2 * N_APPLY + (2 * N_SWEEPS + 2) + (N_SWEEPS + 2) + 1
-    d2 = 2 * N_APPLY + (N_SWEEPS + 2) + (N_SWEEPS // 2 + 2) + 1
+    d2 = 2 * N_APPLY + (N_SWEEPS // 2 + 2) + (N_SWEEPS // 2 + 2) + 1
     return (d3 if n3 else 0) + (d2 if n2 else 0)
 
 

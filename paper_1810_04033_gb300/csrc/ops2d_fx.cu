@@ -836,6 +836,131 @@ __global__ void __launch_bounds__(W2_THREADS) k_gs2_sweep(Geo q, const void *__r
   publish_bound(bnd, (sweep + 1) % 4, R, hmax, red);
 }
 
+// Two Gauss-Seidel sweeps in one pass over memory (temporal blocking).  A warp streams
+// down its rows with four fronts, one step per even row j:
+//   sweep 1, even row j    (colours 0, 1) from X rows j-1, j+1;
+//   sweep 1, odd row j-1   (colours 2, 3) from sweep-1 even rows j-2, j;
+//   sweep 2, even row j-2  (colours 0, 1) from sweep-1 odd rows j-3, j-1;
+//   sweep 2, odd row j-3   (colours 2, 3) from sweep-2 even rows j-4, j-2;
+// every input is the value the sequential colour order of two sweeps reads, and only
+// sweep 2 is stored.  One sweep consumes four columns of the window per side (the
+// shuffles of the two colour steps of each row), so of the 64 staged columns the 48 of
+// lanes 4..27 hold sweep-2 values.  A chunk [js, je] starts its fronts at row js - 2 and
+// runs them to je + 2, so that it can finish sweep 2 on its own rows (even js .. je - 2,
+// odd js + 1 .. je - 1, and je when it is the last row) without another chunk's values.
+// Scale: one R for both sweeps.  A sweep adds at most 4 * 3/8 h^2 max|f| to max|u| (one
+// term per colour), so two sweeps stay below 2 (max|u| + 4 * 3/8 h^2 max|f|) <= 2^R (the
+// spare bit of sweep_R); the int64 sums keep six more bits of headroom.  In FP64 mode
+// (bound unusable) the same fronts run on FP64 buffers with the single-sweep kernel's
+// FP64 formula.
+constexpr int GS2X2_OUT = 48;
+
+template <bool FIX>
+__device__ __forceinline__ void gs_pair_t(Pair &u, const Pair &V, const Pair &gv, const Cols &c, double g) {
+  if (FIX) {
+    gs_pair(u, V, gv, c);
+    return;
+  }
+  const long long Tb = add<false>(V.b, u.b);
+  const long long Tbl = __shfl_up_sync(0xffffffffu, Tb, 1);
+  if (c.ina) {
+    const double N = __longlong_as_double(add<false>(add<false>(Tbl, Tb), V.a));
+    u.a = __double_as_longlong(fma(N, 0.125, g * __longlong_as_double(gv.a)));
+  }
+  const long long Ta = add<false>(V.a, u.a);
+  const long long Tar = __shfl_down_sync(0xffffffffu, Ta, 1);
+  if (c.inb) {
+    const double N = __longlong_as_double(add<false>(add<false>(Ta, Tar), V.b));
+    u.b = __double_as_longlong(fma(N, 0.125, g * __longlong_as_double(gv.b)));
+  }
+}
+
+template <bool FIX, int XF, int YF, bool V16>
+__device__ __forceinline__ void gs2x2_rows(const Geo &q, const void *X, void *Y, const long long *rhs_arr,
+                                           const Cols &c, int64_t js, int64_t je, int lane, const InScale<XF> &cvx,
+                                           int dfr, double g, int R, bool write_bnd, unsigned &hmax) {
+  const bool out_lane = lane >= 4 && lane <= 27;
+  const long long *Xl = (const long long *)X;
+  auto rawx = [&](int64_t j) -> Pair {
+    return (j >= 0 && j <= q.ny) ? ld_pair<V16>(Xl + j * q.pitch, c) : Pair{0ll, 0ll};
+  };
+  // interior rows only: GF is zero elsewhere, and f off the interior is never used
+  auto rawg = [&](int64_t j) -> Pair {
+    return (j >= 1 && j < q.ny) ? ld_pair<V16>(rhs_arr + j * q.pitch, c) : Pair{0ll, 0ll};
+  };
+  auto in = [&](const Pair &p) -> Pair { return FIX ? cvx(p) : p; };
+  auto rhs = [&](const Pair &p) -> Pair { return FIX ? Pair{p.a >> dfr, p.b >> dfr} : p; };
+  auto vsum = [&](const Pair &x, const Pair &y) -> Pair { return Pair{add<FIX>(x.a, y.a), add<FIX>(x.b, y.b)}; };
+  const Pair zero{0ll, 0ll};
+  // carried from the step of row j - 2: X odd row j - 1; sweep-1 even row j - 2 and odd
+  // row j - 3; sweep-2 even row j - 4; the right-hand sides of rows j - 2 and j - 3
+  Pair od_old = in(rawx(js - 3)), s1e_prev = zero, s1o_prev = zero, s2e_prev = zero;
+  Pair ge_prev = zero, go_prev = zero;
+  // raw X rows j, j + 1 and right-hand-side rows j, j - 1 of the next step
+  Pair qe = rawx(js - 2), qo = rawx(js - 1), qge = rawg(js - 2), qgo = rawg(js - 3);
+  for (int64_t j = js - 2; j <= je + 2; j += 2) {
+    const Pair rc = in(qe), rp = in(qo), ge = rhs(qge), go = rhs(qgo);
+    {
+      const int64_t jn = j + 2;
+      const bool ok = jn <= je + 2;  // warp-uniform
+      qe = ok ? rawx(jn) : zero;
+      qo = ok ? rawx(jn + 1) : zero;
+      qge = ok ? rawg(jn) : zero;
+      qgo = ok ? rawg(jn - 1) : zero;
+    }
+    Pair s1e = rc;
+    if (j >= 1 && j < q.ny) gs_pair_t<FIX>(s1e, vsum(od_old, rp), ge, c, g);
+    Pair s1o = od_old;
+    if (j - 1 >= 1 && j - 1 < q.ny) gs_pair_t<FIX>(s1o, vsum(s1e_prev, s1e), go, c, g);
+    Pair s2e = s1e_prev;
+    if (j - 2 >= 1 && j - 2 < q.ny) gs_pair_t<FIX>(s2e, vsum(s1o_prev, s1o), ge_prev, c, g);
+    Pair s2o = s1o_prev;
+    if (j - 3 >= 1 && j - 3 < q.ny) gs_pair_t<FIX>(s2o, vsum(s2e_prev, s2e), go_prev, c, g);
+    // FP64 mode: the buffers hold FP64 bits, stored as they are
+    if (j - 3 >= js + 1 && j - 3 <= je - 1) put_pair<FIX ? YF : SF_FXP, V16>(q, Y, j - 3, c, out_lane, write_bnd, R, s2o, hmax);
+    if (j - 2 >= js && (j - 2 < je || je == q.ny))
+      put_pair<FIX ? YF : SF_FXP, V16>(q, Y, j - 2, c, out_lane, write_bnd, R, s2e, hmax);
+    od_old = rp;
+    s1e_prev = s1e;
+    s1o_prev = s1o;
+    s2e_prev = s2e;
+    ge_prev = ge;
+    go_prev = go;
+  }
+}
+
+template <int XF, int YF, bool V16>
+__global__ void __launch_bounds__(W2_THREADS) k_gs2_sweep2(Geo q, const void *__restrict__ X, void *__restrict__ Y,
+                                                           const double *__restrict__ f,
+                                                           const long long *__restrict__ GF, SweepBounds *bnd,
+                                                           int sweep, int sweeps, double g, bool write_bnd) {
+  __shared__ unsigned red[W2_THREADS / 32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * (W2_THREADS / 32) + wib;
+  const Plan plan = make_plan(bnd, g, sweeps);
+  const int R = sweep_R(bnd, sweep % 4, g);
+  const int Rx = sweep > 0 ? sweep_R(bnd, (sweep + 3) % 4, g) : R;
+  const int dx = XF == SF_FXP ? R - Rx : 0, df = R - plan.Rf;
+  InScale<XF> cvx{1023 + R, dx > 0 ? (dx < 63 ? dx : 63) : 0, dx < 0 ? (-dx < 63 ? -dx : 63) : 0};
+  const int dfr = df < 63 ? df : 63;
+  if (blockIdx.x == 0 && threadIdx.x == 0) bnd->umax[(sweep + 2) % 4] = 0ull;
+  const int64_t nseg = (q.nx + GS2X2_OUT) / GS2X2_OUT;
+  const int64_t seg = gw % nseg, chunk = gw / nseg;
+  const int64_t js = chunk * S2_ROWS;  // even
+  unsigned hmax = 0;
+  if (js <= q.ny) {
+    int64_t je = js + S2_ROWS;
+    if (je > q.ny) je = (q.ny & 1) ? q.ny + 1 : q.ny;
+    const Cols c = make_cols(q, seg * GS2X2_OUT - 8 + 2 * lane);
+    if (plan.fix)
+      gs2x2_rows<true, XF, YF, V16>(q, X, Y, GF, c, js, je, lane, cvx, dfr, g, R, write_bnd, hmax);
+    else  // FP64 buffers throughout the call
+      gs2x2_rows<false, SF_F64, SF_F64, V16>(q, X, Y, (const long long *)f, c, js, je, lane, InScale<SF_F64>{}, 0,
+                                              g, R, write_bnd, hmax);
+  }
+  if (plan.fix) publish_bound(bnd, (sweep + 1) % 4, R, hmax, red);
+}
+
 // Multi-sweep damped Jacobi in the same global-scale fixed point (0 < omega <= 1):
 //   u' = u + omega (3/8 h^2 f + N/8 - u),
 // with omega applied as an integer product: floor(D * Wq / 2^62), Wq = omega 2^62
@@ -1132,37 +1257,55 @@ cudaError_t launch_gs_sweeps_fx2(const Geo &q, double *u, const double *f, int s
     e = cudaGetLastError();
     return e ? e : cudaMemcpyAsync(u, work, (size_t)span * sizeof(double), cudaMemcpyDeviceToDevice, s);
   }
-  const int64_t nseg = (q.nx + GS2_OUT) / GS2_OUT;
+  const int64_t nseg = (q.nx + GS2_OUT) / GS2_OUT, nseg2 = (q.nx + GS2X2_OUT) / GS2X2_OUT;
   const unsigned nb = (unsigned)((nseg * nchunk + W2_THREADS / 32 - 1) / (W2_THREADS / 32));
+  const unsigned nb2 = (unsigned)((nseg2 * nchunk + W2_THREADS / 32 - 1) / (W2_THREADS / 32));
   void *A = work, *B = work + span;
   long long *GF = (long long *)(work + 2 * span);
   SweepBounds *bnd = (SweepBounds *)bounds;
   e = launch_gs_prepass(q, 2, u, f, GF, bounds, sweeps, s);
   // 16-byte row pairs need an even pitch and 16-byte aligned bases (u and work; the
-  // buffers inside work then follow, span being even)
+  // buffers inside work then follow, span being even); the two-sweep kernel also reads
+  // f in pairs when the bound rules out fixed point
   const bool v16 = q.pitch % 2 == 0 && aligned16(u) && aligned16(work);
+  const bool v16f = v16 && aligned16(f);
+  // two sweeps per launch (temporal blocking), a single-sweep launch for an odd rest
   const void *X = u;
-  for (int it = 0; it < sweeps && !e; ++it) {
-    const bool first = it == 0, last = it == sweeps - 1;
+  int done = 0;
+  for (int it = 0; done < sweeps && !e; ++it) {
+    // a two-sweep launch reads X and writes Y, so it is never both the first (X = u) and
+    // the last (Y = u) launch: two sweeps in all go as two single-sweep launches
+    const bool two = sweeps - done >= 2 && sweeps != 2;
+    const bool first = done == 0, last = done + (two ? 2 : 1) == sweeps;
     void *Y = last ? (void *)u : (it % 2 == 0 ? A : B);
-    // the caller's u (last sweep): its Dirichlet values were never overwritten, leave them
-    if (v16) {
-      if (first)
-        k_gs2_sweep<SF_F64, SF_FXP, true><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, true);
-      else if (!last)
-        k_gs2_sweep<SF_FXP, SF_FXP, true><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, true);
+    // the caller's u (last launch): its Dirichlet values were never overwritten, leave them
+    const bool wb = !last;
+#define GS2_LAUNCH(KER, NB, XF_, YF_, V) KER<XF_, YF_, V><<<NB, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, wb)
+#define GS2_PICK(KER, NB, V)                   \
+  do {                                         \
+    if (first)                                 \
+      GS2_LAUNCH(KER, NB, SF_F64, SF_FXP, V);  \
+    else if (!last)                            \
+      GS2_LAUNCH(KER, NB, SF_FXP, SF_FXP, V);  \
+    else                                       \
+      GS2_LAUNCH(KER, NB, SF_FXP, SF_F64, V);  \
+  } while (0)
+    if (two) {
+      if (v16f)
+        GS2_PICK(k_gs2_sweep2, nb2, true);
       else
-        k_gs2_sweep<SF_FXP, SF_F64, true><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, false);
+        GS2_PICK(k_gs2_sweep2, nb2, false);
     } else {
-      if (first)
-        k_gs2_sweep<SF_F64, SF_FXP, false><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, true);
-      else if (!last)
-        k_gs2_sweep<SF_FXP, SF_FXP, false><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, true);
+      if (v16)
+        GS2_PICK(k_gs2_sweep, nb, true);
       else
-        k_gs2_sweep<SF_FXP, SF_F64, false><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, false);
+        GS2_PICK(k_gs2_sweep, nb, false);
     }
+#undef GS2_PICK
+#undef GS2_LAUNCH
     e = cudaGetLastError();
     X = Y;
+    done += two ? 2 : 1;
   }
   return e;
 }

@@ -46,7 +46,8 @@ def test_unit_counts():
     assert b.bytes_per_update("jacobi_sweep", "2") == 12      # two sweeps per pass over memory
     assert b.bytes_per_update("jacobi_sweep", "3") == 24
     assert b.bytes_per_update("jacobi_sweep", "2", fd=True) == 24
-    assert b.bytes_per_update("gs_sweep", "2") == 24
+    assert b.bytes_per_update("gs_sweep", "2") == 12          # two sweeps per pass too
+    assert b.bytes_per_update("gs_sweep", "3") == 24
     p = b.pitch2(16384)
     assert p >= 16385 and p % 8 == 0 and p - 16385 < 8       # 64-byte rows, minimal padding
     # V(2,2) on 8^3: levels 8, 4 (2 is the coarsest: 20 sweeps on its single interior vertex)
@@ -54,8 +55,8 @@ def test_unit_counts():
     # weak scaling: every rank does the same units; the slowest rank's time counts
     assert b.whole_job_rate(1e6, 4, 1000.0) == pytest.approx(4.0)
     # launches per step: 3D 2x50 applies, GS 2 launches per sweep + 2 pre-passes, Jacobi
-    # 1 per sweep + 2, residual 1; 2D the same except GS 1 per sweep, Jacobi 1 per 2 sweeps
-    assert b.launches_per_step(512, 16384) == (100 + 102 + 52 + 1) + (100 + 52 + 27 + 1)
+    # 1 per sweep + 2, residual 1; 2D the same except GS and Jacobi 1 per 2 sweeps
+    assert b.launches_per_step(512, 16384) == (100 + 102 + 52 + 1) + (100 + 27 + 27 + 1)
     # FP64-pipe fraction of the finite-difference kernels: 7 FP64 instructions per 3D
     # apply update, 1e6 updates in 1 ms on 152 SMs at 2 per clock and 2.07 GHz
     assert b.fd_fp64_frac("apply_stencil", "3", 1e6, 1.0, 152) == pytest.approx(7e9 / (2 * 152 * 2.07e9))
