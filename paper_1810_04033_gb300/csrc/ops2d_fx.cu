@@ -1,6 +1,7 @@
 // 2D Q1 (bilinear, 9-point stencil of Fig. 1) operations on the integer pipes:
-// assembled apply, element-wise apply with colour passes, damped Jacobi sweep,
-// residual with norms, and the coloured Gauss-Seidel sweep (one pass per sweep).
+// assembled apply, element-wise apply with colour passes, damped Jacobi sweeps,
+// residual with norms, and coloured Gauss-Seidel sweeps (the multi-sweep smoothers run
+// two sweeps per pass over memory).
 //
 //   3 S u = 8 u - N,  N = sum of the 8 neighbours;   6 K_e (element matrix, h-free) has
 //   entries 4 (same vertex), -1 (differ in one coordinate), -2 (opposite corner).
