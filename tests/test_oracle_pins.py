@@ -291,9 +291,14 @@ def test_fp32_and_bf16_sweeps_track_fp64():
 def test_bf16_rounding_matches_torch():
     import torch
     g = synth.rng(5)
-    xs = np.concatenate([g.standard_normal(2000).astype(np.float32) * 1e3,
-                         np.array([1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -1.0 - 2 ** -8, 0.0, -0.0,
-                                   3.0e38, 1e-40], dtype=np.float32)])
+    # random values, ties to even both ways and signs, zeros, overflow to infinity (the
+    # largest finite FP32 values), infinities, subnormals down to the smallest, and the
+    # just-below-a-tie / just-above-a-tie neighbours of a tie
+    edges = [1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -1.0 - 2 ** -8, -1.0 - 3 * 2 ** -8, 0.0, -0.0, 3.0e38, 1e-40,
+             np.finfo(np.float32).max, -np.finfo(np.float32).max, np.inf, -np.inf, 1.4e-45, -1.4e-45,
+             np.finfo(np.float32).tiny, 2 ** -126 * (1 + 2 ** -8), 3.3961776e38, 3.3895314e38,
+             1.0 + 2 ** -8 + 2 ** -20, 1.0 + 2 ** -8 - 2 ** -20]
+    xs = np.concatenate([g.standard_normal(2000).astype(np.float32) * 1e3, np.array(edges, dtype=np.float32)])
     tb = torch.from_numpy(xs).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
     for x, t in zip(xs, tb):
         assert oracle.f32_to_bf16(x) == int(t)
