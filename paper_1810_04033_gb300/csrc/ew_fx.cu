@@ -416,15 +416,11 @@ cudaError_t launch_apply_elementwise_fx3(const Geo &q, const double *u, double *
   // 16-byte pairs: even pitch (so every plane and row start is even too) and 16-byte
   // aligned arrays
   const bool v16 = q.pitch % 2 == 0 && ((uintptr_t)u % 16) == 0 && ((uintptr_t)y % 16) == 0;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_apply_elementwise_s3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)E3_SMEM);
-    if (!e)
-      e = cudaFuncSetAttribute(k_apply_elementwise_s3<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)E3_SMEM);
+  static PerDeviceOnce attr_t, attr_f;
+  {
+    cudaError_t e = set_smem_limit_once(attr_t, k_apply_elementwise_s3<true>, E3_SMEM);
+    if (!e) e = set_smem_limit_once(attr_f, k_apply_elementwise_s3<false>, E3_SMEM);
     if (e) return e;
-    attr = true;
   }
   if (v16)
     k_apply_elementwise_s3<true><<<(unsigned)blocks, E3_THREADS, E3_SMEM, s>>>(a);

@@ -743,12 +743,10 @@ template <int XF, int NF, int YF>
 static cudaError_t launch_half(const Geo &q, int pz, const void *X, const void *N, void *Y, const double *f,
                                const long long *GF, SweepBounds *bnd, int sweep, int sweeps, double g,
                                bool write_bnd, cudaStream_t s) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_gs_half_sweep<XF, NF, YF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)GS_SMEM);
+  static PerDeviceOnce attr;
+  {
+    cudaError_t e = set_smem_limit_once(attr, k_gs_half_sweep<XF, NF, YF>, GS_SMEM);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   const unsigned tx = (unsigned)((q.nx + 1 + GS_TX - 1) / GS_TX);
   const unsigned ty = (unsigned)((q.ny + 1 + GS_TY - 1) / GS_TY);
@@ -769,12 +767,9 @@ static bool launch_half_t(const Geo &q, int pz, const void *X, const void *N, vo
   if (((uintptr_t)Y | (uintptr_t)f | (uintptr_t)GF) % 16) return false;
   CUtensorMap mx, mn;
   if (!tma_plane_map(q, X, GT_W, GT_H, &mx) || !tma_plane_map(q, N, GT_W, GT_H, &mn)) return false;
-  static bool attr_set = false;
-  if (!attr_set) {
-    *err = cudaFuncSetAttribute(k_gs_half_t<XF, NF, YF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GT_SMEM);
-    if (*err != cudaSuccess) return true;
-    attr_set = true;
-  }
+  static PerDeviceOnce attr;
+  *err = set_smem_limit_once(attr, k_gs_half_t<XF, NF, YF>, GT_SMEM);
+  if (*err != cudaSuccess) return true;
   const unsigned tx = (unsigned)((q.nx + 1 + GT_TX - 1) / GT_TX);
   const unsigned ty = (unsigned)((q.ny + 1 + GT_TY - 1) / GT_TY);
   const int64_t ncentre = (q.nz - pz) / 2 + 1;

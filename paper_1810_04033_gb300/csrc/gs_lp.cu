@@ -419,12 +419,11 @@ __global__ void __launch_bounds__(LP_THREADS) k_gs_lp_t(Geo q, int pz, S *Y, con
 
 template <typename S>
 static cudaError_t gs_lp_sweeps(const Geo &q, S *u, const S *f, int sweeps, S *work, cudaStream_t s) {
-  static bool attr = false;
+  static PerDeviceOnce attr;
   const size_t smem = 3 * (size_t)LP_PLANE * sizeof(float);
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_gs_lp_half<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t e = set_smem_limit_once(attr, k_gs_lp_half<S>, smem);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   const float g = (float)(0.375 * q.h * q.h);
   const unsigned tx = (unsigned)((q.nx + LP_TX) / LP_TX), ty = (unsigned)((q.ny + LP_TY) / LP_TY);
@@ -435,13 +434,9 @@ static cudaError_t gs_lp_sweeps(const Geo &q, S *u, const S *f, int sweeps, S *w
   const bool tma = ((uintptr_t)f % 16) == 0 && tma_plane_map_elem(q, u, (int)sizeof(S), LT_W, LT_H, &mu) &&
                    tma_plane_map_elem(q, work, (int)sizeof(S), LT_W, LT_H, &mw);
   if (tma) {
-    static bool attr_t = false;
-    if (!attr_t) {
-      cudaError_t e =
-          cudaFuncSetAttribute(k_gs_lp_t<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lt_smem<S>());
-      if (e != cudaSuccess) return e;
-      attr_t = true;
-    }
+    static PerDeviceOnce attr_t;
+    cudaError_t e = set_smem_limit_once(attr_t, k_gs_lp_t<S>, lt_smem<S>());
+    if (e != cudaSuccess) return e;
   }
   constexpr int TTX = LtTile<S>::TX;
   const unsigned ttx = (unsigned)((q.nx + TTX) / TTX), tty = (unsigned)((q.ny + LT_TY) / LT_TY);

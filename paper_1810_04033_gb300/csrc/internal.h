@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
 #include <string>
 
 #include "stencil.h"
@@ -33,6 +35,32 @@ inline int64_t span_elems(const Geo &q) { return q.plane * (q.nz + 1); }
 
 // Streaming multiprocessors of the current device (cached per device; 152 on GB300).
 int device_sm_count();
+
+// Per-device "done" flags for set-up that CUDA keeps per device, such as a kernel's
+// dynamic shared-memory limit: a process may drive several GPUs and call the library
+// from several host threads (the request server runs its own).
+struct PerDeviceOnce {
+  static constexpr int kMaxDevices = 64;
+  std::atomic<bool> done[kMaxDevices];
+  std::mutex mu;
+};
+
+// Raises `kernel`'s dynamic shared-memory limit to `bytes` on the current device, once
+// per device; later calls on that device return at once.  Thread-safe.
+template <typename Kernel>
+cudaError_t set_smem_limit_once(PerDeviceOnce &once, Kernel kernel, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= PerDeviceOnce::kMaxDevices)
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (once.done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  std::lock_guard<std::mutex> lk(once.mu);
+  if (once.done[dev].load(std::memory_order_relaxed)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) once.done[dev].store(true, std::memory_order_release);
+  return e;
+}
 
 // Planes (or centre planes) per CTA for kernels that tile x-y and stream through z in
 // chunks: the largest chunk up to cz_max that still gives about two waves of

@@ -278,12 +278,10 @@ __global__ void __launch_bounds__(J3_THREADS, 3) k_jac3_sweep(J3Args a, const __
 
 template <int XF, int YF>
 cudaError_t launch_j3(const J3Args &a, const CUtensorMap &map, dim3 grid, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_jac3_sweep<XF, YF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)J3_SMEM);
+  static PerDeviceOnce attr;
+  {
+    cudaError_t e = set_smem_limit_once(attr, k_jac3_sweep<XF, YF>, J3_SMEM);
     if (e) return e;
-    attr = true;
   }
   k_jac3_sweep<XF, YF><<<grid, J3_THREADS, J3_SMEM, s>>>(a, map);
   return cudaGetLastError();

@@ -656,11 +656,10 @@ dim3 ops_grid(const Geo &q) {
 
 template <int OP>
 cudaError_t launch_op(const OpArgs &a, cudaStream_t s) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_ops3<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)O_SMEM);
+  static PerDeviceOnce attr;
+  {
+    cudaError_t e = set_smem_limit_once(attr, k_ops3<OP>, O_SMEM);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   const dim3 g = ops_grid(a.q);
   if (g.y > 65535 || g.z > 65535) return cudaErrorInvalidConfiguration;
@@ -672,12 +671,9 @@ cudaError_t launch_op(const OpArgs &a, cudaStream_t s) {
   CUtensorMap map;
   if (tma_plane_map(a.q, a.u, OS_W, OS_H, &map)) {
     constexpr size_t smem_t = 4 * (size_t)OS_H * OS_W * sizeof(long long) + 128;
-    static bool attr_t = false;
-    if (!attr_t) {
-      cudaError_t e = cudaFuncSetAttribute(k_ops3t<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
-      if (e != cudaSuccess) return e;
-      attr_t = true;
-    }
+    static PerDeviceOnce attr_t;
+    cudaError_t e = set_smem_limit_once(attr_t, k_ops3t<OP>, smem_t);
+    if (e != cudaSuccess) return e;
     k_ops3t<OP><<<g, O_THREADS, smem_t, s>>>(b, map);
   } else {
     k_ops3<OP><<<g, O_THREADS, O_SMEM, s>>>(b);

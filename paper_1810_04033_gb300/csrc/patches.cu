@@ -312,6 +312,24 @@ struct stencil_batch {
 
 static size_t patch_smem(int maxn) { return 4 * (size_t)(maxn + 1) * (maxn + 1) * sizeof(long long); }
 
+// The shared-memory limit of k_patch_gs is a per-device kernel attribute, while each
+// batch needs its own amount (it grows with the largest patch).  The limit is only ever
+// raised, so a batch created later with smaller patches cannot lower it under a batch
+// that needs more; a launch still asks for exactly its own amount.
+static cudaError_t raise_patch_smem_limit(size_t bytes) {
+  static std::mutex mu;
+  static size_t limit[64] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaFuncSetAttribute(k_patch_gs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  std::lock_guard<std::mutex> lk(mu);
+  if (bytes <= limit[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(k_patch_gs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) limit[dev] = bytes;
+  return e;
+}
+
 extern "C" {
 
 int stencil_patch_batch_create(const stencil_patch_desc_t *patches, int32_t npatch, const int32_t *neighbours,
@@ -352,7 +370,7 @@ int stencil_patch_batch_create(const stencil_patch_desc_t *patches, int32_t npat
        cudaMemcpy(b->d_nbr, neighbours, 27 * (size_t)npatch * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(b->d_order, order.data(), npatch * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
   const size_t smem = patch_smem(maxn);
-  ok = ok && cudaFuncSetAttribute(k_patch_gs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
+  ok = ok && raise_patch_smem_limit(smem) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     stencil_patch_batch_destroy(b);

@@ -82,7 +82,8 @@ __device__ __forceinline__ void cta_sum2(double &a, double &b, double *sh) {
 }
 
 // CTA b sums the contiguous rows [b*R, (b+1)*R); the last CTA to finish adds the
-// partials in CTA order, so the result depends only on the input and the grid.
+// partials in a fixed order (a strided subset per thread, then a fixed shuffle tree),
+// so the result depends only on the input and the grid.
 __global__ void __launch_bounds__(kNoAllocThreads)
     k_residual_noalloc(Geo q, int dim, const double *__restrict__ u, const double *__restrict__ f,
                        double *__restrict__ r, double *norms2, NoAllocScratch *scr, double inv_h2) {

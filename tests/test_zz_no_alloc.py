@@ -4,8 +4,9 @@ It exists for callers that cannot let the library call cudaMalloc (a device-wide
 synchronisation they cannot afford, device memory already owned by another allocator,
 or a no-allocation-after-start-up rule).  The test calls it through the C ABI twice in
 a row, on different grids, and checks each result against the allocating
-stencil_residual within the FP64 parity tolerance; it also checks that the second call
-leaves the device's free memory unchanged and that an oversize grid is refused.
+stencil_residual and against the CPU oracle within the FP64 parity tolerance; it also
+checks that the second call leaves the device's free memory unchanged and that an
+oversize grid is refused.
 This file is collected last so that a run stopping at the first failure has already
 run every other test; it passes alone in a fresh process as well.
 """
@@ -15,6 +16,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_1810_04033_gb300 as st
 import synth
 from tests.parity_util import TOL_F64, apply_err, to_dev, to_host
@@ -48,6 +50,11 @@ def _compare(h, u, ud, fd, r_new, n_new):
     a, b = n_new.cpu().numpy(), n_ref.cpu().numpy()
     assert abs(a[1] - b[1]) <= TOL_F64 * b[1]
     assert abs(a[0] - b[0]) <= TOL_F64 * max(b[0], 1e-300) * 10
+    # and against the oracle: r everywhere, the norm sums as in the parity tests
+    rref, nref = oracle.residual(u, to_host(fd), h)
+    assert apply_err(to_host(r_new), rref, u, h) <= TOL_F64
+    assert abs(a[1] - nref[1]) <= 1e-12 * nref[1]
+    assert abs(a[0] - nref[0]) <= 1e-11 * nref[0]
 
 
 def test_noalloc_residual_matches_allocating_entry_point_twice_in_a_row():
