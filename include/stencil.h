@@ -93,6 +93,22 @@ int stencil_version(void);
 /* Message for the last failing call on this host thread ("" if none). */
 const char *stencil_last_error(void);
 
+/* Calls whose device workspace stencil_workspace_size reports. */
+#define STENCIL_CALL_SMOOTH_COLOURED 1
+#define STENCIL_CALL_SMOOTH_JACOBI 2
+#define STENCIL_CALL_RESIDUAL 3
+
+/*
+ * *bytes = the device workspace (ws_bytes) that `call` needs on grid g for `sweeps`
+ * sweeps (ignored for STENCIL_CALL_RESIDUAL); 0 when the call needs none.  The paper
+ * has no counterpart: it lets callers own every device buffer (Memory, above).  The
+ * size depends on the descriptor, the call, the sweep count and, for the residual, the
+ * SM count of the current device (pass the buffer to calls on that device).  Host-only:
+ * touches no device memory and launches nothing.  Returns STENCIL_EINVAL for a bad
+ * descriptor, call or sweep count.
+ */
+int stencil_workspace_size(const stencil_grid_t *g, int call, int sweeps, size_t *bytes);
+
 /*
  * y = A u.  Section 2: a stencil evaluation per vertex from its neighbours' values;
  * a separate output array makes it the matrix-vector product.
@@ -117,25 +133,35 @@ int stencil_apply(const stencil_grid_t *g, const void *u, void *y, int form, voi
  * u: device array (in/out); f: device array, may not alias u.  dtype F64 (2D, 3D);
  * F32 or BF16 (3D): values stored in that type, arithmetic in FP32, every store of a
  * bf16 value rounded to nearest even.
- * The call may use an internal device workspace of up to three times the size of u
- * (allocated on first use and kept; see stencil_release_workspace).
- * Returns STENCIL_EINVAL, STENCIL_ENOMEM, STENCIL_ECUDA.
+ * ws, ws_bytes: the call's device workspace, owned by the caller: at least
+ * stencil_workspace_size(g, STENCIL_CALL_SMOOTH_COLOURED, sweeps) bytes, 256-byte
+ * aligned, overlapping neither u nor f (F64: up to three times the size of u; no
+ * initial contents needed, contents on return unspecified).  Work queued on the stream
+ * owns it until it completes.  ws = NULL is a convenience: the library then uses its
+ * own workspace for (device, stream), allocated on first use, grown when a larger grid
+ * needs more (which synchronises the stream) and kept until stencil_release_workspace.
+ * Returns STENCIL_EINVAL (also for a short or misaligned ws), STENCIL_ENOMEM,
+ * STENCIL_ECUDA.
  */
-int stencil_smooth_coloured(const stencil_grid_t *g, void *u, const void *f, int sweeps,
-                            void *stream);
+int stencil_smooth_coloured(const stencil_grid_t *g, void *u, const void *f, int sweeps, void *ws,
+                            size_t ws_bytes, void *stream);
 
 /*
  * `sweeps` damped Jacobi sweeps, out of place:
  *   u_i <- u_i + omega * (h^2 f_i - (S u)_i) / S_ii   on interior vertices,
  * every new value computed from the previous sweep's array (the contrast to the
  * in-situ update of Section 2).  work: caller-owned device array with the layout of u,
- * used as scratch (its contents on return are unspecified).  The result of the last
- * sweep is in u; boundary values of u are never changed.  The call may use an internal
- * device workspace of twice the size of u (allocated on first use and kept).
- * dtype F64.  Returns STENCIL_EINVAL, STENCIL_ENOMEM, STENCIL_ECUDA.
+ * the second array of the out-of-place sweep (its contents on return are unspecified).
+ * The result of the last sweep is in u; boundary values of u are never changed.
+ * ws, ws_bytes: further device workspace of the multi-sweep kernels (int64 copies of
+ * the iterate), at least stencil_workspace_size(g, STENCIL_CALL_SMOOTH_JACOBI, sweeps)
+ * bytes (twice the size of u for two or more Q1 sweeps, else 0), 256-byte aligned,
+ * overlapping no other argument; ws = NULL selects the library's own workspace as for
+ * stencil_smooth_coloured.  dtype F64.
+ * Returns STENCIL_EINVAL, STENCIL_ENOMEM, STENCIL_ECUDA.
  */
 int stencil_smooth_jacobi(const stencil_grid_t *g, void *u, const void *f, void *work,
-                          int sweeps, double omega, void *stream);
+                          int sweeps, double omega, void *ws, size_t ws_bytes, void *stream);
 
 /*
  * One damped Jacobi sweep, out of place: u_out = u_in + omega D^-1 (f - A u_in) on
@@ -151,11 +177,15 @@ int stencil_jacobi_step(const stencil_grid_t *g, const void *u_in, const void *f
  * d_norms2[0] = sum of r_i^2, d_norms2[1] = sum of f_i^2 over interior vertices, both
  * in FP64 by a fixed-order two-level reduction (the same bits on every call with the
  * same input and device).  r may be NULL (norms only).  d_norms2: device, 2 doubles.
- * The reduction uses a library-owned device scratch buffer (allocated on first use).
- * dtype F64.  Returns STENCIL_EINVAL, STENCIL_ENOMEM, STENCIL_ECUDA.
+ * ws, ws_bytes: the reduction's device workspace (a counter, which the call clears on
+ * the stream, and one pair of partial sums per CTA), at least
+ * stencil_workspace_size(g, STENCIL_CALL_RESIDUAL, 0) bytes, 256-byte aligned,
+ * overlapping no other argument; ws = NULL selects the library's own workspace as for
+ * stencil_smooth_coloured.  dtype F64.
+ * Returns STENCIL_EINVAL, STENCIL_ENOMEM, STENCIL_ECUDA.
  */
 int stencil_residual(const stencil_grid_t *g, const void *u, const void *f, void *r,
-                     double *d_norms2, void *stream);
+                     double *d_norms2, void *ws, size_t ws_bytes, void *stream);
 
 /*
  * Allocation-free variant of stencil_residual, for callers that cannot let a library

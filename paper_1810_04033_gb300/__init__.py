@@ -119,9 +119,10 @@ def lib():
             "stencil_last_error": (ctypes.c_char_p, []),
             "stencil_release_workspace": (ci, []),
             "stencil_apply": (ci, [gp, vp, vp, ci, vp]),
-            "stencil_smooth_coloured": (ci, [gp, vp, vp, ci, vp]),
-            "stencil_smooth_jacobi": (ci, [gp, vp, vp, vp, ci, cd, vp]),
-            "stencil_residual": (ci, [gp, vp, vp, vp, vp, vp]),
+            "stencil_workspace_size": (ci, [gp, ci, ci, ctypes.POINTER(ctypes.c_size_t)]),
+            "stencil_smooth_coloured": (ci, [gp, vp, vp, ci, vp, ctypes.c_size_t, vp]),
+            "stencil_smooth_jacobi": (ci, [gp, vp, vp, vp, ci, cd, vp, ctypes.c_size_t, vp]),
+            "stencil_residual": (ci, [gp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]),
             "stencil_jacobi_step": (ci, [gp, vp, vp, vp, cd, vp]),
             "stencil_residual_noalloc": (ci, [gp, vp, vp, vp, vp, vp]),
             "stencil_solve": (ci, [gp, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]),
@@ -234,22 +235,46 @@ def stencil_apply(u, y, h, form=FORM_STENCIL, stream=None, op=OP_Q1):
     return y
 
 
-def stencil_smooth_coloured(u, f, h, sweeps, stream=None, op=OP_Q1):
-    """`sweeps` coloured Gauss-Seidel sweeps on A u = f, in place on u (OP_FD: red-black)."""
+CALL_SMOOTH_COLOURED, CALL_SMOOTH_JACOBI, CALL_RESIDUAL = 1, 2, 3
+
+
+def stencil_workspace_size(u, h, call, sweeps=0, op=OP_Q1):
+    """Bytes of device workspace (`ws`) that `call` needs on u's grid for `sweeps` sweeps."""
+    g = grid_for(u, h, op)
+    n = ctypes.c_size_t(0)
+    _check(lib().stencil_workspace_size(ctypes.byref(g), int(call), int(sweeps), ctypes.byref(n)))
+    return int(n.value)
+
+
+def _ws(ws, device):
+    """(pointer, bytes) of a caller workspace tensor, or (NULL, 0) for the library's own."""
+    if ws is None:
+        return ctypes.c_void_p(0), 0
+    if not isinstance(ws, torch.Tensor) or ws.device != device or not ws.is_contiguous():
+        raise ValueError("ws must be a contiguous tensor on the grid's device")
+    return ctypes.c_void_p(ws.data_ptr()), ws.numel() * ws.element_size()
+
+
+def stencil_smooth_coloured(u, f, h, sweeps, stream=None, op=OP_Q1, ws=None):
+    """`sweeps` coloured Gauss-Seidel sweeps on A u = f, in place on u (OP_FD: red-black).
+    ws: optional caller workspace (stencil_workspace_size bytes, e.g. a uint8 tensor)."""
     _same_layout(u, f)
     g = grid_for(u, h, op)
-    _check(lib().stencil_smooth_coloured(ctypes.byref(g), _ptr(u), _ptr(f), int(sweeps),
+    wp, wb = _ws(ws, u.device)
+    _check(lib().stencil_smooth_coloured(ctypes.byref(g), _ptr(u), _ptr(f), int(sweeps), wp, wb,
                                          _stream(stream)))
     return u
 
 
-def stencil_smooth_jacobi(u, f, work, h, sweeps, omega=2.0 / 3.0, stream=None, op=OP_Q1):
-    """`sweeps` damped Jacobi sweeps; result in u, work is scratch of u's layout."""
+def stencil_smooth_jacobi(u, f, work, h, sweeps, omega=2.0 / 3.0, stream=None, op=OP_Q1, ws=None):
+    """`sweeps` damped Jacobi sweeps; result in u, work is scratch of u's layout;
+    ws: optional caller workspace as for stencil_smooth_coloured."""
     _same_layout(u, f)
     _same_layout(u, work)
     g = grid_for(u, h, op)
+    wp, wb = _ws(ws, u.device)
     _check(lib().stencil_smooth_jacobi(ctypes.byref(g), _ptr(u), _ptr(f), _ptr(work),
-                                       int(sweeps), float(omega), _stream(stream)))
+                                       int(sweeps), float(omega), wp, wb, _stream(stream)))
     return u
 
 
@@ -263,8 +288,9 @@ def stencil_jacobi_step(u_in, f, u_out, h, omega=2.0 / 3.0, stream=None, op=OP_Q
     return u_out
 
 
-def stencil_residual(u, f, h, r=None, norms2=None, stream=None, op=OP_Q1):
-    """r = f - A u (if r given) and norms2 = [sum r^2, sum f^2] (device float64[2])."""
+def stencil_residual(u, f, h, r=None, norms2=None, stream=None, op=OP_Q1, ws=None):
+    """r = f - A u (if r given) and norms2 = [sum r^2, sum f^2] (device float64[2]);
+    ws: optional caller workspace as for stencil_smooth_coloured."""
     _same_layout(u, f)
     if r is not None:
         _same_layout(u, r)
@@ -272,9 +298,10 @@ def stencil_residual(u, f, h, r=None, norms2=None, stream=None, op=OP_Q1):
         norms2 = torch.empty(2, dtype=torch.float64, device=u.device)
     _device_buffer(norms2, "norms2", u.device, 2)
     g = grid_for(u, h, op)
+    wp, wb = _ws(ws, u.device)
     _check(lib().stencil_residual(ctypes.byref(g), _ptr(u), _ptr(f),
                                   _ptr(r) if r is not None else ctypes.c_void_p(0),
-                                  _ptr(norms2), _stream(stream)))
+                                  _ptr(norms2), wp, wb, _stream(stream)))
     return norms2
 
 

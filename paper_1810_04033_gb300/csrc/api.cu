@@ -219,6 +219,90 @@ static bool overlap(const void *a, const void *b, size_t bytes) {
   return x < y + bytes && y < x + bytes;
 }
 
+// [a, a + na) and [b, b + nb) intersect.
+static bool overlap2(const void *a, size_t na, const void *b, size_t nb) {
+  const char *x = (const char *)a, *y = (const char *)b;
+  return x < y + nb && y < x + na;
+}
+
+// ------------------------------------------------------------ call workspaces
+// The device workspace of a call is at most two parts, each starting on a 256-byte
+// boundary of one buffer.  A caller that passes its own buffer (at least total() bytes,
+// 256-byte aligned) gets no allocation from the call; a NULL buffer selects the
+// library's per-(device, stream) scratch slots.
+static size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct WsNeed {
+  size_t part[2] = {0, 0};
+  int slot[2] = {0, 0};
+  bool zero_head = false;  // part 0 starts with a reduction counter that must be 0
+  size_t total() const { return part[1] ? round256(part[0]) + part[1] : part[0]; }
+};
+
+static WsNeed smooth_coloured_need(const stencil_grid_t *g, int sweeps) {
+  WsNeed w;
+  if (sweeps <= 0 || g->op == STENCIL_OP_FD) return w;
+  const size_t span = (size_t)span_elems(make_geo(*g));
+  if (g->dtype != STENCIL_F64) {
+    w.part[0] = span * elem_size(g->dtype);
+    w.slot[0] = SCRATCH_LP;
+    return w;
+  }
+  w.part[0] = 3 * span * 8;  // two int64 ping-pong copies and 3/8 h^2 f in fixed point
+  w.slot[0] = SCRATCH_PINGPONG;
+  w.part[1] = gs_fx_bounds_bytes();
+  w.slot[1] = SCRATCH_BOUNDS;
+  return w;
+}
+
+// Multi-sweep Q1 Jacobi runs its fast path for 0 < omega <= 1; the size does not
+// depend on omega (other omegas need less).
+static WsNeed smooth_jacobi_need(const stencil_grid_t *g, int sweeps) {
+  WsNeed w;
+  if (g->op != STENCIL_OP_Q1 || sweeps < 2) return w;
+  w.part[0] = 2 * (size_t)span_elems(make_geo(*g)) * 8;
+  w.slot[0] = SCRATCH_PINGPONG;
+  w.part[1] = gs_fx_bounds_bytes();
+  w.slot[1] = SCRATCH_BOUNDS;
+  return w;
+}
+
+static WsNeed residual_need(const stencil_grid_t *g) {
+  WsNeed w;
+  const Geo q = make_geo(*g);
+  w.part[0] = g->op == STENCIL_OP_FD ? fd_reduce_bytes(q) : g->dim == 3 ? ops_fx_reduce_bytes(q) : ops2_reduce_bytes(q);
+  w.slot[0] = SCRATCH_REDUCE;
+  w.zero_head = true;
+  return w;
+}
+
+// Checks a caller workspace against the need (synchronously, before any device work).
+static int check_ws(const WsNeed &need, const void *ws, size_t ws_bytes, const char *what) {
+  if (!ws) return STENCIL_OK;
+  if ((uintptr_t)ws % 256)
+    return set_error(STENCIL_EINVAL, std::string(what) + ": workspace must be 256-byte aligned");
+  if (ws_bytes < need.total())
+    return set_error(STENCIL_EINVAL, std::string(what) + ": workspace too small (" + std::to_string(ws_bytes) +
+                                         " bytes given, " + std::to_string(need.total()) + " needed)");
+  return STENCIL_OK;
+}
+
+// Resolves the parts: carved from the caller's buffer, or the library's scratch.
+static int take_ws(const WsNeed &need, void *ws, cudaStream_t s, void *out[2], const char *what) {
+  out[0] = out[1] = nullptr;
+  if (ws) {
+    out[0] = need.part[0] ? ws : nullptr;
+    out[1] = need.part[1] ? (char *)ws + round256(need.part[0]) : nullptr;
+    if (need.zero_head && cudaMemsetAsync(ws, 0, 16, s) != cudaSuccess)
+      return set_error(STENCIL_ECUDA, std::string(what) + ": clearing the workspace counter failed");
+    return STENCIL_OK;
+  }
+  for (int i = 0; i < 2; ++i)
+    if (need.part[i] && !(out[i] = device_scratch(need.slot[i], need.part[i], s)))
+      return set_error(STENCIL_ENOMEM, std::string(what) + ": workspace allocation failed");
+  return STENCIL_OK;
+}
+
 }  // namespace stencil
 
 using namespace stencil;
@@ -230,6 +314,21 @@ int stencil_version(void) { return 10000; }
 const char *stencil_last_error(void) { return g_last_error.c_str(); }
 
 int stencil_release_workspace(void) { return release_scratch(); }
+
+int stencil_workspace_size(const stencil_grid_t *g, int call, int sweeps, size_t *bytes) {
+  if (!bytes) return set_error(STENCIL_EINVAL, "workspace_size: bytes is NULL");
+  *bytes = 0;
+  int rc = check_grid(g);
+  if (rc) return rc;
+  if (sweeps < 0) return set_error(STENCIL_EINVAL, "workspace_size: sweeps < 0");
+  switch (call) {
+    case STENCIL_CALL_SMOOTH_COLOURED: *bytes = smooth_coloured_need(g, sweeps).total(); break;
+    case STENCIL_CALL_SMOOTH_JACOBI: *bytes = smooth_jacobi_need(g, sweeps).total(); break;
+    case STENCIL_CALL_RESIDUAL: *bytes = residual_need(g).total(); break;
+    default: return set_error(STENCIL_EINVAL, "workspace_size: unknown call");
+  }
+  return STENCIL_OK;
+}
 
 int stencil_apply(const stencil_grid_t *g, const void *u, void *y, int form, void *stream) {
   int rc = check_grid(g);
@@ -257,8 +356,8 @@ int stencil_apply(const stencil_grid_t *g, const void *u, void *y, int form, voi
   return STENCIL_OK;
 }
 
-int stencil_smooth_coloured(const stencil_grid_t *g, void *u, const void *f, int sweeps,
-                            void *stream) {
+int stencil_smooth_coloured(const stencil_grid_t *g, void *u, const void *f, int sweeps, void *ws,
+                            size_t ws_bytes, void *stream) {
   int rc = check_grid(g);
   if (rc) return rc;
   if ((rc = check_ptr(u, g, "u")) || (rc = check_ptr(f, g, "f"))) return rc;
@@ -268,27 +367,26 @@ int stencil_smooth_coloured(const stencil_grid_t *g, void *u, const void *f, int
   const Geo q = make_geo(*g);
   const size_t esz = elem_size(g->dtype);
   if (overlap(u, f, (size_t)span_elems(q) * esz)) return set_error(STENCIL_EINVAL, "u and f overlap");
+  const WsNeed need = smooth_coloured_need(g, sweeps);
+  if ((rc = check_ws(need, ws, ws_bytes, "smooth_coloured"))) return rc;
+  const size_t wsb = need.total(), ub = (size_t)span_elems(q) * esz;
+  if (ws && wsb && (overlap2(ws, wsb, u, ub) || overlap2(ws, wsb, f, ub)))
+    return set_error(STENCIL_EINVAL, "smooth_coloured: workspace overlaps u or f");
   if (sweeps == 0) return STENCIL_OK;
   cudaStream_t s = (cudaStream_t)stream;
+  void *part[2];
+  if ((rc = take_ws(need, ws, s, part, "smooth_coloured"))) return rc;
   cudaError_t e;
   if (g->op == STENCIL_OP_FD) {
     e = launch_fd_gs_redblack(q, g->dim, (double *)u, (const double *)f, sweeps, s);
   } else if (g->dtype != STENCIL_F64) {
-    void *work = device_scratch(SCRATCH_LP, (size_t)span_elems(q) * esz, s);
-    if (!work) return set_error(STENCIL_ENOMEM, "smooth_coloured workspace allocation failed");
     e = g->dtype == STENCIL_F32
-            ? launch_gs_sweeps_f32_3d(q, (float *)u, (const float *)f, sweeps, (float *)work, s)
-            : launch_gs_sweeps_bf16_3d(q, u, f, sweeps, work, s);
+            ? launch_gs_sweeps_f32_3d(q, (float *)u, (const float *)f, sweeps, (float *)part[0], s)
+            : launch_gs_sweeps_bf16_3d(q, u, f, sweeps, part[0], s);
   } else if (g->dim == 3) {
-    void *work = device_scratch(SCRATCH_PINGPONG, 3 * (size_t)span_elems(q) * 8, s);
-    void *bnd = device_scratch(SCRATCH_BOUNDS, gs_fx_bounds_bytes(), s);
-    if (!work || !bnd) return set_error(STENCIL_ENOMEM, "smooth_coloured workspace allocation failed");
-    e = launch_gs_sweeps_fx3(q, (double *)u, (const double *)f, sweeps, (double *)work, bnd, s);
+    e = launch_gs_sweeps_fx3(q, (double *)u, (const double *)f, sweeps, (double *)part[0], part[1], s);
   } else {
-    void *work = device_scratch(SCRATCH_PINGPONG, 3 * (size_t)span_elems(q) * 8, s);
-    void *bnd = device_scratch(SCRATCH_BOUNDS, gs_fx_bounds_bytes(), s);
-    if (!work || !bnd) return set_error(STENCIL_ENOMEM, "smooth_coloured workspace allocation failed");
-    e = launch_gs_sweeps_fx2(q, (double *)u, (const double *)f, sweeps, (double *)work, bnd, s);
+    e = launch_gs_sweeps_fx2(q, (double *)u, (const double *)f, sweeps, (double *)part[0], part[1], s);
   }
   if (e != cudaSuccess)
     return set_error(STENCIL_ECUDA, std::string("smooth_coloured: ") + cudaGetErrorString(e));
@@ -296,7 +394,7 @@ int stencil_smooth_coloured(const stencil_grid_t *g, void *u, const void *f, int
 }
 
 int stencil_smooth_jacobi(const stencil_grid_t *g, void *u, const void *f, void *work,
-                          int sweeps, double omega, void *stream) {
+                          int sweeps, double omega, void *ws, size_t ws_bytes, void *stream) {
   int rc = check_grid(g);
   if (rc) return rc;
   if ((rc = check_ptr(u, g, "u")) || (rc = check_ptr(f, g, "f")) ||
@@ -309,11 +407,16 @@ int stencil_smooth_jacobi(const stencil_grid_t *g, void *u, const void *f, void 
   const size_t bytes = (size_t)span_elems(q) * 8;
   if (overlap(u, f, bytes) || overlap(u, work, bytes) || overlap(f, work, bytes))
     return set_error(STENCIL_EINVAL, "u, f and work must not overlap");
+  const WsNeed need = smooth_jacobi_need(g, sweeps);
+  if ((rc = check_ws(need, ws, ws_bytes, "smooth_jacobi"))) return rc;
+  const size_t wsb = need.total();
+  if (ws && wsb && (overlap2(ws, wsb, u, bytes) || overlap2(ws, wsb, f, bytes) || overlap2(ws, wsb, work, bytes)))
+    return set_error(STENCIL_EINVAL, "smooth_jacobi: workspace overlaps u, f or work");
   cudaStream_t s = (cudaStream_t)stream;
   if (g->op == STENCIL_OP_Q1 && sweeps >= 2 && omega > 0.0 && omega <= 1.0) {
-    void *scr = device_scratch(SCRATCH_PINGPONG, 2 * bytes, s);
-    void *bnd = device_scratch(SCRATCH_BOUNDS, gs_fx_bounds_bytes(), s);
-    if (!scr || !bnd) return set_error(STENCIL_ENOMEM, "jacobi workspace allocation failed");
+    void *part[2];
+    if ((rc = take_ws(need, ws, s, part, "smooth_jacobi"))) return rc;
+    void *scr = part[0], *bnd = part[1];
     cudaError_t e =
         g->dim == 2 ? launch_jacobi_sweeps_fx2(q, (double *)u, (const double *)f, sweeps, omega, (double *)work,
                                                (double *)scr, bnd, s)
@@ -365,7 +468,7 @@ int stencil_jacobi_step(const stencil_grid_t *g, const void *u_in, const void *f
 }
 
 int stencil_residual(const stencil_grid_t *g, const void *u, const void *f, void *r,
-                     double *d_norms2, void *stream) {
+                     double *d_norms2, void *ws, size_t ws_bytes, void *stream) {
   int rc = check_grid(g);
   if (rc) return rc;
   if ((rc = check_ptr(u, g, "u")) || (rc = check_ptr(f, g, "f"))) return rc;
@@ -376,11 +479,15 @@ int stencil_residual(const stencil_grid_t *g, const void *u, const void *f, void
   const size_t bytes = (size_t)span_elems(q) * 8;
   if (r && (overlap(r, u, bytes) || overlap(r, f, bytes)))
     return set_error(STENCIL_EINVAL, "r overlaps u or f");
-  const size_t need = g->op == STENCIL_OP_FD ? fd_reduce_bytes(q)
-                      : g->dim == 3         ? ops_fx_reduce_bytes(q)
-                                            : ops2_reduce_bytes(q);
-  void *scratch = device_scratch(SCRATCH_REDUCE, need, (cudaStream_t)stream);
-  if (!scratch) return set_error(STENCIL_ENOMEM, "residual scratch allocation failed");
+  const WsNeed need = residual_need(g);
+  if ((rc = check_ws(need, ws, ws_bytes, "residual"))) return rc;
+  const size_t wsb = need.total();
+  if (ws && (overlap2(ws, wsb, u, bytes) || overlap2(ws, wsb, f, bytes) || (r && overlap2(ws, wsb, r, bytes)) ||
+             overlap2(ws, wsb, d_norms2, 16)))
+    return set_error(STENCIL_EINVAL, "residual: workspace overlaps an argument");
+  void *part[2];
+  if ((rc = take_ws(need, ws, (cudaStream_t)stream, part, "residual"))) return rc;
+  void *scratch = part[0];
   cudaError_t e =
       g->op == STENCIL_OP_FD
           ? launch_fd_residual(q, g->dim, (const double *)u, (const double *)f, (double *)r, d_norms2, scratch,

@@ -95,4 +95,59 @@ def test_null_and_misaligned_pointers_rejected():
     # overlapping input/output
     assert L.stencil_apply(ctypes.byref(g), ctypes.c_void_p(4096), ctypes.c_void_p(4096 + 64), 1, None) == -1
     assert "overlap" in L.stencil_last_error().decode()
-    assert L.stencil_smooth_coloured(ctypes.byref(g), ctypes.c_void_p(4096), ctypes.c_void_p(1 << 20), -1, None) == -1
+    assert L.stencil_smooth_coloured(ctypes.byref(g), ctypes.c_void_p(4096), ctypes.c_void_p(1 << 20), -1,
+                                     None, 0, None) == -1
+
+
+def _ws_size(g, call, sweeps):
+    n = ctypes.c_size_t(0)
+    rc = st.lib().stencil_workspace_size(ctypes.byref(g), call, sweeps, ctypes.byref(n))
+    return rc, n.value
+
+
+def test_workspace_size_without_gpu():
+    """Sizes follow from the descriptor: F64 GS needs three int64 copies of the grid
+    plus the per-sweep bounds, multi-sweep Jacobi two copies, FD red-black none."""
+    g = _grid(n=(7, 5, 3), pitch=10)
+    span = 10 * 6 * 4
+    rc, gs = _ws_size(g, st.CALL_SMOOTH_COLOURED, 4)
+    assert rc == 0 and 3 * span * 8 < gs <= 3 * span * 8 + 256 + 1024
+    assert gs > 3 * span * 8 + 255 - (3 * span * 8) % 256  # bounds part starts on 256 bytes
+    rc, jac = _ws_size(g, st.CALL_SMOOTH_JACOBI, 4)
+    assert rc == 0 and 2 * span * 8 < jac <= 2 * span * 8 + 256 + 1024
+    assert _ws_size(g, st.CALL_SMOOTH_JACOBI, 1) == (0, 0)
+    assert _ws_size(g, st.CALL_SMOOTH_COLOURED, 0) == (0, 0)
+    rc, red = _ws_size(g, st.CALL_RESIDUAL, 0)
+    assert rc == 0 and red >= 16 + 16
+    g32 = _grid(n=(7, 5, 3), pitch=12, dtype=st.F32)
+    assert _ws_size(g32, st.CALL_SMOOTH_COLOURED, 3) == (0, 12 * 6 * 4 * 4)
+    gfd = _grid(op=st.OP_FD)
+    assert _ws_size(gfd, st.CALL_SMOOTH_COLOURED, 3) == (0, 0)
+    assert _ws_size(g, 99, 1)[0] == -1
+    assert "unknown call" in st.lib().stencil_last_error().decode()
+    assert _ws_size(g, st.CALL_SMOOTH_COLOURED, -1)[0] == -1
+    assert _ws_size(_grid(dim=5), st.CALL_RESIDUAL, 0)[0] == -1
+
+
+def test_short_or_misaligned_workspace_rejected_without_gpu():
+    """A caller workspace smaller than stencil_workspace_size, or not 256-byte aligned,
+    or overlapping an argument, is refused before any device work."""
+    L = st.lib()
+    g = _grid(n=(7, 5, 3))
+    u, f, w = ctypes.c_void_p(1 << 20), ctypes.c_void_p(2 << 20), ctypes.c_void_p(3 << 20)
+    _, need = _ws_size(g, st.CALL_SMOOTH_COLOURED, 4)
+    ws = ctypes.c_void_p(8 << 20)
+    assert L.stencil_smooth_coloured(ctypes.byref(g), u, f, 4, ws, need - 1, None) == -1
+    assert "too small" in L.stencil_last_error().decode()
+    assert L.stencil_smooth_coloured(ctypes.byref(g), u, f, 4, ctypes.c_void_p((8 << 20) + 128), need,
+                                     None) == -1
+    assert "256-byte" in L.stencil_last_error().decode()
+    assert L.stencil_smooth_coloured(ctypes.byref(g), u, f, 4, ctypes.c_void_p(1 << 20), need, None) == -1
+    assert "overlaps" in L.stencil_last_error().decode()
+    _, jneed = _ws_size(g, st.CALL_SMOOTH_JACOBI, 4)
+    assert L.stencil_smooth_jacobi(ctypes.byref(g), u, f, w, 4, 0.5, ws, jneed - 8, None) == -1
+    assert "too small" in L.stencil_last_error().decode()
+    _, rneed = _ws_size(g, st.CALL_RESIDUAL, 0)
+    assert L.stencil_residual(ctypes.byref(g), u, f, None, ctypes.c_void_p(4 << 20), ws, rneed - 1,
+                              None) == -1
+    assert "too small" in L.stencil_last_error().decode()

@@ -55,10 +55,18 @@ def _check_applies_and_residual(u, f, h, pad):
     nrm = st.stencil_residual(ud, fd, h, r=rd).cpu().numpy()
     got = to_host(rd)
     del rd
-    rref, nref = oracle.residual(u, f, h, nthreads=NT)
+    rref, _ = oracle.residual(u, f, h, nthreads=NT)
     assert apply_err(got, rref, u, h) <= TOL_F64
-    assert abs(nrm[1] - nref[1]) <= 1e-12 * nref[1]
-    assert abs(nrm[0] - nref[0]) <= 1e-11 * nref[0]
+    # The oracle adds its ~10^8 squares one after the other: the forward error bound of
+    # that order is (N - 1) eps of the sum (1.5e-8 at 513^3), and its typical error,
+    # about sqrt(N) eps, already reaches 1e-12.  The reference norms here are pairwise
+    # sums (numpy's order over a contiguous array, error below ~log2(N) eps = 3e-15) of
+    # the oracle's squares, so that 1e-12 measures the kernel's error, not the oracle's.
+    inner = tuple(slice(1, -1) for _ in u.shape)
+    nr = float(np.sum(np.square(np.ascontiguousarray(rref[inner]).ravel())))
+    nf = float(np.sum(np.square(np.ascontiguousarray(f[inner]).ravel())))
+    assert abs(nrm[1] - nf) <= 1e-12 * nf
+    assert abs(nrm[0] - nr) <= 1e-12 * nr
 
 
 def _check_smoothers(u, f, h, pad, sweeps):
