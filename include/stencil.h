@@ -97,6 +97,8 @@ const char *stencil_last_error(void);
 #define STENCIL_CALL_SMOOTH_COLOURED 1
 #define STENCIL_CALL_SMOOTH_JACOBI 2
 #define STENCIL_CALL_RESIDUAL 3
+#define STENCIL_CALL_APPLY_ELEMENTWISE 4 /* stencil_apply, element-wise form: no workspace */
+#define STENCIL_CALL_APPLY_STENCIL 5     /* stencil_apply, stencil form: no workspace */
 
 /*
  * *bytes = the device workspace (ws_bytes) that `call` needs on grid g for `sweeps`
@@ -480,6 +482,57 @@ int stencil_server_destroy(stencil_server_t *s);
 /* Frees the internal workspaces of the current device (not thread-safe against
  * concurrent calls on that device). */
 int stencil_release_workspace(void);
+
+/* ---------------------------------------------------------------- launch-shape tuning
+ * The plane-streaming 3D kernels process a chunk of z-planes per CTA and the 2D kernels
+ * a chunk of rows per warp; the 2D multi-sweep smoothers run one or two sweeps per pass
+ * over memory.  The built-in rule picks these from the grid size and the SM count;
+ * stencil_autotune measures the alternatives instead.  The paper has no counterpart (its
+ * Sections 5-6 discuss tile sizes and the fusion of colours as the levers of a
+ * coloured sweep).  Tuned shapes apply to F64 Q1 calls of the same call kind, grid
+ * shape (n, pitch) and device name, process-wide.  The smoothers give identical bits
+ * under every shape; the single-pass applies keep a per-CTA (3D) or per-warp (2D)
+ * fixed-point scale, so their results can differ between shapes by rounding only
+ * (within the FP64 tolerance).
+ */
+typedef struct stencil_tuning {
+  int32_t chunk; /* 3D: z-planes per CTA; 2D: rows per warp (even); 0 = built-in rule */
+  int32_t depth; /* 2D GS/Jacobi: sweeps per pass over memory, 1 or 2; 0 = built-in (2) */
+  double ms;     /* stencil_autotune: time of one call with this shape, else as set */
+} stencil_tuning_t;
+
+/*
+ * Times every candidate shape of `call` (STENCIL_CALL_APPLY_ELEMENTWISE,
+ * STENCIL_CALL_APPLY_STENCIL, STENCIL_CALL_SMOOTH_COLOURED with `sweeps` sweeps,
+ * STENCIL_CALL_SMOOTH_JACOBI with omega 2/3) on grid g, on scratch arrays it allocates
+ * and fills itself (3D candidates: 4, 8, 16, 32 planes per CTA, 2..16 for GS; 2D: 16..256
+ * rows per warp for the applies, 64..1024 rows x 1 or 2 sweeps per pass for the
+ * smoothers), one untimed call and the best of three per candidate, CUDA events on
+ * `stream`.  Records the fastest for (device, call, g) and returns it in *out.
+ * Blocking (synchronises the stream); allocates about four arrays of g's size, plus the
+ * call's workspace, and frees them before returning.  Run it when no other thread
+ * launches calls on this grid shape.  F64, STENCIL_OP_Q1; smoothers 2..1000 sweeps.
+ * Returns STENCIL_EINVAL, STENCIL_ENOMEM, STENCIL_ECUDA.
+ */
+int stencil_autotune(const stencil_grid_t *g, int call, int sweeps, stencil_tuning_t *out, void *stream);
+
+/* Sets (t != NULL) or removes (t == NULL) the shape used for (device, call, g). */
+int stencil_tuning_set(const stencil_grid_t *g, int call, const stencil_tuning_t *t);
+/* The recorded shape for (device, call, g); STENCIL_ENOTFOUND if there is none. */
+int stencil_tuning_get(const stencil_grid_t *g, int call, stencil_tuning_t *t);
+/* Forgets every recorded shape. */
+int stencil_tuning_clear(void);
+/*
+ * Writes every recorded shape to `path` as JSON ({"format": "stencil_gb300_tuning",
+ * "version": 1, "entries": [{"device", "call", "dim", "n": [nx, ny, nz], "pitch",
+ * "chunk", "depth", "ms"}, ...]}), through a temporary file renamed into place; or
+ * reads such a file and adds its entries (all or none).  The first tuning lookup of the
+ * process also loads the file named by the environment variable STENCIL_TUNING_CACHE,
+ * if that file exists, so a saved cache steers later processes without code changes.
+ * Returns STENCIL_EINVAL for an unreadable/unwritable path or a malformed file.
+ */
+int stencil_tuning_save(const char *path);
+int stencil_tuning_load(const char *path);
 
 #ifdef __cplusplus
 }

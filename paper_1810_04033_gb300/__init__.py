@@ -99,6 +99,10 @@ class MgInfo(ctypes.Structure):
                 ("relres_history", ctypes.POINTER(ctypes.c_double))]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("chunk", ctypes.c_int32), ("depth", ctypes.c_int32), ("ms", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -120,6 +124,12 @@ def lib():
             "stencil_release_workspace": (ci, []),
             "stencil_apply": (ci, [gp, vp, vp, ci, vp]),
             "stencil_workspace_size": (ci, [gp, ci, ci, ctypes.POINTER(ctypes.c_size_t)]),
+            "stencil_autotune": (ci, [gp, ci, ci, ctypes.POINTER(Tuning), vp]),
+            "stencil_tuning_set": (ci, [gp, ci, ctypes.POINTER(Tuning)]),
+            "stencil_tuning_get": (ci, [gp, ci, ctypes.POINTER(Tuning)]),
+            "stencil_tuning_clear": (ci, []),
+            "stencil_tuning_save": (ci, [ctypes.c_char_p]),
+            "stencil_tuning_load": (ci, [ctypes.c_char_p]),
             "stencil_smooth_coloured": (ci, [gp, vp, vp, ci, vp, ctypes.c_size_t, vp]),
             "stencil_smooth_jacobi": (ci, [gp, vp, vp, vp, ci, cd, vp, ctypes.c_size_t, vp]),
             "stencil_residual": (ci, [gp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]),
@@ -236,6 +246,7 @@ def stencil_apply(u, y, h, form=FORM_STENCIL, stream=None, op=OP_Q1):
 
 
 CALL_SMOOTH_COLOURED, CALL_SMOOTH_JACOBI, CALL_RESIDUAL = 1, 2, 3
+CALL_APPLY_ELEMENTWISE, CALL_APPLY_STENCIL = 4, 5
 
 
 def stencil_workspace_size(u, h, call, sweeps=0, op=OP_Q1):
@@ -590,3 +601,46 @@ class Server:
 
 def stencil_release_workspace():
     _check(lib().stencil_release_workspace())
+
+
+# ------------------------------------------------------------------ launch-shape tuning
+def stencil_autotune(u, h, call, sweeps=0, stream=None):
+    """Times the candidate launch shapes of `call` on u's grid shape (scratch arrays of
+    the library's own) and records the fastest; returns (chunk, depth, ms)."""
+    g = grid_for(u, h)
+    t = Tuning()
+    _check(lib().stencil_autotune(ctypes.byref(g), int(call), int(sweeps), ctypes.byref(t), _stream(stream)))
+    return t.chunk, t.depth, t.ms
+
+
+def stencil_tuning_set(u, h, call, chunk=0, depth=0, ms=0.0):
+    """Records a launch shape for (device, call, u's grid); chunk=None removes it."""
+    g = grid_for(u, h)
+    if chunk is None:
+        _check(lib().stencil_tuning_set(ctypes.byref(g), int(call), None))
+    else:
+        t = Tuning(int(chunk), int(depth), float(ms))
+        _check(lib().stencil_tuning_set(ctypes.byref(g), int(call), ctypes.byref(t)))
+
+
+def stencil_tuning_get(u, h, call):
+    """(chunk, depth, ms) recorded for (device, call, u's grid), or None."""
+    g = grid_for(u, h)
+    t = Tuning()
+    rc = lib().stencil_tuning_get(ctypes.byref(g), int(call), ctypes.byref(t))
+    if rc == -7:
+        return None
+    _check(rc)
+    return t.chunk, t.depth, t.ms
+
+
+def stencil_tuning_clear():
+    _check(lib().stencil_tuning_clear())
+
+
+def stencil_tuning_save(path):
+    _check(lib().stencil_tuning_save(os.fsencode(path)))
+
+
+def stencil_tuning_load(path):
+    _check(lib().stencil_tuning_load(os.fsencode(path)))

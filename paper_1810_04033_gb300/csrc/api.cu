@@ -325,6 +325,8 @@ int stencil_workspace_size(const stencil_grid_t *g, int call, int sweeps, size_t
     case STENCIL_CALL_SMOOTH_COLOURED: *bytes = smooth_coloured_need(g, sweeps).total(); break;
     case STENCIL_CALL_SMOOTH_JACOBI: *bytes = smooth_jacobi_need(g, sweeps).total(); break;
     case STENCIL_CALL_RESIDUAL: *bytes = residual_need(g).total(); break;
+    case STENCIL_CALL_APPLY_ELEMENTWISE:
+    case STENCIL_CALL_APPLY_STENCIL: break;
     default: return set_error(STENCIL_EINVAL, "workspace_size: unknown call");
   }
   return STENCIL_OK;

@@ -402,7 +402,8 @@ __global__ void __launch_bounds__(E3_THREADS) k_apply_elementwise_s3(EwArgs a) {
 
 cudaError_t launch_apply_elementwise_fx3(const Geo &q, const double *u, double *y, cudaStream_t s) {
   const int64_t nseg = (q.nx + E3_OUT) / E3_OUT, njc = (q.ny + E3_R) / E3_R;
-  const int cz = z_chunk(nseg * njc, q.nz + 1, E3_CZ, 4, 64);
+  const int cz = tuned_chunk(tuning_lookup(STENCIL_CALL_APPLY_ELEMENTWISE, q), z_chunk(nseg * njc, q.nz + 1, E3_CZ, 4, 64),
+                            4, E3_CZ);
   const int64_t nzc = (q.nz + cz) / cz;
   const int64_t warps = nseg * njc * nzc;
   const int64_t blocks = (warps + E3_THREADS / 32 - 1) / (E3_THREADS / 32);

@@ -773,7 +773,8 @@ static bool launch_half_t(const Geo &q, int pz, const void *X, const void *N, vo
   const unsigned tx = (unsigned)((q.nx + 1 + GT_TX - 1) / GT_TX);
   const unsigned ty = (unsigned)((q.ny + 1 + GT_TY - 1) / GT_TY);
   const int64_t ncentre = (q.nz - pz) / 2 + 1;
-  const int cz = z_chunk((int64_t)tx * ty, ncentre, GS_CZ, 2, 2);
+  const int cz = tuned_chunk(tuning_lookup(STENCIL_CALL_SMOOTH_COLOURED, q),
+                             z_chunk((int64_t)tx * ty, ncentre, GS_CZ, 2, 2), 2, GS_CZ);
   const unsigned tz = (unsigned)((ncentre + cz - 1) / cz);
   if (ty > 65535 || tz > 65535) {
     *err = cudaErrorInvalidConfiguration;

@@ -74,8 +74,27 @@ inline int z_chunk(int64_t tiles_xy, int64_t units, int cz_max, int cz_min, int 
   return (int)cz;
 }
 
-// Error plumbing (api.cu).
+// Launch shapes chosen by stencil_autotune or stencil_tuning_set (tuning.cu), keyed by
+// the call, the grid's shape and pitch and the device's name.  chunk: 3D planes per CTA
+// (or per warp) of the plane-streaming kernels, 2D rows per warp; depth: sweeps per
+// pass over memory of the 2D multi-sweep smoothers (1 or 2).  0 = the built-in rule.
+// Only F64 Q1 calls are tuned; the kernels' results do not depend on these shapes
+// (exact fixed-point sums), except that the single-pass applies keep a per-CTA or
+// per-warp scale, whose rounding can move by a unit in the last place.
+struct Tuning {
+  int chunk = 0;
+  int depth = 0;
+};
+Tuning tuning_lookup(int call, const Geo &q);
+// The tuned chunk if one is set, clamped into [lo, hi], else `fallback`.
+inline int tuned_chunk(const Tuning &t, int fallback, int lo, int hi) {
+  if (t.chunk <= 0) return fallback;
+  return t.chunk < lo ? lo : (t.chunk > hi ? hi : t.chunk);
+}
+
+// Error plumbing and descriptor check (api.cu).
 int set_error(int code, const std::string &msg);
+int check_grid(const stencil_grid_t *g);
 int check_launch(const char *what);
 
 // Library-owned scratch (api.cu), one set per (device, stream): returns a device

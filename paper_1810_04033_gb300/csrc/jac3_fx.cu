@@ -327,7 +327,7 @@ cudaError_t launch_jacobi_sweeps_fx3(const Geo &q, double *u, const double *f, i
   a.c2 = -omega * 0.375 / 12.0;
   a.Wq = (long long)llrint(omega * 0x1p62);
   const int64_t tx = (q.nx + J3_TX) / J3_TX, ty = (q.ny + J3_TY) / J3_TY;
-  a.cz = z_chunk(tx * ty, q.nz + 1, J3_CZ, 4, 3);
+  a.cz = tuned_chunk(tuning_lookup(STENCIL_CALL_SMOOTH_JACOBI, q), z_chunk(tx * ty, q.nz + 1, J3_CZ, 4, 3), 4, J3_CZ);
   const dim3 grid((unsigned)tx, (unsigned)ty, (unsigned)((q.nz + a.cz) / a.cz));
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
   const CUtensorMap *X = &mu;

@@ -58,6 +58,7 @@ struct Op2Args {
   double *partials;
   unsigned *counter;
   double *norms2;
+  int rows;  // rows per warp (W2_ROWS unless a tuned shape says otherwise)
 };
 
 struct WarpScale {
@@ -458,7 +459,7 @@ __global__ void __launch_bounds__(W2_THREADS) k_ops2(Op2Args a) {
   __shared__ bool last;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   Stream2 s;
-  ops2_warp<OP, V16>(a, lane, (int64_t)blockIdx.x * (W2_THREADS / 32) + wib, s, W2_ROWS);
+  ops2_warp<OP, V16>(a, lane, (int64_t)blockIdx.x * (W2_THREADS / 32) + wib, s, a.rows);
   double rr = s.rr, ff = s.ff;
   if (OP == O2_RESIDUAL) {
 #pragma unroll
@@ -514,8 +515,8 @@ __global__ void __launch_bounds__(W2_THREADS) k_ops2(Op2Args a) {
   }
 }
 
-unsigned ops2_blocks(const Geo &q) {
-  return (unsigned)((ops2_units(q, W2_ROWS) + W2_THREADS / 32 - 1) / (W2_THREADS / 32));
+unsigned ops2_blocks(const Geo &q, int rows) {
+  return (unsigned)((ops2_units(q, rows) + W2_THREADS / 32 - 1) / (W2_THREADS / 32));
 }
 
 // ------------------------------------------------------------------ Gauss-Seidel
@@ -754,7 +755,7 @@ template <int XF, int YF, bool V16>
 __global__ void __launch_bounds__(W2_THREADS) k_gs2_sweep(Geo q, const void *__restrict__ X, void *__restrict__ Y,
                                                           const double *__restrict__ f,
                                                           const long long *__restrict__ GF, SweepBounds *bnd,
-                                                          int sweep, int sweeps, double g, bool write_bnd) {
+                                                          int sweep, int sweeps, double g, bool write_bnd, int rows) {
   __shared__ unsigned red[W2_THREADS / 32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * (W2_THREADS / 32) + wib;
@@ -762,9 +763,9 @@ __global__ void __launch_bounds__(W2_THREADS) k_gs2_sweep(Geo q, const void *__r
   if (!plan.fix) {
     // bound unusable for fixed point: every sweep of the call keeps FP64 buffers and
     // runs the per-warp adaptive kernel's work units (24-column segments), grid-stride
-    const int64_t nseg24 = (q.nx + 24) / 24, units = nseg24 * ((q.ny + S2_ROWS) / S2_ROWS);
+    const int64_t nseg24 = (q.nx + 24) / 24, units = nseg24 * ((q.ny + rows) / rows);
     for (int64_t w = gw; w < units; w += (int64_t)gridDim.x * (W2_THREADS / 32))
-      gs2_fused_warp(q, (const double *)X, (double *)Y, f, g, w % nseg24, (w / nseg24) * S2_ROWS, lane, S2_ROWS);
+      gs2_fused_warp(q, (const double *)X, (double *)Y, f, g, w % nseg24, (w / nseg24) * rows, lane, rows);
     return;
   }
   const int R = sweep_R(bnd, sweep % 4, g);
@@ -778,9 +779,9 @@ __global__ void __launch_bounds__(W2_THREADS) k_gs2_sweep(Geo q, const void *__r
   unsigned hmax = 0;
   const int64_t nseg = (q.nx + GS2_OUT) / GS2_OUT;
   const int64_t seg = gw % nseg, chunk = gw / nseg;
-  const int64_t js = chunk * S2_ROWS;  // even
+  const int64_t js = chunk * rows;  // even
   if (js <= q.ny) {
-    int64_t je = js + S2_ROWS;
+    int64_t je = js + rows;
     if (je > q.ny) je = (q.ny & 1) ? q.ny + 1 : q.ny;
     const Cols c = make_cols(q, seg * GS2_OUT - 4 + 2 * lane);
     const bool out_lane = lane >= 2 && lane <= 29;
@@ -934,7 +935,7 @@ template <int XF, int YF, bool V16>
 __global__ void __launch_bounds__(W2_THREADS) k_gs2_sweep2(Geo q, const void *__restrict__ X, void *__restrict__ Y,
                                                            const double *__restrict__ f,
                                                            const long long *__restrict__ GF, SweepBounds *bnd,
-                                                           int sweep, int sweeps, double g, bool write_bnd) {
+                                                           int sweep, int sweeps, double g, bool write_bnd, int rows) {
   __shared__ unsigned red[W2_THREADS / 32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * (W2_THREADS / 32) + wib;
@@ -947,10 +948,10 @@ __global__ void __launch_bounds__(W2_THREADS) k_gs2_sweep2(Geo q, const void *__
   if (blockIdx.x == 0 && threadIdx.x == 0) bnd->umax[(sweep + 2) % 4] = 0ull;
   const int64_t nseg = (q.nx + GS2X2_OUT) / GS2X2_OUT;
   const int64_t seg = gw % nseg, chunk = gw / nseg;
-  const int64_t js = chunk * S2_ROWS;  // even
+  const int64_t js = chunk * rows;  // even
   unsigned hmax = 0;
   if (js <= q.ny) {
-    int64_t je = js + S2_ROWS;
+    int64_t je = js + rows;
     if (je > q.ny) je = (q.ny & 1) ? q.ny + 1 : q.ny;
     const Cols c = make_cols(q, seg * GS2X2_OUT - 8 + 2 * lane);
     if (plan.fix)
@@ -979,7 +980,7 @@ __global__ void __launch_bounds__(W2_THREADS) k_jac2_sweep(Geo q, const void *__
                                                            const double *__restrict__ f,
                                                            const long long *__restrict__ GF, SweepBounds *bnd,
                                                            int sweep, int sweeps, double g, double omega,
-                                                           long long Wq, bool write_bnd) {
+                                                           long long Wq, bool write_bnd, int rows) {
   __shared__ unsigned red[W2_THREADS / 32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * (W2_THREADS / 32) + wib;
@@ -994,10 +995,10 @@ __global__ void __launch_bounds__(W2_THREADS) k_jac2_sweep(Geo q, const void *__
     a.out = (double *)Y;
     a.c1 = omega * g;
     a.c2 = -omega * 0.375 / 3.0;
-    const int64_t units = ops2_units(q, S2_ROWS);
+    const int64_t units = ops2_units(q, rows);
     for (int64_t w = gw; w < units; w += (int64_t)gridDim.x * (W2_THREADS / 32)) {
       Stream2 s;
-      ops2_warp<O2_JACOBI, V16>(a, lane, w, s, S2_ROWS);
+      ops2_warp<O2_JACOBI, V16>(a, lane, w, s, rows);
     }
     return;
   }
@@ -1010,10 +1011,10 @@ __global__ void __launch_bounds__(W2_THREADS) k_jac2_sweep(Geo q, const void *__
   const Omega om(Wq);
   const int64_t nseg = (q.nx + JAC2_OUT) / JAC2_OUT;
   const int64_t seg = gw % nseg, chunk = gw / nseg;
-  const int64_t js = chunk * S2_ROWS;
+  const int64_t js = chunk * rows;
   unsigned hmax = 0;
   if (js <= q.ny) {
-    const int64_t je = js + S2_ROWS < q.ny + 1 ? js + S2_ROWS : q.ny + 1;
+    const int64_t je = js + rows < q.ny + 1 ? js + rows : q.ny + 1;
     const Cols c = make_cols(q, seg * JAC2_OUT - 2 + 2 * lane);
     const bool out_lane = lane >= 1 && lane <= 30;
     const long long *Xl = (const long long *)X;
@@ -1147,7 +1148,7 @@ __global__ void __launch_bounds__(W2_THREADS) k_jac2_sweep2(Geo q, const void *_
                                                             const double *__restrict__ f,
                                                             const long long *__restrict__ GF, SweepBounds *bnd,
                                                             int sweep, int sweeps, double g, double omega,
-                                                            long long Wq, bool write_bnd) {
+                                                            long long Wq, bool write_bnd, int rows) {
   __shared__ unsigned red[W2_THREADS / 32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * (W2_THREADS / 32) + wib;
@@ -1162,10 +1163,10 @@ __global__ void __launch_bounds__(W2_THREADS) k_jac2_sweep2(Geo q, const void *_
   const double c1 = omega * g, c2 = -omega * 0.375 / 3.0;
   const int64_t nseg = (q.nx + JAC2_OUT) / JAC2_OUT;
   const int64_t seg = gw % nseg, chunk = gw / nseg;
-  const int64_t js = chunk * S2_ROWS;
+  const int64_t js = chunk * rows;
   unsigned hmax = 0;
   if (js <= q.ny) {
-    const int64_t je = js + S2_ROWS < q.ny + 1 ? js + S2_ROWS : q.ny + 1;
+    const int64_t je = js + rows < q.ny + 1 ? js + rows : q.ny + 1;
     const Cols c = make_cols(q, seg * JAC2_OUT - 2 + 2 * lane);
     if (plan.fix)
       jac2x2_rows<true, XF, YF, V16>(q, X, Y, GF, c, js, je, lane, cvx, dfr, om, c1, c2, R, write_bnd, hmax);
@@ -1183,10 +1184,16 @@ __global__ void __launch_bounds__(W2_THREADS) k_jac2_sweep2(Geo q, const void *_
 // Null counts as aligned (an absent array is never accessed).
 static bool aligned16(const void *p) { return ((uintptr_t)p % 16) == 0; }
 
-size_t ops2_reduce_bytes(const Geo &q) { return 16 + (size_t)ops2_blocks(q) * 2 * sizeof(double); }
+size_t ops2_reduce_bytes(const Geo &q) { return 16 + (size_t)ops2_blocks(q, W2_ROWS) * 2 * sizeof(double); }
+
+// Rows per warp from a tuned shape: even, in [16, 4096]; `fallback` when none is set.
+static int tuned_rows(int call, const Geo &q, int fallback) {
+  const int r = tuned_chunk(tuning_lookup(call, q), fallback, 16, 4096);
+  return r & ~1;
+}
 
 static cudaError_t launch_ops2(int op, const Op2Args &a, cudaStream_t s) {
-  const unsigned nb = ops2_blocks(a.q);
+  const unsigned nb = ops2_blocks(a.q, a.rows);
   // 16-byte row pairs: even pitch and 16-byte aligned u, f and output
   const bool v16 = a.q.pitch % 2 == 0 && aligned16(a.u) && aligned16(a.f) && aligned16(a.out);
   if (v16) {
@@ -1213,6 +1220,7 @@ cudaError_t launch_apply_fx2(const Geo &q, const double *u, double *y, bool elem
   a.u = u;
   a.out = y;
   a.c1 = elementwise ? 1.0 / (6.0 * q.h * q.h) : 1.0 / (3.0 * q.h * q.h);
+  a.rows = tuned_rows(elementwise ? STENCIL_CALL_APPLY_ELEMENTWISE : STENCIL_CALL_APPLY_STENCIL, q, W2_ROWS);
   return launch_ops2(elementwise ? O2_ELEMENTWISE : O2_APPLY, a, s);
 }
 
@@ -1225,6 +1233,7 @@ cudaError_t launch_jacobi_fx2(const Geo &q, const double *u, const double *f, do
   a.out = unew;
   a.c1 = omega * 0.375 * q.h * q.h;
   a.c2 = -omega * 0.375 / 3.0;
+  a.rows = W2_ROWS;
   return launch_ops2(O2_JACOBI, a, s);
 }
 
@@ -1239,6 +1248,7 @@ cudaError_t launch_residual_fx2(const Geo &q, const double *u, const double *f, 
   a.counter = (unsigned *)scratch;
   a.partials = (double *)((char *)scratch + 16);
   a.norms2 = norms2;
+  a.rows = W2_ROWS;
   return launch_ops2(O2_RESIDUAL, a, s);
 }
 
@@ -1248,16 +1258,20 @@ cudaError_t launch_residual_fx2(const Geo &q, const double *u, const double *f, 
 cudaError_t launch_gs_sweeps_fx2(const Geo &q, double *u, const double *f, int sweeps, double *work, void *bounds,
                                  cudaStream_t s) {
   const double g = 0.375 * q.h * q.h;
-  const int64_t nchunk = (q.ny + S2_ROWS) / S2_ROWS;
+  const Tuning tune = tuning_lookup(STENCIL_CALL_SMOOTH_COLOURED, q);
+  const int rows = tuned_chunk(tune, S2_ROWS, 16, 4096) & ~1;
+  const bool depth1 = tune.depth == 1;  // a tuned shape may ask for one sweep per pass
   const int64_t span = span_elems(q);
   cudaError_t e;
   if (sweeps == 1) {
+    const int64_t nchunk = (q.ny + S2_ROWS) / S2_ROWS;
     const int64_t nseg = (q.nx + 24) / 24;
     const unsigned nb = (unsigned)((nseg * nchunk + W2_THREADS / 32 - 1) / (W2_THREADS / 32));
     k_gs2_fused<<<nb, W2_THREADS, 0, s>>>(q, u, work, f, g);
     e = cudaGetLastError();
     return e ? e : cudaMemcpyAsync(u, work, (size_t)span * sizeof(double), cudaMemcpyDeviceToDevice, s);
   }
+  const int64_t nchunk = (q.ny + rows) / rows;
   const int64_t nseg = (q.nx + GS2_OUT) / GS2_OUT, nseg2 = (q.nx + GS2X2_OUT) / GS2X2_OUT;
   const unsigned nb = (unsigned)((nseg * nchunk + W2_THREADS / 32 - 1) / (W2_THREADS / 32));
   const unsigned nb2 = (unsigned)((nseg2 * nchunk + W2_THREADS / 32 - 1) / (W2_THREADS / 32));
@@ -1276,12 +1290,13 @@ cudaError_t launch_gs_sweeps_fx2(const Geo &q, double *u, const double *f, int s
   for (int it = 0; done < sweeps && !e; ++it) {
     // a two-sweep launch reads X and writes Y, so it is never both the first (X = u) and
     // the last (Y = u) launch: two sweeps in all go as two single-sweep launches
-    const bool two = sweeps - done >= 2 && sweeps != 2;
+    const bool two = !depth1 && sweeps - done >= 2 && sweeps != 2;
     const bool first = done == 0, last = done + (two ? 2 : 1) == sweeps;
     void *Y = last ? (void *)u : (it % 2 == 0 ? A : B);
     // the caller's u (last launch): its Dirichlet values were never overwritten, leave them
     const bool wb = !last;
-#define GS2_LAUNCH(KER, NB, XF_, YF_, V) KER<XF_, YF_, V><<<NB, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, wb)
+#define GS2_LAUNCH(KER, NB, XF_, YF_, V) \
+  KER<XF_, YF_, V><<<NB, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, wb, rows)
 #define GS2_PICK(KER, NB, V)                   \
   do {                                         \
     if (first)                                 \
@@ -1321,8 +1336,11 @@ namespace stencil {
 cudaError_t launch_jacobi_sweeps_fx2(const Geo &q, double *u, const double *f, int sweeps, double omega, double *A,
                                      double *scratch, void *bounds, cudaStream_t s) {
   const double g = 0.375 * q.h * q.h;
+  const Tuning tune = tuning_lookup(STENCIL_CALL_SMOOTH_JACOBI, q);
+  const int rows = tuned_chunk(tune, S2_ROWS, 16, 4096) & ~1;
+  const bool depth1 = tune.depth == 1;
   const int64_t nseg = (q.nx + JAC2_OUT) / JAC2_OUT;
-  const int64_t nchunk = (q.ny + S2_ROWS) / S2_ROWS;
+  const int64_t nchunk = (q.ny + rows) / rows;
   const unsigned nb = (unsigned)((nseg * nchunk + W2_THREADS / 32 - 1) / (W2_THREADS / 32));
   const int64_t span = span_elems(q);
   void *B = scratch;
@@ -1343,12 +1361,12 @@ cudaError_t launch_jacobi_sweeps_fx2(const Geo &q, double *u, const double *f, i
   for (int it = 0; done < sweeps && !e; ++it) {
     // a fused launch reads X and writes Y, so it is never both the first (X = u) and the
     // last (Y = u) launch: two sweeps in all go as two single-sweep launches
-    const bool two = sweeps - done >= 2 && sweeps != 2;
+    const bool two = !depth1 && sweeps - done >= 2 && sweeps != 2;
     const bool first = done == 0, last = done + (two ? 2 : 1) == sweeps;
     void *Y = last ? (void *)u : (it % 2 == 0 ? (void *)A : B);
     const bool wb = !last;  // the caller's u keeps its Dirichlet values
 #define JAC2_LAUNCH(KER, XF_, YF_, V)                                                                   \
-  KER<XF_, YF_, V><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, omega, Wq, wb)
+  KER<XF_, YF_, V><<<nb, W2_THREADS, 0, s>>>(q, X, Y, f, GF, bnd, it, sweeps, g, omega, Wq, wb, rows)
 #define JAC2_PICK(KER, V)                                   \
   do {                                                      \
     if (first)                                              \

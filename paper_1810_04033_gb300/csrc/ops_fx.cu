@@ -643,13 +643,16 @@ __global__ void __launch_bounds__(O_THREADS, ops3_min_blocks<OP>())
   if (OP == OP_RESIDUAL) ops3_reduce_norms(a, rr, ff, sh2, &last);
 }
 
-int ops_cz(const Geo &q) {
+// Planes per CTA; the stencil apply may take a tuned value (the residual may not: its
+// reduction workspace is sized from this grid).
+int ops_cz(const Geo &q, bool tuned) {
   const int64_t txy = ((q.nx + OT_X) / OT_X) * ((q.ny + OT_Y) / OT_Y);
-  return z_chunk(txy, q.nz + 1, O_CZ, 4, 3);
+  const int cz = z_chunk(txy, q.nz + 1, O_CZ, 4, 3);
+  return tuned ? tuned_chunk(tuning_lookup(STENCIL_CALL_APPLY_STENCIL, q), cz, 4, O_CZ) : cz;
 }
 
-dim3 ops_grid(const Geo &q) {
-  const int cz = ops_cz(q);
+dim3 ops_grid(const Geo &q, bool tuned) {
+  const int cz = ops_cz(q, tuned);
   return dim3((unsigned)((q.nx + OT_X) / OT_X), (unsigned)((q.ny + OT_Y) / OT_Y),
               (unsigned)((q.nz + cz) / cz));
 }
@@ -661,11 +664,11 @@ cudaError_t launch_op(const OpArgs &a, cudaStream_t s) {
     cudaError_t e = set_smem_limit_once(attr, k_ops3<OP>, O_SMEM);
     if (e != cudaSuccess) return e;
   }
-  const dim3 g = ops_grid(a.q);
+  const dim3 g = ops_grid(a.q, OP == OP_APPLY);
   if (g.y > 65535 || g.z > 65535) return cudaErrorInvalidConfiguration;
   if (a.q.plane >= ((int64_t)1 << 31) - OS_W * OS_H) return cudaErrorInvalidValue;
   OpArgs b = a;
-  b.cz = ops_cz(a.q);
+  b.cz = ops_cz(a.q, OP == OP_APPLY);
   b.v16 = a.q.pitch % 2 == 0 && ((uintptr_t)a.f % 16) == 0 &&
           (a.out_kind != 0 || ((uintptr_t)a.out % 16) == 0);
   CUtensorMap map;
@@ -685,7 +688,7 @@ cudaError_t launch_op(const OpArgs &a, cudaStream_t s) {
 }  // namespace
 
 size_t ops_fx_reduce_bytes(const Geo &q) {
-  const dim3 g = ops_grid(q);
+  const dim3 g = ops_grid(q, false);
   return (size_t)g.x * g.y * g.z * 2 * sizeof(double) + 16;
 }
 

@@ -151,3 +151,46 @@ def test_short_or_misaligned_workspace_rejected_without_gpu():
     assert L.stencil_residual(ctypes.byref(g), u, f, None, ctypes.c_void_p(4 << 20), ws, rneed - 1,
                               None) == -1
     assert "too small" in L.stencil_last_error().decode()
+
+
+def test_tuning_table_save_load_roundtrip_without_gpu(tmp_path):
+    """The launch-shape table: set, get, save as JSON, clear, load back; malformed
+    files and out-of-range shapes are refused (host-only calls)."""
+    import json
+    import torch
+    u3 = torch.zeros(9, 7, 12, dtype=torch.float64)[..., :10]  # n = (9, 6, 8), pitch 12
+    u2 = torch.zeros(33, 40, dtype=torch.float64)
+    st.stencil_tuning_clear()
+    assert st.stencil_tuning_get(u3, 0.1, st.CALL_SMOOTH_COLOURED) is None
+    st.stencil_tuning_set(u3, 0.1, st.CALL_SMOOTH_COLOURED, chunk=4)
+    st.stencil_tuning_set(u2, 0.1, st.CALL_SMOOTH_JACOBI, chunk=128, depth=1, ms=1.5)
+    st.stencil_tuning_set(u2, 0.1, st.CALL_APPLY_ELEMENTWISE, chunk=32)
+    assert st.stencil_tuning_get(u3, 0.1, st.CALL_SMOOTH_COLOURED) == (4, 0, 0.0)
+    path = str(tmp_path / "tuning.json")
+    st.stencil_tuning_save(path)
+    doc = json.load(open(path))
+    assert doc["format"] == "stencil_gb300_tuning" and len(doc["entries"]) == 3
+    e = [x for x in doc["entries"] if x["call"] == st.CALL_SMOOTH_JACOBI][0]
+    assert e["dim"] == 2 and e["n"] == [39, 32, 0] and e["pitch"] == 40 and e["depth"] == 1 and e["ms"] == 1.5
+    st.stencil_tuning_clear()
+    assert st.stencil_tuning_get(u2, 0.1, st.CALL_SMOOTH_JACOBI) is None
+    st.stencil_tuning_load(path)
+    assert st.stencil_tuning_get(u2, 0.1, st.CALL_SMOOTH_JACOBI) == (128, 1, 1.5)
+    assert st.stencil_tuning_get(u2, 0.1, st.CALL_APPLY_ELEMENTWISE) == (32, 0, 0.0)
+    st.stencil_tuning_set(u2, 0.1, st.CALL_APPLY_ELEMENTWISE, chunk=None)  # remove
+    assert st.stencil_tuning_get(u2, 0.1, st.CALL_APPLY_ELEMENTWISE) is None
+    bad = tmp_path / "bad.json"
+    bad.write_text('{"format": "stencil_gb300_tuning", "entries": [{"call": 9}]}')
+    with pytest.raises(st.StencilError):
+        st.stencil_tuning_load(str(bad))
+    bad.write_text('{"format": "something else", "entries": []}')
+    with pytest.raises(st.StencilError):
+        st.stencil_tuning_load(str(bad))
+    bad.write_text('{"format": "stencil_gb300_tuning", "entries": [')
+    with pytest.raises(st.StencilError):
+        st.stencil_tuning_load(str(bad))
+    with pytest.raises(st.StencilError):
+        st.stencil_tuning_set(u2, 0.1, st.CALL_SMOOTH_JACOBI, chunk=64, depth=3)
+    with pytest.raises(st.StencilError):
+        st.stencil_tuning_set(u2, 0.1, st.CALL_RESIDUAL, chunk=64)
+    st.stencil_tuning_clear()

@@ -37,7 +37,7 @@ def test_caller_workspace_gives_identical_bits(dim, n, pad):
         assert torch.equal(a, b), ("gs", sweeps)
         assert rel_err(to_host(b), oracle.gs_coloured(u0, f, h, sweeps)) <= TOL_F64
         a, b = to_dev(u0, pad), to_dev(u0, pad)
-        wa, wb = torch.empty_like(a), torch.empty_like(b)
+        wa, wb = to_dev(np.zeros(shape), pad), to_dev(np.zeros(shape), pad)
         st.stencil_smooth_jacobi(a, fd, wa, h, sweeps, 2.0 / 3.0)
         st.stencil_smooth_jacobi(b, fd, wb, h, sweeps, 2.0 / 3.0, ws=_ws(b, h, st.CALL_SMOOTH_JACOBI, sweeps))
         torch.cuda.synchronize()
