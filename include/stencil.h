@@ -491,9 +491,9 @@ int stencil_release_workspace(void);
  * Sections 5-6 discuss tile sizes and the fusion of colours as the levers of a
  * coloured sweep).  Tuned shapes apply to F64 Q1 calls of the same call kind, grid
  * shape (n, pitch) and device name, process-wide.  The smoothers give identical bits
- * under every shape; the single-pass applies keep a per-CTA (3D) or per-warp (2D)
- * fixed-point scale, so their results can differ between shapes by rounding only
- * (within the FP64 tolerance).
+ * under every chunk; the 2D depth (one fixed-point scale for the two sweeps of a pass)
+ * and, in the single-pass applies, the per-CTA (3D) or per-warp (2D) fixed-point scale
+ * make results differ between shapes by rounding only (within the FP64 tolerance).
  */
 typedef struct stencil_tuning {
   int32_t chunk; /* 3D: z-planes per CTA; 2D: rows per warp (even); 0 = built-in rule */

@@ -78,9 +78,10 @@ inline int z_chunk(int64_t tiles_xy, int64_t units, int cz_max, int cz_min, int 
 // the call, the grid's shape and pitch and the device's name.  chunk: 3D planes per CTA
 // (or per warp) of the plane-streaming kernels, 2D rows per warp; depth: sweeps per
 // pass over memory of the 2D multi-sweep smoothers (1 or 2).  0 = the built-in rule.
-// Only F64 Q1 calls are tuned; the kernels' results do not depend on these shapes
-// (exact fixed-point sums), except that the single-pass applies keep a per-CTA or
-// per-warp scale, whose rounding can move by a unit in the last place.
+// Only F64 Q1 calls are tuned.  The smoothers' results do not depend on the chunk
+// (exact fixed-point sums at a grid-wide scale per sweep); the 2D depth changes the
+// scale (one for both sweeps of a pass) and the single-pass applies keep a per-CTA or
+// per-warp scale, so those can move the rounding by units in the last place.
 struct Tuning {
   int chunk = 0;
   int depth = 0;

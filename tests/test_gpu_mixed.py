@@ -32,6 +32,24 @@ def _bits_to_f64(b):
     return torch.from_numpy(b.view(np.int16)).view(torch.bfloat16).to(torch.float64).numpy()
 
 
+def _bf16_iterate_bound(hist, k, sweeps=8):
+    """Bound on |x_k(GPU) - x_k(oracle)|_inf / |x_k|_inf for bf16-storage refinement.
+
+    Both sides run the same algorithm; their FP32 arithmetic differs in rounding order
+    (FMA contraction), so a bf16 store can round to the other neighbour: one bf16 unit,
+    at most 2^-7 of the stored value.  A GS update is a convex combination of its
+    neighbours (3D weights (2 E + C)/32 sum to 1), so a difference does not grow in the
+    max norm through later updates; each of the `sweeps` inner sweeps, and the bf16
+    rounding of the residual, adds at most one unit.  Correction i thus differs by at
+    most (sweeps + 1) 2^-7 |e_i|_inf, and x_k = e_1 + ... + e_k."""
+    prev = np.zeros_like(hist[0])
+    total = 0.0
+    for i in range(k):
+        total += float(np.max(np.abs(hist[i] - prev)))
+        prev = hist[i]
+    return (sweeps + 1) * 2.0 ** -7 * total / float(np.max(np.abs(hist[k - 1])))
+
+
 @pytest.mark.parametrize("n", [(8, 8, 8), (33, 9, 7), (64, 40, 20), (3, 70, 35)])
 def test_fp32_gs_matches_fp32_oracle(n):
     h = 1.0 / max(n)
@@ -62,10 +80,11 @@ def test_bf16_gs_matches_bf16_oracle(n):
         assert rel_err(ud.double().cpu().numpy(), ref) <= TOL_BF16, sweeps
 
 
-@pytest.mark.parametrize("prec,tol", [(st.F64, TOL_F64), (st.F32, 1e-5), (st.BF16, 5e-2)])
+@pytest.mark.parametrize("prec,tol", [(st.F64, TOL_F64), (st.F32, 1e-5), (st.BF16, None)])
 def test_refinement_iterates_match_oracle(prec, tol):
     """Iterate k of the GPU refinement against iterate k of the oracle (same algorithm
-    in the same precisions), k = 1..4; error relative to the iterate's max norm."""
+    in the same precisions), k = 1..4; error relative to the iterate's max norm (bf16:
+    the bound of _bf16_iterate_bound)."""
     n = 24
     h = 1.0 / n
     f = synth.sin_rhs(3, n, (2, 3, 1))
@@ -75,7 +94,8 @@ def test_refinement_iterates_match_oracle(prec, tol):
         ud = torch.zeros(f.shape, dtype=torch.float64, device="cuda")
         res = st.stencil_solve(ud, to_dev(f), h, rel_tol=0.0, max_outer=it, inner_sweeps=8, inner_dtype=prec)
         assert res["iterations"] == it
-        assert rel_err(to_host(ud), hist[it - 1]) <= tol, it
+        bound = tol if tol is not None else _bf16_iterate_bound(hist, it)
+        assert rel_err(to_host(ud), hist[it - 1]) <= bound, it
 
 
 @pytest.mark.parametrize("prec", [st.F64, st.F32, st.BF16])
@@ -184,4 +204,4 @@ def test_refinement_iterates_match_oracle_padded_bf16():
         assert ud.stride(1) % 8 == 0
         res = st.stencil_solve(ud, fd, h, rel_tol=0.0, max_outer=it, inner_sweeps=8, inner_dtype=st.BF16)
         assert res["iterations"] == it
-        assert rel_err(to_host(ud), hist[it - 1]) <= 5e-2, it
+        assert rel_err(to_host(ud), hist[it - 1]) <= _bf16_iterate_bound(hist, it), it

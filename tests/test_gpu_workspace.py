@@ -44,7 +44,7 @@ def test_caller_workspace_gives_identical_bits(dim, n, pad):
         assert torch.equal(a, b), ("jacobi", sweeps)
         assert rel_err(to_host(b), oracle.jacobi(u0, f, h, 2.0 / 3.0, sweeps)) <= TOL_F64
     ud = to_dev(u0, pad)
-    ra, rb = torch.full_like(ud, float("nan")), torch.full_like(ud, float("nan"))
+    ra, rb = to_dev(np.full(shape, np.nan), pad), to_dev(np.full(shape, np.nan), pad)
     na = st.stencil_residual(ud, fd, h, r=ra)
     ws = _ws(ud, h, st.CALL_RESIDUAL, 0)
     ws.fill_(0xA5)  # the call clears its counter itself
