@@ -112,7 +112,7 @@ def parse_args():
                          "sweeps; patches: 4096 uneven patches x 20 sweeps; refine: refinement to 1e-10 "
                          "at 256^3 (FP32 / bf16 inner) vs FP64 inner; serve: request server; fd: the "
                          "grid op mix with the 5/7-point finite-difference operator (red-black GS)")
-    ap.add_argument("--requests", type=int, default=400, help="serve: requests per arrival rate")
+    ap.add_argument("--requests", type=int, default=10000, help="serve: requests per arrival rate")
     ap.add_argument("--rates", default="200,1000,5000", help="serve: arrival rates (req/s)")
     ap.add_argument("--solver", default="mg", choices=["mg", "refine"],
                     help="serve: SOLVE requests by multigrid V-cycles (mg) or by refinement with FP32 GS")
@@ -409,7 +409,7 @@ def run_e2e(torch, st, wl, stream, args, world):
     and overlap the other grid's compute: a grid's inputs go up while the other grid
     computes, and its results come down while the other grid computes (events order
     each grid's copy-in, compute and copy-out)."""
-    steps = max(1, min(args.steps, 3))
+    steps = args.steps
     h_out = {g: torch.empty_like(wl.host["u" + g]).pin_memory() for g in wl.grids}
     h_nrm = torch.empty(4, dtype=torch.float64).pin_memory()
     bi = sum(wl.host[k + g].numel() * 8 for k in ("u", "f") for g in wl.grids)
@@ -527,6 +527,38 @@ def _events(torch):
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
+def _hbm_peak():
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    if "hbm_gbs" in peaks:
+        return peaks["hbm_gbs"], "measured (MEASURED_PEAKS.json hbm_gbs)"
+    return 6800.0, "fallback 6800 GB/s"
+
+
+def _roofline(bytes_moved, ms, kernel, note=None):
+    """HBM roofline of a workload line: algorithmic bytes over the measured time."""
+    peak, src = _hbm_peak()
+    gbs = bytes_moved / (ms * 1e-3) / 1e9
+    r = {"bound": "hbm", "kernel": kernel, "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+         "frac": round(gbs / peak, 4), "peak_source": src, "traffic": None}
+    if note:
+        r["note"] = note
+    return r
+
+
+def _oracle_rate(fn, updates_per_call, budget_s=10.0):
+    """Calls fn (one oracle pass of `updates_per_call` updates) until about budget_s
+    seconds have passed; returns (Mupdates/s, calls, seconds)."""
+    t0 = time.perf_counter()
+    calls = 0
+    while True:
+        fn()
+        calls += 1
+        sec = time.perf_counter() - t0
+        if sec >= budget_s:
+            return updates_per_call * calls / sec / 1e6, calls, sec
+
+
 def run_small(args):
     """32^3 cells: one element-wise apply on u ~ U[-1,1] (seed 0), then 10 coloured GS
     sweeps on A u = f, f = 3 pi^2 sin sin sin, u0 = 0."""
@@ -555,17 +587,36 @@ def run_small(args):
         step()
     graph.replay()
     torch.cuda.synchronize()
+    steps = max(args.steps, 2000)  # a step is ~25 us: enough steps for the clock record
+    clocks = ClockSampler(0)
+    clocks.start()
     e0, e1 = _events(torch)
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         graph.replay()
     e1.record()
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    clock_info = clocks.stop()
+    ms = e0.elapsed_time(e1) / steps
     upd = 11 * (n - 1) ** 3
+    # oracle on the host cores: the same step (apply + 10 sweeps from u0 = 0)
+    import oracle
+    nt = os.cpu_count() or 1
+    un, fn_ = synth.uniform_field(s3, 0), synth.sin_rhs(3, n)
+
+    def ostep():
+        oracle.apply_elementwise(un, h, nthreads=nt)
+        oracle.gs_coloured(np.zeros_like(fn_), fn_, h, 10, nthreads=nt)
+
+    rate, calls, sec = _oracle_rate(ostep, upd, budget_s=5.0)
     return {"metric": "Mupdates/s (32^3 Q1: 1 element-wise apply + 10 coloured GS sweeps)", "workload": "small",
             "value": round(upd / ms / 1e3, 1), "unit": "Mupdates/s", "ms_per_step": round(ms, 4),
-            "steps": args.steps, "dtype": "f64",
+            "steps": steps, "dtype": "f64", "clocks": clock_info,
+            "roofline": _roofline((16 + 10 * 24) * (n - 1) ** 3, ms, "apply + 10 GS sweeps, 33^3",
+                                  "launch-bound size: 0.27 MB per array, L2-resident; the fraction is of "
+                                  "algorithmic bytes only"),
+            "cpu_baseline": {"value": round(rate, 1), "unit": "Mupdates/s", "cores": nt, "kind": "oracle",
+                             "sample": "the whole step (apply + 10 GS sweeps at 32^3), %d times, %.1f s" % (calls, sec)},
             "note": "launch-bound size (30K interior vertices); one CUDA graph replay per step"}
 
 
@@ -592,17 +643,22 @@ def run_patches(args):
     for _ in range(args.warmup):
         b.smooth(u, f, 20)
     torch.cuda.synchronize()
+    steps = max(args.steps, 100)
+    clocks = ClockSampler(0)
+    clocks.start()
     e0, e1 = _events(torch)
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         b.smooth(u, f, 20)
     e1.record()
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    clock_info = clocks.stop()
+    ms = e0.elapsed_time(e1) / steps
     upd = 20 * L.interior_updates_per_sweep
     return {"metric": "Mupdates/s (4096 uneven patches, 20 GS sweeps with halo fill)", "workload": "patches",
-            "value": round(upd / ms / 1e3, 1), "unit": "Mupdates/s", "ms_per_step": round(ms, 3),
-            "algorithmic_gbs": round(24 * upd / ms / 1e6, 1), "hbm_frac": round(24 * upd / ms / 1e6 / 6683.2, 4),
+            "value": round(upd / ms / 1e3, 1), "unit": "Mupdates/s", "ms_per_step": round(ms, 3), "steps": steps,
+            "clocks": clock_info,
+            "roofline": _roofline(24 * upd, ms, "k_patch_gs + k_patch_halo (24 B per update and sweep)"),
             "autotuned_launch": {"threads": tuned[0], "ctas_per_sm": tuned[1]}, "dtype": "f64",
             "patches": int(L.np_sizes.size), "vertices": L.total, "cpu_baseline": patches_cpu_baseline()}
 
@@ -655,12 +711,15 @@ def run_fd(args):
     ev = [{(op, g): (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for op in ops for g in wl.grids} for _ in range(steps)]
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(0)
+    clocks.start()
     with torch.cuda.stream(stream):
         t0.record(stream)
         for k in range(steps):
             wl.step(stream, ev[k], ops=ops)
         t1.record(stream)
     stream.synchronize()
+    clock_info = clocks.stop()
     ms = t0.elapsed_time(t1)
     upd = sum(PASSES[op] * (interior(3, n3) + interior(2, n2)) for op in ops) * steps
     per = {}
@@ -704,7 +763,7 @@ def run_fd(args):
                       "50 Jacobi sweeps, 1 residual per grid)", "workload": "fd", "redblack_and_expensive": cmp,
             "value": round(upd / (ms * 1e-3) / 1e6, 1), "unit": "Mupdates/s", "steps": steps,
             "ms_per_step": round(ms / steps, 3), "grid_3d": n3, "grid_2d": n2, "dtype": "f64",
-            "per_op": per}
+            "clocks": clock_info, "per_op": per}
 
 
 def run_refine(args):
@@ -734,6 +793,8 @@ def run_refine(args):
 
     fd = padded(f)
     out = {}
+    clocks = ClockSampler(0)
+    clocks.start()
     for name, prec in (("fp64", st.F64), ("fp32", st.F32), ("bf16", st.BF16)):
         ud = padded(np.zeros_like(f))
         torch.cuda.synchronize()
@@ -757,12 +818,48 @@ def run_refine(args):
     err = float(np.max(np.abs(ud.cpu().numpy() - uh)) / np.max(np.abs(uh)))
     out["mg"] = {"seconds": round(sec, 4), "cycles": res["cycles"], "levels": res["levels"],
                  "relres": res["relres"], "converged": res["converged"], "rel_err_vs_closed_form": err}
+    clock_info = clocks.stop()
+    # error per iterate: the GPU's iterates 1..K of each inner precision against the FP64
+    # oracle's iterates (plain FP64 inner sweeps, same loop) and against the oracle of the
+    # same precision; K bounded by the oracle's host time (one correction of 8 sweeps
+    # at 256^3 is ~1.4e8 updates)
+    import oracle
+    K = 3
+    t = time.perf_counter()
+    ref = {}
+    for name, po in (("fp64", 0), ("fp32", 1), ("bf16", 2)):
+        _, _, _, _, hist = oracle.ir_solve(np.zeros_like(f), f, h, 0.0, K, 8, po, keep_history=True)
+        ref[name] = hist
+    osec = time.perf_counter() - t
+    per_iter = {}
+    for name, prec in (("fp64", st.F64), ("fp32", st.F32), ("bf16", st.BF16)):
+        rows = []
+        for k in range(1, K + 1):
+            ud = padded(np.zeros_like(f))
+            st.stencil_solve(ud, fd, h, rel_tol=0.0, max_outer=k, inner_sweeps=8, inner_dtype=prec, history=False)
+            x = ud.cpu().numpy()
+            nrm = float(np.max(np.abs(ref["fp64"][k - 1])))
+            rows.append({"iterate": k,
+                         "rel_err_vs_fp64_oracle": float(np.max(np.abs(x - ref["fp64"][k - 1])) / nrm),
+                         "rel_err_vs_same_precision_oracle":
+                             float(np.max(np.abs(x - ref[name][k - 1])) / float(np.max(np.abs(ref[name][k - 1]))))})
+        per_iter[name] = rows
+    # cpu baseline: the oracle's FP64-inner refinement, per correction (K corrections,
+    # timed above together with the other precisions: a third of the time each)
+    upd_corr = 8 * (n - 1) ** 3 + (n - 1) ** 3
+    orate = upd_corr * K / (osec / 3) / 1e6
     return {"metric": "time to relative residual 1e-10, 256^3 (speedup of mixed precision over FP64)",
             "workload": "refine", "value": round(out["fp64"]["seconds"] / out["fp32"]["seconds"], 3),
             "mg_speedup_over_fp64_refinement": round(out["fp64"]["seconds"] / out["mg"]["seconds"], 1),
             "unit": "x (FP64 time / FP32-inner time)", "bf16_speedup": round(out["fp64"]["seconds"] /
                                                                              out["bf16"]["seconds"], 3),
-            "pitch": pitch, "runs": out}
+            "pitch": pitch, "runs": out, "clocks": clock_info, "per_iterate_error": per_iter,
+            "cpu_baseline": {"value": round(orate, 2), "unit": "Mupdates/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d refinement corrections (8 GS sweeps + a residual each) at 256^3 in each "
+                                       "of FP64, FP32, bf16 inner precision, %.1f s in all; rate of one precision"
+                                       % (K, osec),
+                             "fp64_refinement_to_1e-10_s_extrapolated":
+                                 round(out["fp64"]["corrections"] * osec / 3 / K, 1)}}
 
 
 def run_serve(args):
@@ -778,6 +875,8 @@ def run_serve(args):
         solver = st.SOLVER_MG if args.solver == "mg" else st.SOLVER_REFINE
         srv = st.Server(64 << 30, streams=8, max_inflight=64, inner_dtype=st.F32, solver=solver)
         torch.cuda.synchronize()
+        clocks = ClockSampler(0)
+        clocks.start()
         t0 = time.perf_counter()
         tickets = []
         for r in reqs:
@@ -797,9 +896,11 @@ def run_serve(args):
                 upd += 8 * res["iterations"] * (r["edge"] - 1) ** 3
             srv.release(t)
         wall = time.perf_counter() - t0
+        clock_info = clocks.stop()
         srv.close()
         lat = np.array(lat)
-        lines.append({"rate_req_s": rate, "requests": len(reqs), "p50_s": round(float(np.percentile(lat, 50)), 4),
+        lines.append({"rate_req_s": rate, "requests": len(reqs), "clocks": clock_info,
+                      "p50_s": round(float(np.percentile(lat, 50)), 4),
                       "p99_s": round(float(np.percentile(lat, 99)), 4), "wall_s": round(wall, 2),
                       "requests_per_s": round(len(reqs) / wall, 1),
                       "aggregate_mupdates_s": round(upd / wall / 1e6, 1)})
