@@ -104,6 +104,8 @@ def parse_args():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="grid workload: keep the built-in launch shapes instead of autotuning them first")
     ap.add_argument("--n3", type=int, default=N3, help="3D cells per edge (0: no 3D grid)")
     ap.add_argument("--n2", type=int, default=N2, help="2D cells per edge (0: no 2D grid)")
     ap.add_argument("--workload", default="grid",
@@ -210,6 +212,22 @@ class GpuWorkload:
         buf = self.torch.zeros((t.shape[0], t.shape[1], self.p3), dtype=t.dtype)
         buf[..., :t.shape[2]] = t
         return buf
+
+    def autotune(self):
+        """Tunes the launch shape of every tunable call on each grid (stencil_autotune:
+        candidates timed on scratch arrays of the same shape), before any timing; the
+        calls then use the recorded shapes.  Returns {grid: {call: [chunk, depth]}}."""
+        st = self.st
+        calls = (("apply_elementwise", st.CALL_APPLY_ELEMENTWISE, 0), ("apply_stencil", st.CALL_APPLY_STENCIL, 0),
+                 ("gs_sweep", st.CALL_SMOOTH_COLOURED, N_SWEEPS), ("jacobi_sweep", st.CALL_SMOOTH_JACOBI, N_SWEEPS))
+        out = {}
+        for g in self.grids:
+            u = self.view("u" + g)
+            out[g] = {}
+            for name, call, sweeps in calls:
+                chunk, depth, _ = st.stencil_autotune(u, self.h[g], call, sweeps)
+                out[g][name] = [chunk, depth]
+        return out
 
     def view(self, key):
         t = self.d[key]
@@ -322,6 +340,7 @@ def run_gpu(args, rank, world):
     n3, n2 = args.n3, args.n2
     wl = GpuWorkload(torch, st, dev, n3, n2)
     stream = torch.cuda.Stream(device=dev)
+    tuned = None if args.no_autotune else wl.autotune()
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
@@ -395,7 +414,8 @@ def run_gpu(args, rank, world):
                       "pitch_3d": wl.p3 or None,
                       "l2": "inputs larger than L2 (no flush)" if n3 >= 256 or n2 >= 8192
                             else "small case (profiling)",
-                      "parallelism": "replicas" if world > 1 else "single GPU"},
+                      "parallelism": "replicas" if world > 1 else "single GPU",
+                      "launch_shapes": {"autotuned": tuned} if tuned else "built-in"},
            "roofline": roofline, "clocks": clock_info,
            "gpu_launches": launches_per_step(n3, n2) * args.steps,
            "e2e": e2e}
@@ -877,24 +897,40 @@ def run_serve(args):
         torch.cuda.synchronize()
         clocks = ClockSampler(0)
         clocks.start()
+        # a client that takes each result as it completes: a collector thread waits on
+        # the tickets in submission order and releases each result (its resident grid
+        # counts against the HBM budget until then); ctypes calls drop the GIL
+        import queue
+        inbox = queue.Queue()
+        lat, upd = [], [0]
+
+        def collect():
+            while True:
+                item = inbox.get()
+                if item is None:
+                    return
+                t, r = item
+                res = srv.wait(t)
+                lat.append(res["t_done"] - res["t_submit"])
+                if r["kind"] == "smooth":
+                    upd[0] += 20 * (r["edge"] - 1) ** 3
+                elif args.solver == "mg":
+                    upd[0] += res["iterations"] * mg_cycle_updates(r["edge"])
+                else:
+                    upd[0] += 8 * res["iterations"] * (r["edge"] - 1) ** 3
+                srv.release(t)
+
+        collector = threading.Thread(target=collect, daemon=True)
+        collector.start()
         t0 = time.perf_counter()
-        tickets = []
         for r in reqs:
             while time.perf_counter() - t0 < r["t"]:
                 time.sleep(0.0002)
             kind = st.REQ_SOLVE if r["kind"] == "solve" else st.REQ_SMOOTH
-            tickets.append((srv.submit(kind, r["edge"], sweeps=20, rel_tol=1e-8, f_seed=r["seed"]), r))
-        lat, upd = [], 0
-        for t, r in tickets:
-            res = srv.wait(t)
-            lat.append(res["t_done"] - res["t_submit"])
-            if r["kind"] == "smooth":
-                upd += 20 * (r["edge"] - 1) ** 3
-            elif args.solver == "mg":
-                upd += res["iterations"] * mg_cycle_updates(r["edge"])
-            else:
-                upd += 8 * res["iterations"] * (r["edge"] - 1) ** 3
-            srv.release(t)
+            inbox.put((srv.submit(kind, r["edge"], sweeps=20, rel_tol=1e-8, f_seed=r["seed"]), r))
+        inbox.put(None)
+        collector.join()
+        upd = upd[0]
         wall = time.perf_counter() - t0
         clock_info = clocks.stop()
         srv.close()

@@ -98,6 +98,9 @@ struct stencil_server {
   std::condition_variable cv_done, cv_work;
   std::deque<uint64_t> pending;
   std::map<uint64_t, Req *> reqs;
+  // admitted requests not yet finished: the engine polls only these, so results that
+  // stay resident until released cost it nothing
+  std::vector<Req *> running;
   uint64_t next_ticket = 1;
   int inflight = 0;
   int next_stream = 0;
@@ -191,15 +194,21 @@ cudaError_t issue_correction(stencil_server *s, Req *q) {
 }
 
 // Allocate and initialise an admitted request; queue its first step.
-cudaError_t admit(stencil_server *s, Req *q) {
+// Called with the server's mutex held: the request's stream and pinned norms slot.
+void assign_slots(stencil_server *s, Req *q) {
   q->stream = s->next_stream;
   s->next_stream = (s->next_stream + 1) % (int)s->streams.size();
-  cudaStream_t st = s->streams[q->stream];
-  const size_t span = (size_t)span_elems(q->q);
-  cudaError_t e = cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming);
   q->hslot = s->hfree.back();
   s->hfree.pop_back();
   q->hnorms = s->hpool + 8 * q->hslot;
+}
+
+// Called without the mutex: only the engine thread touches a running request's
+// buffers, and the allocator and streams are thread-safe.
+cudaError_t admit(stencil_server *s, Req *q) {
+  cudaStream_t st = s->streams[q->stream];
+  const size_t span = (size_t)span_elems(q->q);
+  cudaError_t e = cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming);
   if (!e) e = dalloc(s, (void **)&q->u, span * 8, st);
   if (!e) e = dalloc(s, (void **)&q->f, span * 8, st);
   if (!e) e = dalloc(s, (void **)&q->norms, 64, st);
@@ -275,12 +284,19 @@ void finish(stencil_server *s, Req *q, int status) {
   s->stats.completed++;
 }
 
+// The engine thread.  The mutex guards the queues, the budget, the counters and the
+// phase of every request; it is held for that bookkeeping only, never across kernel
+// launches, allocations or event queries, so submissions, polls and releases from
+// client threads are not held up by the device work being issued.
 void engine_loop(stencil_server *s) {
   cudaSetDevice(s->device);
+  std::vector<Req *> admitted, run, done;
+  std::vector<int> done_status;
   std::unique_lock<std::mutex> lk(s->mu);
   while (!s->stop) {
     bool progress = false;
     // admission (FIFO, looking past a blocked head at the next few requests)
+    admitted.clear();
     int looked = 0;
     for (auto it = s->pending.begin(); it != s->pending.end() && looked < 16;) {
       Req *q = s->reqs[*it];
@@ -290,53 +306,74 @@ void engine_loop(stencil_server *s) {
         ++s->inflight;
         q->phase = P_RUNNING;
         q->t_admit = now_s(s->t0);
-        cudaError_t e = admit(s, q);
-        if (e) {
-          s->engine_error = cudaGetErrorString(e);
-          finish(s, q, STENCIL_ECUDA);
-          s->cv_done.notify_all();
-        }
+        assign_slots(s, q);
+        admitted.push_back(q);
         it = s->pending.erase(it);
-        progress = true;
       } else {
         ++it;
       }
     }
-    // advance running requests whose last step has completed
-    for (auto &kv : s->reqs) {
-      Req *q = kv.second;
-      if (q->phase != P_RUNNING || !q->step_in_flight) continue;
+    run = s->running;
+    lk.unlock();
+    // device work, without the mutex
+    done.clear();
+    done_status.clear();
+    for (Req *q : admitted) {
+      progress = true;
+      cudaError_t e = admit(s, q);
+      if (e) {
+        std::lock_guard<std::mutex> g(s->mu);
+        s->engine_error = cudaGetErrorString(e);
+        done.push_back(q);
+        done_status.push_back(STENCIL_ECUDA);
+      } else {
+        run.push_back(q);
+      }
+    }
+    for (Req *q : run) {
+      if (!q->step_in_flight) continue;
       const cudaError_t qe = cudaEventQuery(q->ev);
       if (qe == cudaErrorNotReady) continue;
       progress = true;
       q->step_in_flight = false;
+      int status = 1;  // 1: keep running
       if (qe != cudaSuccess) {
+        std::lock_guard<std::mutex> g(s->mu);
         s->engine_error = cudaGetErrorString(qe);
-        finish(s, q, STENCIL_ECUDA);
-        s->cv_done.notify_all();
-        continue;
-      }
-      if (q->r.kind == STENCIL_REQ_SMOOTH) {
+        status = STENCIL_ECUDA;
+      } else if (q->r.kind == STENCIL_REQ_SMOOTH) {
         q->iterations = q->r.sweeps;
-        finish(s, q, STENCIL_OK);
-        s->cv_done.notify_all();
-        continue;
+        status = STENCIL_OK;
+      } else {
+        const double rr = q->hnorms[0], ff = q->hnorms[1];
+        q->relres = ff > 0.0 ? std::sqrt(rr) / std::sqrt(ff) : std::sqrt(rr);
+        if (q->relres <= q->r.rel_tol || q->iterations >= s->o.max_outer) {
+          status = q->relres <= q->r.rel_tol ? STENCIL_OK : STENCIL_ENOTCONV;
+        } else {
+          cudaError_t e = issue_correction(s, q);
+          ++q->iterations;
+          if (!e) e = issue_residual(s, q);
+          if (e) {
+            std::lock_guard<std::mutex> g(s->mu);
+            s->engine_error = cudaGetErrorString(e);
+            status = STENCIL_ECUDA;
+          }
+        }
       }
-      const double rr = q->hnorms[0], ff = q->hnorms[1];
-      q->relres = ff > 0.0 ? std::sqrt(rr) / std::sqrt(ff) : std::sqrt(rr);
-      if (q->relres <= q->r.rel_tol || q->iterations >= s->o.max_outer) {
-        finish(s, q, q->relres <= q->r.rel_tol ? STENCIL_OK : STENCIL_ENOTCONV);
-        s->cv_done.notify_all();
-        continue;
+      if (status != 1) {
+        done.push_back(q);
+        done_status.push_back(status);
       }
-      cudaError_t e = issue_correction(s, q);
-      ++q->iterations;
-      if (!e) e = issue_residual(s, q);
-      if (e) {
-        s->engine_error = cudaGetErrorString(e);
-        finish(s, q, STENCIL_ECUDA);
-        s->cv_done.notify_all();
-      }
+    }
+    lk.lock();
+    for (Req *q : admitted)
+      if (q->phase == P_RUNNING) s->running.push_back(q);
+    for (size_t i = 0; i < done.size(); ++i) finish(s, done[i], done_status[i]);
+    if (!done.empty()) {
+      s->running.erase(std::remove_if(s->running.begin(), s->running.end(),
+                                      [](const Req *q) { return q->phase != P_RUNNING; }),
+                       s->running.end());
+      s->cv_done.notify_all();
     }
     if (!progress) {
       // nothing to do right now: wait for a submission, or poll the GPU again shortly

@@ -265,19 +265,22 @@ def test_out_of_place_ops_extreme_and_mixed_magnitudes(scale):
 
 
 def test_full_size_sampled_apply_and_gs():
-    """512^3 cells in the launch configuration the benchmark times: apply and one GS
-    sweep compared with the oracle on sampled vertices (the oracle evaluates the
-    3x3x3 neighbourhood of each sample)."""
+    """512^3 cells at the benchmark's pitch (520: the TMA-staged kernels): the stencil
+    apply compared with the oracle on sampled vertices (the oracle evaluates the 3x3x3
+    neighbourhood of each sample), then one GS sweep compared everywhere.  The
+    benchmark's own calls (both applies, 6- and 50-sweep smoothers, residual) are
+    compared everywhere in test_gpu_bench_layout.py."""
     n = 512
     h = 1.0 / n
     shape = synth.grid_shape(3, n)
     u = synth.uniform_field(shape, 1)
     f = synth.sin_rhs(3, n)
-    ud, fd = to_dev(u), to_dev(f)
-    yd = torch.empty_like(ud)
+    ud, fd = to_dev(u, 7), to_dev(f, 7)
+    assert ud.stride(1) == 520
+    yd = to_dev(np.zeros(shape), 7)
     st.stencil_apply(ud, yd, h, st.FORM_STENCIL)
     torch.cuda.synchronize()
-    y = yd.cpu().numpy()
+    y = to_host(yd)
     g = synth.rng(5)
     pts = g.integers(1, n, size=(400, 3))
     pts = np.vstack([pts, [[1, 1, 1], [n - 1, n - 1, n - 1], [1, n - 1, 1], [256, 256, 256]]])
@@ -291,7 +294,7 @@ def test_full_size_sampled_apply_and_gs():
     st.stencil_smooth_coloured(ud, fd, h, 1)
     ref = oracle.gs_coloured(u, f, h, 1, nthreads=os.cpu_count() or 1)
     torch.cuda.synchronize()
-    assert rel_err(ud.cpu().numpy(), ref) <= TOL_F64
+    assert rel_err(to_host(ud), ref) <= TOL_F64
 
 
 @pytest.mark.parametrize("n", [(200, 150), (61, 300), (29, 29), (31, 130), (45, 601), (70, 514)])
