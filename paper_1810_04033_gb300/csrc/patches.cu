@@ -86,38 +86,58 @@ __device__ __forceinline__ int halo_index(int idx, int d, int n, int m) {
   return t < 1 ? 1 : (t > m - 1 ? m - 1 : t);
 }
 
+// One CTA per patch (grid-stride).  The 26 neighbour entries (id, edge, offset) are
+// read into shared memory once; then the block's threads run over the whole shell as one
+// index space (the two z faces, the two y faces without their z edges, the two x faces
+// without their y and z edges), each vertex finding its outward direction from its
+// indices, so that every thread has work whatever the direction.
 __global__ void k_patch_halo(const PatchDev *pd, const int *nbr, int npatch, double *u,
                              unsigned long long *hmax) {
   __shared__ unsigned long long red[32];
+  __shared__ int s_m[27];
+  __shared__ long long s_off[27];
   for (int p = blockIdx.x; p < npatch; p += gridDim.x) {
-    const int n = pd[p].n, W = n + 1;
+    const int n = pd[p].n, W = n + 1, P = W * W;
     const int64_t off = pd[p].off;
-    unsigned long long mh = 0;
-    // the shell vertices by outward direction (dx, dy, dz): per axis index 0 (d = -1),
-    // n (d = +1) or 1 .. n-1 (d = 0), a rectangle per direction; one neighbour lookup
-    // per direction, the block's threads over its vertices (x fastest)
-    for (int dir = 0; dir < 27; ++dir) {
-      if (dir == 13) continue;  // (0, 0, 0): the interior
-      const int dx = dir % 3 - 1, dy = (dir / 3) % 3 - 1, dz = dir / 9 - 1;
-      const int q = nbr[27 * p + dir];
-      const int m = q >= 0 ? pd[q].n : 0, M = m + 1;
-      const int64_t qoff = q >= 0 ? pd[q].off : 0;
-      const int lx = dx ? 1 : n - 1, ly = dy ? 1 : n - 1, lz = dz ? 1 : n - 1;
-      const int bx = dx < 0 ? 0 : (dx > 0 ? n : 1), by = dy < 0 ? 0 : (dy > 0 ? n : 1),
-                bz = dz < 0 ? 0 : (dz > 0 ? n : 1);
-      const int count = lx * ly * lz;
-      for (int t = threadIdx.x; t < count; t += blockDim.x) {
-        const int i = bx + t % lx, j = by + (t / lx) % ly, k = bz + t / (lx * ly);
-        double v = 0.0;
-        if (q >= 0) {
-          const int iq = halo_index(i, dx, n, m), jq = halo_index(j, dy, n, m), kq = halo_index(k, dz, n, m);
-          v = u[qoff + ((int64_t)kq * M + jq) * M + iq];
-        }
-        u[off + ((int64_t)k * W + j) * W + i] = v;
-        mh = umax64(mh, fx::abs_bits(v));
-      }
+    if (threadIdx.x < 27) {
+      const int q = threadIdx.x == 13 ? -1 : nbr[27 * p + threadIdx.x];
+      s_m[threadIdx.x] = q >= 0 ? pd[q].n : -1;
+      s_off[threadIdx.x] = q >= 0 ? pd[q].off : 0;
     }
-    mh = block_max_u64(mh, red);
+    __syncthreads();
+    unsigned long long mh = 0;
+    const int nA = 2 * P, nB = 2 * W * (n - 1), nC = 2 * (n - 1) * (n - 1);
+    for (int t = threadIdx.x; t < nA + nB + nC; t += blockDim.x) {
+      int i, j, k;
+      if (t < nA) {  // z = 0 and z = n, whole planes
+        k = t < P ? 0 : n;
+        const int r = t < P ? t : t - P;
+        j = r / W;
+        i = r - j * W;
+      } else if (t < nA + nB) {  // y = 0 and y = n, z = 1 .. n-1
+        const int r = t - nA, zz = r / (2 * W), rr = r - zz * 2 * W;
+        k = 1 + zz;
+        j = rr < W ? 0 : n;
+        i = rr < W ? rr : rr - W;
+      } else {  // x = 0 and x = n, y and z = 1 .. n-1
+        const int r = t - nA - nB, zz = r / (2 * (n - 1)), rr = r - zz * 2 * (n - 1);
+        k = 1 + zz;
+        j = 1 + (rr >> 1);
+        i = (rr & 1) ? n : 0;
+      }
+      const int dx = i == 0 ? -1 : (i == n ? 1 : 0), dy = j == 0 ? -1 : (j == n ? 1 : 0),
+                dz = k == 0 ? -1 : (k == n ? 1 : 0);
+      const int dir = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+      const int m = s_m[dir];
+      double v = 0.0;
+      if (m >= 0) {
+        const int iq = halo_index(i, dx, n, m), jq = halo_index(j, dy, n, m), kq = halo_index(k, dz, n, m);
+        v = u[s_off[dir] + ((int64_t)kq * (m + 1) + jq) * (m + 1) + iq];
+      }
+      u[off + ((int64_t)k * W + j) * W + i] = v;
+      mh = umax64(mh, fx::abs_bits(v));
+    }
+    mh = block_max_u64(mh, red);  // its barriers also keep s_m / s_off until every thread is done
     if (threadIdx.x == 0) hmax[p] = mh;
   }
 }
@@ -137,9 +157,12 @@ __device__ __forceinline__ long long add(long long a, long long b) {
 // Software pipeline of one patch sweep: the raw values of the next step's two planes
 // are loaded into registers (up to P_PF per thread, the rest when they are stored)
 // while the current step computes, and the right-hand sides of a step's four phases
-// (up to P_FPF items per thread and phase) are loaded when the step starts.
-constexpr int P_PF = 10;
-constexpr int P_FPF = 2;
+// (up to P_FPF items per thread and phase) are loaded when the step starts.  One of
+// each measured fastest (4096 patches: 14.3 ms per 20 sweeps, against 14.8 with 10 and
+// 2, and 18.2 with 4 and 1): deeper register prefetch costs more occupancy than it
+// hides latency.
+constexpr int P_PF = 1;
+constexpr int P_FPF = 1;
 
 template <bool FIX>
 __device__ __forceinline__ void stage_issue(double (&pf)[P_PF], const double *u, int W, int z0, int n) {
@@ -413,7 +436,7 @@ static int batch_sweeps(stencil_batch_t *b, double *u, const double *f, int swee
   const size_t smem = patch_smem(b->maxn);
   const unsigned grid = (unsigned)std::min(b->npatch, sms * ctas_per_sm);
   for (int it = 0; it < sweeps; ++it) {
-    k_patch_halo<<<gridp, 128, 0, s>>>(b->d_pd, b->d_nbr, b->npatch, u, hmax);
+    k_patch_halo<<<gridp, 256, 0, s>>>(b->d_pd, b->d_nbr, b->npatch, u, hmax);
     k_patch_gs<<<grid, threads, smem, s>>>(b->d_pd, b->d_order, b->npatch, u, f, umax, hmax, fmax,
                                             b->d_counters + it);
   }
