@@ -32,6 +32,11 @@ namespace {
 constexpr int W2_THREADS = 128;
 constexpr int W2_ROWS = 64;   // rows per warp (single-pass operations)
 constexpr int S2_ROWS = 256;  // rows per warp (multi-sweep GS and Jacobi)
+// CTAs per SM the two-sweep kernels are compiled for: with 5 the GS kernel fits in 96
+// registers instead of 106 (4 CTAs per SM), one more CTA of warps to hide the latency
+// of the row fronts (measured at 16385^2: GS 40.1 -> 37.5 ms and Jacobi 43.6 ->
+// 42.7 ms per 50 sweeps; 6, at 80 registers, spills and is slower)
+constexpr int S2X2_MIN_CTAS = 5;
 constexpr int R_MIN = -900, R_MAX = 1000;
 
 enum { O2_APPLY = 0, O2_JACOBI = 1, O2_RESIDUAL = 2, O2_ELEMENTWISE = 3 };
@@ -932,7 +937,7 @@ __device__ __forceinline__ void gs2x2_rows(const Geo &q, const void *X, void *Y,
 }
 
 template <int XF, int YF, bool V16>
-__global__ void __launch_bounds__(W2_THREADS) k_gs2_sweep2(Geo q, const void *__restrict__ X, void *__restrict__ Y,
+__global__ void __launch_bounds__(W2_THREADS, S2X2_MIN_CTAS) k_gs2_sweep2(Geo q, const void *__restrict__ X, void *__restrict__ Y,
                                                            const double *__restrict__ f,
                                                            const long long *__restrict__ GF, SweepBounds *bnd,
                                                            int sweep, int sweeps, double g, bool write_bnd, int rows) {
@@ -1144,7 +1149,7 @@ __device__ __forceinline__ void jac2x2_rows(const Geo &q, const void *X, void *Y
 }
 
 template <int XF, int YF, bool V16>
-__global__ void __launch_bounds__(W2_THREADS) k_jac2_sweep2(Geo q, const void *__restrict__ X, void *__restrict__ Y,
+__global__ void __launch_bounds__(W2_THREADS, S2X2_MIN_CTAS) k_jac2_sweep2(Geo q, const void *__restrict__ X, void *__restrict__ Y,
                                                             const double *__restrict__ f,
                                                             const long long *__restrict__ GF, SweepBounds *bnd,
                                                             int sweep, int sweeps, double g, double omega,
