@@ -551,3 +551,44 @@ def test_equal_patches_converge_to_the_collapsed_global_solution(L, n):
         g = U2[pz * n + 1:pz * n + n, py * n + 1:py * n + n, px * n + 1:px * n + n]
         err2 = max(err2, np.max(np.abs(lat.view(out, p)[1:n, 1:n, 1:n] - g)))
     assert err2 > 1e-3 * scale
+
+
+def test_uneven_halo_is_the_nearest_vertex_by_exact_geometry():
+    """The halo rule restated geometrically and evaluated by brute force in exact
+    rational arithmetic, against the oracle's integer index formula, on every shell
+    vertex of a 3 x 2 x 2 lattice of uneven patches (2 to 7 cells).  Shell vertex i
+    (per axis) of patch p at lattice cell P sits at P + i / n_p; its outward direction d
+    picks the neighbour cell Q = P + d (0 outside the lattice); per axis the source is
+    the vertex t of Q, among all t = 0 .. n_q, whose position Q + t / n_q is nearest
+    (the lower t on a tie), moved into Q's interior 1 .. n_q - 1."""
+    from fractions import Fraction as Fr
+    lat = synth.PatchLattice(lat=(3, 2, 2), seed=4, edges=(2, 3, 4, 5, 6, 7))
+    sizes = (lat.np_sizes.astype(np.int64) + 1) ** 3
+    u = np.arange(int(sizes.sum()), dtype=np.float64) + 0.25  # every value distinct
+    out = oracle.patch_halo_fill(lat.lat, lat.np_sizes, lat.offsets, u)
+    L = [int(v) for v in lat.lat]
+    npatch = L[0] * L[1] * L[2]
+    assert len(set(int(v) for v in lat.np_sizes)) >= 4  # genuinely uneven
+    for p in range(npatch):
+        P = (p % L[0], (p // L[0]) % L[1], p // (L[0] * L[1]))
+        n = int(lat.np_sizes[p])
+        got = lat.view(out, p)
+        for k in range(n + 1):
+            for j in range(n + 1):
+                for i in range(n + 1):
+                    idx = (i, j, k)
+                    d = tuple(-1 if v == 0 else (1 if v == n else 0) for v in idx)
+                    if d == (0, 0, 0):
+                        continue
+                    Q = tuple(P[a] + d[a] for a in range(3))
+                    if any(Q[a] < 0 or Q[a] >= L[a] for a in range(3)):
+                        assert got[k, j, i] == 0.0
+                        continue
+                    q = Q[0] + L[0] * (Q[1] + L[1] * Q[2])
+                    m = int(lat.np_sizes[q])
+                    src = []
+                    for a in range(3):
+                        x = P[a] + Fr(idx[a], n)
+                        t = min(range(m + 1), key=lambda s: (abs(Q[a] + Fr(s, m) - x), s))
+                        src.append(min(max(t, 1), m - 1))
+                    assert got[k, j, i] == lat.view(u, q)[src[2], src[1], src[0]], (p, idx)
