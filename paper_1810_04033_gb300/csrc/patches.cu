@@ -154,41 +154,41 @@ __device__ __forceinline__ long long add(long long a, long long b) {
   return __double_as_longlong(__longlong_as_double(a) + __longlong_as_double(b));
 }
 
-// Software pipeline of one patch sweep: the raw values of the next step's two planes
-// are loaded into registers (up to P_PF per thread, the rest when they are stored)
-// while the current step computes, and the right-hand sides of a step's four phases
-// (up to P_FPF items per thread and phase) are loaded when the step starts.  One of
-// each measured fastest (4096 patches: 14.3 ms per 20 sweeps, against 14.8 with 10 and
-// 2, and 18.2 with 4 and 1): deeper register prefetch costs more occupancy than it
-// hides latency.
-constexpr int P_PF = 1;
+// Software pipeline of one patch sweep: the next step's two planes are copied from
+// global memory into their shared-memory slots by cp.async while the current step
+// computes (six slots: four planes in use, two arriving), and converted to fixed point
+// in place when the step starts; the right-hand side of a thread's first item of each
+// phase (P_FPF) is loaded when the step starts, the rest inside the phase.
+constexpr int P_SLOTS = 6;
 constexpr int P_FPF = 1;
 
-template <bool FIX>
-__device__ __forceinline__ void stage_issue(double (&pf)[P_PF], const double *u, int W, int z0, int n) {
-  const int P = W * W;
-#pragma unroll
-  for (int k = 0; k < P_PF; ++k) {
-    const int idx = threadIdx.x + k * (int)blockDim.x;  // over planes z0, z0 + 1
-    const int z = z0 + idx / P;
-    pf[k] = idx < 2 * P && z <= n ? u[(int64_t)z0 * P + idx] : 0.0;
+__device__ __forceinline__ long long *patch_slot(long long *smem, int P, int z) { return smem + (z % P_SLOTS) * P; }
+
+// Start copying planes z0 and z0 + 1 (those <= n) into their slots, raw FP64 bits; one
+// commit group.
+__device__ __forceinline__ void stage_async(long long *smem, const double *u, int P, int z0, int n) {
+  for (int idx = threadIdx.x; idx < 2 * P; idx += blockDim.x) {
+    const int up = idx >= P, z = z0 + up, e = idx - (up ? P : 0);
+    if (z <= n) {
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(patch_slot(smem, P, z) + e);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(u + (int64_t)z * P + e) : "memory");
+    }
   }
+  asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// store planes z0, z0 + 1 (those <= n) into their slots: prefetched values first
-template <bool FIX, typename SlotFn>
-__device__ __forceinline__ void stage_commit(const double (&pf)[P_PF], const double *u, int W, int z0, int n,
-                                             int rb, SlotFn slot) {
-  const int P = W * W;
-#pragma unroll
-  for (int k = 0; k < P_PF; ++k) {
-    const int idx = threadIdx.x + k * (int)blockDim.x;
-    const int z = z0 + idx / P;
-    if (idx < 2 * P && z <= n) slot(z)[idx % P] = enc<FIX>(pf[k], rb);
-  }
-  for (int idx = threadIdx.x + P_PF * (int)blockDim.x; idx < 2 * P; idx += blockDim.x) {
-    const int z = z0 + idx / P;
-    if (z <= n) slot(z)[idx % P] = enc<FIX>(u[(int64_t)z0 * P + idx], rb);
+// Wait for this thread's copies of planes z0, z0 + 1 and convert them in place (the
+// same element mapping as stage_async, so every thread converts what it copied).
+template <bool FIX>
+__device__ __forceinline__ void stage_convert(long long *smem, int P, int z0, int n, int rb) {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if (!FIX) return;
+  for (int idx = threadIdx.x; idx < 2 * P; idx += blockDim.x) {
+    const int up = idx >= P, z = z0 + up, e = idx - (up ? P : 0);
+    if (z <= n) {
+      long long *v = patch_slot(smem, P, z) + e;
+      *v = enc<true>(__longlong_as_double(*v), rb);
+    }
   }
 }
 
@@ -210,13 +210,23 @@ template <bool FIX>
 __device__ void patch_phase(long long *ce, const long long *lo, const long long *up, int n, int pr,
                             const double *fplane, const double (&fv)[P_FPF], double *uplane, double g, int rb,
                             int e2, unsigned long long &vmax) {
-  const int W = n + 1;
+  const int W = n + 1, nm1 = n - 1;
   const int j0 = pr ? 1 : 2;  // first interior row of parity pr
   const int nrows = n - 1 >= j0 ? (n - 1 - j0) / 2 + 1 : 0;
-  const int items = nrows * (n - 1);
+  const int items = nrows * nm1;
+  // item it is (row it / nm1, column it % nm1); the thread's items advance by blockDim,
+  // so row and column advance by fixed steps (no division per item)
+  int r = (int)threadIdx.x / nm1, cc = (int)threadIdx.x - r * nm1;
+  const int dr = (int)blockDim.x / nm1, dc = (int)blockDim.x - dr * nm1;
   int k = 0;
   for (int it = threadIdx.x; it < items; it += blockDim.x, ++k) {
-    const int j = j0 + 2 * (it / (n - 1)), i = 1 + it % (n - 1);
+    const int j = j0 + 2 * r, i = 1 + cc;
+    cc += dc;
+    r += dr;
+    if (cc >= nm1) {
+      cc -= nm1;
+      ++r;
+    }
     const int c = j * W + i;
     // E: edges (x,y in plane; x,z; y,z), C: corners; face weights are 0
     const long long Exy = add<FIX>(add<FIX>(ce[c - W - 1], ce[c - W + 1]), add<FIX>(ce[c + W - 1], ce[c + W + 1]));
@@ -247,13 +257,14 @@ __device__ void patch_sweep(int n, double *u, const double *f, double g, int R, 
                             unsigned long long &vmax) {
   const int W = n + 1, P = W * W;
   const int rb = 1023 + R, e2 = R - fx::FRAC - 5;
-  auto slot = [&](int z) -> long long * { return smem + (z & 3) * P; };
-  double pf[P_PF];
-  stage_issue<FIX>(pf, u, W, 0, n);
+  auto slot = [&](int z) -> long long * { return patch_slot(smem, P, z); };
+  stage_async(smem, u, P, 0, n);
   for (int t = 0; 2 * t - 1 <= n; ++t) {
     const int za = 2 * t, zc = 2 * t - 1;
-    if (za <= n) stage_commit<FIX>(pf, u, W, za, n, rb, slot);
-    if (za + 2 <= n) stage_issue<FIX>(pf, u, W, za + 2, n);
+    // planes za, za+1 arrived (issued one step ago); the next two go into the slots of
+    // za-4, za-3, which the previous step was the last to read
+    if (za <= n) stage_convert<FIX>(smem, P, za, n, rb);
+    if (za + 2 <= n) stage_async(smem, u, P, za + 2, n);
     const bool da = za >= 1 && za <= n - 1, dc = zc >= 1 && zc <= n - 1;
     double fa0[P_FPF], fa1[P_FPF], fc0[P_FPF], fc1[P_FPF];
     phase_f(fa0, da ? f + (int64_t)za * P : nullptr, n, 0);
@@ -278,6 +289,7 @@ __device__ void patch_sweep(int n, double *u, const double *f, double g, int R, 
     }
     __syncthreads();
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");  // nothing in flight when the CTA moves on
 }
 
 __global__ void __launch_bounds__(512) k_patch_gs(const PatchDev *pd, const int *order, int npatch, double *u, const double *f,
@@ -333,7 +345,7 @@ struct stencil_batch {
   int64_t interior_updates = 0;
 };
 
-static size_t patch_smem(int maxn) { return 4 * (size_t)(maxn + 1) * (maxn + 1) * sizeof(long long); }
+static size_t patch_smem(int maxn) { return P_SLOTS * (size_t)(maxn + 1) * (maxn + 1) * sizeof(long long); }
 
 // The shared-memory limit of k_patch_gs is a per-device kernel attribute, while each
 // batch needs its own amount (it grows with the largest patch).  The limit is only ever
