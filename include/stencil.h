@@ -483,6 +483,23 @@ int stencil_server_destroy(stencil_server_t *s);
  * concurrent calls on that device). */
 int stencil_release_workspace(void);
 
+/* Bits of stencil_device_status: a kernel's bounded wait on a TMA plane load ran out
+ * and the CTA left without its outputs (the results of that call are incomplete). */
+#define STENCIL_STATUS_TMA_OPS3 1u   /* 3D applies, Jacobi step, residual */
+#define STENCIL_STATUS_TMA_GS3 2u    /* 3D Gauss-Seidel half sweeps */
+#define STENCIL_STATUS_TMA_JAC3 4u   /* 3D multi-sweep Jacobi */
+#define STENCIL_STATUS_TMA_GS_LP 8u  /* 3D FP32 / bf16 Gauss-Seidel */
+
+/*
+ * *flags = the STENCIL_STATUS_* bits set on the current device since the flags were
+ * last cleared (0: every bounded device wait completed); clear != 0 clears them.  The
+ * paper has no counterpart: the kernels bound every wait (a TMA completion, a
+ * neighbour's progress), and this call reports the ones that ran out, which an
+ * asynchronous call cannot return.  Synchronises the device first.
+ * Returns STENCIL_EINVAL (flags NULL), STENCIL_ECUDA.
+ */
+int stencil_device_status(uint32_t *flags, int clear);
+
 /* ---------------------------------------------------------------- launch-shape tuning
  * The plane-streaming 3D kernels process a chunk of z-planes per CTA and the 2D kernels
  * a chunk of rows per warp; the 2D multi-sweep smoothers run one or two sweeps per pass

@@ -124,6 +124,7 @@ def lib():
             "stencil_release_workspace": (ci, []),
             "stencil_apply": (ci, [gp, vp, vp, ci, vp]),
             "stencil_workspace_size": (ci, [gp, ci, ci, ctypes.POINTER(ctypes.c_size_t)]),
+            "stencil_device_status": (ci, [ctypes.POINTER(ctypes.c_uint32), ci]),
             "stencil_autotune": (ci, [gp, ci, ci, ctypes.POINTER(Tuning), vp]),
             "stencil_tuning_set": (ci, [gp, ci, ctypes.POINTER(Tuning)]),
             "stencil_tuning_get": (ci, [gp, ci, ctypes.POINTER(Tuning)]),
@@ -644,3 +645,11 @@ def stencil_tuning_save(path):
 
 def stencil_tuning_load(path):
     _check(lib().stencil_tuning_load(os.fsencode(path)))
+
+
+def stencil_device_status(clear=False):
+    """Bits of the bounded device waits that ran out on the current device (0: none);
+    synchronises the device."""
+    v = ctypes.c_uint32(0)
+    _check(lib().stencil_device_status(ctypes.byref(v), 1 if clear else 0))
+    return int(v.value)

@@ -315,6 +315,22 @@ const char *stencil_last_error(void) { return g_last_error.c_str(); }
 
 int stencil_release_workspace(void) { return release_scratch(); }
 
+int stencil_device_status(uint32_t *flags, int clear) {
+  if (!flags) return set_error(STENCIL_EINVAL, "device_status: flags is NULL");
+  *flags = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return set_error(STENCIL_ECUDA, std::string("device_status: ") + cudaGetErrorString(e));
+  cudaError_t (*const readers[4])(unsigned *, bool) = {tma_wait_flag_ops3, tma_wait_flag_gs3, tma_wait_flag_jac3,
+                                                       tma_wait_flag_gs_lp};
+  for (int i = 0; i < 4; ++i) {
+    unsigned v = 0;
+    e = readers[i](&v, clear != 0);
+    if (e != cudaSuccess) return set_error(STENCIL_ECUDA, std::string("device_status: ") + cudaGetErrorString(e));
+    if (v) *flags |= 1u << i;
+  }
+  return STENCIL_OK;
+}
+
 int stencil_workspace_size(const stencil_grid_t *g, int call, int sweeps, size_t *bytes) {
   if (!bytes) return set_error(STENCIL_EINVAL, "workspace_size: bytes is NULL");
   *bytes = 0;

@@ -835,3 +835,18 @@ cudaError_t launch_gs_sweeps_fx3(const Geo &q, double *u, const double *f, int s
 }
 
 }  // namespace stencil
+
+namespace stencil {
+
+// The TMA wait flag of this file's kernels (1 once a bounded wait ran out); cleared on
+// request.  Synchronous.
+cudaError_t tma_wait_flag_gs3(unsigned *value, bool clear) {
+  cudaError_t e = cudaMemcpyFromSymbol(value, g_gs_tma_error, sizeof(unsigned));
+  if (e == cudaSuccess && clear && *value) {
+    const unsigned zero = 0u;
+    e = cudaMemcpyToSymbol(g_gs_tma_error, &zero, sizeof(unsigned));
+  }
+  return e;
+}
+
+}  // namespace stencil

@@ -93,6 +93,13 @@ inline int tuned_chunk(const Tuning &t, int fallback, int lo, int hi) {
   return t.chunk < lo ? lo : (t.chunk > hi ? hi : t.chunk);
 }
 
+// Flags the TMA-staged kernels set when a bounded wait on a TMA completion ran out
+// (ops_fx.cu, gs_fx.cu, jac3_fx.cu, gs_lp.cu); read synchronously, optionally cleared.
+cudaError_t tma_wait_flag_ops3(unsigned *value, bool clear);
+cudaError_t tma_wait_flag_gs3(unsigned *value, bool clear);
+cudaError_t tma_wait_flag_jac3(unsigned *value, bool clear);
+cudaError_t tma_wait_flag_gs_lp(unsigned *value, bool clear);
+
 // Error plumbing and descriptor check (api.cu).
 int set_error(int code, const std::string &msg);
 int check_grid(const stencil_grid_t *g);

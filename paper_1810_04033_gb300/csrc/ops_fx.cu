@@ -729,3 +729,18 @@ cudaError_t launch_residual_fx3(const Geo &q, const double *u, const double *f, 
 }
 
 }  // namespace stencil
+
+namespace stencil {
+
+// The TMA wait flag of this file's kernels (1 once a bounded wait ran out); cleared on
+// request.  Synchronous.
+cudaError_t tma_wait_flag_ops3(unsigned *value, bool clear) {
+  cudaError_t e = cudaMemcpyFromSymbol(value, g_ops3_tma_error, sizeof(unsigned));
+  if (e == cudaSuccess && clear && *value) {
+    const unsigned zero = 0u;
+    e = cudaMemcpyToSymbol(g_ops3_tma_error, &zero, sizeof(unsigned));
+  }
+  return e;
+}
+
+}  // namespace stencil
