@@ -839,6 +839,10 @@ def run_refine(args):
     out["mg"] = {"seconds": round(sec, 4), "cycles": res["cycles"], "levels": res["levels"],
                  "relres": res["relres"], "converged": res["converged"], "rel_err_vs_closed_form": err}
     clock_info = clocks.stop()
+    if args.no_cpu:  # timing only (e.g. under a profiler): no oracle runs
+        return {"metric": "time to relative residual 1e-10, 256^3 (speedup of mixed precision over FP64)",
+                "workload": "refine", "value": round(out["fp64"]["seconds"] / out["fp32"]["seconds"], 3),
+                "unit": "x (FP64 time / FP32-inner time)", "pitch": pitch, "runs": out, "clocks": clock_info}
     # error per iterate: the GPU's iterates 1..K of each inner precision against the FP64
     # oracle's iterates (plain FP64 inner sweeps, same loop) and against the oracle of the
     # same precision; K bounded by the oracle's host time (one correction of 8 sweeps
