@@ -199,7 +199,7 @@ __device__ __forceinline__ void phase(const Ctx &c, long long *ce, const long lo
     if (inner) {
       const long long S = add<FIXA>(add<FIXA>(Pm, Pp), add<FIXA>(Q, Q));  // 2E + C
       if (FIXA)
-        rep = shr(fv[(WHICH - 1) * 4 + k], c.df) + (S >> 5);
+        rep = (fv[(WHICH - 1) * 4 + k] >> c.df) + (S >> 5);
       else
         rep = __double_as_longlong(fma(__longlong_as_double(S), 0.03125,
                                        c.g * __longlong_as_double(fv[(WHICH - 1) * 4 + k])));
@@ -318,7 +318,9 @@ __global__ void __launch_bounds__(GS_THREADS, 2)
   const int Rx = sweep > 0 ? sweep_R(bnd, (sweep + 3) % 4, g) : c.R;  // scale of the previous sweep
   c.dx = XF == FXP ? c.R - Rx : 0;
   c.dn = NF == FXP ? (pz == 0 ? c.dx : 0) : 0;  // odd launch: N is this sweep's output
-  c.df = c.R - plan.Rf;
+  // R >= Rf (the sweep's bound includes 4 (3/8) h^2 max|f|): GF needs a right shift,
+  // clamped at 63 (which leaves 0 or -1, below one unit of the last place)
+  c.df = min(c.R - plan.Rf, 63);
   if (pz == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
     bnd->umax[cl] = 0ull;  // to be accumulated by sweep s + 1
 
@@ -450,8 +452,8 @@ __device__ __forceinline__ void phase_t(const Ctx &c, long long *ce, const long 
     const long long Sa = add<FIXA>(add<FIXA>(Pl, P.b), add<FIXA>(Q.a, Q.a));  // 2E + C
     const long long Sb = add<FIXA>(add<FIXA>(P.a, Pr), add<FIXA>(Q.b, Q.b));
     if (FIXA) {
-      if (ja) nw.a = shr(fv[k].a, c.df) + (Sa >> 5);
-      if (jb) nw.b = shr(fv[k].b, c.df) + (Sb >> 5);
+      if (ja) nw.a = (fv[k].a >> c.df) + (Sa >> 5);
+      if (jb) nw.b = (fv[k].b >> c.df) + (Sb >> 5);
     } else {
       if (ja) nw.a = __double_as_longlong(fma(__longlong_as_double(Sa), 0.03125, c.g * __longlong_as_double(fv[k].a)));
       if (jb) nw.b = __double_as_longlong(fma(__longlong_as_double(Sb), 0.03125, c.g * __longlong_as_double(fv[k].b)));
@@ -626,7 +628,9 @@ __global__ void __launch_bounds__(GT_THREADS, 2)
   const int Rx = sweep > 0 ? sweep_R(bnd, (sweep + 3) % 4, g) : c.R;
   c.dx = XF == FXP ? c.R - Rx : 0;
   c.dn = NF == FXP ? (pz == 0 ? c.dx : 0) : 0;
-  c.df = c.R - plan.Rf;
+  // R >= Rf (the sweep's bound includes 4 (3/8) h^2 max|f|): GF needs a right shift,
+  // clamped at 63 (which leaves 0 or -1, below one unit of the last place)
+  c.df = min(c.R - plan.Rf, 63);
   if (pz == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) bnd->umax[cl] = 0ull;
   if (threadIdx.x == 0) {
     for (int i = 0; i < GT_NSLOT; ++i) mbar_init(&bars[i], 1);
