@@ -7,8 +7,11 @@
 //   12 (K u_e)_w = 5 u_w + F_w - T,   F_w = sum of the 3 face-adjacent vertices of w,
 //   T = sum of all 8 vertex values of the cell,
 // evaluated exactly in int64 fixed point (fixed.cuh), so the accumulated vertex sums
-// do not depend on the order of the additions.  y = sum / (12 h^2) on interior
-// vertices, 0 on the boundary.
+// do not depend on the order of the additions.  In fixed point the cell adds -G_w to
+// vertex w, 12 (K u_e)_w = 4 u_w - G_w with G_w = T - u_w - F_w (the four vertices that
+// share no edge with w), and the 4 u_w parts of a vertex's eight cells are added once,
+// as 32 u_w: the same integer sum with fewer operations per cell.  y = sum / (12 h^2)
+// on interior vertices, 0 on the boundary.
 //
 // The scatter runs in registers, one warp per column of cells (layout below): the z
 // colours are the cell layers processed in order, the y colours the cell rows processed
@@ -152,6 +155,24 @@ __device__ __forceinline__ void cell12(long long b0, long long b1, long long b2,
   ct[3] = add<FIX>(sub<FIX>(times4<FIX>(t3), t0), sub<FIX>(b3, Sb));
 }
 
+// Fixed-point form of the same cell: 12 (K u_e)_w = 4 u_w - G_w, G_w = the sum of the
+// four cell vertices that share no edge with w (the three face diagonals and the body
+// diagonal); gb / gt receive G_w of the bottom / top vertices.  The 4 u_w parts of a
+// vertex's eight cells are added once, as 32 u_w, when its plane is complete.
+__device__ __forceinline__ void cell_g(long long b0, long long b1, long long b2, long long b3, long long t0,
+                                       long long t1, long long t2, long long t3, long long (&gb)[4],
+                                       long long (&gt)[4]) {
+  const long long Sb = (b0 + b1) + (b2 + b3), St = (t0 + t1) + (t2 + t3);
+  gb[0] = b3 + St - t0;
+  gb[1] = b2 + St - t1;
+  gb[2] = b1 + St - t2;
+  gb[3] = b0 + St - t3;
+  gt[0] = t3 + Sb - b0;
+  gt[1] = t2 + Sb - b1;
+  gt[2] = t1 + Sb - b2;
+  gt[3] = t0 + Sb - b3;
+}
+
 // This lane's staged pair of row c and the next lane's xa value of that row.
 struct Row3 {
   long long a, b, r;
@@ -191,6 +212,17 @@ __device__ __forceinline__ int64_t ew3_layers(const EwArgs &a, Ew3Lane &L, int64
         const int Rp = (int)em - 1022 + 1;
         long long *ob = bot + 2 * L.lane;
         if (em == 2047 || Rp > E3_RMAX || (Rp < E3_RMIN && L.R == E3_RMIN)) {
+          if (k >= 1 && k <= q.nz) {
+            // the 4 u_v parts of layer k-1's cells: 2 cells (A) at xa, 4 at xb, 2 (B) at
+            // the next lane's xa, for each vertex row
+#pragma unroll
+            for (int r = 0; r < E3_R; ++r) {
+              const long long *row = ob + (r + 1) * E3_W;
+              L.acc[r].a += 8 * row[0];
+              L.acc[r].b += 16 * row[1];
+              L.accR[r] += 8 * row[2];
+            }
+          }
           auto cv = [&](long long v) { return __double_as_longlong(fx::to_double(v, L.R - fx::FRAC)); };
 #pragma unroll
           for (int c = 0; c < E3_ROWS; ++c) {
@@ -244,7 +276,35 @@ __device__ __forceinline__ int64_t ew3_layers(const EwArgs &a, Ew3Lane &L, int64
         const int64_t cj = j0 - 1 + c;
         if (cj >= 0 && cj < q.ny) {  // warp-uniform
           long long cb[4], ct[4];
-          if (E3_ALLCELLS || L.cellA) {  // vertices xa, xb of rows cj, cj+1
+          if (FIX) {
+            long long gb[4], gt[4];
+            cell_g(b0.a, b0.b, b1.a, b1.b, t0.a, t0.b, t1.a, t1.b, gb, gt);  // cell A
+            if (c >= 1) {
+              L.acc[c - 1].a -= gb[0];
+              L.acc[c - 1].b -= gb[1];
+              part[c - 1].a -= gt[0];
+              part[c - 1].b -= gt[1];
+            }
+            if (c < E3_R) {
+              L.acc[c].a -= gb[2];
+              L.acc[c].b -= gb[3];
+              part[c].a -= gt[2];
+              part[c].b -= gt[3];
+            }
+            cell_g(b0.b, b0.r, b1.b, b1.r, t0.b, t0.r, t1.b, t1.r, gb, gt);  // cell B
+            if (c >= 1) {
+              L.acc[c - 1].b -= gb[0];
+              L.accR[c - 1] -= gb[1];
+              part[c - 1].b -= gt[0];
+              partR[c - 1] -= gt[1];
+            }
+            if (c < E3_R) {
+              L.acc[c].b -= gb[2];
+              L.accR[c] -= gb[3];
+              part[c].b -= gt[2];
+              partR[c] -= gt[3];
+            }
+          } else if (E3_ALLCELLS || L.cellA) {  // vertices xa, xb of rows cj, cj+1
             cell12<FIX>(b0.a, b0.b, b1.a, b1.b, t0.a, t0.b, t1.a, t1.b, cb, ct);
             if (c >= 1) {
               L.acc[c - 1].a = add<FIX>(L.acc[c - 1].a, cb[0]);
@@ -259,7 +319,7 @@ __device__ __forceinline__ int64_t ew3_layers(const EwArgs &a, Ew3Lane &L, int64
               part[c].b = add<FIX>(part[c].b, ct[3]);
             }
           }
-          if (E3_ALLCELLS || L.cellB) {  // vertices xb and the next lane's xa
+          if (!FIX && (E3_ALLCELLS || L.cellB)) {  // vertices xb and the next lane's xa
             cell12<FIX>(b0.b, b0.r, b1.b, b1.r, t0.b, t0.r, t1.b, t1.r, cb, ct);
             if (c >= 1) {
               L.acc[c - 1].b = add<FIX>(L.acc[c - 1].b, cb[0]);
@@ -298,9 +358,15 @@ __device__ __forceinline__ int64_t ew3_layers(const EwArgs &a, Ew3Lane &L, int64
         const bool jin = zin && j >= 1 && j < q.ny;
         // the odd column converts with integer instructions (E3_SPLIT), moving a quarter
         // of the conversions' FP64-pipe work to the integer pipes; the same bits
-        const double va = FIX ? __ll2double_rn(L.acc[r].a) : __longlong_as_double(L.acc[r].a);
-        const double vb = !FIX ? __longlong_as_double(L.acc[r].b)
-                          : E3_SPLIT ? fx::to_double(L.acc[r].b, L.R - fx::FRAC) : __ll2double_rn(L.acc[r].b);
+        long long sa = L.acc[r].a, sbv = L.acc[r].b;
+        if (FIX) {  // the 4 u_v parts of the eight cells
+          const longlong2 uk = *(const longlong2 *)(bot + (r + 1) * E3_W + 2 * L.lane);
+          sa += 32 * uk.x;
+          sbv += 32 * uk.y;
+        }
+        const double va = FIX ? __ll2double_rn(sa) : __longlong_as_double(sa);
+        const double vb = !FIX ? __longlong_as_double(sbv)
+                          : E3_SPLIT ? fx::to_double(sbv, L.R - fx::FRAC) : __ll2double_rn(sbv);
         const double sb = FIX && E3_SPLIT ? a.scale : sc;
         const long long ya = __double_as_longlong(jin && L.ina ? va * sc : 0.0);
         const long long yb = __double_as_longlong(jin && L.inb ? vb * sb : 0.0);

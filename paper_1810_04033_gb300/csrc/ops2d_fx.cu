@@ -201,7 +201,8 @@ struct Stream2 {
 };
 
 // Element matrix 6 K_e of one cell times its vertex values v0 = (x, y), v1 = (x+1, y),
-// v2 = (x, y+1), v3 = (x+1, y+1): 4 v_w - (the two face-adjacent values) - 2 v_opposite.
+// v2 = (x, y+1), v3 = (x+1, y+1): 4 v_w - (the two face-adjacent values) - 2 v_opposite
+// (the FP64 path; the fixed-point path forms the same sums as in ew2_rows).
 template <bool FIX>
 __device__ __forceinline__ void cell_contrib(long long v0, long long v1, long long v2, long long v3, long long &c0,
                                              long long &c1, long long &c2, long long &c3) {
@@ -255,6 +256,7 @@ __device__ __forceinline__ int64_t ew2_rows(const Op2Args &a, WarpScale &w, Stre
       if (FIX) {
         const int d = admit_row(w, em, 1);
         if (d < 0) {  // leave this row to the FP64 loop
+          if (cj >= 1) alo = Pair{alo.a + 12 * ua.a, alo.b + 12 * ua.b};  // the 6 u_v of cell row cj - 1
           ua = pair_f64(ua, w.R);
           alo = pair_f64(alo, w.R);
           ahi = pair_f64(ahi, w.R);
@@ -275,23 +277,48 @@ __device__ __forceinline__ int64_t ew2_rows(const Op2Args &a, WarpScale &w, Stre
       const bool crow = cj >= 0 && cj < q.ny;
       const bool cellA = crow && c.xa >= 0 && c.xa < q.nx;
       const bool cellB = crow && s.lane <= 30 && c.xa + 1 >= 0 && c.xa + 1 < q.nx;
-      long long a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
-      if (EW2_ALLCELLS ? crow : cellA) cell_contrib<FIX>(ua.a, ua.b, ub.a, ub.b, a0, a1, a2, a3);
-      if (EW2_ALLCELLS ? crow : cellB) cell_contrib<FIX>(ua.b, uar, ub.b, ubr, b0, b1, b2, b3);
-      long long b1l = __shfl_up_sync(0xffffffffu, b1, 1), b3l = __shfl_up_sync(0xffffffffu, b3, 1);
-      if (s.lane == 0) b1l = b3l = 0;
-      // vertex xa: cell A (even x) then the left lane's cell B; vertex xb: A then B
-      alo.a = add<FIX>(add<FIX>(alo.a, a0), b1l);
-      ahi.a = add<FIX>(add<FIX>(ahi.a, a2), b3l);
-      alo.b = add<FIX>(add<FIX>(alo.b, a1), b0);
-      ahi.b = add<FIX>(add<FIX>(ahi.b, a3), b2);
+      if (FIX) {
+        // 6 K_e u_e at a vertex of the cell = 6 u_v - d, d = s + 2 s' with s the sum of
+        // the vertex's two edge neighbours in the cell and s' the sum of the vertex and
+        // its opposite: one d for each diagonal pair of the cell.  The 6 u_v parts of the
+        // vertex's four cells are added once, as 24 u_v, when the row is complete.
+        long long dA03 = 0, dA12 = 0, dB03 = 0, dB12 = 0;
+        if (EW2_ALLCELLS ? crow : cellA) {
+          const long long s12 = ua.b + ub.a, s03 = ua.a + ub.b;
+          dA03 = s12 + 2 * s03;
+          dA12 = s03 + 2 * s12;
+        }
+        if (EW2_ALLCELLS ? crow : cellB) {
+          const long long s12 = uar + ub.b, s03 = ua.b + ubr;
+          dB03 = s12 + 2 * s03;
+          dB12 = s03 + 2 * s12;
+        }
+        long long dB12l = __shfl_up_sync(0xffffffffu, dB12, 1), dB03l = __shfl_up_sync(0xffffffffu, dB03, 1);
+        if (s.lane == 0) dB12l = dB03l = 0;
+        alo.a -= dA03 + dB12l;
+        ahi.a -= dA12 + dB03l;
+        alo.b -= dA12 + dB03;
+        ahi.b -= dA03 + dB12;
+      } else {
+        long long a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+        if (EW2_ALLCELLS ? crow : cellA) cell_contrib<FIX>(ua.a, ua.b, ub.a, ub.b, a0, a1, a2, a3);
+        if (EW2_ALLCELLS ? crow : cellB) cell_contrib<FIX>(ua.b, uar, ub.b, ubr, b0, b1, b2, b3);
+        long long b1l = __shfl_up_sync(0xffffffffu, b1, 1), b3l = __shfl_up_sync(0xffffffffu, b3, 1);
+        if (s.lane == 0) b1l = b3l = 0;
+        // vertex xa: cell A (even x) then the left lane's cell B; vertex xb: A then B
+        alo.a = add<FIX>(add<FIX>(alo.a, a0), b1l);
+        ahi.a = add<FIX>(add<FIX>(ahi.a, a2), b3l);
+        alo.b = add<FIX>(add<FIX>(alo.b, a1), b0);
+        ahi.b = add<FIX>(add<FIX>(ahi.b, a3), b2);
+      }
       if (cj >= js) {
         const bool jin = cj >= 1 && cj < q.ny;
         // FIX: the converted sum times c1 2^(R-52) (exact power-of-two scaling of c1)
         constexpr bool SPLIT = OP2_SPLIT[O2_ELEMENTWISE];
-        const double va = FIX ? __ll2double_rn(alo.a) : __longlong_as_double(alo.a);
-        const double vb = !FIX ? __longlong_as_double(alo.b)
-                          : SPLIT ? fx::to_double(alo.b, w.R - fx::FRAC) : __ll2double_rn(alo.b);
+        const long long sa = FIX ? alo.a + 24 * ua.a : alo.a, sbv = FIX ? alo.b + 24 * ua.b : alo.b;
+        const double va = FIX ? __ll2double_rn(sa) : __longlong_as_double(sa);
+        const double vb = !FIX ? __longlong_as_double(sbv)
+                          : SPLIT ? fx::to_double(sbv, w.R - fx::FRAC) : __ll2double_rn(sbv);
         const double sb = FIX && SPLIT ? a.c1 : sc;
         st_pair<V16>((long long *)a.out + cj * q.pitch, c, s.out_lane && c.oka, s.out_lane && c.okb,
                      __double_as_longlong(jin && c.ina ? va * sc : 0.0),

@@ -262,6 +262,16 @@ def test_out_of_place_ops_extreme_and_mixed_magnitudes(scale):
     torch.cuda.synchronize()
     assert apply_err(to_host(yd), oracle.apply_stencil(u, h), u, h) <= TOL_F64
     assert rel_err(to_host(od), oracle.jacobi(u, f, h, 0.8, 1)) <= TOL_F64
+    # the element-wise form on both of its kernels (odd pitch, and 16-byte pairs at an
+    # even pitch): warps whose planes leave the fixed-point range part-way up the z
+    # column continue in FP64 from that layer, and a growing scale rescales their sums
+    ref = oracle.apply_elementwise(u, h)
+    for pad in (0, 7):
+        ue = to_dev(u, pad)
+        ye = to_dev(np.full(shape, np.nan), pad)
+        st.stencil_apply(ue, ye, h, st.FORM_ELEMENTWISE)
+        torch.cuda.synchronize()
+        assert apply_err(to_host(ye), ref, u, h) <= TOL_F64, pad
 
 
 def test_full_size_sampled_apply_and_gs():
@@ -348,6 +358,11 @@ def test_2d_extreme_and_growing_magnitudes(scale):
         st.stencil_apply(ud, yd, h, form)
         torch.cuda.synchronize()
         assert apply_err(to_host(yd), ref, u, h) <= TOL_F64
+        # the same at an even pitch (16-byte pairs)
+        ue, ye = to_dev(u, 7), to_dev(np.full(shape, np.nan), 7)
+        st.stencil_apply(ue, ye, h, form)
+        torch.cuda.synchronize()
+        assert apply_err(to_host(ye), ref, u, h) <= TOL_F64
     gd = ud.clone()
     st.stencil_smooth_coloured(gd, fd, h, 2)
     od = torch.empty_like(ud)
