@@ -394,11 +394,12 @@ __device__ __forceinline__ LP ldsp(const long long *p) {
 
 // Right-hand side pair (GF in fixed arithmetic, f otherwise) of row j at columns xa,
 // xa + 1 for an interior row; zeros where the columns leave the grid.
+template <bool INNER>
 __device__ __forceinline__ LP ld_rhs(const Ctx &c, const void *fplane, int j, int xa) {
   LP p{0ll, 0ll};
   if (!fplane || j < 1 || j >= c.ny) return p;
   const long long *row = (const long long *)fplane + (int64_t)j * c.pitch;
-  if (xa >= 0 && xa + 1 <= c.nx) {
+  if (INNER || (xa >= 0 && xa + 1 <= c.nx)) {
     const longlong2 v = *(const longlong2 *)(row + xa);
     p.a = v.x;
     p.b = v.y;
@@ -464,7 +465,14 @@ __device__ __forceinline__ void phase_t(const Ctx &c, long long *ce, const long 
     const bool rcore = r >= 2 && r <= 31;
     const bool wa = core && rcore && jok && xa_ok && (ja || c.write_bnd);
     const bool wb = core && rcore && jok && xb_ok && (jb || c.write_bnd);
-    if (wa || wb) {
+    if (INNER && FIXA && YF == FXP) {
+      // inside the grid both columns of a core lane are updated and written
+      if (core && rcore) {
+        *(longlong2 *)((long long *)yplane + (int64_t)j * c.pitch + xa) = make_longlong2(nw.a, nw.b);
+        const long long ma = nw.a < 0 ? -nw.a : nw.a, mb = nw.b < 0 ? -nw.b : nw.b;
+        vmax = max(vmax, max(ma, mb));
+      }
+    } else if (wa || wb) {
       long long ya = nw.a, yb = nw.b;
       if (FIXA && YF == F64) {  // last sweep: only updated vertices are written
         ya = __double_as_longlong(fx::to_double_cvt(nw.a, c.R - fx::FRAC));
@@ -533,8 +541,8 @@ __device__ void run_half_t(Ctx &c, int pz, int i0, int i1, const void *F, void *
     const bool zin = z >= 1 && z <= q.nz - 1;
     const void *fp = zin ? Fc + z * P * 8 : nullptr;
     for (int k = 0; k < 2; ++k) {
-      f1[k] = ld_rhs(c, fp, c.y0 - 2 + 2 + 4 * warp + 2 * k, xa);
-      f2[k] = ld_rhs(c, fp, c.y0 - 2 + 3 + 4 * warp + 2 * k, xa);
+      f1[k] = ld_rhs<INNER>(c, fp, c.y0 - 2 + 2 + 4 * warp + 2 * k, xa);
+      f2[k] = ld_rhs<INNER>(c, fp, c.y0 - 2 + 3 + 4 * warp + 2 * k, xa);
     }
   };
   {
