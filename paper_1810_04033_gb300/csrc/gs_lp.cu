@@ -259,7 +259,7 @@ __device__ __forceinline__ void st2(__nv_bfloat16 *p, float a, float b) {
 // One phase: WHICH 1 = even rows 2 + 4w, 4 + 4w on staged columns HL-1 .. HL+TX
 // (written back into ce); WHICH 2 = odd rows 3 + 4w, 5 + 4w (up to 31) on the tile's
 // columns HL .. HL+TX-1.  Y receives the tile (rows 2..31) inside the grid.
-template <typename S, int WHICH>
+template <typename S, int WHICH, bool INNER>
 __device__ __forceinline__ void lpt_phase(const Geo &q, int x0, int y0, S *ce, const S *lo, const S *up,
                                           const S *fplane, S *yplane, float g) {
   constexpr int TX = LtTile<S>::TX, HL = LtTile<S>::HL;
@@ -270,8 +270,8 @@ __device__ __forceinline__ void lpt_phase(const Geo &q, int x0, int y0, S *ce, c
   const int64_t xa = x0 - HL + col;
   const bool va = col >= c0 && col <= c1, vb = col + 1 >= c0 && col + 1 <= c1;
   const bool core = col >= HL && col + 1 <= HL + TX - 1;
-  const bool xa_in = xa >= 1 && xa < q.nx, xb_in = xa + 1 >= 1 && xa + 1 < q.nx;
-  const bool xa_ok = xa >= 0 && xa <= q.nx, xb_ok = xa + 1 >= 0 && xa + 1 <= q.nx;
+  const bool xa_in = INNER || (xa >= 1 && xa < q.nx), xb_in = INNER || (xa + 1 >= 1 && xa + 1 < q.nx);
+  const bool xa_ok = INNER || (xa >= 0 && xa <= q.nx), xb_ok = INNER || (xa + 1 >= 0 && xa + 1 <= q.nx);
   const S *lc = lo + col, *uc = up + col;
   S *cc = ce + col;
   F2 Dm = ld2(lc + (r0 - 1) * LT_W), Dum = ld2(uc + (r0 - 1) * LT_W);
@@ -282,14 +282,14 @@ __device__ __forceinline__ void lpt_phase(const Geo &q, int x0, int y0, S *ce, c
     const int r = r0 + 2 * k;
     if (WHICH == 2 && r > 31) break;  // warp-uniform
     const int64_t j = y0 - 2 + r;
-    const bool jin = j >= 1 && j < q.ny;
+    const bool jin = INNER || (j >= 1 && j < q.ny);
     const bool ja = va && xa_in && jin, jb = vb && xb_in && jin;
     // right-hand side 3/8 h^2 f (FP32) of the updated vertices
     F2 gf{0.f, 0.f};
-    if (ja && jb && fplane) {
+    if (ja && jb && (INNER || fplane)) {
       const F2 fv = ld2(fplane + j * q.pitch + xa);
       gf = F2{g * fv.a, g * fv.b};
-    } else if (fplane) {
+    } else if (INNER || fplane) {
       if (ja) gf.a = g * ld<S>(fplane, j * q.pitch + xa);
       if (jb) gf.b = g * ld<S>(fplane, j * q.pitch + xa + 1);
     }
@@ -309,7 +309,7 @@ __device__ __forceinline__ void lpt_phase(const Geo &q, int x0, int y0, S *ce, c
     if (ja) nw.a = quant<S>(fmaf(Pl + P.b + 2.0f * Q.a, 0.03125f, gf.a));
     if (jb) nw.b = quant<S>(fmaf(P.a + Pr + 2.0f * Q.b, 0.03125f, gf.b));
     if (WHICH == 1) st2(cc + r * LT_W, nw.a, nw.b);
-    const bool jok = j >= 0 && j <= q.ny;
+    const bool jok = INNER || (j >= 0 && j <= q.ny);
     const bool rcore = r >= 2 && r <= 31;
     const bool wa = core && rcore && jok && xa_ok, wb = core && rcore && jok && xb_ok;
     S *yrow = yplane + j * q.pitch;
@@ -333,6 +333,8 @@ __global__ void __launch_bounds__(LP_THREADS) k_gs_lp_t(Geo q, int pz, S *Y, con
   S *sm = (S *)(((uintptr_t)lt_raw + 127) & ~(uintptr_t)127);
   auto slot = [&](int i) -> S * { return sm + i * LT_SLOT; };
   const int x0 = (int)blockIdx.x * TX, y0 = (int)blockIdx.y * LT_TY;
+  // every computed vertex (staged columns HL-1 .. HL+TX, rows 2..32) interior
+  const bool inner = x0 - 1 >= 1 && x0 + TX <= q.nx - 1 && y0 >= 1 && y0 + 30 <= q.ny - 1;
   const int64_t ncentre = (q.nz - pz) / 2 + 1;
   const int64_t i0 = (int64_t)blockIdx.z * cz;
   const int64_t i1 = i0 + cz < ncentre ? i0 + cz : ncentre;
@@ -384,9 +386,15 @@ __global__ void __launch_bounds__(LP_THREADS) k_gs_lp_t(Geo q, int pz, S *Y, con
     S *yp = Y + z * q.plane;
     if (z >= 1 && z < q.nz) {
       const S *fp = f + z * q.plane;
-      lpt_phase<S, 1>(q, x0, y0, slot(sl_ce), slot(sl_lo), slot(sl_up), fp, yp, g);
-      __syncthreads();
-      lpt_phase<S, 2>(q, x0, y0, slot(sl_ce), slot(sl_lo), slot(sl_up), fp, yp, g);
+      if (inner) {
+        lpt_phase<S, 1, true>(q, x0, y0, slot(sl_ce), slot(sl_lo), slot(sl_up), fp, yp, g);
+        __syncthreads();
+        lpt_phase<S, 2, true>(q, x0, y0, slot(sl_ce), slot(sl_lo), slot(sl_up), fp, yp, g);
+      } else {
+        lpt_phase<S, 1, false>(q, x0, y0, slot(sl_ce), slot(sl_lo), slot(sl_up), fp, yp, g);
+        __syncthreads();
+        lpt_phase<S, 2, false>(q, x0, y0, slot(sl_ce), slot(sl_lo), slot(sl_up), fp, yp, g);
+      }
     } else {
       // Dirichlet plane: carry the tile through
       const S *cs = slot(sl_ce);
