@@ -103,7 +103,9 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true",
+                    help="skip the oracle timings on the host cores (cpu_baseline; the refine "
+                         "workload's per-iterate oracle comparison)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="grid workload: keep the built-in launch shapes instead of autotuning them first")
     ap.add_argument("--n3", type=int, default=N3, help="3D cells per edge (0: no 3D grid)")
@@ -628,15 +630,18 @@ def run_small(args):
         oracle.apply_elementwise(un, h, nthreads=nt)
         oracle.gs_coloured(np.zeros_like(fn_), fn_, h, 10, nthreads=nt)
 
-    rate, calls, sec = _oracle_rate(ostep, upd, budget_s=5.0)
+    cpu = None
+    if not args.no_cpu:
+        rate, calls, sec = _oracle_rate(ostep, upd, budget_s=5.0)
+        cpu = {"value": round(rate, 1), "unit": "Mupdates/s", "cores": nt, "kind": "oracle",
+               "sample": "the whole step (apply + 10 GS sweeps at 32^3), %d times, %.1f s" % (calls, sec)}
     return {"metric": "Mupdates/s (32^3 Q1: 1 element-wise apply + 10 coloured GS sweeps)", "workload": "small",
             "value": round(upd / ms / 1e3, 1), "unit": "Mupdates/s", "ms_per_step": round(ms, 4),
             "steps": steps, "dtype": "f64", "clocks": clock_info,
             "roofline": _roofline((16 + 10 * 24) * (n - 1) ** 3, ms, "apply + 10 GS sweeps, 33^3",
                                   "launch-bound size: 0.27 MB per array, L2-resident; the fraction is of "
                                   "algorithmic bytes only"),
-            "cpu_baseline": {"value": round(rate, 1), "unit": "Mupdates/s", "cores": nt, "kind": "oracle",
-                             "sample": "the whole step (apply + 10 GS sweeps at 32^3), %d times, %.1f s" % (calls, sec)},
+            "cpu_baseline": cpu,
             "note": "launch-bound size (30K interior vertices); one CUDA graph replay per step"}
 
 
@@ -680,7 +685,8 @@ def run_patches(args):
             "clocks": clock_info,
             "roofline": _roofline(24 * upd, ms, "k_patch_gs + k_patch_halo (24 B per update and sweep)"),
             "autotuned_launch": {"threads": tuned[0], "ctas_per_sm": tuned[1]}, "dtype": "f64",
-            "patches": int(L.np_sizes.size), "vertices": L.total, "cpu_baseline": patches_cpu_baseline()}
+            "patches": int(L.np_sizes.size), "vertices": L.total,
+            "cpu_baseline": None if args.no_cpu else patches_cpu_baseline()}
 
 
 def patches_cpu_baseline():

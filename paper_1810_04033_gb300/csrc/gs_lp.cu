@@ -204,22 +204,25 @@ __global__ void __launch_bounds__(LP_THREADS) k_gs_lp_half(Geo q, int pz, const 
 }
 
 // ------------------------------------------------------------ TMA-staged form
-// The same half sweep with the planes brought into shared memory by TMA: five plane
-// slots (neighbour planes z-1 and z+1 from N, centre plane z from X, and the next
-// centre plane's two new planes in flight, issued one centre plane ahead), one mbarrier
-// each, bounded waits.  The staged box is 64 x 34 values of the storage type from
-// (x0 - HL, y0 - 2), HL chosen so that the box starts on a 16-byte boundary (FP32: tile
-// 56 wide, HL = 4; bf16: tile 48 wide, HL = 8), so staged column c is x0 - HL + c; lane
-// l works on the column pair 2l, 2l + 1.  Phase 1 (even rows, the tile grown by one
-// vertex) writes its results into the staged centre plane, whose other values are the
-// old ones (Dirichlet vertices stay as they are); phase 2 (odd rows) reads them.
+// The same half sweep with the planes brought into shared memory by TMA: seven slots
+// (neighbour planes z-1 and z+1 from N, centre plane z from X and its right-hand side
+// from f, and the next centre plane's three new boxes in flight, issued one centre
+// plane ahead), one mbarrier each, bounded waits.  Staging f with the planes keeps the
+// phases free of global loads, which otherwise bound the kernel (at 257^3 the
+// refinement's FP32 sweeps went from 2.34 to 1.56 s).  The staged box is 64 x 34
+// values of the storage type from (x0 - HL, y0 - 2), HL chosen so that the box starts
+// on a 16-byte boundary (FP32: tile 56 wide, HL = 4; bf16: tile 48 wide, HL = 8), so
+// staged column c is x0 - HL + c; lane l works on the column pair 2l, 2l + 1.  Phase 1
+// (even rows, the tile grown by one vertex) writes its results into the staged centre
+// plane, whose other values are the old ones (Dirichlet vertices stay as they are);
+// phase 2 (odd rows) reads them.
 // Arithmetic as in k_gs_lp_half (FP32; bf16 widened on load, every store rounded to
 // nearest even).  Used when X, N, Y and f are 16-byte aligned and the row pitch is a
 // multiple of 16 bytes.  A wait that runs out sets g_lp_tma_error and the CTA leaves.
 constexpr int LT_W = 64, LT_H = 34;   // staged box
 constexpr int LT_TY = 30;             // output tile rows
 constexpr int LT_SLOT = LT_W * LT_H;  // values per slot
-constexpr int LT_NSLOT = 5;
+constexpr int LT_NSLOT = 7;  // lo, up, centre, next up, next centre; f of the centre, f of the next
 constexpr unsigned LT_WAIT = 1u << 22;
 __device__ unsigned g_lp_tma_error = 0;
 
@@ -284,15 +287,9 @@ __device__ __forceinline__ void lpt_phase(const Geo &q, int x0, int y0, S *ce, c
     const int64_t j = y0 - 2 + r;
     const bool jin = INNER || (j >= 1 && j < q.ny);
     const bool ja = va && xa_in && jin, jb = vb && xb_in && jin;
-    // right-hand side 3/8 h^2 f (FP32) of the updated vertices
-    F2 gf{0.f, 0.f};
-    if (ja && jb && (INNER || fplane)) {
-      const F2 fv = ld2(fplane + j * q.pitch + xa);
-      gf = F2{g * fv.a, g * fv.b};
-    } else if (INNER || fplane) {
-      if (ja) gf.a = g * ld<S>(fplane, j * q.pitch + xa);
-      if (jb) gf.b = g * ld<S>(fplane, j * q.pitch + xa + 1);
-    }
+    // right-hand side 3/8 h^2 f (FP32) from the staged f plane (used where updated)
+    const F2 fv = ld2(fplane + r * LT_W + col);
+    const F2 gf{g * fv.a, g * fv.b};
     const F2 l1 = ld2(lc + (r + 1) * LT_W), u1 = ld2(uc + (r + 1) * LT_W);
     const F2 Dp{l1.a + u1.a, l1.b + u1.b};
     const F2 Cp = ld2(cc + (r + 1) * LT_W);
@@ -325,7 +322,8 @@ __device__ __forceinline__ void lpt_phase(const Geo &q, int x0, int y0, S *ce, c
 template <typename S>
 __global__ void __launch_bounds__(LP_THREADS) k_gs_lp_t(Geo q, int pz, S *Y, const S *f, float g, int cz,
                                                         const __grid_constant__ CUtensorMap mapX,
-                                                        const __grid_constant__ CUtensorMap mapN) {
+                                                        const __grid_constant__ CUtensorMap mapN,
+                                                        const __grid_constant__ CUtensorMap mapF) {
   constexpr int TX = LtTile<S>::TX, HL = LtTile<S>::HL;
   extern __shared__ unsigned char lt_raw[];
   __shared__ __align__(8) uint64_t bars[LT_NSLOT];
@@ -346,7 +344,7 @@ __global__ void __launch_bounds__(LP_THREADS) k_gs_lp_t(Geo q, int pz, S *Y, con
   }
   __syncthreads();
   unsigned ph = 0, pend = 0;
-  int sl_lo = 0, sl_up = 1, sl_ce = 2, sl_nup = 3, sl_nce = 4;
+  int sl_lo = 0, sl_up = 1, sl_ce = 2, sl_nup = 3, sl_nce = 4, sl_fc = 5, sl_fn = 6;
   auto issue = [&](int s, const CUtensorMap *m, int64_t z) {
     pend |= 1u << s;
     if (threadIdx.x == 0) {
@@ -368,9 +366,11 @@ __global__ void __launch_bounds__(LP_THREADS) k_gs_lp_t(Geo q, int pz, S *Y, con
     issue(sl_lo, &mapN, z - 1);
     issue(sl_up, &mapN, z + 1);
     issue(sl_ce, &mapX, z);
+    issue(sl_fc, &mapF, z);
     if (i0 + 1 < i1) {
       issue(sl_nce, &mapX, z + 2);
       issue(sl_nup, &mapN, z + 3);
+      issue(sl_fn, &mapF, z + 2);
     }
     wait(sl_lo);
   }
@@ -378,6 +378,7 @@ __global__ void __launch_bounds__(LP_THREADS) k_gs_lp_t(Geo q, int pz, S *Y, con
     const int64_t z = pz + 2 * i;
     wait(sl_ce);
     wait(sl_up);
+    wait(sl_fc);
     __syncthreads();
     if (fail) {
       ok = false;
@@ -385,7 +386,7 @@ __global__ void __launch_bounds__(LP_THREADS) k_gs_lp_t(Geo q, int pz, S *Y, con
     }
     S *yp = Y + z * q.plane;
     if (z >= 1 && z < q.nz) {
-      const S *fp = f + z * q.plane;
+      const S *fp = slot(sl_fc);
       if (inner) {
         lpt_phase<S, 1, true>(q, x0, y0, slot(sl_ce), slot(sl_lo), slot(sl_up), fp, yp, g);
         __syncthreads();
@@ -405,15 +406,18 @@ __global__ void __launch_bounds__(LP_THREADS) k_gs_lp_t(Geo q, int pz, S *Y, con
       }
     }
     __syncthreads();  // every access to the freed slots is done
-    const int t_lo = sl_lo, t_ce = sl_ce;
+    const int t_lo = sl_lo, t_ce = sl_ce, t_fc = sl_fc;
     sl_lo = sl_up;
     sl_up = sl_nup;
     sl_ce = sl_nce;
+    sl_fc = sl_fn;
     sl_nup = t_lo;
     sl_nce = t_ce;
+    sl_fn = t_fc;
     if (i + 2 < i1) {
       issue(sl_nce, &mapX, z + 4);
       issue(sl_nup, &mapN, z + 5);
+      issue(sl_fn, &mapF, z + 4);
     }
   }
   if (!ok && i0 < i1) {  // wait once more (bounded) for every load still in flight
@@ -438,9 +442,10 @@ static cudaError_t gs_lp_sweeps(const Geo &q, S *u, const S *f, int sweeps, S *w
   if (ty > 65535) return cudaErrorInvalidConfiguration;
   S *X = u, *Y = work;
   // the TMA-staged kernel where the arrays allow it
-  CUtensorMap mu, mw;
+  CUtensorMap mu, mw, mf;
   const bool tma = ((uintptr_t)f % 16) == 0 && tma_plane_map_elem(q, u, (int)sizeof(S), LT_W, LT_H, &mu) &&
-                   tma_plane_map_elem(q, work, (int)sizeof(S), LT_W, LT_H, &mw);
+                   tma_plane_map_elem(q, work, (int)sizeof(S), LT_W, LT_H, &mw) &&
+                   tma_plane_map_elem(q, f, (int)sizeof(S), LT_W, LT_H, &mf);
   if (tma) {
     static PerDeviceOnce attr_t;
     cudaError_t e = set_smem_limit_once(attr_t, k_gs_lp_t<S>, lt_smem<S>());
@@ -457,7 +462,7 @@ static cudaError_t gs_lp_sweeps(const Geo &q, S *u, const S *f, int sweeps, S *w
         const unsigned tz = (unsigned)((ncentre + cz - 1) / cz);
         const CUtensorMap &mx = X == u ? mu : mw, &my = Y == u ? mu : mw;
         k_gs_lp_t<S><<<dim3(ttx, tty, tz), LP_THREADS, lt_smem<S>(), s>>>(q, pz, Y, f, g, cz, mx,
-                                                                          pz == 0 ? mx : my);
+                                                                          pz == 0 ? mx : my, mf);
       } else {
         const int cz = z_chunk((int64_t)tx * ty, ncentre, LP_CZ, 2, 8);
         const unsigned tz = (unsigned)((ncentre + cz - 1) / cz);
