@@ -441,25 +441,37 @@ def run_e2e(torch, st, wl, stream, args, world):
     copy = {g: torch.cuda.Stream(device=wl.dev) for g in wl.grids}
 
     def ev():
-        return torch.cuda.Event()
+        return torch.cuda.Event(enable_timing=True)
 
-    def one(stream):
+    marks = []  # per step and grid: events around the copy-in, the compute and the copy-out
+
+    def one(stream, rec=None):
         for i, g in enumerate(wl.grids):
             cs = copy[g]
             with torch.cuda.stream(cs):
+                a_in = ev()
+                a_in.record(cs)
                 wl.d["u" + g].copy_(wl.host["u" + g], non_blocking=True)
                 wl.d["f" + g].copy_(wl.host["f" + g], non_blocking=True)
                 e_in = ev()
                 e_in.record(cs)
             stream.wait_event(e_in)
+            c0 = ev()
+            c0.record(stream)
             for op in OPS:
                 wl.run_op(op, g, stream)
             done = ev()
             done.record(stream)
             with torch.cuda.stream(cs):
                 cs.wait_event(done)
+                o0 = ev()
+                o0.record(cs)
                 h_out[g].copy_(wl.d["u" + g], non_blocking=True)
                 h_nrm[2 * i:2 * i + 2].copy_(wl.d["n" + g], non_blocking=True)
+                o1 = ev()
+                o1.record(cs)
+            if rec is not None:
+                rec.append((a_in, e_in, c0, done, o0, o1))
 
     with torch.cuda.stream(stream):
         one(stream)
@@ -469,7 +481,7 @@ def run_e2e(torch, st, wl, stream, args, world):
         for g in wl.grids:
             copy[g].wait_event(t0)
         for _ in range(steps):
-            one(stream)
+            one(stream, marks)
         for g in wl.grids:
             end_copy = ev()
             end_copy.record(copy[g])
@@ -478,8 +490,16 @@ def run_e2e(torch, st, wl, stream, args, world):
     torch.cuda.synchronize()
     ms = max_over_ranks(torch, t0.elapsed_time(t1), world, wl.dev)
     val = whole_job_rate(updates_per_step(args.n3, args.n2) * steps, world, ms)
+    # where the time went (read after the timed region): copy durations, and the time the
+    # compute stream waited between one grid's ops and the next (for that grid's inputs)
+    h2d = sum(a.elapsed_time(b) for a, b, *_ in marks)
+    d2h = sum(o0.elapsed_time(o1) for *_, o0, o1 in marks)
+    idle = sum(max(0.0, marks[k][2].elapsed_time(marks[k + 1][2]) - marks[k][2].elapsed_time(marks[k][3]))
+               for k in range(len(marks) - 1))
     return {"value": round(val, 1), "unit": "Mupdates/s", "h2d_bytes_per_step": bi,
-            "d2h_bytes_per_step": bo, "steps": steps, "copies": "a copy stream per grid, overlapped with the other grid's compute"}
+            "d2h_bytes_per_step": bo, "steps": steps, "copies": "a copy stream per grid, overlapped with the other grid's compute",
+            "h2d_ms_per_step": round(h2d / steps, 2), "d2h_ms_per_step": round(d2h / steps, 2),
+            "compute_idle_ms_per_step": round(idle / steps, 2)}
 
 
 # ------------------------------------------------------------------ CPU oracle
