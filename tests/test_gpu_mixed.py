@@ -171,10 +171,11 @@ def test_refinement_iterates_match_oracle_padded_fp32():
         assert rel_err(to_host(ud), hist[it - 1]) <= 1e-5, it
 
 
-@pytest.mark.parametrize("n", [(33, 9, 7), (100, 40, 20)])
+@pytest.mark.parametrize("n", [(33, 9, 7), (100, 40, 20), (100, 64, 12)])
 def test_bf16_gs_padded_matches_bf16_oracle(n):
     """bf16-storage sweeps on arrays whose pitch is a multiple of 8 (the TMA-staged
-    kernel): several tiles with ragged tails, nonzero Dirichlet data."""
+    kernel): several tiles with ragged tails, nonzero Dirichlet data; (100, 64, 12)
+    also has tiles whose computed vertices are all interior (the edge-free path)."""
     h = 1.0 / max(n)
     shape = synth.grid_shape(3, n)
     u0 = synth.uniform_field(shape, 2300 + sum(n), zero_bc=False)
