@@ -427,67 +427,79 @@ def run_gpu(args, rank, world):
 def run_e2e(torch, st, wl, stream, args, world):
     """Same op mix through the public API with host buffers: every step copies u and f
     of each grid from pinned host memory, runs the ops, and reads u and the norms
-    back; copies are inside the timed region.  The copies run on one stream per grid
-    and overlap the other grid's compute: a grid's inputs go up while the other grid
-    computes, and its results come down while the other grid computes (events order
-    each grid's copy-in, compute and copy-out)."""
+    back; copies are inside the timed region.  Each grid has a copy-in and a copy-out
+    stream and two sets of device inputs (u, f, norms) used in alternate steps, so a
+    step's inputs go up while the previous step still computes on, or copies back from,
+    the other set; events order each grid's copy-in, compute and copy-out, and a set is
+    refilled only after its previous results have left."""
     steps = args.steps
     h_out = {g: torch.empty_like(wl.host["u" + g]).pin_memory() for g in wl.grids}
     h_nrm = torch.empty(4, dtype=torch.float64).pin_memory()
     bi = sum(wl.host[k + g].numel() * 8 for k in ("u", "f") for g in wl.grids)
     bo = sum(h_out[g].numel() * 8 for g in h_out) + 16 * len(wl.grids)
-    # one copy stream per grid: a grid's next inputs wait only for its own previous
-    # results to leave, so they travel while the other grid computes
-    copy = {g: torch.cuda.Stream(device=wl.dev) for g in wl.grids}
+    cin = {g: torch.cuda.Stream(device=wl.dev) for g in wl.grids}
+    cout = {g: torch.cuda.Stream(device=wl.dev) for g in wl.grids}
+    keys = [k + g for k in ("u", "f", "n") for g in wl.grids]
+    home = {k: wl.d[k] for k in keys}
+    sets = [home, {k: torch.empty_like(home[k]) for k in keys}]
+    freed = {}  # (set, grid) -> event after that set's last copy-out
 
     def ev():
         return torch.cuda.Event(enable_timing=True)
 
     marks = []  # per step and grid: events around the copy-in, the compute and the copy-out
 
-    def one(stream, rec=None):
+    def one(stream, k, rec=None):
+        cur = sets[k % 2]
         for i, g in enumerate(wl.grids):
-            cs = copy[g]
-            with torch.cuda.stream(cs):
+            ci, co = cin[g], cout[g]
+            with torch.cuda.stream(ci):
+                if (k % 2, g) in freed:
+                    ci.wait_event(freed[(k % 2, g)])
                 a_in = ev()
-                a_in.record(cs)
-                wl.d["u" + g].copy_(wl.host["u" + g], non_blocking=True)
-                wl.d["f" + g].copy_(wl.host["f" + g], non_blocking=True)
+                a_in.record(ci)
+                cur["u" + g].copy_(wl.host["u" + g], non_blocking=True)
+                cur["f" + g].copy_(wl.host["f" + g], non_blocking=True)
                 e_in = ev()
-                e_in.record(cs)
+                e_in.record(ci)
             stream.wait_event(e_in)
+            for key in ("u" + g, "f" + g, "n" + g):
+                wl.d[key] = cur[key]
             c0 = ev()
             c0.record(stream)
             for op in OPS:
                 wl.run_op(op, g, stream)
             done = ev()
             done.record(stream)
-            with torch.cuda.stream(cs):
-                cs.wait_event(done)
+            with torch.cuda.stream(co):
+                co.wait_event(done)
                 o0 = ev()
-                o0.record(cs)
-                h_out[g].copy_(wl.d["u" + g], non_blocking=True)
-                h_nrm[2 * i:2 * i + 2].copy_(wl.d["n" + g], non_blocking=True)
+                o0.record(co)
+                h_out[g].copy_(cur["u" + g], non_blocking=True)
+                h_nrm[2 * i:2 * i + 2].copy_(cur["n" + g], non_blocking=True)
                 o1 = ev()
-                o1.record(cs)
+                o1.record(co)
+            freed[(k % 2, g)] = o1
             if rec is not None:
                 rec.append((a_in, e_in, c0, done, o0, o1))
 
     with torch.cuda.stream(stream):
-        one(stream)
+        one(stream, 1)
+        one(stream, 0)
         torch.cuda.synchronize()
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0.record(stream)
         for g in wl.grids:
-            copy[g].wait_event(t0)
-        for _ in range(steps):
-            one(stream, marks)
+            cin[g].wait_event(t0)
+        for k in range(steps):
+            one(stream, k, marks)
         for g in wl.grids:
             end_copy = ev()
-            end_copy.record(copy[g])
+            end_copy.record(cout[g])
             stream.wait_event(end_copy)
         t1.record(stream)
     torch.cuda.synchronize()
+    wl.d.update(home)
     ms = max_over_ranks(torch, t0.elapsed_time(t1), world, wl.dev)
     val = whole_job_rate(updates_per_step(args.n3, args.n2) * steps, world, ms)
     # where the time went (read after the timed region): copy durations, and the time the
@@ -497,7 +509,7 @@ def run_e2e(torch, st, wl, stream, args, world):
     idle = sum(max(0.0, marks[k][2].elapsed_time(marks[k + 1][2]) - marks[k][2].elapsed_time(marks[k][3]))
                for k in range(len(marks) - 1))
     return {"value": round(val, 1), "unit": "Mupdates/s", "h2d_bytes_per_step": bi,
-            "d2h_bytes_per_step": bo, "steps": steps, "copies": "a copy stream per grid, overlapped with the other grid's compute",
+            "d2h_bytes_per_step": bo, "steps": steps, "copies": "a copy-in and a copy-out stream per grid, two sets of device inputs in alternate steps",
             "h2d_ms_per_step": round(h2d / steps, 2), "d2h_ms_per_step": round(d2h / steps, 2),
             "compute_idle_ms_per_step": round(idle / steps, 2)}
 
